@@ -1,0 +1,273 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, a direct linear solve, invariants proved in the paper, the paper's
+worked Forward-Push example, finite differences, and special cases with a
+known answer. None of them needs a GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ALPHA = 0.15
+C = 1.0 - ALPHA
+
+
+def _graph_P(g):
+    return O.transition_matrix(g.n, g.row_ptr, g.col, g.weight)
+
+
+def _csr_from_edges(n, edges, undirected):
+    pairs = list(edges) + ([(b, a) for a, b in edges] if undirected else [])
+    pairs = sorted(set(pairs))
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    for a, _ in pairs:
+        row_ptr[a + 1] += 1
+    row_ptr = np.cumsum(row_ptr)
+    col = np.array([b for _, b in pairs], dtype=np.int32)
+    return row_ptr, col
+
+
+# --------------------------------------------------------------------------
+# PPR (Sec. 3.1) and DPPR (Definition 1)
+# --------------------------------------------------------------------------
+def test_power_iteration_matches_direct_solve_small_graphs():
+    graphs = [
+        synth.chung_lu(150, 8, 2.5, seed=3),
+        synth.sbm([30, 30, 40], 0.15, 0.01, seed=5),          # has isolated nodes
+        synth.dense_clustered(90, blocks=3, density=0.2, seed=2),  # weighted
+    ]
+    for g in graphs:
+        P = _graph_P(g)
+        Pi = O.ppr_direct(P, ALPHA)
+        rows = O.ppr_rows(P, np.arange(g.n), ALPHA)
+        cols = O.ppr_cols(P, np.arange(g.n), ALPHA)
+        assert np.abs(rows - Pi).max() < 1e-13
+        assert np.abs(cols - Pi).max() < 1e-13
+
+
+def test_complete_graph_closed_form():
+    # K_n: P = (J - I)/(n - 1) has eigenvalue 1 on the ones vector and
+    # -1/(n-1) elsewhere, so Pi = J/n + q (I - J/n), q = alpha (n-1)/(n-1+c).
+    n = 7
+    edges = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    rp, col = _csr_from_edges(n, edges, True)
+    P = O.transition_matrix(n, rp, col)
+    q = ALPHA * (n - 1) / (n - 1 + C)
+    Pi = O.ppr_rows(P, np.arange(n), ALPHA)
+    assert np.allclose(np.diag(Pi), q * (1 - 1 / n) + 1 / n, atol=1e-14, rtol=0)
+    off = ~np.eye(n, dtype=bool)
+    assert np.allclose(Pi[off], 1 / n - q / n, atol=1e-14, rtol=0)
+
+
+def test_star_closed_form_and_pdist():
+    # centre 0 with L leaves: pi(leaf, centre) = a, pi(centre, centre) = b with
+    # b = alpha + c a and a = c b, so a = c / (1 + c); by symmetry of pi_d the
+    # centre-leaf DPPR is c/(1+c) both ways and leaf-leaf is c^2 / (L (1+c)).
+    L = 9
+    n = L + 1
+    rp, col = _csr_from_edges(n, [(0, i) for i in range(1, n)], True)
+    P = O.transition_matrix(n, rp, col)
+    d = O.degrees(n, rp, col)
+    D = O.dppr_rows(O.ppr_rows(P, np.arange(n), ALPHA), d, np.arange(n))
+    assert abs(D[0, 3] - C / (1 + C)) < 1e-14
+    assert abs(D[3, 0] - C / (1 + C)) < 1e-14
+    assert abs(D[2, 5] - C * C / (L * (1 + C))) < 1e-14
+    Delta = O.pdist_from_dppr(D, n)
+    # leaf-leaf: 1 - ln(2 c^2 / (L (1 + c))) = 3.4443009 at alpha = 0.15, L = 9
+    assert abs(Delta[2, 5] - (1 - math.log(2 * C * C / (L * (1 + C))))) < 1e-13
+    assert abs(Delta[2, 5] - 3.4443009) < 1e-7
+    assert Delta[0, 4] == 2.0                           # clamped at the lower bound
+    assert np.all(np.diag(Delta) == 0)
+
+
+def test_single_edge_closed_form():
+    rp, col = _csr_from_edges(2, [(0, 1)], True)
+    Pi = O.ppr_rows(O.transition_matrix(2, rp, col), [0, 1], ALPHA)
+    assert abs(Pi[0, 0] - 1 / (1 + C)) < 1e-15
+    assert abs(Pi[0, 1] - C / (1 + C)) < 1e-15
+
+
+def test_invariants_on_random_graph():
+    g = synth.chung_lu(300, 10, 2.5, seed=1)
+    P = _graph_P(g)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    Pi = O.ppr_rows(P, np.arange(g.n), ALPHA)
+    D = O.dppr_rows(Pi, d, np.arange(g.n))
+    assert np.abs(Pi.sum(axis=1) - 1).max() < 1e-13              # each row is a distribution
+    assert np.all(np.diag(Pi) >= ALPHA - 1e-15)                    # ends at once w.p. alpha
+    assert np.abs(D - D.T).max() < 1e-13                           # reversibility (undirected)
+    m = g.nnz
+    assert abs(D.sum() - m) < 1e-9 * m                             # Eq. (11): sum z = 2m
+    Delta = O.pdist_from_dppr(D, g.n)
+    # Theorem 2: every edge has Delta <= 1 - ln(2 alpha (1 - alpha))
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    bound = 1 - math.log(2 * ALPHA * (1 - ALPHA))
+    assert Delta[src, g.col].max() <= bound + 1e-12
+    # Theorem 1: ND = sum_{i<j} 1/Delta^2 <= 0.215 e m + 0.0175 n^2
+    iu = np.triu_indices(g.n, 1)
+    assert (1 / Delta[iu] ** 2).sum() <= 0.215 * math.e * m + 0.0175 * g.n ** 2
+    assert Delta[iu].min() >= 2.0 and Delta[iu].max() <= 2 * math.log(g.n) + 1e-12
+
+
+def test_dangling_node_reading():
+    # an isolated node keeps its walk: pi(v, v) = 1, d(v) = 0 so its DPPR row
+    # is zero, and every PDist entry with it is the upper clamp 2 ln n.
+    g = synth.sbm([5, 5, 1], 0.9, 0.0, seed=7)
+    iso = 10
+    assert g.row_ptr[iso + 1] == g.row_ptr[iso]
+    P = _graph_P(g)
+    Pi = O.ppr_rows(P, np.arange(g.n), ALPHA)
+    assert abs(Pi[iso, iso] - 1) < 1e-15
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    D = O.dppr_rows(Pi, d, np.arange(g.n))
+    assert np.all(D[iso] == 0)
+    Delta = O.pdist_from_dppr(D, g.n)
+    others = [j for j in range(g.n) if j != iso]
+    assert np.all(Delta[iso, others] == 2 * math.log(g.n))
+
+
+def test_pdist_clamps_and_zero():
+    n = 100
+    z = np.array([0.0, 1e-300, math.e ** -1, 1.0, 5.0, math.e ** (1 - 2 * math.log(n)) * 1.5])
+    out = O.pdist_from_z(z, n)
+    assert out[0] == 2 * math.log(n) and out[1] == 2 * math.log(n)
+    assert out[2] == 2.0 and out[3] == 2.0 and out[4] == 2.0
+    assert abs(out[5] - (2 * math.log(n) - math.log(1.5))) < 1e-12
+
+
+def test_forward_push_running_example():
+    with open(os.path.join(GOLDEN, "forward_push_example.json")) as f:
+        ex = json.load(f)
+    n = ex["n"]
+    rp, col = _csr_from_edges(n, [tuple(e) for e in ex["edges"]], False)
+    d = O.degrees(n, rp, col)
+    a = ex["alpha"]
+    est, r = O.forward_push(n, rp, col, d, ex["source"], a, ex["after_first_push"]["order"])
+    for v, val in ex["after_first_push"]["estimate"].items():
+        assert abs(est[int(v)] - val) < 1e-12
+    for v, val in ex["after_first_push"]["residue"].items():
+        assert abs(r[int(v)] - val) < 1e-12
+    est, r = O.forward_push(n, rp, col, d, ex["source"], a, ex["after_second_hop"]["order"])
+    for v, val in ex["after_second_hop"]["residue"].items():
+        assert abs(r[int(v)] - val) < 1e-12
+    # Eq. (3): pi_d(s, t) = estimate_t + sum_k r_k pi(k, t)  (r in DPPR units)
+    P = O.transition_matrix(n, rp, col)
+    Pi = O.ppr_direct(P, a)
+    lhs = d[ex["source"]] * Pi[ex["source"]]
+    rhs = est + r @ Pi
+    assert np.abs(lhs - rhs).max() < 1e-14
+
+
+def test_residual_certificate_bounds_error_and_matches_closed_form():
+    g = synth.chung_lu(200, 8, 2.5, seed=4)
+    P = _graph_P(g)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    Pi = O.ppr_direct(P, ALPHA)
+    src = np.arange(0, g.n, 17)
+    for T in (5, 20, 40):
+        B = np.zeros((len(src), g.n)); B[np.arange(len(src)), src] = ALPHA
+        X = B.copy()
+        for _ in range(T):
+            X = B + C * (sp.csr_matrix(P.T) @ X.T).T
+        cert = O.residual_certificate(P, X, src, d, ALPHA)
+        err = (d[src][:, None] * np.abs(X - Pi[src])).max(axis=1)
+        assert np.all(err <= cert * (1 + 1e-9))
+        # power iteration leaves exactly (1 - alpha)^(T+1) walk mass unended
+        assert np.allclose(cert, d[src] * C ** (T + 1), rtol=1e-9, atol=0)
+    assert O.power_sweeps_needed(ALPHA, 1e-15) == 212
+
+
+# --------------------------------------------------------------------------
+# Stress (Eq. (7)) and stress majorization (Appendix A.1, Eq. (10))
+# --------------------------------------------------------------------------
+def _random_delta(k, seed):
+    r = synth.uniform(seed, 77, np.arange(k * k, dtype=np.uint64)).reshape(k, k)
+    D = 2.0 + 4.0 * (r + r.T) / 2
+    np.fill_diagonal(D, 0.0)
+    return D
+
+
+def test_stress_gradient_finite_differences():
+    k = 12
+    D = _random_delta(k, 1)
+    X = synth.uniform_x0(k, seed=2).astype(np.float64) * 3
+    g = O.stress_grad(X, D)
+    h = 1e-6
+    num = np.zeros_like(X)
+    for i in range(k):
+        for a in range(2):
+            Xp = X.copy(); Xp[i, a] += h
+            Xm = X.copy(); Xm[i, a] -= h
+            num[i, a] = (O.stress(Xp, D) - O.stress(Xm, D)) / (2 * h)
+    assert np.abs(num - g).max() < 1e-7 * max(1, np.abs(g).max())
+    gD = O.stress_grad_pdist(X, D)
+    i, j = 3, 8
+    Dp = D.copy(); Dp[i, j] += h; Dp[j, i] += h
+    Dm = D.copy(); Dm[i, j] -= h; Dm[j, i] -= h
+    fd = (O.stress(X, Dp) - O.stress(X, Dm)) / (2 * h)
+    assert abs(fd - (gD[i, j] + gD[j, i])) < 1e-7
+
+
+def test_stress_invariances_and_zero_for_realisable_delta():
+    k = 9
+    pts = synth.uniform_x0(k, seed=5).astype(np.float64) * 4
+    D = np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1))
+    assert O.stress(pts, D) < 1e-28
+    X = synth.uniform_x0(k, seed=6).astype(np.float64)
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    e0 = O.stress(X, D)
+    assert abs(O.stress(X @ R.T + np.array([3.0, -1.0]), D) - e0) < 1e-12 * e0
+    # stress majorization drives a realisable Delta to zero stress from a
+    # start in the basin of the realising configuration
+    Xs, hist = O.smacof(pts + 0.3 * X, D, 400)
+    assert hist[-1] < 1e-10
+
+
+def test_smacof_step_properties():
+    k = 25
+    D = _random_delta(k, 3)
+    X = synth.uniform_x0(k, seed=4).astype(np.float64)
+    e_prev = O.stress(X, D)
+    for _ in range(30):
+        X = O.smacof_step(X, D)
+        e = O.stress(X, D)
+        assert e <= e_prev * (1 + 1e-12)            # majorization: never increases
+        assert np.abs(X.mean(axis=0)).max() < 1e-13  # centred
+        e_prev = e
+    # the pinned Cholesky solve equals the pseudo-inverse form of Eq. (10)
+    Y = X + 0.1 * synth.uniform_x0(k, seed=9)
+    ref = np.linalg.pinv(O.lw_matrix(D)) @ (O.ly_matrix(Y, D) @ Y)
+    assert np.abs(O.smacof_step(Y, D) - ref).max() < 1e-11
+    # the update is the Guttman form X = Y - (L^w)^+ grad / 2 (gradient = 2 (L^w Y - L^Y Y))
+    gstep = Y - np.linalg.pinv(O.lw_matrix(D)) @ O.stress_grad(Y, D) / 2
+    assert np.abs(O.smacof_step(Y, D) - (gstep - gstep.mean(0))).max() < 1e-10
+
+
+def test_smacof_two_points_reach_target_in_one_step():
+    D = np.array([[0.0, 3.7], [3.7, 0.0]])
+    X = np.array([[0.2, -0.4], [0.9, 0.1]])
+    Xn = O.smacof_step(X, D)
+    assert abs(np.linalg.norm(Xn[0] - Xn[1]) - 3.7) < 1e-14
+    assert O.stress(Xn, D) < 1e-28
+
+
+def test_level_dppr_reduces_to_node_dppr_for_singletons():
+    g = synth.chung_lu(60, 6, 2.5, seed=8)
+    P = _graph_P(g)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    D = O.dppr_rows(O.ppr_direct(P, ALPHA), d, np.arange(g.n))
+    sets = [[i] for i in range(g.n)]
+    assert np.abs(O.level_dppr(D, sets) - D).max() == 0
+    sets = [list(range(0, 20)), list(range(20, 60))]
+    lv = O.level_dppr(D, sets)
+    assert abs(lv[0, 1] - D[:20, 20:].mean()) < 1e-14
