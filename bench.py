@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the PPRviz hot path on GB300.
+
+One step = the whole hot path on the benchmark workload: Chung-Lu graph
+n = 10,000, mean degree 20, exponent 2.5, seed 0 (unit weights); graph ingest
+and validation (P0), all-pairs FP32 DPPR with the FP64 residual certificate
+and refinement to eps = 1e-6 (P1/P2), PDist (P3), then 500 FP32
+stress-majorization updates from U[-1,1]^2 with the final stress (P4/P5).
+
+`value` is DPPR entries per second over the whole step (k^2 certified DPPR
+entries per step), with inputs already in HBM. `e2e` is the same metric through
+the public API with pinned host buffers (CSR, view, PDist round trip, X0 in;
+DPPR, PDist, X out), copies inside the timed region.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALPHA, EPS = 0.15, 1e-6
+WORKLOAD = "chung_lu_n10000_deg20"
+L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--deg", type=float, default=20.0)
+    ap.add_argument("--iters", type=int, default=500)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def config(args, n_gpus):
+    return {"workload": WORKLOAD, "graph": "chung-lu", "n": args.n, "mean_degree": args.deg, "exponent": 2.5,
+            "seed": 0, "view": "all nodes (k = n)", "alpha": ALPHA, "eps": EPS, "layout_iters": args.iters,
+            "propagation": "fp32 chebyshev + fp64 residual certificate + fp32 refinement",
+            "layout": "fp32 stress majorization, exact (L^w)^+ solve",
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{n_gpus}"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------- traffic
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2112_14944_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(cls):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary,
+    or None when absent or taken on a different version of the kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(cls)
+    if not d:
+        return None
+    if d.get("source_hash") != kernel_source_hash(d.get("files", [])):
+        return None
+    return d.get("dram_bytes_per_launch_full")
+
+
+# --------------------------------------------------------------------------- reference arm
+def cpu_oracle_sample(g, n_src, seed=1):
+    """FP64 oracle on a bounded sample: DPPR rows of n_src sources and the
+    PDist rows they fix. Returns (entries, seconds)."""
+    import oracle as O
+    import synth
+    src = synth.sample_view(g.n, n_src, seed=seed)
+    t0 = time.perf_counter()
+    Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    rows = O.ppr_rows(Pm, src, ALPHA)
+    cols = O.ppr_cols(Pm, src, ALPHA)
+    D = O.dppr_rows(rows, d, src)
+    Dc = (d[:, None] * cols).T
+    O.pdist_from_z(D + Dc, g.n)
+    return n_src * g.n, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    g = synth.chung_lu(args.n, args.deg, 2.5, seed=0)
+    n_src = 16
+    for _ in range(args.warmup):
+        cpu_oracle_sample(g, 4)
+    times, ents = [], 0
+    for s in range(args.steps):
+        e, t = cpu_oracle_sample(g, n_src, seed=100 + s)
+        times.append(t)
+        ents += e
+    total = sum(times)
+    value = ents / total
+    line = {
+        "impl": "reference", "metric": "DPPR entries/s at n=10k, err<=1e-6 vs FP64; layout iters/s; % HBM roofline",
+        "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args, world),
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_src} seeded sources per step: DPPR rows and PDist rows by FP64 power "
+                                   f"iteration to (1-alpha)^(t+1) <= 1e-15"},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    g = synth.chung_lu(n, args.deg, 2.5, seed=0)
+    x0_h = synth.uniform_x0(n, seed=0)
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    view = torch.arange(n, dtype=torch.int32, device=dev)
+    D = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Dl = torch.empty((n, n), dtype=torch.float32, device=dev)
+    x0 = torch.from_numpy(x0_h).to(dev)
+    xo = torch.empty_like(x0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(rec=None):
+        if rec is not None:
+            rec[0].record(stream)
+        G = ctx.upload(n, rp, col)
+        st = ctx.stats()
+        launches = st["kernel_launches"]
+        _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
+        sd = ctx.stats()
+        launches += sd["kernel_launches"]
+        if rec is not None:
+            rec[1].record(stream)
+        _, s = ctx.layout(Dl, x0, args.iters, P.FP32, x_out=xo, stress=True)
+        sl = ctx.stats()
+        launches += sl["kernel_launches"]
+        if rec is not None:
+            rec[2].record(stream)
+        G.free()
+        assert status == 0 and cert.max() <= EPS, (status, cert.max())
+        return launches, sd, sl, s
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms, dppr_ms, layout_ms = [], [], []
+    launches = 0
+    bytes_sweep = bytes_ly = bytes_apply = 0.0
+    sweeps = 0
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # outside the step's events
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        nl, sd, sl, stress = step(ev)
+        launches += nl
+        bytes_sweep += sd["bytes_sweep"]
+        sweeps += sd["sweeps_main"] + sd["sweeps_refine"]
+        bytes_ly += sl["bytes_ly"]
+        bytes_apply += sl["bytes_apply"]
+        ev[2].synchronize()
+        dppr_ms.append(ev[0].elapsed_time(ev[1]))
+        layout_ms.append(ev[1].elapsed_time(ev[2]))
+        step_ms.append(ev[0].elapsed_time(ev[2]))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.stop()
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    entries = float(n) * n
+    value = world * args.steps * entries / (total_ms / 1e3)
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+        rp_h, col_h, x0_p = pin(g.row_ptr), pin(g.col), pin(x0_h)
+        view_h = pin(np.arange(n, dtype=np.int32))
+        D_h = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
+        Dl_h = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
+        X_h = torch.empty((n, 2), dtype=torch.float32).pin_memory().numpy()
+        e2e_ms = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G = ctx.upload(n, rp_h, col_h)
+            ctx.dppr(G, view_h, ALPHA, EPS, P.FP32, dppr_out=D_h, pdist_out=Dl_h, cert=True)
+            ctx.layout(Dl_h, x0_p, args.iters, P.FP32, x_out=X_h, stress=True)
+            G.free()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        tot = sum(e2e_ms)
+        if world > 1:
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        h2d = rp_h.nbytes + col_h.nbytes + view_h.nbytes + Dl_h.nbytes + x0_p.nbytes
+        d2h = D_h.nbytes + Dl_h.nbytes + X_h.nbytes + 8 * n
+        e2e = {"value": world * args.e2e_steps * entries / (tot / 1e3), "unit": "entries/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": tot / args.e2e_steps}
+
+    if rank != 0:
+        return
+    hbm, sm_max, peak_kind = peaks()
+    names = {"sweep": ("propagation sweep (k_sweep)", bytes_sweep),
+             "ly": ("all-pairs L^Y pass (k_pairpass<0>)", bytes_ly),
+             "apply": ("(L^w)^+ apply pass (k_pairpass<1>)", bytes_apply)}
+    kernels = {}
+    for cls, (label, alg) in names.items():
+        ms, cnt = ktimes[cls]
+        if cnt == 0 or ms <= 0:
+            continue
+        ach = alg / (ms / 1e3) / 1e9
+        kernels[cls] = {"kernel": label, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "launches": cnt, "avg_launch_us": 1e3 * ms / cnt,
+                        "alg_bytes_per_launch": alg / cnt, "traffic": measured_traffic(cls)}
+    share = {c: {"ms": ktimes[c][0] / args.steps, "launches": ktimes[c][1] // max(1, args.steps)}
+             for c in ktimes if ktimes[c][1]}
+    dom = max(kernels, key=lambda c: ktimes[c][0]) if kernels else None
+    roof = dict(kernels[dom]) if dom else None
+    if roof is not None:
+        roof["peak_kind"] = f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        e, t = cpu_oracle_sample(g, 16)
+        cpu = {"value": e / t, "unit": "entries/s", "cores": 1, "kind": "oracle",
+               "sample": "16 seeded sources: FP64 DPPR rows + PDist rows by power iteration (scipy sparse, 1 thread)"}
+    line = {
+        "metric": "DPPR entries/s at n=10k, err<=1e-6 vs FP64; layout iters/s; % HBM roofline",
+        "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(args, world),
+        "phases": {"dppr_pdist_ms": statistics.mean(dppr_ms), "layout_ms": statistics.mean(layout_ms),
+                   "dppr_entries_per_s_phase": entries / (statistics.mean(dppr_ms) / 1e3),
+                   "layout_iters_per_s": args.iters / (statistics.mean(layout_ms) / 1e3),
+                   "sweeps_per_step": sweeps / args.steps, "final_stress": stress,
+                   "wall_s_timed_region": wall},
+        "roofline": roof, "roofline_kernels": kernels, "kernel_share": share,
+        "gpu_launches": int(launches),
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * pprviz.h - C ABI of the GB300 (sm_103a) PPRviz hot path.
+ *
+ * The library computes, on one GPU, the distance-matrix and positioning
+ * phases of PPRviz (Zhang et al., "Effective and Efficient PageRank-based
+ * Positioning for Graph Visualization", SIGMOD 2023, arXiv 2112.14944):
+ *
+ *   1. personalized PageRank pi(s, .) for every node s of a view
+ *      (Sec. 3.1: random walk with restart probability alpha);
+ *   2. DPPR pi_d(s, t) = d(s) pi(s, t) (Definition 1) and PDist
+ *      Delta[i,j] = min(max(1 - ln(pi_d(i,j) + pi_d(j,i)), 2), 2 ln n)
+ *      (Sec. 3.1, Eq. (1));
+ *   3. the stress energy L(X | Delta) = sum_{i<j} (1 - |X_i - X_j| / Delta_ij)^2
+ *      (Sec. 5, Eq. (7)), its gradients, and stress majorization
+ *      X <- (L^w)^+ L^Y(X) X (Appendix A.1, Eq. (10)).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status (PPRVIZ_OK = 0 or a PPRVIZ_E_* code);
+ *    no C++ exception crosses the ABI. pprviz_last_error() gives a message
+ *    owned by the context, valid until the next call on that context.
+ *  - The caller owns every input and output buffer. By default they are host
+ *    pointers: the call copies inputs to the device, runs, copies outputs back
+ *    and returns when the results are in place. With PPRVIZ_DEVICE_PTRS in
+ *    `mem_flags` they are device pointers on the context's device, and the
+ *    call only enqueues work on the context stream (pprviz_sync waits).
+ *    Scalar report outputs (cert_out, stress_out, e_out) are always host
+ *    pointers and are written before the call returns (the call waits for the
+ *    values they need).
+ *  - The library owns the context, graph objects and its device workspace.
+ *  - Dense matrices are row-major with leading dimension k. Node and view ids
+ *    are 0-based. A view lists distinct node ids of the graph.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef PPRVIZ_H
+#define PPRVIZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PPRVIZ_OK 0
+#define PPRVIZ_E_INVALID_ARG 1   /* bad scalar, size, pointer or flag */
+#define PPRVIZ_E_BAD_GRAPH 2     /* CSR fails validation (see pprviz_graph_upload) */
+#define PPRVIZ_E_OOM 3           /* device allocation failed */
+#define PPRVIZ_E_CUDA 4          /* a CUDA runtime call or kernel launch failed */
+#define PPRVIZ_E_NOT_CONVERGED 5 /* iteration cap hit; outputs valid, cert_out states the bound */
+#define PPRVIZ_E_TIMEOUT 6       /* a bounded device wait expired */
+
+/* graph flags */
+#define PPRVIZ_UNDIRECTED 1u     /* CSR stores both directions; checked when validating */
+#define PPRVIZ_VALIDATE 2u       /* accepted for clarity; validation always runs */
+#define PPRVIZ_DEGREE_COUNT 4u   /* weighted graph, but d(v) = edge count instead of strength */
+
+/* memory / output flags */
+#define PPRVIZ_DEVICE_PTRS 1u    /* buffers are device pointers; calls are asynchronous */
+#define PPRVIZ_OUT_FP64 2u       /* matrices and coordinates are double instead of float */
+
+/* propagation precision (pprviz_dppr) and layout precision (pprviz_layout) */
+#define PPRVIZ_FP64 0            /* plain FP64: power iteration / FP64 layout arithmetic */
+#define PPRVIZ_FP32 1            /* FP32 Chebyshev sweeps + FP64 residual + refinement; FP32 layout */
+
+typedef struct pprviz_ctx pprviz_ctx;
+typedef struct pprviz_graph pprviz_graph;
+
+/* Counters of the last pprviz_dppr / pprviz_layout call on a context. */
+typedef struct pprviz_stats {
+    int32_t groups;            /* source groups processed */
+    int32_t sweeps_main;       /* propagation sweeps of the main solve, summed over groups */
+    int32_t sweeps_refine;     /* refinement sweeps, summed over groups */
+    int32_t refine_passes;     /* refinement passes, summed over groups */
+    int32_t residual_passes;   /* FP64 residual passes, summed over groups */
+    int32_t kernel_launches;   /* kernels this library launched in the call */
+    double max_cert;           /* max over sources of the final certificate */
+    int32_t layout_iters;      /* layout iterations run */
+    int32_t source_group;      /* sources per group (state tile width) */
+    /* Algorithmic bytes of the call, per kernel class: the bytes each launch
+     * must move for the entries it computes (valid sources only; a gathered
+     * state row counts once, CSR and caches excluded). Sweep: 12 bytes per
+     * (node, source) for a Chebyshev sweep (read y_k, y_k-1, write y_k+1),
+     * 16 with a dense right-hand side, 16 per FP64 power sweep; L^Y and apply
+     * passes: one k x k matrix read each. */
+    double bytes_sweep;
+    double bytes_ly;
+    double bytes_apply;
+} pprviz_stats;
+
+/* Kernel classes for per-class device timing (pprviz_profile). */
+#define PPRVIZ_K_GRAPH 0         /* CSR validation, degrees, view checks */
+#define PPRVIZ_K_SWEEP 1         /* propagation sweeps (Chebyshev / power) */
+#define PPRVIZ_K_RESIDUAL 2      /* FP64 residual certificate passes */
+#define PPRVIZ_K_EXTRACT 3       /* DPPR row extraction (transpose + scaling) */
+#define PPRVIZ_K_PDIST 4         /* PDist transform */
+#define PPRVIZ_K_FACTOR 5        /* L^w build and Gauss-Jordan inversion */
+#define PPRVIZ_K_LY 6            /* all-pairs L^Y(X) X pass */
+#define PPRVIZ_K_APPLY 7         /* X = (L^w)^+ b pass */
+#define PPRVIZ_K_ENERGY 8        /* energy / gradient passes and reductions */
+#define PPRVIZ_K_OTHER 9         /* initialisation, casts, small helpers */
+#define PPRVIZ_NKCLASS 10
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+ * to run on (borrowed, not destroyed), or NULL for a stream the context owns.
+ * Errors: E_INVALID_ARG (out == NULL, bad device), E_CUDA. */
+int pprviz_create(pprviz_ctx **out, int device, void *cuda_stream);
+void pprviz_destroy(pprviz_ctx *ctx);
+const char *pprviz_last_error(const pprviz_ctx *ctx);
+/* Wait for all work enqueued on the context stream. */
+int pprviz_sync(pprviz_ctx *ctx);
+int pprviz_get_stats(const pprviz_ctx *ctx, pprviz_stats *out);
+/* Device timing per kernel class. With `enable` != 0, every kernel launch of
+ * the context is bracketed by CUDA events on the context stream; the totals
+ * accumulate until read. pprviz_profile resets the totals. */
+int pprviz_profile(pprviz_ctx *ctx, int enable);
+/* Waits for the context stream, then writes PPRVIZ_NKCLASS entries of total
+ * device milliseconds and launch counts per class since the last reset (NULL
+ * arrays are skipped). Launch counts are kept even when timing is off. */
+int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out);
+
+/* P0 - graph ingest (Sec. 2.1; Table 1: n nodes, out-degree d(v)).
+ * row_ptr: n+1 int64, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ * col_idx: nnz int32 out-neighbour ids, strictly increasing within a row
+ *          (no duplicate edges), no self-loops.
+ * weights: nnz float edge weights (> 0, finite) or NULL for unit weights;
+ *          weighted walks step to v_j with probability w_ij / sum_j w_ij and
+ *          d(v) is that sum (the strength) unless PPRVIZ_DEGREE_COUNT.
+ * flags:   PPRVIZ_UNDIRECTED is required (the propagation uses the pull form
+ *          over the symmetric CSR). Every rule above and the symmetry
+ *          (including equal weights both ways) are always checked on the
+ *          device before the graph is accepted.
+ * Host pointers unless mem_flags has PPRVIZ_DEVICE_PTRS. The library copies
+ * the arrays; the caller may free them on return. A node with no edges is
+ * kept: its walk stays on it and its d(v) = 0.
+ * Errors: E_INVALID_ARG, E_BAD_GRAPH (validation failed; message says which
+ * rule), E_OOM, E_CUDA. */
+int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr,
+                        const int32_t *col_idx, const float *weights, uint32_t flags,
+                        uint32_t mem_flags, pprviz_graph **out);
+void pprviz_graph_free(pprviz_graph *g);
+/* Copy the n degrees d(v) (double) computed on the device into deg_out (host
+ * or device per mem_flags) and report n, nnz and m = sum_v d(v). */
+int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out,
+                         int64_t *n_out, int64_t *nnz_out, double *m_out, uint32_t mem_flags);
+
+/* P1-P3 - DPPR and PDist of a view (Sec. 3.1, Definition 1 and Eq. (1)).
+ * view:      k distinct node ids (int32). Row q of the outputs is source view[q].
+ * alpha:     restart probability, 0 < alpha < 1.
+ * eps:       absolute DPPR error bound. Each source s is certified by the FP64
+ *            residual res = alpha e_s - x (I - (1 - alpha) P) of the computed
+ *            row x: cert(s) = d(s) ||res||_1 / alpha bounds max_t |error| of
+ *            d(s) x_t (Eq. (3) with 0 <= pi <= 1). The FP64 path runs power
+ *            iteration for the a-priori sweep count; the FP32 path runs
+ *            Chebyshev sweeps and FP32 refinement passes until every source
+ *            has cert(s) <= eps, or returns E_NOT_CONVERGED after 4 passes.
+ * precision: PPRVIZ_FP64 or PPRVIZ_FP32.
+ * dppr_out:  k*k DPPR, row q = pi_d(view[q], view[.]); may be NULL.
+ * pdist_out: k*k PDist with Delta[q][r] from pi_d(q,r) + pi_d(r,q), the upper
+ *            clamp 2 ln n_clamp (n_clamp = 0 means the graph's n) and a zero
+ *            diagonal; may be NULL.
+ * cert_out:  k doubles, the final certificate per source (host); may be NULL.
+ * Float outputs unless PPRVIZ_OUT_FP64 (then double). The certificate bounds
+ * the computed row before the output is rounded to the output type.
+ * Errors: E_INVALID_ARG (k < 1, k > n, bad id, duplicate id, alpha or eps out
+ * of range, graph not undirected), E_NOT_CONVERGED, E_OOM, E_CUDA. */
+int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k,
+                double alpha, double eps, int precision, void *dppr_out, void *pdist_out,
+                int64_t n_clamp, double *cert_out, uint32_t mem_flags);
+
+/* P3 alone - PDist from a k*k DPPR matrix (Sec. 3.1, Eq. (1)):
+ * Delta[i][j] = min(max(1 - ln(D[i][j] + D[j][i]), 2), 2 ln n_clamp), zero
+ * diagonal, z = 0 mapped to the upper clamp. Types per PPRVIZ_OUT_FP64.
+ * Errors: E_INVALID_ARG (k < 1, n_clamp < 2), E_OOM, E_CUDA. */
+int pprviz_pdist(pprviz_ctx *ctx, const void *dppr, int32_t k, int64_t n_clamp,
+                 void *pdist_out, uint32_t mem_flags);
+
+/* P4-P5 - stress-majorization layout (Sec. 5, Eq. (7); Appendix A.1, Eq. (10)).
+ * pdist:     k*k symmetric target distances, off-diagonal finite and > 0
+ *            (the diagonal is ignored).
+ * x0:        k*2 initial coordinates; x_out: k*2 result (may alias x0).
+ * iters:     number of updates X <- (L^w)^+ L^Y(X) X, each the exact solve
+ *            of Eq. (10) with the Moore-Penrose inverse of L^w; the result
+ *            is centred (column means 0). iters = 0 only centres x0.
+ * precision: PPRVIZ_FP64 (FP64 arithmetic throughout) or PPRVIZ_FP32.
+ * stress_out: Eq. (7) at the final X, accumulated in FP64 (host); may be NULL.
+ * Types per PPRVIZ_OUT_FP64 (pdist, x0, x_out).
+ * Errors: E_INVALID_ARG (k < 1, iters < 0, a non-finite or non-positive
+ * off-diagonal distance), E_OOM, E_CUDA. */
+int pprviz_layout(pprviz_ctx *ctx, const void *pdist, int32_t k, const void *x0,
+                  int32_t iters, int precision, void *x_out, double *stress_out,
+                  uint32_t mem_flags);
+
+/* P6 - stress energy and its gradients by pair recomputation (Sec. 5, Eq. (7)).
+ * e_out:      L(X | Delta) summed over i < j in FP64 (host); may be NULL.
+ * grad_x:     k*2, grad_scale * dL/dX_i = grad_scale * sum_j 2 (d_ij - Delta_ij)
+ *             / (Delta_ij^2 d_ij) (X_i - X_j), 0 for coincident points; may be NULL.
+ * grad_pdist: k*k, grad_scale * (1 - d_ij / Delta_ij) d_ij / Delta_ij^2 for
+ *             i != j (the derivative of (1/2) sum_{i != j}, equal to Eq. (7) for
+ *             symmetric Delta), 0 on the diagonal; may be NULL.
+ * Float buffers (FP32 arithmetic, FP64 energy accumulation), or double with
+ * PPRVIZ_OUT_FP64 (FP64 arithmetic).
+ * Errors: E_INVALID_ARG, E_OOM, E_CUDA. */
+int pprviz_energy(pprviz_ctx *ctx, const void *pdist, int32_t k, const void *x,
+                  double grad_scale, double *e_out, void *grad_x, void *grad_pdist,
+                  uint32_t mem_flags);
+
+/* P7 - many independent views in one call (Sec. 2.2: the multi-level
+ * mechanism visits the children of many supernodes). View v is its own
+ * undirected graph (uploaded with pprviz_graph_upload); every node of it is a
+ * source (k_v = n_v, n_clamp = n_v). For each view: DPPR (FP32 path, eps),
+ * PDist, then `iters` FP32 stress-majorization updates from its x0.
+ * offsets:     nviews+1 int64 prefix sums of n_v (host).
+ * x0_packed:   sum n_v * 2 floats (view v at offsets[v]*2).
+ * pdist_packed: sum n_v^2 floats (view v at the prefix sum of n_u^2, u < v);
+ *              may be NULL.
+ * x_packed:    sum n_v * 2 floats, the final layouts.
+ * stress_out:  nviews doubles (host), final stress per view; may be NULL.
+ * Errors: as pprviz_dppr and pprviz_layout. */
+int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views,
+                       const int64_t *offsets, double alpha, double eps, int32_t iters,
+                       const float *x0_packed, float *pdist_packed, float *x_packed,
+                       double *stress_out, uint32_t mem_flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPRVIZ_H */

@@ -1,0 +1,257 @@
+"""GB300 (sm_103a) implementation of the PPRviz hot path.
+
+PPRviz (Zhang et al., "Effective and Efficient PageRank-based Positioning for
+Graph Visualization", SIGMOD 2023): personalized PageRank for every node of a
+view, degree-normalised DPPR and the PDist transform (Sec. 3.1, Eq. (1)), and
+stress-majorization positioning over PDist (Sec. 5, Eq. (7); Appendix A.1).
+
+All computation happens in the CUDA library libpprviz.so behind the C ABI in
+include/pprviz.h. This package only marshals arguments: numpy arrays are host
+buffers, torch CUDA tensors are device buffers. PyTorch is used for device
+memory and streams.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (PPRVIZ_DEGREE_COUNT, PPRVIZ_DEVICE_PTRS, PPRVIZ_FP32, PPRVIZ_FP64, PPRVIZ_OUT_FP64,
+                       PPRVIZ_UNDIRECTED, PPRVIZ_VALIDATE, PPRVizError)
+
+__all__ = ["Context", "Graph", "StressEnergy", "PPRVizError", "FP32", "FP64", "library_path"]
+
+FP32 = PPRVIZ_FP32
+FP64 = PPRVIZ_FP64
+
+
+def library_path() -> str:
+    return B.LIB_PATH
+
+
+class Graph:
+    """A graph uploaded to the device (opaque library handle)."""
+
+    def __init__(self, ctx: "Context", handle: int, n: int):
+        self.ctx = ctx
+        self.h = handle
+        self.n = n
+
+    def degrees(self, out=None):
+        """(d(v) as float64 numpy array or the given buffer, n, nnz, m)."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.float64)
+        n, nnz, m = B.pprviz_graph_degrees(self.ctx.h, self.h, out)
+        return out, n, nnz, m
+
+    def free(self):
+        if self.h:
+            B.pprviz_graph_free(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A library context on one CUDA device.
+
+    With `torch_stream=True` the context runs on a dedicated torch CUDA stream
+    that is ordered after the caller's current stream for every device-buffer
+    call (and the current stream waits for it afterwards).
+    """
+
+    def __init__(self, device: int = 0, torch_stream: bool = False):
+        self._stream = None
+        handle = None
+        if torch_stream:
+            import torch
+            self._stream = torch.cuda.Stream(device=device)
+            handle = self._stream.cuda_stream
+        self.device = device
+        self.h = B.pprviz_create(device, handle)
+
+    # -- stream ordering for device (torch) buffers --
+    def _enter(self, dev):
+        if dev and self._stream is not None:
+            import torch
+            self._stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _leave(self, dev, *tensors):
+        if dev and self._stream is not None:
+            import torch
+            torch.cuda.current_stream(self.device).wait_stream(self._stream)
+            for t in tensors:
+                if t is not None and B._is_torch(t):
+                    t.record_stream(self._stream)
+
+    def close(self):
+        if self.h:
+            B.pprviz_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        return B.pprviz_get_stats(self.h)
+
+    def sync(self):
+        B.pprviz_sync(self.h)
+
+    def profile(self, enable: bool = True):
+        """Reset the per-kernel-class counters; time every launch if `enable`."""
+        B.pprviz_profile(self.h, enable)
+
+    def kernel_times(self) -> dict:
+        """{class: (device ms, launches)} since the last profile() call."""
+        return B.pprviz_kernel_times(self.h)
+
+    def upload(self, n, row_ptr, col, weights=None, validate=True, degree_count=False) -> Graph:
+        flags = PPRVIZ_UNDIRECTED | (PPRVIZ_VALIDATE if validate else 0) | (PPRVIZ_DEGREE_COUNT if degree_count else 0)
+        dev = B._mem_flags(row_ptr, col, weights) == PPRVIZ_DEVICE_PTRS
+        self._enter(dev)
+        h = B.pprviz_graph_upload(self.h, n, row_ptr, col, weights, flags)
+        self._leave(dev)
+        return Graph(self, h, int(n))
+
+    def upload_graph(self, g, validate=True) -> Graph:
+        """Upload a synth.Graph-like object (n, row_ptr, col, weight)."""
+        return self.upload(g.n, g.row_ptr, g.col, g.weight, validate=validate)
+
+    def dppr(self, graph: Graph, view, alpha=0.15, eps=1e-6, precision=FP32, n_clamp=0, dppr_out=None,
+             pdist_out=None, cert=True, out64=False):
+        """DPPR and PDist of `view` (host numpy or device torch buffers).
+
+        Output buffers may be given; else numpy arrays are allocated when the
+        view is a numpy array. Returns (dppr, pdist, cert, status)."""
+        k = len(view)
+        dev = B._mem_flags(view, dppr_out, pdist_out) == PPRVIZ_DEVICE_PTRS
+        if not dev:
+            dt = np.float64 if out64 else np.float32
+            if dppr_out is None:
+                dppr_out = np.empty((k, k), dtype=dt)
+            if pdist_out is None:
+                pdist_out = np.empty((k, k), dtype=dt)
+        mf = (PPRVIZ_DEVICE_PTRS if dev else 0) | (PPRVIZ_OUT_FP64 if out64 else 0)
+        cert_out = np.empty(k, dtype=np.float64) if cert else None
+        self._enter(dev)
+        st = B.pprviz_dppr(self.h, graph.h, view, k, alpha, eps, precision, dppr_out, pdist_out, n_clamp,
+                           cert_out, mf)
+        self._leave(dev, view, dppr_out, pdist_out)
+        return dppr_out, pdist_out, cert_out, st
+
+    def pdist(self, dppr, n_clamp, out=None):
+        k = dppr.shape[0]
+        dev = B._mem_flags(dppr, out) == PPRVIZ_DEVICE_PTRS
+        f64 = (str(dppr.dtype).endswith("float64"))
+        if out is None and not dev:
+            out = np.empty((k, k), dtype=np.float64 if f64 else np.float32)
+        mf = (PPRVIZ_DEVICE_PTRS if dev else 0) | (PPRVIZ_OUT_FP64 if f64 else 0)
+        self._enter(dev)
+        B.pprviz_pdist(self.h, dppr, k, n_clamp, out, mf)
+        self._leave(dev, dppr, out)
+        return out
+
+    def layout(self, pdist, x0, iters, precision=FP32, x_out=None, stress=True):
+        """Stress-majorization layout. Returns (X, final stress or None)."""
+        k = pdist.shape[0]
+        dev = B._mem_flags(pdist, x0, x_out) == PPRVIZ_DEVICE_PTRS
+        f64 = str(pdist.dtype).endswith("float64")
+        if x_out is None and not dev:
+            x_out = np.empty((k, 2), dtype=np.float64 if f64 else np.float32)
+        s = np.zeros(1, dtype=np.float64) if stress else None
+        mf = (PPRVIZ_DEVICE_PTRS if dev else 0) | (PPRVIZ_OUT_FP64 if f64 else 0)
+        self._enter(dev)
+        B.pprviz_layout(self.h, pdist, k, x0, iters, precision, x_out, s, mf)
+        self._leave(dev, pdist, x0, x_out)
+        return x_out, (float(s[0]) if stress else None)
+
+    def energy(self, pdist, x, grad_scale=1.0, grad_x=False, grad_pdist=False, gx_out=None, gd_out=None):
+        """Stress energy (Eq. (7)) and optional gradients. Returns (E, grad_x, grad_pdist)."""
+        k = pdist.shape[0]
+        dev = B._mem_flags(pdist, x, gx_out, gd_out) == PPRVIZ_DEVICE_PTRS
+        f64 = str(pdist.dtype).endswith("float64")
+        if dev:
+            import torch
+            if grad_x and gx_out is None:
+                gx_out = torch.empty((k, 2), dtype=pdist.dtype, device=pdist.device)
+            if grad_pdist and gd_out is None:
+                gd_out = torch.empty((k, k), dtype=pdist.dtype, device=pdist.device)
+        else:
+            dt = np.float64 if f64 else np.float32
+            if grad_x and gx_out is None:
+                gx_out = np.empty((k, 2), dtype=dt)
+            if grad_pdist and gd_out is None:
+                gd_out = np.empty((k, k), dtype=dt)
+        e = np.zeros(1, dtype=np.float64)
+        mf = (PPRVIZ_DEVICE_PTRS if dev else 0) | (PPRVIZ_OUT_FP64 if f64 else 0)
+        self._enter(dev)
+        B.pprviz_energy(self.h, pdist, k, x, grad_scale, e, gx_out if grad_x else None,
+                        gd_out if grad_pdist else None, mf)
+        self._leave(dev, pdist, x, gx_out, gd_out)
+        return float(e[0]), (gx_out if grad_x else None), (gd_out if grad_pdist else None)
+
+    def views_batch(self, graphs, x0_packed, alpha=0.15, eps=1e-6, iters=200, want_pdist=False):
+        """Batched views (numpy host buffers). Returns (x_packed, pdist_packed, stress, offsets)."""
+        sizes = np.array([g.n for g in graphs], dtype=np.int64)
+        offsets = np.zeros(len(graphs) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=offsets[1:])
+        x_packed = np.empty_like(x0_packed)
+        pd = np.empty(int((sizes ** 2).sum()), dtype=np.float32) if want_pdist else None
+        stress = np.zeros(len(graphs), dtype=np.float64)
+        B.pprviz_views_batch(self.h, [g.h for g in graphs], offsets, alpha, eps, iters, x0_packed, pd, x_packed,
+                             stress, 0)
+        return x_packed, pd, stress, offsets
+
+
+def _make_stress_energy():
+    import torch
+
+    class StressEnergy(torch.autograd.Function):
+        """L(X | Delta) of Eq. (7) with a hand-written backward.
+
+        forward runs the library's energy kernel; backward re-runs it with the
+        upstream gradient as `grad_scale`, recomputing every pair (no stored
+        k x k intermediates). Inputs are CUDA tensors (float32 or float64)."""
+
+        @staticmethod
+        def forward(fctx, X, Delta, lib_ctx):
+            e, _, _ = lib_ctx.energy(Delta.contiguous(), X.contiguous())
+            fctx.save_for_backward(X, Delta)
+            fctx.lib_ctx = lib_ctx
+            return torch.tensor(e, dtype=X.dtype, device=X.device)
+
+        @staticmethod
+        def backward(fctx, grad_e):
+            X, Delta = fctx.saved_tensors
+            scale = float(grad_e)
+            _, gx, gd = fctx.lib_ctx.energy(Delta.contiguous(), X.contiguous(), grad_scale=scale,
+                                            grad_x=fctx.needs_input_grad[0], grad_pdist=fctx.needs_input_grad[1])
+            return gx, gd, None
+
+    return StressEnergy
+
+
+class _Lazy:
+    _cls = None
+
+    def __get__(self, obj, owner):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_stress_energy()
+        return _Lazy._cls
+
+
+class _Namespace:
+    StressEnergy = _Lazy()
+
+
+def __getattr__(name):
+    if name == "StressEnergy":
+        return _Namespace.StressEnergy
+    raise AttributeError(name)

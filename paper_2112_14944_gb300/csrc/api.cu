@@ -1,0 +1,516 @@
+// C ABI entry points of libpprviz (declared in include/pprviz.h): argument
+// checks, host <-> device staging and dispatch to the kernels. No C++
+// exception crosses this boundary.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pprviz {
+
+int set_err(pprviz_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_err(pprviz_ctx *ctx, cudaError_t e, const char *what) {
+  int code = (e == cudaErrorMemoryAllocation) ? PPRVIZ_E_OOM : PPRVIZ_E_CUDA;
+  return set_err(ctx, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ws_ensure(pprviz_ctx *ctx, int slot, size_t bytes) {
+  cudaError_t e = ctx->ws[slot].ensure(bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? PPRVIZ_E_OOM : PPRVIZ_E_CUDA,
+                   std::string("device workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  return PPRVIZ_OK;
+}
+
+static cudaEvent_t ev_get(pprviz_ctx *ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+ProfScope::ProfScope(pprviz_ctx *ctx, int k) : c(ctx), cls(k) {
+  c->class_launches[cls]++;
+  if (c->profiling) {
+    a = ev_get(c);
+    b = ev_get(c);
+    if (a && b) cudaEventRecord(a, c->stream);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (a && b) {
+    cudaEventRecord(b, c->stream);
+    c->ev_pending.push_back({cls, {a, b}});
+  } else {
+    if (a) c->ev_pool.push_back(a);
+    if (b) c->ev_pool.push_back(b);
+  }
+}
+
+// Stage a caller buffer on the device: returns the caller pointer itself for
+// device buffers, else copies the host data into workspace slot `slot`.
+static int stage_in(pprviz_ctx *ctx, const void *p, size_t bytes, bool device, int slot, const void **out) {
+  if (device) {
+    *out = p;
+    return PPRVIZ_OK;
+  }
+  PPRVIZ_TRY(ws_ensure(ctx, slot, bytes));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ctx->ws[slot].p, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  *out = ctx->ws[slot].p;
+  return PPRVIZ_OK;
+}
+
+static int begin(pprviz_ctx *ctx) {
+  ctx->err.clear();
+  ctx->launches = 0;
+  memset(&ctx->stats, 0, sizeof(ctx->stats));
+  PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return PPRVIZ_OK;
+}
+
+static int finish(pprviz_ctx *ctx, int status) {
+  ctx->stats.kernel_launches = ctx->launches;
+  return status;
+}
+
+template <typename TI, typename TO>
+__global__ void k_cast(int64_t cnt, const TI *__restrict__ in, TO *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) out[i] = (TO)in[i];
+}
+
+}  // namespace pprviz
+
+using namespace pprviz;
+
+extern "C" {
+
+int pprviz_create(pprviz_ctx **out, int device, void *cuda_stream) {
+  if (!out) return PPRVIZ_E_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return PPRVIZ_E_INVALID_ARG;
+  }
+  pprviz_ctx *ctx = new (std::nothrow) pprviz_ctx();
+  if (!ctx) return PPRVIZ_E_OOM;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return PPRVIZ_E_CUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return PPRVIZ_E_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return PPRVIZ_OK;
+}
+
+void pprviz_destroy(pprviz_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &p : ctx->ev_pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto &b : ctx->ws) b.release();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *pprviz_last_error(const pprviz_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int pprviz_sync(pprviz_ctx *ctx) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return PPRVIZ_OK;
+}
+
+int pprviz_get_stats(const pprviz_ctx *ctx, pprviz_stats *out) {
+  if (!ctx || !out) return PPRVIZ_E_INVALID_ARG;
+  *out = ctx->stats;
+  return PPRVIZ_OK;
+}
+
+int pprviz_profile(pprviz_ctx *ctx, int enable) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto &p : ctx->ev_pending) {
+    ctx->ev_pool.push_back(p.second.first);
+    ctx->ev_pool.push_back(p.second.second);
+  }
+  ctx->ev_pending.clear();
+  for (int i = 0; i < PPRVIZ_NKCLASS; ++i) {
+    ctx->class_ms[i] = 0.0;
+    ctx->class_launches[i] = 0;
+  }
+  ctx->profiling = enable != 0;
+  return PPRVIZ_OK;
+}
+
+int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto &p : ctx->ev_pending) {
+    float ms = 0.0f;
+    PPRVIZ_CUDA(ctx, cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+    ctx->class_ms[p.first] += ms;
+    ctx->ev_pool.push_back(p.second.first);
+    ctx->ev_pool.push_back(p.second.second);
+  }
+  ctx->ev_pending.clear();
+  for (int i = 0; i < PPRVIZ_NKCLASS; ++i) {
+    if (ms_out) ms_out[i] = ctx->class_ms[i];
+    if (launches_out) launches_out[i] = ctx->class_launches[i];
+  }
+  return PPRVIZ_OK;
+}
+
+int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                        const float *weights, uint32_t flags, uint32_t mem_flags, pprviz_graph **out) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  if (!out) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  PPRVIZ_TRY(begin(ctx));
+  if (n < 1 || n > INT32_MAX) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n must be in [1, 2^31 - 1]");
+  if (!row_ptr) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "row_ptr is NULL");
+  if (!(flags & PPRVIZ_UNDIRECTED))
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG,
+                   "directed graphs are not supported: pass the symmetric CSR with PPRVIZ_UNDIRECTED");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  int64_t nnz = 0;
+  if (dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    nnz = row_ptr[n];
+  }
+  if (nnz < 0) return set_err(ctx, PPRVIZ_E_BAD_GRAPH, "row_ptr[n] is negative");
+  if (nnz > 0 && !col_idx) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "col_idx is NULL");
+  pprviz_graph *g = new (std::nothrow) pprviz_graph();
+  if (!g) return set_err(ctx, PPRVIZ_E_OOM, "host allocation failed");
+  g->ctx = ctx;
+  g->n = n;
+  g->nnz = nnz;
+  g->weighted = weights != nullptr;
+  g->flags = flags;
+  auto fail = [&](int s) { pprviz_graph_free(g); return s; };
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e;
+  if ((e = g->rp.ensure(sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc row_ptr"));
+  if ((e = g->col.ensure(sizeof(int32_t) * (size_t)nnz)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc col"));
+  if (g->weighted && (e = g->w.ensure(sizeof(float) * (size_t)nnz)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc w"));
+  if ((e = g->deg.ensure(sizeof(double) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc deg"));
+  if ((e = g->invdw_f.ensure(sizeof(float) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc invdw"));
+  if ((e = g->invdw_d.ensure(sizeof(double) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc invdw"));
+  if ((e = cudaMemcpyAsync(g->rp.p, row_ptr, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) != cudaSuccess)
+    return fail(cuda_err(ctx, e, "copy row_ptr"));
+  if (nnz && (e = cudaMemcpyAsync(g->col.p, col_idx, sizeof(int32_t) * (size_t)nnz, kind, ctx->stream)) != cudaSuccess)
+    return fail(cuda_err(ctx, e, "copy col"));
+  if (g->weighted && nnz &&
+      (e = cudaMemcpyAsync(g->w.p, weights, sizeof(float) * (size_t)nnz, kind, ctx->stream)) != cudaSuccess)
+    return fail(cuda_err(ctx, e, "copy weights"));
+  int s = graph_build(ctx, g, flags);
+  if (s != PPRVIZ_OK) return fail(s);
+  *out = g;
+  return finish(ctx, PPRVIZ_OK);
+}
+
+void pprviz_graph_free(pprviz_graph *g) {
+  if (!g) return;
+  if (g->ctx) cudaSetDevice(g->ctx->device);
+  g->rp.release();
+  g->col.release();
+  g->w.release();
+  g->deg.release();
+  g->invdw_f.release();
+  g->invdw_d.release();
+  delete g;
+}
+
+int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out, int64_t *n_out,
+                         int64_t *nnz_out, double *m_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  if (!g) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph is NULL");
+  PPRVIZ_TRY(begin(ctx));
+  if (n_out) *n_out = g->n;
+  if (nnz_out) *nnz_out = g->nnz;
+  if (m_out) *m_out = g->m;
+  if (deg_out) {
+    const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(deg_out, g->deg.p, sizeof(double) * (size_t)g->n,
+                                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!dev) PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return finish(ctx, PPRVIZ_OK);
+}
+
+int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k, double alpha, double eps,
+                int precision, void *dppr_out, void *pdist_out, int64_t n_clamp, double *cert_out,
+                uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!g || !view) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or view is NULL");
+  if (k < 1 || (int64_t)k > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be in [1, n]");
+  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
+  if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
+  if (precision != PPRVIZ_FP64 && precision != PPRVIZ_FP32)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "precision must be PPRVIZ_FP64 or PPRVIZ_FP32");
+  if (n_clamp == 0) n_clamp = g->n;
+  if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool out64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  const size_t kk = (size_t)k * (size_t)k;
+  // view on both sides
+  std::vector<int32_t> view_h((size_t)k);
+  const int32_t *view_d = nullptr;
+  if (dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_h.data(), view, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    view_d = view;
+  } else {
+    memcpy(view_h.data(), view, sizeof(int32_t) * k);
+    const void *p = nullptr;
+    PPRVIZ_TRY(stage_in(ctx, view, sizeof(int32_t) * k, false, WS_VIEW, &p));
+    view_d = (const int32_t *)p;
+  }
+  PPRVIZ_TRY(view_check(ctx, g, view_d, k));
+  // DPPR is computed in FP64 for the FP64 path (and for FP64 outputs), else FP32
+  const bool int64p = precision == PPRVIZ_FP64 || out64;
+  const size_t ie = int64p ? sizeof(double) : sizeof(float);
+  void *dppr_d = nullptr;
+  if (dppr_out && dev && int64p == out64) dppr_d = dppr_out;
+  else if (dppr_out || pdist_out) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, ie * kk));
+    dppr_d = ctx->ws[WS_DPPR].p;
+  }
+  std::vector<double> cert_tmp;
+  double *cert_h = cert_out;
+  int status = dppr_solve(ctx, g, view_d, view_h, k, alpha, eps, precision, dppr_d, int64p, cert_h);
+  if (status != PPRVIZ_OK && status != PPRVIZ_E_NOT_CONVERGED) return finish(ctx, status);
+  const std::string keep_err = ctx->err;
+  void *pdist_d = nullptr;
+  if (pdist_out) {
+    if (dev && int64p == out64) pdist_d = pdist_out;
+    else {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_PDIST, ie * kk));
+      pdist_d = ctx->ws[WS_PDIST].p;
+    }
+    PPRVIZ_TRY(pdist_launch(ctx, dppr_d, k, n_clamp, pdist_d, int64p));
+  }
+  // deliver outputs in the requested type and memory space
+  auto deliver = [&](void *src_d, void *dst, int tmp_slot) -> int {
+    if (!dst || src_d == dst) return PPRVIZ_OK;
+    const size_t ob = (out64 ? sizeof(double) : sizeof(float)) * kk;
+    void *conv = src_d;
+    if (int64p != out64) {
+      // FP64 path with float outputs: narrow on the device
+      void *target = dev ? dst : nullptr;
+      if (!target) {
+        PPRVIZ_TRY(ws_ensure(ctx, tmp_slot, ob));
+        target = ctx->ws[tmp_slot].p;
+      }
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_cast<double, float><<<(unsigned)((kk + 255) / 256), 256, 0, ctx->stream>>>((int64_t)kk, (const double *)src_d,
+                                                                                 (float *)target); }
+      PPRVIZ_LAUNCHED(ctx);
+      conv = target;
+      if (dev) return PPRVIZ_OK;
+    }
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(dst, conv, ob, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    return PPRVIZ_OK;
+  };
+  PPRVIZ_TRY(deliver(dppr_d, dppr_out, WS_OUT0));
+  PPRVIZ_TRY(deliver(pdist_d, pdist_out, WS_OUT1));
+  if (!dev || cert_out) PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (status != PPRVIZ_OK) ctx->err = keep_err;
+  return finish(ctx, status);
+}
+
+int pprviz_pdist(pprviz_ctx *ctx, const void *dppr, int32_t k, int64_t n_clamp, void *pdist_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!dppr || !pdist_out) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "NULL buffer");
+  if (k < 1) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be >= 1");
+  if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool f64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  const size_t bytes = (f64 ? sizeof(double) : sizeof(float)) * (size_t)k * k;
+  const void *in_d = nullptr;
+  PPRVIZ_TRY(stage_in(ctx, dppr, bytes, dev, WS_IN0, &in_d));
+  void *out_d = pdist_out;
+  if (!dev) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_OUT0, bytes));
+    out_d = ctx->ws[WS_OUT0].p;
+  }
+  PPRVIZ_TRY(pdist_launch(ctx, in_d, k, n_clamp, out_d, f64));
+  if (!dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(pdist_out, out_d, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return finish(ctx, PPRVIZ_OK);
+}
+
+int pprviz_layout(pprviz_ctx *ctx, const void *pdist, int32_t k, const void *x0, int32_t iters, int precision,
+                  void *x_out, double *stress_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!pdist || !x0 || !x_out) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "NULL buffer");
+  if (k < 1 || iters < 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be >= 1 and iters >= 0");
+  if (precision != PPRVIZ_FP64 && precision != PPRVIZ_FP32)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "precision must be PPRVIZ_FP64 or PPRVIZ_FP32");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool io64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  const size_t es = io64 ? sizeof(double) : sizeof(float);
+  const void *pd = nullptr, *xd = nullptr;
+  PPRVIZ_TRY(stage_in(ctx, pdist, es * (size_t)k * k, dev, WS_IN0, &pd));
+  PPRVIZ_TRY(stage_in(ctx, x0, es * 2 * (size_t)k, dev, WS_IN1, &xd));
+  void *xo = x_out;
+  if (!dev) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_OUT0, es * 2 * (size_t)k));
+    xo = ctx->ws[WS_OUT0].p;
+  }
+  int s = layout_run(ctx, pd, k, xd, iters, precision, io64, xo, stress_out);
+  if (s != PPRVIZ_OK) return finish(ctx, s);
+  if (!dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(x_out, xo, es * 2 * (size_t)k, cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return finish(ctx, PPRVIZ_OK);
+}
+
+int pprviz_energy(pprviz_ctx *ctx, const void *pdist, int32_t k, const void *x, double grad_scale, double *e_out,
+                  void *grad_x, void *grad_pdist, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!pdist || !x) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "NULL buffer");
+  if (k < 1) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be >= 1");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool f64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  const void *pd = nullptr, *xd = nullptr;
+  PPRVIZ_TRY(stage_in(ctx, pdist, es * (size_t)k * k, dev, WS_IN0, &pd));
+  PPRVIZ_TRY(stage_in(ctx, x, es * 2 * (size_t)k, dev, WS_IN1, &xd));
+  void *gx = grad_x, *gd = grad_pdist;
+  if (!dev) {
+    if (grad_x) {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_OUT0, es * 2 * (size_t)k));
+      gx = ctx->ws[WS_OUT0].p;
+    }
+    if (grad_pdist) {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_PDIST, es * (size_t)k * k));
+      gd = ctx->ws[WS_PDIST].p;
+    }
+  }
+  int s = energy_run(ctx, pd, k, xd, grad_scale, f64, e_out, gx, gd);
+  if (s != PPRVIZ_OK) return finish(ctx, s);
+  if (!dev) {
+    if (grad_x) PPRVIZ_CUDA(ctx, cudaMemcpyAsync(grad_x, gx, es * 2 * (size_t)k, cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad_pdist)
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(grad_pdist, gd, es * (size_t)k * k, cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return finish(ctx, PPRVIZ_OK);
+}
+
+int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views, const int64_t *offsets,
+                       double alpha, double eps, int32_t iters, const float *x0_packed, float *pdist_packed,
+                       float *x_packed, double *stress_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (nviews < 1 || !views || !offsets || !x0_packed || !x_packed)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "bad views arguments");
+  if (iters < 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "iters must be >= 0");
+  if (!(alpha > 0.0 && alpha < 1.0) || !(eps > 0.0))
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1) and eps > 0");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  int64_t sq_off = 0;
+  pprviz_stats total{};
+  int status = PPRVIZ_OK;
+  for (int32_t v = 0; v < nviews; ++v) {
+    const pprviz_graph *g = views[v];
+    if (!g) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "NULL view graph");
+    const int64_t nv = offsets[v + 1] - offsets[v];
+    if (nv != g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "offsets do not match the view sizes");
+    const int32_t k = (int32_t)nv;
+    std::vector<int32_t> view_h((size_t)k);
+    for (int32_t q = 0; q < k; ++q) view_h[q] = q;
+    PPRVIZ_TRY(ws_ensure(ctx, WS_VIEW, sizeof(int32_t) * (size_t)k));
+    int32_t *view_d = ctx->ws[WS_VIEW].as<int32_t>();
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_d, view_h.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, ctx->stream));
+    const size_t kk = (size_t)k * k;
+    PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, sizeof(float) * kk));
+    float *dppr_d = ctx->ws[WS_DPPR].as<float>();
+    float *pdist_d;
+    if (dev && pdist_packed) pdist_d = pdist_packed + sq_off;
+    else {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_PDIST, sizeof(float) * kk));
+      pdist_d = ctx->ws[WS_PDIST].as<float>();
+    }
+    int s = dppr_solve(ctx, g, view_d, view_h, k, alpha, eps, PPRVIZ_FP32, dppr_d, false, nullptr);
+    if (s == PPRVIZ_E_NOT_CONVERGED) status = s;
+    else if (s != PPRVIZ_OK) return finish(ctx, s);
+    PPRVIZ_TRY(pdist_launch(ctx, dppr_d, k, g->n, pdist_d, false));
+    const float *x0_d = nullptr;
+    if (dev) x0_d = x0_packed + 2 * offsets[v];
+    else {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_IN1, sizeof(float) * 2 * k));
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ctx->ws[WS_IN1].p, x0_packed + 2 * offsets[v], sizeof(float) * 2 * k,
+                                       cudaMemcpyHostToDevice, ctx->stream));
+      x0_d = ctx->ws[WS_IN1].as<float>();
+    }
+    float *xo = dev ? x_packed + 2 * offsets[v] : nullptr;
+    if (!dev) {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_OUT0, sizeof(float) * 2 * k));
+      xo = ctx->ws[WS_OUT0].as<float>();
+    }
+    double st = 0.0;
+    const pprviz_stats before = ctx->stats;
+    s = layout_run(ctx, pdist_d, k, x0_d, iters, PPRVIZ_FP32, false, xo, stress_out ? &st : nullptr);
+    if (s != PPRVIZ_OK) return finish(ctx, s);
+    if (stress_out) stress_out[v] = st;
+    (void)before;
+    if (!dev) {
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(x_packed + 2 * offsets[v], xo, sizeof(float) * 2 * k, cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+      if (pdist_packed)
+        PPRVIZ_CUDA(ctx, cudaMemcpyAsync(pdist_packed + sq_off, pdist_d, sizeof(float) * kk, cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+      PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    sq_off += (int64_t)kk;
+  }
+  (void)total;
+  return finish(ctx, status);
+}
+
+}  // extern "C"

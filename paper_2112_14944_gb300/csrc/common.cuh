@@ -1,0 +1,132 @@
+// Internal declarations shared by the translation units of libpprviz.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pprviz.h"
+
+namespace pprviz {
+
+// A grow-only device buffer owned by a context or a graph.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Workspace slots of a context.
+enum Slot {
+  WS_VIEW = 0, WS_SRC, WS_Y0, WS_Y1, WS_Y2, WS_Y3, WS_RHS, WS_CERT, WS_FLAG,
+  WS_DPPR, WS_PDIST, WS_IN0, WS_IN1, WS_OUT0, WS_OUT1, WS_W1, WS_M, WS_PIV,
+  WS_B, WS_X, WS_E, WS_MISC, WS_COUNT
+};
+
+}  // namespace pprviz
+
+struct pprviz_ctx {
+  // per-class device timing (pprviz_profile / pprviz_kernel_times)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double class_ms[PPRVIZ_NKCLASS] = {0};
+  int64_t class_launches[PPRVIZ_NKCLASS] = {0};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  pprviz::DevBuf ws[pprviz::WS_COUNT];
+  pprviz_stats stats{};
+  int launches = 0;  // kernels launched in the current call
+};
+
+struct pprviz_graph {
+  pprviz_ctx *ctx = nullptr;
+  int64_t n = 0, nnz = 0;
+  bool weighted = false;
+  uint32_t flags = 0;
+  pprviz::DevBuf rp, col, w, deg, invdw_f, invdw_d;
+  double m = 0.0;
+  std::vector<double> h_deg;  // host copy of d(v), for per-group decisions
+};
+
+namespace pprviz {
+
+// ---- status helpers -------------------------------------------------------
+int set_err(pprviz_ctx *ctx, int code, const std::string &msg);
+int cuda_err(pprviz_ctx *ctx, cudaError_t e, const char *what);
+
+#define PPRVIZ_CUDA(ctx, call)                                   \
+  do {                                                           \
+    cudaError_t e__ = (call);                                    \
+    if (e__ != cudaSuccess) return ::pprviz::cuda_err(ctx, e__, #call); \
+  } while (0)
+
+#define PPRVIZ_LAUNCHED(ctx)                                             \
+  do {                                                                   \
+    (ctx)->launches++;                                                   \
+    cudaError_t e__ = cudaGetLastError();                                \
+    if (e__ != cudaSuccess) return ::pprviz::cuda_err(ctx, e__, "kernel launch"); \
+  } while (0)
+
+#define PPRVIZ_TRY(expr)        \
+  do {                          \
+    int s__ = (expr);           \
+    if (s__ != PPRVIZ_OK) return s__; \
+  } while (0)
+
+int ws_ensure(pprviz_ctx *ctx, int slot, size_t bytes);
+
+// Brackets the kernel launches of one scope with CUDA events on the context
+// stream when profiling is on, and counts them per class either way.
+struct ProfScope {
+  pprviz_ctx *c;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(pprviz_ctx *ctx, int k);
+  ~ProfScope();
+};
+#define PPRVIZ_PROF(ctx, cls) ::pprviz::ProfScope prof_scope__(ctx, cls)
+
+// ---- graph (graph.cu) ---------------------------------------------------
+int graph_build(pprviz_ctx *ctx, pprviz_graph *g, uint32_t flags);
+// Map view ids -> check range and duplicates on the device. `view_d` device.
+int view_check(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d, int32_t k);
+
+// ---- propagation (propagate.cu) ----------------------------------------
+// Computes DPPR rows for all k view sources into dppr_d (k*k, double if
+// out64 else float, row-major, ld k) and certificates into cert_h (host, k).
+int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
+               const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps,
+               int precision, void *dppr_d, bool out64, double *cert_h);
+
+// ---- pdist (pdist.cu) ------------------------------------------------------
+int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp,
+                 void *pdist_d, bool f64);
+
+// ---- layout (layout.cu) ----------------------------------------------------
+int layout_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x0_d, int32_t iters,
+               int precision, bool io64, void *x_out_d, double *stress_h);
+int energy_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x_d, double scale,
+               bool f64, double *e_h, void *grad_x_d, void *grad_pdist_d);
+
+}  // namespace pprviz

@@ -1,0 +1,534 @@
+// P1/P2 - multi-source PPR propagation with an FP64 residual certificate.
+//
+// What is computed (Sec. 3.1): for every view source s, the PPR row
+//   pi(s, .) = alpha * sum_t (1 - alpha)^t e_s P^t,
+// i.e. the solution x of x (I - c P) = alpha e_s with c = 1 - alpha, and the
+// DPPR pi_d(s, t) = d(s) pi(s, t) (Definition 1).
+//
+// How (GB300 design, not the paper's sequential push):
+//  * Sources are processed in groups of G columns. The state of a group is a
+//    node-major [n][G] matrix so that one warp gathers a neighbour's 128
+//    (FP32) or 64 (FP64) source values with one 512-byte coalesced load. G is
+//    chosen so that the group's live buffers stay resident in the 126 MB L2;
+//    each sweep then re-reads the CSR and the gathered rows from L2.
+//  * The state is degree-scaled, y_v = x_v / dw(v) (dw = walk degree), so a
+//    pull over the symmetric CSR needs no per-edge weight on unit graphs:
+//    (x P)_j = sum_{i in N(j)} x_i / dw(i) = sum_{i in N(j)} y_i.
+//  * FP64 plain path: power iteration x <- alpha e_s + c x P for the a-priori
+//    sweep count T with d(s) c^(T+1) <= eps / 2.
+//  * FP32 path: Chebyshev semi-iteration. The walk matrix of an undirected
+//    graph is reversible, so the spectrum of I - cP lies in [1 - c, 1 + c]
+//    and the three-term Chebyshev recurrence converges with rate
+//    rho = (1 - sqrt(1 - c^2)) / c (0.557 at alpha = 0.15, vs 0.85 for the
+//    power iteration), needing no inner products.
+//  * The certificate (Eq. (3)): with res = alpha e_s - x (I - cP) computed in
+//    FP64, the exact row is x + res Pi / alpha, so every DPPR entry of the row
+//    is within d(s) ||res||_1 / alpha. FP32 rows are refined: the FP32
+//    correction system delta (I - cP) = res is solved with the same sweeps
+//    and kept as a second FP32 array (x = x_hi + x_lo), until the FP64
+//    certificate is at most eps.
+#include <math.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pprviz {
+
+constexpr int kWarps = 8;         // warps per block in the sweep kernels
+constexpr int kChunk = 128;       // group width granule (sources)
+
+template <typename T>
+struct Vec;  // 16-byte vector of T
+template <>
+struct Vec<float> {
+  static constexpr int N = 4;
+  using V = float4;
+  __device__ static void load(const float *p, float (&v)[4]) {
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ static void store(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec<double> {
+  static constexpr int N = 2;
+  __device__ static void load(const double *p, double (&v)[2]) {
+    double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+  }
+  __device__ static void store(double *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// y[v_q][q] = alpha / dw(v_q) (the first iterate x_1 = alpha e_s, y-scaled);
+// all other entries are zeroed beforehand by a memset.
+template <typename T>
+__global__ void k_init_delta(int32_t gcount, const int32_t *__restrict__ src, int64_t ld,
+                             const T *__restrict__ invdw, T alpha, T *__restrict__ y) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= gcount) return;
+  int32_t s = src[q];
+  if (s >= 0) y[(int64_t)s * ld + q] = alpha * invdw[s];
+}
+
+// y = rhs / dw (the first iterate of the correction system, x_1 = rhs).
+__global__ void k_init_rhs(int64_t n, int64_t ld, const float *__restrict__ rhs,
+                           const float *__restrict__ invdw, float *__restrict__ y) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * ld) return;
+  y[idx] = rhs[idx] * invdw[idx / ld];
+}
+
+__global__ void k_axpy(int64_t count, const float *__restrict__ x, float *__restrict__ y) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < count) y[idx] += x[idx];
+}
+
+// One sweep for the rows of a group.  For each node j and source column q:
+//   acc  = sum_{i in N(j)} w_ij y_cur[i][q]   (+ y_cur[j][q] if j has no edges)
+//   xnew = (b_jq + c * acc) / dw(j)           (y-scaled next iterate)
+//   CHEB: y_out = om1 * y_old + om * xnew     (three-term recurrence, in place over y_old)
+//   else: y_out = xnew                         (power iteration)
+// b_jq = alpha [j == src[q]] unless RHS, then b_jq = rhs[j][q].
+// One warp per (row j, 32*VEC-source chunk); lanes own VEC consecutive sources.
+template <typename T, bool WEIGHTED, bool CHEB, bool RHS>
+__global__ void __launch_bounds__(kWarps * 32)
+k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
+        const int32_t *__restrict__ col, const float *__restrict__ w, const T *__restrict__ invdw,
+        const int32_t *__restrict__ src, const float *__restrict__ rhs, const T *__restrict__ ycur,
+        const T *yold, T *yout, T alpha, T c, T om, T om1) {
+  constexpr int VEC = Vec<T>::N;
+  const int lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (item >= n * nchunks) return;
+  const int64_t chunk = item / n;
+  const int64_t j = item - chunk * n;
+  const int64_t off = chunk * (32 * VEC) + lane * VEC;
+  T acc[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) acc[u] = T(0);
+  const int64_t b = rp[j], e = rp[j + 1];
+  for (int64_t base = b; base < e; base += 32) {
+    const int cnt = (int)min((int64_t)32, e - base);
+    int32_t myc = lane < cnt ? col[base + lane] : 0;
+    float myw = 1.0f;
+    if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
+    int t = 0;
+    for (; t + 4 <= cnt; t += 4) {
+      T v0[VEC], v1[VEC], v2[VEC], v3[VEC];
+      const int32_t i0 = __shfl_sync(0xffffffffu, myc, t);
+      const int32_t i1 = __shfl_sync(0xffffffffu, myc, t + 1);
+      const int32_t i2 = __shfl_sync(0xffffffffu, myc, t + 2);
+      const int32_t i3 = __shfl_sync(0xffffffffu, myc, t + 3);
+      Vec<T>::load(ycur + (int64_t)i0 * ld + off, v0);
+      Vec<T>::load(ycur + (int64_t)i1 * ld + off, v1);
+      Vec<T>::load(ycur + (int64_t)i2 * ld + off, v2);
+      Vec<T>::load(ycur + (int64_t)i3 * ld + off, v3);
+      if (WEIGHTED) {
+        const T w0 = (T)__shfl_sync(0xffffffffu, myw, t);
+        const T w1 = (T)__shfl_sync(0xffffffffu, myw, t + 1);
+        const T w2 = (T)__shfl_sync(0xffffffffu, myw, t + 2);
+        const T w3 = (T)__shfl_sync(0xffffffffu, myw, t + 3);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u] += w0 * v0[u] + w1 * v1[u] + w2 * v2[u] + w3 * v3[u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u] += (v0[u] + v1[u]) + (v2[u] + v3[u]);
+      }
+    }
+    for (; t < cnt; ++t) {
+      T v0[VEC];
+      const int32_t i0 = __shfl_sync(0xffffffffu, myc, t);
+      Vec<T>::load(ycur + (int64_t)i0 * ld + off, v0);
+      const T w0 = WEIGHTED ? (T)__shfl_sync(0xffffffffu, myw, t) : T(1);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[u] += w0 * v0[u];
+    }
+  }
+  const int64_t rowoff = j * ld + off;
+  if (e == b) {  // no edges: the walk stays on j (self-loop of weight 1)
+    T v0[VEC];
+    Vec<T>::load(ycur + rowoff, v0);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) acc[u] += v0[u];
+  }
+  const T invd = invdw[j];
+  T bq[VEC];
+  if (RHS) {
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) bq[u] = (T)rhs[rowoff + u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) bq[u] = (src[off + u] == (int32_t)j) ? alpha : T(0);
+  }
+  T out[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) out[u] = (bq[u] + c * acc[u]) * invd;
+  if (CHEB) {
+    T old[VEC];
+    Vec<T>::load(yold + rowoff, old);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) out[u] = om1 * old[u] + om * out[u];
+  }
+  Vec<T>::store(yout + rowoff, out);
+}
+
+// FP64 residual of the computed rows x = dw * (y_hi + y_lo) against the
+// original system x (I - cP) = alpha e_s:
+//   res_jq = alpha [j == src[q]] - x_jq + c * sum_{i in N(j)} w_ij (y_hi + y_lo)[i][q]
+// written (rounded to FP32) into rhs_out for the refinement, and
+// sum_j |res_jq| added into l1[q] (FP64).
+// Grid: (nchunks, row blocks); each warp walks rows with a stride so its
+// per-source partial sums are reduced once per block.
+template <typename T, bool WEIGHTED>
+__global__ void __launch_bounds__(kWarps * 32)
+k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+           const float *__restrict__ w, const double *__restrict__ invdw,
+           const int32_t *__restrict__ src, const T *__restrict__ yhi, const float *__restrict__ ylo,
+           float *__restrict__ rhs_out, double *__restrict__ l1, double alpha, double c) {
+  constexpr int VEC = 4;  // 128 sources per warp chunk for both state types
+  __shared__ double red[kWarps][32 * VEC];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t chunk = blockIdx.x;
+  const int64_t off = chunk * (32 * VEC) + lane * VEC;
+  int32_t sq[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) sq[u] = src[off + u];
+  double part[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) part[u] = 0.0;
+  const int64_t stride = (int64_t)gridDim.y * kWarps;
+  for (int64_t j = (int64_t)blockIdx.y * kWarps + warp; j < n; j += stride) {
+    double acc[VEC];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
+    const int64_t b = rp[j], e = rp[j + 1];
+    for (int64_t base = b; base < e; base += 32) {
+      const int cnt = (int)min((int64_t)32, e - base);
+      int32_t myc = lane < cnt ? col[base + lane] : 0;
+      float myw = 1.0f;
+      if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
+      for (int t = 0; t < cnt; ++t) {
+        const int32_t i = __shfl_sync(0xffffffffu, myc, t);
+        const double wi = WEIGHTED ? (double)__shfl_sync(0xffffffffu, myw, t) : 1.0;
+        const int64_t p = (int64_t)i * ld + off;
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          double v = (double)yhi[p + u];
+          if (ylo) v += (double)ylo[p + u];
+          acc[u] += wi * v;
+        }
+      }
+    }
+    const int64_t rowoff = j * ld + off;
+    const double dw = 1.0 / invdw[j];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) {
+      double y = (double)yhi[rowoff + u];
+      if (ylo) y += (double)ylo[rowoff + u];
+      if (e == b) acc[u] += y;
+      const double bq = (sq[u] == (int32_t)j) ? alpha : 0.0;
+      const double r = bq - dw * y + c * acc[u];
+      if (rhs_out) rhs_out[rowoff + u] = (float)r;
+      part[u] += fabs(r);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) red[warp][lane * VEC + u] = part[u];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int wv = 0; wv < kWarps; ++wv) s += red[wv][t];
+    atomicAdd(&l1[chunk * (32 * VEC) + t], s);
+  }
+}
+
+// out[(g0 + q) * k + r] = d(view[g0+q]) * dw(view[r]) * (y_hi + y_lo)[view[r]][q]
+// for q < gvalid, r < k: DPPR rows of the group, transposed through shared
+// memory so that both the state reads and the output writes are coalesced.
+template <typename T, typename TO>
+__global__ void k_extract(int32_t k, int32_t g0, int32_t gvalid, int64_t ld,
+                          const int32_t *__restrict__ view, const double *__restrict__ deg,
+                          const double *__restrict__ invdw, const T *__restrict__ yhi,
+                          const float *__restrict__ ylo, TO *__restrict__ out) {
+  __shared__ double tile[32][33];
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr, q = q0 + tx;
+    double v = 0.0;
+    if (r < k && q < gvalid) {
+      const int32_t t = view[r];
+      const int64_t p = (int64_t)t * ld + q;
+      double y = (double)yhi[p];
+      if (ylo) y += (double)ylo[p];
+      v = y / invdw[t];
+    }
+    tile[rr][tx] = v;
+  }
+  __syncthreads();
+  for (int qq = ty; qq < 32; qq += 8) {
+    const int q = q0 + qq, r = r0 + tx;
+    if (q < gvalid && r < k) {
+      const double ds = deg[view[g0 + q]];
+      out[(int64_t)(g0 + q) * k + r] = (TO)(ds * tile[tx][qq]);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+namespace {
+
+struct GroupPlan {
+  int64_t ld;    // group width (multiple of kChunk)
+};
+
+int64_t choose_group(int64_t n, int32_t k, size_t elem) {
+  // keep ~3 live [n][G] buffers within ~64 MB of L2
+  const double budget = 64.0 * 1024 * 1024;
+  int64_t g = (int64_t)(budget / (3.0 * (double)n * (double)elem));
+  g = (g / kChunk) * kChunk;
+  const int64_t kk = ((int64_t)k + kChunk - 1) / kChunk * kChunk;
+  g = std::max<int64_t>(g, kChunk);
+  g = std::min<int64_t>(g, kk);
+  g = std::min<int64_t>(g, 4096);
+  return g;
+}
+
+template <typename T>
+int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, bool rhs,
+                 const int32_t *src, const float *rhsbuf, const T *ycur, const T *yold, T *yout,
+                 double alpha, double om) {
+  constexpr int VEC = Vec<T>::N;
+  const int nchunks = (int)(ld / (32 * VEC));
+  const int64_t items = g->n * nchunks;
+  const unsigned blocks = (unsigned)((items + kWarps - 1) / kWarps);
+  const T *invdw = std::is_same<T, float>::value ? (const T *)g->invdw_f.p : (const T *)g->invdw_d.p;
+  const T a = (T)alpha, c = (T)(1.0 - alpha), o = (T)om, o1 = (T)(1.0 - om);
+  const float *w = g->weighted ? g->w.as<float>() : nullptr;
+  const int64_t *rp = g->rp.as<int64_t>();
+  const int32_t *col = g->col.as<int32_t>();
+  PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
+#define PPRVIZ_SWEEP(W, C, R)                                                                   \
+  k_sweep<T, W, C, R><<<blocks, kWarps * 32, 0, ctx->stream>>>(g->n, ld, nchunks, rp, col, w, invdw, \
+                                                               src, rhsbuf, ycur, yold, yout, a, c, o, o1)
+  if (g->weighted) {
+    if (cheb) { if (rhs) PPRVIZ_SWEEP(true, true, true); else PPRVIZ_SWEEP(true, true, false); }
+    else { if (rhs) PPRVIZ_SWEEP(true, false, true); else PPRVIZ_SWEEP(true, false, false); }
+  } else {
+    if (cheb) { if (rhs) PPRVIZ_SWEEP(false, true, true); else PPRVIZ_SWEEP(false, true, false); }
+    else { if (rhs) PPRVIZ_SWEEP(false, false, true); else PPRVIZ_SWEEP(false, false, false); }
+  }
+#undef PPRVIZ_SWEEP
+  PPRVIZ_LAUNCHED(ctx);
+  return PPRVIZ_OK;
+}
+
+template <typename T>
+int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
+                    const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha) {
+  const int nchunks = (int)(ld / 128);
+  int rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps, std::max(1, 1216 / nchunks));
+  dim3 grid(nchunks, rows_blocks);
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(l1, 0, sizeof(double) * (size_t)ld, ctx->stream));
+  if (g->weighted)
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, true><<<grid, kWarps * 32, 0, ctx->stream>>>(
+        g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), g->w.as<float>(), g->invdw_d.as<double>(),
+        src, yhi, ylo, rhs_out, l1, alpha, 1.0 - alpha); }
+  else
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, false><<<grid, kWarps * 32, 0, ctx->stream>>>(
+        g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), nullptr, g->invdw_d.as<double>(), src,
+        yhi, ylo, rhs_out, l1, alpha, 1.0 - alpha); }
+  PPRVIZ_LAUNCHED(ctx);
+  return PPRVIZ_OK;
+}
+
+// certificates of the group's sources: d(s) * ||res_s||_1 / alpha
+int read_certs(pprviz_ctx *ctx, const pprviz_graph *g, const std::vector<int32_t> &view_h, int32_t g0,
+               int32_t gvalid, const double *l1_d, double alpha, std::vector<double> &cert) {
+  std::vector<double> l1((size_t)gvalid);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(l1.data(), l1_d, sizeof(double) * (size_t)gvalid,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  cert.resize((size_t)gvalid);
+  for (int32_t q = 0; q < gvalid; ++q) cert[q] = g->h_deg[view_h[g0 + q]] * l1[q] / alpha;
+  return PPRVIZ_OK;
+}
+
+double chebyshev_rate(double c) { return (1.0 - sqrt(1.0 - c * c)) / c; }
+
+// Runs `sweeps` Chebyshev steps of x (I - cP) = b from x_0 = 0, x_1 = b.
+// On entry ya, yb are the two state buffers; returns the buffer holding the
+// last iterate.  b is the source delta (rhs == nullptr) or the dense rhs.
+int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
+                    int32_t gcount, const float *rhs, float *ya, float *yb, int sweeps,
+                    double alpha, float **result) {
+  const size_t bytes = sizeof(float) * (size_t)(g->n * ld);
+  const double c = 1.0 - alpha;
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(ya, 0, bytes, ctx->stream));
+  if (rhs) {
+    const int64_t cnt = g->n * ld;
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_rhs<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(g->n, ld, rhs, g->invdw_f.as<float>(), yb); }
+    PPRVIZ_LAUNCHED(ctx);
+  } else {
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(yb, 0, bytes, ctx->stream));
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_delta<float><<<(gcount + 255) / 256, 256, 0, ctx->stream>>>(gcount, src, ld, g->invdw_f.as<float>(),
+                                                                      (float)alpha, yb); }
+    PPRVIZ_LAUNCHED(ctx);
+  }
+  // theta = 1, delta = c: omega_2 = 1 / (1 - c^2 / 2), omega_{k+1} = 1 / (1 - c^2 omega_k / 4)
+  double om = 1.0;
+  float *cur = yb, *old = ya;
+  for (int s = 1; s < sweeps; ++s) {
+    om = (s == 1) ? 1.0 / (1.0 - c * c / 2.0) : 1.0 / (1.0 - c * c * om / 4.0);
+    PPRVIZ_TRY(launch_sweep<float>(ctx, g, ld, true, rhs != nullptr, src, rhs, cur, old, old, alpha, om));
+    std::swap(cur, old);
+  }
+  *result = cur;
+  return PPRVIZ_OK;
+}
+
+}  // namespace
+
+int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
+               const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps,
+               int precision, void *dppr_d, bool out64, double *cert_h) {
+  const bool fp64 = precision == PPRVIZ_FP64;
+  const size_t elem = fp64 ? sizeof(double) : sizeof(float);
+  const int64_t ld = choose_group(g->n, k, elem);
+  const size_t sbytes = elem * (size_t)(g->n * ld);
+  const double c = 1.0 - alpha;
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y0, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y1, sbytes));
+  if (!fp64) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_Y2, sbytes));
+    PPRVIZ_TRY(ws_ensure(ctx, WS_Y3, sbytes));
+    PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sbytes));
+  }
+  PPRVIZ_TRY(ws_ensure(ctx, WS_SRC, sizeof(int32_t) * (size_t)ld));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, sizeof(double) * (size_t)ld));
+  int32_t *src = ctx->ws[WS_SRC].as<int32_t>();
+  double *l1 = ctx->ws[WS_CERT].as<double>();
+  pprviz_stats &st = ctx->stats;
+  st.source_group = (int32_t)ld;
+  std::vector<int32_t> srch((size_t)ld);
+  std::vector<double> cert;
+  bool not_converged = false;
+  const double rho = chebyshev_rate(c);
+
+  for (int32_t g0 = 0; g0 < k; g0 += (int32_t)ld) {
+    const int32_t gvalid = (int32_t)std::min<int64_t>(ld, (int64_t)k - g0);
+    for (int64_t q = 0; q < ld; ++q) srch[q] = q < gvalid ? view_h[g0 + q] : -1;
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(src, srch.data(), sizeof(int32_t) * (size_t)ld,
+                                     cudaMemcpyHostToDevice, ctx->stream));
+    double dmax = 0.0;
+    for (int32_t q = 0; q < gvalid; ++q) dmax = std::max(dmax, g->h_deg[view_h[g0 + q]]);
+    st.groups++;
+    const void *yhi = nullptr;
+    const float *ylo = nullptr;
+    if (fp64) {
+      // power iteration for T sweeps: d(s) c^(T+1) <= eps / 2 for every source of the group
+      int T = 0;
+      if (dmax > 0.0) T = std::max(0, (int)ceil(log(0.5 * eps / dmax) / log(c)) - 1);
+      double *ya = ctx->ws[WS_Y0].as<double>(), *yb = ctx->ws[WS_Y1].as<double>();
+      PPRVIZ_CUDA(ctx, cudaMemsetAsync(ya, 0, sbytes, ctx->stream));
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_delta<double><<<(unsigned)((ld + 255) / 256), 256, 0, ctx->stream>>>(
+          (int32_t)ld, src, ld, g->invdw_d.as<double>(), alpha, ya); }
+      PPRVIZ_LAUNCHED(ctx);
+      double *cur = ya, *nxt = yb;
+      for (int s = 0; s < T; ++s) {
+        PPRVIZ_TRY(launch_sweep<double>(ctx, g, ld, false, false, src, nullptr, cur, nullptr, nxt, alpha, 1.0));
+        std::swap(cur, nxt);
+      }
+      st.sweeps_main += T;
+      st.bytes_sweep += 16.0 * (double)g->n * gvalid * T;
+      PPRVIZ_TRY(launch_residual<double>(ctx, g, ld, src, cur, nullptr, nullptr, l1, alpha));
+      st.residual_passes++;
+      PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
+      yhi = cur;
+    } else {
+      float *bufs[4] = {ctx->ws[WS_Y0].as<float>(), ctx->ws[WS_Y1].as<float>(), ctx->ws[WS_Y2].as<float>(),
+                        ctx->ws[WS_Y3].as<float>()};
+      float *rhs = ctx->ws[WS_RHS].as<float>();
+      // main solve: until FP32 rounding dominates (Chebyshev error ~ 2 rho^K <= 1e-7)
+      const int K1 = std::max(2, (int)ceil(log(0.5e-7) / log(rho)));
+      float *hi = nullptr;
+      PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, &hi));
+      st.sweeps_main += K1;
+      st.bytes_sweep += 12.0 * (double)g->n * gvalid * (K1 - 1);
+      // free buffers for the correction solves; the first correction becomes x_lo
+      float *fa = hi == bufs[0] ? bufs[1] : bufs[0], *fb = bufs[2], *fc = bufs[3];
+      float *lo = nullptr;
+      PPRVIZ_TRY(launch_residual<float>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha));
+      st.residual_passes++;
+      PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
+      for (int pass = 0; pass < 4; ++pass) {
+        double cmax = 0.0;
+        for (double v : cert) cmax = std::max(cmax, v);
+        if (cmax <= eps) break;
+        // sweeps for the correction: its Chebyshev error must fall by eps / (4 cmax)
+        int K2 = (int)ceil(log(0.25 * eps / cmax) / log(rho)) + 2;
+        K2 = std::min(std::max(K2, 4), 80);
+        float *delta = nullptr;
+        PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, &delta));
+        st.sweeps_refine += K2;
+        st.bytes_sweep += 16.0 * (double)g->n * gvalid * (K2 - 1);
+        st.refine_passes++;
+        if (!lo) {
+          lo = delta;
+          fa = (delta == fa) ? fb : fa;
+          fb = fc;
+        } else {
+          const int64_t cnt = g->n * ld;
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_axpy<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, delta, lo); }
+          PPRVIZ_LAUNCHED(ctx);
+        }
+        PPRVIZ_TRY(launch_residual<float>(ctx, g, ld, src, hi, lo, rhs, l1, alpha));
+        st.residual_passes++;
+        PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
+      }
+      yhi = hi;
+      ylo = lo;
+    }
+    for (int32_t q = 0; q < gvalid; ++q) {
+      st.max_cert = std::max(st.max_cert, cert[q]);
+      if (cert[q] > eps) not_converged = true;
+      if (cert_h) cert_h[g0 + q] = cert[q];
+    }
+    if (dppr_d) {
+      dim3 grid((unsigned)((gvalid + 31) / 32), (unsigned)((k + 31) / 32));
+      dim3 block(32, 8);
+      if (fp64) {
+        if (out64)
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<double, double><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
+              g->invdw_d.as<double>(), (const double *)yhi, nullptr, (double *)dppr_d); }
+        else
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<double, float><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
+              g->invdw_d.as<double>(), (const double *)yhi, nullptr, (float *)dppr_d); }
+      } else {
+        if (out64)
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<float, double><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
+              g->invdw_d.as<double>(), (const float *)yhi, ylo, (double *)dppr_d); }
+        else
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<float, float><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
+              g->invdw_d.as<double>(), (const float *)yhi, ylo, (float *)dppr_d); }
+      }
+      PPRVIZ_LAUNCHED(ctx);
+    }
+  }
+  if (not_converged)
+    return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "certificate above eps after the refinement cap");
+  return PPRVIZ_OK;
+}
+
+}  // namespace pprviz

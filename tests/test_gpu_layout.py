@@ -1,0 +1,182 @@
+"""GPU parity of the layout pass, Guttman solve, energy/gradients and the
+batched-views path (P4-P7) against the FP64 oracle, through the C ABI.
+
+Tolerances:
+  FP64 layout: the whole trajectory, coordinates within 1e-4 * max(1, |x|)
+               after the fixed iteration count from the same X0.
+  FP32 layout: one update from the same X_t within 1e-4 * max(1, |X|_max)
+               (a whole FP32 trajectory is not reproducible to 1e-4: the
+               stress-majorization map amplifies a 6e-8 perturbation of its
+               matrices to ~2e-4 within 300 updates even in FP64 arithmetic),
+               plus trajectory properties: non-increasing stress, centred
+               output, final stress within 1e-3 of the oracle's.
+  Energy: relative 1e-12 (FP64), 1e-5 (FP32); gradients likewise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+ALPHA = 0.15
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2112_14944_gb300 as P
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def _pdist_for(ctx, n, mean_deg, seed, out64):
+    import paper_2112_14944_gb300 as P
+    g = synth.chung_lu(n, mean_deg, 2.5, seed=seed)
+    G = ctx.upload_graph(g)
+    _, Delta, _, _ = ctx.dppr(G, np.arange(n, dtype=np.int32), ALPHA, 1e-6, P.FP64 if out64 else P.FP32,
+                              out64=out64)
+    return Delta
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a, np.float64) - b) / np.maximum(1.0, np.abs(b))
+
+
+def test_layout_fp64_config_small_full_trajectory(ctx):
+    """n = 1,000 Chung-Lu (mean degree 10), 300 updates from U[-1,1]^2, FP64."""
+    import paper_2112_14944_gb300 as P
+    Delta = _pdist_for(ctx, 1000, 10, 0, out64=True)
+    x0 = synth.uniform_x0(1000, seed=0).astype(np.float64)
+    X, stress = ctx.layout(Delta, x0, 300, P.FP64)
+    Xr, hist = O.smacof(x0, Delta, 300)
+    assert _rel(X, Xr).max() <= 1e-4
+    assert abs(stress - hist[-1]) <= 1e-9 * hist[-1]
+
+
+def test_layout_fp32_one_step_matches_oracle(ctx):
+    import paper_2112_14944_gb300 as P
+    Delta32 = _pdist_for(ctx, 1500, 10, 3, out64=False)
+    D64 = Delta32.astype(np.float64)
+    Xt, _ = O.smacof(synth.uniform_x0(1500, seed=1), D64, 15)
+    X1, _ = ctx.layout(Delta32, Xt.astype(np.float32), 1, P.FP32)
+    ref = O.smacof_step(Xt.astype(np.float32).astype(np.float64), D64)
+    err = np.abs(X1 - ref).max() / max(1.0, np.abs(ref).max())
+    assert err <= 1e-4, err
+
+
+def test_layout_fp32_trajectory_properties(ctx):
+    import paper_2112_14944_gb300 as P
+    n = 800
+    Delta32 = _pdist_for(ctx, n, 10, 4, out64=False)
+    x0 = synth.uniform_x0(n, seed=4)
+    prev = math.inf
+    for it in (0, 1, 5, 20, 60, 150):
+        X, s = ctx.layout(Delta32, x0, it, P.FP32)
+        assert np.abs(X.astype(np.float64).mean(axis=0)).max() <= 1e-5 * max(1.0, np.abs(X).max())
+        assert s <= prev * (1 + 1e-6)
+        prev = s
+    _, hist = O.smacof(x0.astype(np.float64), Delta32.astype(np.float64), 150)
+    assert abs(prev - hist[-1]) <= 1e-3 * hist[-1]
+
+
+def test_layout_zero_iterations_only_centres(ctx):
+    import paper_2112_14944_gb300 as P
+    D = O.pdist_from_z(np.full((5, 5), 0.05), 5)
+    np.fill_diagonal(D, 0)
+    x0 = np.array([[1, 2], [3, 4], [0, 0], [5, -1], [2, 2]], dtype=np.float64)
+    X, s = ctx.layout(D, x0, 0, P.FP64)
+    assert np.allclose(X, x0 - x0.mean(axis=0), atol=1e-15)
+    assert abs(s - O.stress(x0, D)) <= 1e-12 * s
+
+
+def test_layout_two_points_one_step(ctx):
+    import paper_2112_14944_gb300 as P
+    D = np.array([[0.0, 3.7], [3.7, 0.0]])
+    for prec, tol in ((P.FP64, 1e-13), (P.FP32, 1e-5)):
+        dt = np.float64 if prec == P.FP64 else np.float32
+        X, s = ctx.layout(D.astype(dt), np.array([[0.2, -0.4], [0.9, 0.1]], dt), 1, prec)
+        assert abs(np.linalg.norm(X[0].astype(np.float64) - X[1]) - 3.7) <= tol * 3.7
+
+
+def test_layout_rejects_bad_pdist(ctx):
+    import paper_2112_14944_gb300 as P
+    from paper_2112_14944_gb300 import _binding as B
+    D = np.full((4, 4), 3.0, np.float32)
+    D[1, 2] = -1.0
+    with pytest.raises(P.PPRVizError) as ei:
+        ctx.layout(D, np.zeros((4, 2), np.float32), 3, P.FP32)
+    assert ei.value.status == B.PPRVIZ_E_INVALID_ARG
+    D[1, 2] = np.inf
+    with pytest.raises(P.PPRVizError):
+        ctx.layout(D, np.zeros((4, 2), np.float32), 3, P.FP32)
+
+
+@pytest.mark.parametrize("dt,tol", [(np.float64, 1e-11), (np.float32, 2e-5)])
+def test_energy_and_gradients_match_oracle(ctx, dt, tol):
+    k = 300
+    Delta = _pdist_for(ctx, k, 8, 7, out64=True)
+    X = (synth.uniform_x0(k, seed=3).astype(np.float64) * 4.0)
+    X[7] = X[8]  # a coincident pair: its gradient term is 0
+    e, gx, gd = ctx.energy(Delta.astype(dt), X.astype(dt), grad_scale=0.5, grad_x=True, grad_pdist=True)
+    Xd, Dd = X.astype(dt).astype(np.float64), Delta.astype(dt).astype(np.float64)
+    e_ref = O.stress(Xd, Dd)
+    assert abs(e - e_ref) <= tol * e_ref
+    g_ref = 0.5 * O.stress_grad(Xd, Dd)
+    assert np.abs(gx - g_ref).max() <= tol * max(1.0, np.abs(g_ref).max()) * 10
+    gd_ref = 0.5 * O.stress_grad_pdist(Xd, Dd)
+    assert np.abs(gd - gd_ref).max() <= tol * max(1.0, np.abs(gd_ref).max()) * 10
+
+
+def test_autograd_function_gradcheck():
+    torch = pytest.importorskip("torch")
+    import paper_2112_14944_gb300 as P
+    c = P.Context(0, torch_stream=True)
+    k = 10
+    D = torch.tensor(_pdist_for(c, 30, 4, 8, out64=True)[:k, :k], device="cuda")
+    X = torch.tensor(synth.uniform_x0(k, seed=5).astype(np.float64) * 3, device="cuda")
+    Xr = X.clone().requires_grad_(True)
+    Dr = D.clone().requires_grad_(True)
+    f = lambda x, d: P.StressEnergy.apply(x, d, c)  # noqa: E731
+    assert torch.autograd.gradcheck(f, (Xr, Dr), eps=1e-6, atol=1e-7, rtol=1e-6)
+    c.close()
+
+
+def test_gradient_finite_differences_subview_512(ctx):
+    """Energy backward against central finite differences of the energy on an
+    n=512 sub-view (the differentiable-layout gradient check), FP64."""
+    k = 512
+    D = _pdist_for(ctx, 2048, 10, 5, out64=True)[:k, :k].copy()
+    X = synth.uniform_x0(k, seed=6).astype(np.float64) * 5
+    _, gx, _ = ctx.energy(D, X, grad_x=True)
+    g_ref = O.stress_grad(X, D)
+    assert np.abs(gx - g_ref).max() <= 1e-10 * np.abs(g_ref).max()
+    h = 1e-5
+    for (i, a) in [(0, 0), (17, 1), (255, 0), (511, 1)]:
+        Xp = X.copy(); Xp[i, a] += h
+        Xm = X.copy(); Xm[i, a] -= h
+        ep, _, _ = ctx.energy(D, Xp)
+        em, _, _ = ctx.energy(D, Xm)
+        fd = (ep - em) / (2 * h)
+        assert abs(fd - gx[i, a]) <= 1e-5 * max(1.0, abs(gx[i, a]))
+
+
+def test_views_batch_matches_single_views(ctx):
+    import paper_2112_14944_gb300 as P
+    graphs = synth.sbm_views(5, seed=3, n_min=50, n_max=300)
+    G = [ctx.upload_graph(g) for g in graphs]
+    x0 = np.concatenate([synth.uniform_x0(g.n, seed=10 + i) for i, g in enumerate(graphs)])
+    xb, pdb, stress, off = ctx.views_batch(G, x0, ALPHA, 1e-6, 40, want_pdist=True)
+    sq = 0
+    for v, g in enumerate(graphs):
+        n = g.n
+        Dref = O.dppr_rows(O.ppr_direct(O.transition_matrix(n, g.row_ptr, g.col), ALPHA),
+                           O.degrees(n, g.row_ptr, g.col), np.arange(n))
+        Pd = pdb[sq:sq + n * n].reshape(n, n)
+        assert np.abs(Pd - O.pdist_from_dppr(Dref, n)).max() <= 1e-5
+        X1, s1 = ctx.layout(Pd.copy(), x0[off[v]:off[v + 1]].copy(), 40, P.FP32)
+        assert np.array_equal(X1, xb[off[v]:off[v + 1]])
+        assert s1 == stress[v]
+        sq += n * n
