@@ -49,7 +49,37 @@ def parse():
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", action="store_true",
+                    help="one untimed pass of the hot path (for profiler command lines)")
     return ap.parse_args()
+
+
+def run_case(args):
+    """One pass of the hot path on the workload, untimed: ingest, FP32 DPPR +
+    PDist with certificate, `--iters` layout updates, energy with gradient."""
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    import synth
+    n = args.n
+    g = synth.chung_lu(n, args.deg, 2.5, seed=0)
+    ctx = P.Context(0, torch_stream=True)
+    dev = torch.device("cuda", 0)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    view = torch.arange(n, dtype=torch.int32, device=dev)
+    D = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Dl = torch.empty_like(D)
+    x0 = torch.from_numpy(synth.uniform_x0(n, seed=0)).to(dev)
+    xo = torch.empty_like(x0)
+    G = ctx.upload(n, rp, col)
+    _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
+    st = ctx.stats()
+    _, s = ctx.layout(Dl, x0, args.iters, P.FP32, x_out=xo)
+    e, _, _ = ctx.energy(Dl, xo, grad_x=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": WORKLOAD, "n": n, "iters": args.iters, "status": status,
+                      "max_cert": float(cert.max()), "stress": s, "energy": e, "dppr_stats": st}))
 
 
 def peaks():
@@ -354,6 +384,9 @@ def run_ours(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

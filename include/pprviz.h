@@ -153,7 +153,9 @@ int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out
  *            d(s) x_t (Eq. (3) with 0 <= pi <= 1). The FP64 path runs power
  *            iteration for the a-priori sweep count; the FP32 path runs
  *            Chebyshev sweeps and FP32 refinement passes until every source
- *            has cert(s) <= eps, or returns E_NOT_CONVERGED after 4 passes.
+ *            has cert(s) <= eps, or returns E_NOT_CONVERGED after 6 passes.
+ *            Through Eq. (1) the certificates bound the PDist error too:
+ *            |dDelta_ij| <= (c_i + c_j) / max(z_ij - c_i - c_j, e / n_clamp^2).
  * precision: PPRVIZ_FP64 or PPRVIZ_FP32.
  * dppr_out:  k*k DPPR, row q = pi_d(view[q], view[.]); may be NULL.
  * pdist_out: k*k PDist with Delta[q][r] from pi_d(q,r) + pi_d(r,q), the upper

@@ -123,6 +123,13 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
 int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp,
                  void *pdist_d, bool f64);
 
+// ---- factor (factor.cu) ----------------------------------------------------
+// In-place inverse of the SPD kp x kp matrix A (kp % 128 == 0); on return A
+// holds A^-1 on its upper 64-block triangle and on the 128 x 128 diagonal tiles.
+// `work` holds 2 * 64 * kp + 64 * 64 elements.
+int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work);
+int spd_inverse_f64(pprviz_ctx *ctx, int32_t kp, double *A, double *work);
+
 // ---- layout (layout.cu) ----------------------------------------------------
 int layout_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x0_d, int32_t iters,
                int precision, bool io64, void *x_out_d, double *stress_h);

@@ -10,16 +10,15 @@
 //  * L^w does not depend on X, so it is inverted once per view. L^w is a
 //    Laplacian (singular on the ones vector); A = L^w + J/k is SPD with
 //    A 1 = 1, and for b = L^Y Y (zero column sums) A^-1 b is exactly the
-//    centred Moore-Penrose solution. A is inverted in place by a blocked
-//    Gauss-Jordan sweep (64-wide pivot blocks, no pivoting needed for SPD):
-//    a one-block pivot inverse, panel products, and a register-tiled rank-64
-//    trailing update, which carries the O(k^3) work.
-//  * Each iteration is two streaming passes over k x k matrices: the L^Y pass
-//    b_i = sum_j (x_i - x_j) / (Delta_ij d_ij) over the stored 1/Delta, and
-//    X = M b over M = A^-1. Both read their matrix once, coalesced along
-//    rows, with the 2-D coordinates staged in shared memory; the column range
-//    is split over several blocks whose partial sums are added (in a fixed
-//    order) by the consumer, so no atomics and bitwise-reproducible results.
+//    centred Moore-Penrose solution. A is inverted once in place by the
+//    symmetric block sweep of factor.cu.
+//  * The layout works on the symmetric part Delta_s = (Delta + Delta^T)/2 (equal
+//    to Delta for the symmetric PDist of Eq. (1)), so 1/Delta_s and M = A^-1 are
+//    symmetric and each update reads only their upper-triangle 128 x 128 tiles:
+//    a tile (I, J), I < J, adds its row sums to rows I and its column sums to
+//    rows J. Two streaming passes per update (b = L^Y X over 1/Delta_s, then
+//    X = M b) read half of each k x k matrix once. Partial sums are written
+//    per (tile, row) and added in a fixed order: no atomics, reproducible.
 //  * The energy and its gradients recompute every pair from X and Delta; no
 //    k x k intermediate is stored.
 #include <math.h>
@@ -32,9 +31,11 @@
 namespace pprviz {
 
 constexpr int NB = 64;        // Gauss-Jordan pivot block
-constexpr int LWARPS = 8;     // warps per block in the pair passes
-constexpr int RPW = 4;        // rows per warp in the pair passes
-constexpr int XCH = 1024;     // coordinates staged per shared-memory chunk
+constexpr int ST = 128;       // symmetric pass tile edge
+constexpr int SRPI = 8;       // rows per warp per sub-iteration in the symmetric pass
+constexpr int LWARPS = 8;     // warps per block in the energy pass
+constexpr int RPW = 4;        // rows per warp in the energy pass
+constexpr int XCH = 1024;     // coordinates staged per shared-memory chunk (energy)
 
 template <typename T> struct T2;
 template <> struct T2<float> { using type = float2; };
@@ -47,319 +48,217 @@ __device__ __forceinline__ float rsqrt_pos<float>(float d2) { return d2 > 0.0f ?
 template <>
 __device__ __forceinline__ double rsqrt_pos<double>(double d2) { return d2 > 0.0 ? 1.0 / sqrt(d2) : 0.0; }
 
+// four consecutive values, 16-byte aligned
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // ---------------------------------------------------------------------------
-// W1 = 1/Delta (zero diagonal) and A = L^w + J/k (identity on padded rows).
-// One warp per row; the diagonal of L^w is the FP64 sum of the row's 1/Delta^2.
+// Build from Delta_s = (Delta + Delta^T) / 2, in 32 x 32 tiles with the mirrored
+// tile staged in shared memory:
+//   W1[i][j] = 1/Delta_s (0 on the diagonal and in the padding),
+//   A[i][j]  = 1/k - 1/Delta_s^2 off the diagonal, identity on padded rows,
+//   rowpart[J][i] = sum over the tile's 32 columns of 1/Delta_s^2 (FP64);
+// k_build_diag then sets A[i][i] = sum_J rowpart[J][i] + 1/k in a fixed order.
 // ---------------------------------------------------------------------------
 template <typename TI, typename T>
-__global__ void k_build(int32_t k, int32_t kp, const TI *__restrict__ D, T *__restrict__ W1,
-                        T *__restrict__ A, int *__restrict__ flag) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= kp) return;
-  T *Ai = A + i * kp;
-  if (i >= k) {
-    for (int64_t j = lane; j < kp; j += 32) Ai[j] = (j == i) ? T(1) : T(0);
-    return;
+__global__ void k_build_sym(int32_t k, int32_t kp, const TI *__restrict__ D, T *__restrict__ W1,
+                            T *__restrict__ A, double *__restrict__ rowpart, int *__restrict__ flag) {
+  __shared__ TI tr[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj, i = i0 + tx;
+    tr[jj][tx] = (j < k && i < k) ? D[(int64_t)j * k + i] : TI(0);
   }
-  T *Wi = W1 + i * kp;
-  const TI *Di = D + i * (int64_t)k;
+  __syncthreads();
   const T invk = (T)(1.0 / (double)k);
-  double rowsum = 0.0;
   int bad = 0;
-  for (int64_t j = lane; j < kp; j += 32) {
-    if (j < k && j != i) {
-      const T d = (T)Di[j];
-      if (!(d > T(0)) || !isfinite((double)d)) bad = 1;
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + tx;
+    double wsq_d = 0.0;
+    if (i < k && j < k && i != j) {
+      const TI a = D[(int64_t)i * k + j], b = tr[tx][ii];
+      // every input entry must itself be a valid distance (this element checks a;
+      // b is checked by the element (j, i))
+      if (!(a > TI(0)) || !isfinite((double)a)) bad = 1;
+      const T d = (T)((a + b) * TI(0.5));
       const T w1 = T(1) / d;
       const T wsq = w1 * w1;
-      Wi[j] = w1;
-      Ai[j] = invk - wsq;
-      rowsum += (double)wsq;
+      W1[(int64_t)i * kp + j] = w1;
+      A[(int64_t)i * kp + j] = invk - wsq;
+      wsq_d = (double)wsq;
     } else {
-      Wi[j] = T(0);
-      if (j != i) Ai[j] = T(0);
+      W1[(int64_t)i * kp + j] = T(0);
+      if (i != j || i >= k) A[(int64_t)i * kp + j] = (i == j) ? T(1) : T(0);
     }
+    for (int o = 16; o > 0; o >>= 1) wsq_d += __shfl_xor_sync(0xffffffffu, wsq_d, o);
+    if (tx == 0) rowpart[(int64_t)blockIdx.x * kp + i] = wsq_d;
   }
-  for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
-  if (lane == 0) Ai[i] = (T)(rowsum + 1.0 / (double)k);
   if (bad) atomicOr(flag, 1);
 }
 
+template <typename T>
+__global__ void k_build_diag(int32_t k, int32_t kp, const double *__restrict__ rowpart, T *__restrict__ A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < kp / 32; ++b) s += rowpart[(int64_t)b * kp + i];
+  A[(int64_t)i * kp + i] = (T)(s + 1.0 / (double)k);
+}
+
 // ---------------------------------------------------------------------------
-// Blocked Gauss-Jordan inversion of the SPD matrix A (kp x kp, kp % NB == 0).
-// Sweeping pivot block K with P = A_KK^-1 maps
-//   A_KK -> P,  A_KJ -> P A_KJ,  A_IK -> -A_IK P,  A_IJ -> A_IJ - A_IK P A_KJ;
-// after sweeping every block the matrix holds A^-1.
+// Symmetric pair pass over the upper-triangle tiles of a symmetric kp x kp
+// matrix Mat (zero beyond k). Block (J, I), I <= J, 8 warps: warp w owns tile
+// rows 16w..16w+15 (two sub-iterations of SRPI rows), lane l the four columns
+// 4l..4l+3. With v = the staged vector (x for MODE 0, b for MODE 1):
+//   MODE 0 (L^Y): t_ij = Mat_ij (v_i - v_j) / |v_i - v_j|; row i gets +t_ij,
+//                 column j gets -t_ij (since t_ji = -t_ij)
+//   MODE 1 (apply M): row i gets Mat_ij v_j, column j gets Mat_ij v_i
+// Row sums go to Part[J][i], column sums (off-diagonal tiles only) to Part[I][j].
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_gj_diag(int32_t kp, int32_t K0, T *__restrict__ A, T *__restrict__ P) {
-  __shared__ T a[NB][NB + 1];
-  __shared__ T rowp[NB], colp[NB];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    a[r][c] = A[(int64_t)(K0 + r) * kp + K0 + c];
-  }
-  for (int p = 0; p < NB; ++p) {
-    __syncthreads();
-    if (threadIdx.x < NB) {
-      rowp[threadIdx.x] = a[p][threadIdx.x];
-      colp[threadIdx.x] = a[threadIdx.x][p];
-    }
-    __syncthreads();
-    const T piv = T(1) / rowp[p];
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      const int r = e / NB, c = e % NB;
-      T v;
-      if (r == p && c == p) v = piv;
-      else if (r == p) v = rowp[c] * piv;
-      else if (c == p) v = -colp[r] * piv;
-      else v = a[r][c] - colp[r] * (rowp[c] * piv);
-      a[r][c] = v;
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    A[(int64_t)(K0 + r) * kp + K0 + c] = a[r][c];
-    P[e] = a[r][c];
-  }
-}
-
-// Vt[t][i] = A[i][K0 + t]: the old column panel, transposed (32x32 tiles).
-template <typename T>
-__global__ void k_gj_vt(int32_t kp, int32_t K0, const T *__restrict__ A, T *__restrict__ Vt) {
-  __shared__ T tile[32][33];
-  const int i0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += 8) tile[r][threadIdx.x] = A[(int64_t)(i0 + r) * kp + K0 + t0 + threadIdx.x];
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) Vt[(int64_t)(t0 + r) * kp + i0 + threadIdx.x] = tile[threadIdx.x][r];
-}
-
-// Row panel: A[K0 + r][J0 + c] <- sum_t P[r][t] A[K0 + t][J0 + c] for every J block != K.
-template <typename T>
-__global__ void k_gj_rowpanel(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ P) {
-  const int J0 = blockIdx.x * NB;
-  if (J0 == K0) return;
-  extern __shared__ unsigned char smem_raw[];
-  T *sP = reinterpret_cast<T *>(smem_raw);  // [NB][NB]
-  T *sB = sP + NB * NB;                     // [NB][NB]
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    sP[e] = P[e];
-    sB[e] = A[(int64_t)(K0 + r) * kp + J0 + c];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    T s = T(0);
-#pragma unroll 8
-    for (int t = 0; t < NB; ++t) s += sP[r * NB + t] * sB[t * NB + c];
-    A[(int64_t)(K0 + r) * kp + J0 + c] = s;
-  }
-}
-
-// Column panel: A[I0 + r][K0 + c] <- -sum_t Vt[t][I0 + r] P[t][c] for every I block != K.
-template <typename T>
-__global__ void k_gj_colpanel(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ Vt,
-                              const T *__restrict__ P) {
-  const int I0 = blockIdx.x * NB;
-  if (I0 == K0) return;
-  extern __shared__ unsigned char smem_raw[];
-  T *sP = reinterpret_cast<T *>(smem_raw);  // [NB][NB]
-  T *sV = sP + NB * NB;                     // [NB][NB]: sV[t][r] = Vt[t][I0 + r]
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int t = e / NB, r = e % NB;
-    sP[e] = P[e];
-    sV[e] = Vt[(int64_t)t * kp + I0 + r];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    T s = T(0);
-#pragma unroll 8
-    for (int t = 0; t < NB; ++t) s += sV[t * NB + r] * sP[t * NB + c];
-    A[(int64_t)(I0 + r) * kp + K0 + c] = -s;
-  }
-}
-
-// Trailing update A[i][j] -= sum_t Vt[t][i] A[K0 + t][j] for i, j outside the
-// pivot block. TM x TM tile per block of 256 threads, R x R outputs per thread
-// split into two SUB x SUB quadrants so that shared-memory reads are vectors.
-template <typename T, int TM>
-__global__ void __launch_bounds__(256)
-k_gj_trailing(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ Vt) {
-  constexpr int R = TM / 16, SUB = R / 2, HALF = TM / 2;
-  extern __shared__ unsigned char smem_raw[];
-  T *sA = reinterpret_cast<T *>(smem_raw);  // [NB][TM]  sA[t][i] = Vt[t][I0 + i]
-  T *sB = sA + NB * TM;                     // [NB][TM]  sB[t][j] = A[K0 + t][J0 + j]
-  const int I0 = blockIdx.y * TM, J0 = blockIdx.x * TM;
-  // a tile lying entirely inside the pivot block row/column has nothing to do
-  if ((I0 >= K0 && I0 + TM <= K0 + NB) || (J0 >= K0 && J0 + TM <= K0 + NB)) return;
-  for (int e = threadIdx.x; e < NB * TM; e += 256) {
-    const int t = e / TM, x = e % TM;
-    sA[e] = (I0 + x < kp) ? Vt[(int64_t)t * kp + I0 + x] : T(0);
-    sB[e] = (J0 + x < kp) ? A[(int64_t)(K0 + t) * kp + J0 + x] : T(0);
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[R][R];
+// Sum over the 32 lanes of NV values per lane; returns, in every lane, the
+// total of value index lane / (32 / NV). Recursive halving: 31 shuffles for
+// NV = 32, 15 + 1 for NV = 16.
+template <int NV, typename T>
+__device__ __forceinline__ T lanes_transpose_sum(T (&v)[NV], int lane) {
+  constexpr int LOG = NV == 32 ? 5 : NV == 16 ? 4 : NV == 8 ? 3 : NV == 4 ? 2 : NV == 2 ? 1 : 0;
 #pragma unroll
-  for (int r = 0; r < R; ++r)
+  for (int s = 0; s < LOG; ++s) {
+    const int off = 16 >> s;
+    const int half = (NV >> s) / 2;
+    const bool up = (lane & off) != 0;
 #pragma unroll
-    for (int c = 0; c < R; ++c) acc[r][c] = T(0);
-#pragma unroll 4
-  for (int t = 0; t < NB; ++t) {
-    T a[R], b[R];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int s = 0; s < SUB; ++s) {
-        a[h * SUB + s] = sA[t * TM + h * HALF + ty * SUB + s];
-        b[h * SUB + s] = sB[t * TM + h * HALF + tx * SUB + s];
-      }
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int c = 0; c < R; ++c) acc[r][c] += a[r] * b[c];
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int i = I0 + (r / SUB) * HALF + ty * SUB + (r % SUB);
-    if (i >= kp || (i >= K0 && i < K0 + NB)) continue;
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const int j = J0 + (c / SUB) * HALF + tx * SUB + (c % SUB);
-      if (j >= kp || (j >= K0 && j < K0 + NB)) continue;
-      A[(int64_t)i * kp + j] -= acc[r][c];
+    for (int i = 0; i < half; ++i) {
+      const T send = up ? v[i] : v[i + half];
+      const T keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
+  T r = v[0];
+#pragma unroll
+  for (int off = 16 >> LOG; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+  return r;
 }
 
-// ---------------------------------------------------------------------------
-// Pair passes. Coordinates live as S column-split partial sums Xp[s][k]; the
-// consumer adds the S parts in order. Block = 8 warps x 4 rows; blockIdx.y
-// selects the column split.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ typename T2<T>::type sum_parts(const typename T2<T>::type *__restrict__ Xp, int S,
-                                                          int64_t k, int64_t j) {
-  typename T2<T>::type v = Xp[j];
-  for (int s = 1; s < S; ++s) {
-    const typename T2<T>::type u = Xp[(int64_t)s * k + j];
-    v.x += u.x;
-    v.y += u.y;
-  }
-  return v;
-}
-
-// MODE 0: L^Y pass, out_i = sum_j W1_ij (x_i - x_j) / |x_i - x_j|  (W1 = 1/Delta)
-// MODE 1: apply,    out_i = sum_j M_ij v_j
-// Mat is k x kp with kp a multiple of 128 and zero columns j >= k, so every
-// block streams whole 128-column bands with 16-byte loads and no tail; the
-// staged coordinates are zero beyond k. Each lane owns VW consecutive columns.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(LWARPS * 32)
-k_pairpass(int32_t k, int32_t kp, const T *__restrict__ Mat, const typename T2<T>::type *__restrict__ Vp,
-           int S_in, typename T2<T>::type *__restrict__ Outp) {
+__global__ void __launch_bounds__(256)
+k_sympass(int32_t kp, const T *__restrict__ Mat, const typename T2<T>::type *__restrict__ V,
+          typename T2<T>::type *__restrict__ Part) {
   using V2 = typename T2<T>::type;
-  constexpr int VW = 16 / sizeof(T);
-  __shared__ __align__(16) T sx[XCH];
-  __shared__ __align__(16) T sy[XCH];
+  constexpr int NV = 2 * SRPI;
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J < I) return;
+  __shared__ V2 sVi[ST];
+  __shared__ T colred[8][2 * ST];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int S = gridDim.y, s = blockIdx.y;
-  const int64_t bands = kp / 128;
-  const int64_t jlo = bands * s / S * 128, jhi = bands * (s + 1) / S * 128;
-  int64_t rows[RPW];
-  T xi[RPW], yi[RPW], ax[RPW], ay[RPW];
+  const int64_t i0 = (int64_t)I * ST, j0 = (int64_t)J * ST;
+  if (threadIdx.x < ST) sVi[threadIdx.x] = V[i0 + threadIdx.x];
+  T xj[4], yj[4];
 #pragma unroll
-  for (int r = 0; r < RPW; ++r) {
-    rows[r] = ((int64_t)blockIdx.x * LWARPS + warp) * RPW + r;
-    ax[r] = T(0);
-    ay[r] = T(0);
-    xi[r] = T(0);
-    yi[r] = T(0);
-    if (MODE == 0 && rows[r] < k) {
-      const V2 v = sum_parts<T>(Vp, S_in, k, rows[r]);
-      xi[r] = v.x;
-      yi[r] = v.y;
-    }
+  for (int u = 0; u < 4; ++u) {
+    const V2 v = V[j0 + lane * 4 + u];
+    xj[u] = v.x;
+    yj[u] = v.y;
   }
-  for (int64_t c0 = jlo; c0 < jhi; c0 += XCH) {
-    const int cn = (int)min((int64_t)XCH, jhi - c0);  // a multiple of 128
-    __syncthreads();
-    for (int t = threadIdx.x; t < cn; t += blockDim.x) {
-      V2 v;
-      if (c0 + t < k) v = sum_parts<T>(Vp, S_in, k, c0 + t);
-      else { v.x = T(0); v.y = T(0); }
-      sx[t] = v.x;
-      sy[t] = v.y;
-    }
-    __syncthreads();
-#pragma unroll 2
-    for (int t = lane * VW; t < cn; t += 32 * VW) {
-      T m[RPW][VW];
+  __syncthreads();
+  T cx[4], cy[4];
 #pragma unroll
-      for (int r = 0; r < RPW; ++r) {
-        if (rows[r] < k) {
-          const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(Mat + rows[r] * kp + c0 + t));
-          memcpy(m[r], &raw, 16);
+  for (int u = 0; u < 4; ++u) cx[u] = cy[u] = T(0);
+  T *part = reinterpret_cast<T *>(Part);
+#pragma unroll
+  for (int sub = 0; sub < 16 / SRPI; ++sub) {
+    const int rbase = warp * 16 + sub * SRPI;
+    T m[SRPI][4];
+#pragma unroll
+    for (int r = 0; r < SRPI; ++r) ld4(Mat + (i0 + rbase + r) * kp + j0 + lane * 4, m[r]);
+    T acc[NV];
+#pragma unroll
+    for (int r = 0; r < SRPI; ++r) {
+      const V2 vi = sVi[rbase + r];
+      T ax = T(0), ay = T(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (MODE == 0) {
+          const T dx = vi.x - xj[u], dy = vi.y - yj[u];
+          const T coef = m[r][u] * rsqrt_pos<T>(dx * dx + dy * dy);
+          const T tx = coef * dx, ty = coef * dy;
+          ax += tx;
+          ay += ty;
+          cx[u] -= tx;
+          cy[u] -= ty;
         } else {
-#pragma unroll
-          for (int u = 0; u < VW; ++u) m[r][u] = T(0);
+          ax += m[r][u] * xj[u];
+          ay += m[r][u] * yj[u];
+          cx[u] += m[r][u] * vi.x;
+          cy[u] += m[r][u] * vi.y;
         }
       }
-      T xv[VW], yv[VW];
-      {
-        const uint4 rx = *reinterpret_cast<const uint4 *>(sx + t);
-        const uint4 ry = *reinterpret_cast<const uint4 *>(sy + t);
-        memcpy(xv, &rx, 16);
-        memcpy(yv, &ry, 16);
-      }
-#pragma unroll
-      for (int u = 0; u < VW; ++u) {
-#pragma unroll
-        for (int r = 0; r < RPW; ++r) {
-          if (MODE == 0) {
-            const T dx = xi[r] - xv[u], dy = yi[r] - yv[u];
-            const T coef = m[r][u] * rsqrt_pos<T>(dx * dx + dy * dy);
-            ax[r] += coef * dx;
-            ay[r] += coef * dy;
-          } else {
-            ax[r] += m[r][u] * xv[u];
-            ay[r] += m[r][u] * yv[u];
-          }
-        }
-      }
+      acc[2 * r] = ax;
+      acc[2 * r + 1] = ay;
+    }
+    const T tot = lanes_transpose_sum<NV, T>(acc, lane);
+    constexpr int REP = 32 / NV;
+    if (lane % REP == 0) {
+      const int idx = lane / REP;
+      part[((int64_t)J * kp + i0 + rbase + (idx >> 1)) * 2 + (idx & 1)] = tot;
     }
   }
+  if (I != J) {
 #pragma unroll
-  for (int r = 0; r < RPW; ++r) {
-    T vx = ax[r], vy = ay[r];
-    for (int o = 16; o > 0; o >>= 1) {
-      vx += __shfl_xor_sync(0xffffffffu, vx, o);
-      vy += __shfl_xor_sync(0xffffffffu, vy, o);
+    for (int u = 0; u < 4; ++u) {
+      colred[warp][(lane * 4 + u) * 2] = cx[u];
+      colred[warp][(lane * 4 + u) * 2 + 1] = cy[u];
     }
-    if (lane == 0 && rows[r] < k) {
-      V2 o;
-      o.x = vx;
-      o.y = vy;
-      Outp[(int64_t)s * k + rows[r]] = o;
-    }
+    __syncthreads();
+    T s = T(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += colred[w][threadIdx.x];
+    part[((int64_t)I * kp + j0) * 2 + threadIdx.x] = s;
   }
 }
 
-// X = sum of parts, mean subtracted, converted to the output type. One block
-// (deterministic FP64 mean).
+// V[row] = sum_{o < nb} Part[o][row], in order.
+template <typename T>
+__global__ void k_reduce_parts(int32_t kp, int nb, const typename T2<T>::type *__restrict__ Part,
+                               typename T2<T>::type *__restrict__ V) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= kp) return;
+  typename T2<T>::type s = Part[r];
+  for (int o = 1; o < nb; ++o) {
+    const typename T2<T>::type u = Part[(int64_t)o * kp + r];
+    s.x += u.x;
+    s.y += u.y;
+  }
+  V[r] = s;
+}
+
+// X (kp x 2) = x0 for rows < k, zero on the padding.
+template <typename TI, typename T>
+__global__ void k_load_x(int32_t k, int32_t kp, const TI *__restrict__ x, typename T2<T>::type *__restrict__ X) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kp) return;
+  typename T2<T>::type v;
+  v.x = i < k ? (T)x[2 * i] : T(0);
+  v.y = i < k ? (T)x[2 * i + 1] : T(0);
+  X[i] = v;
+}
+
+// Centre X (FP64 mean, one block, fixed order) and convert to the output type.
 template <typename T, typename TO>
-__global__ void k_finish(int32_t k, const typename T2<T>::type *__restrict__ Xp, int S, TO *__restrict__ out,
+__global__ void k_finish(int32_t k, const typename T2<T>::type *__restrict__ X, TO *__restrict__ out,
                          typename T2<T>::type *__restrict__ Xc) {
   __shared__ double sx[1024], sy[1024];
   double mx = 0.0, my = 0.0;
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
-    const typename T2<T>::type v = sum_parts<T>(Xp, S, k, i);
-    mx += (double)v.x;
-    my += (double)v.y;
+    mx += (double)X[i].x;
+    my += (double)X[i].y;
   }
   sx[threadIdx.x] = mx;
   sy[threadIdx.x] = my;
@@ -373,8 +272,7 @@ __global__ void k_finish(int32_t k, const typename T2<T>::type *__restrict__ Xp,
   }
   const double ax = sx[0] / k, ay = sy[0] / k;
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
-    const typename T2<T>::type v = sum_parts<T>(Xp, S, k, i);
-    const T cx = (T)((double)v.x - ax), cy = (T)((double)v.y - ay);
+    const T cx = (T)((double)X[i].x - ax), cy = (T)((double)X[i].y - ay);
     out[2 * i] = (TO)cx;
     out[2 * i + 1] = (TO)cy;
     if (Xc) {
@@ -384,21 +282,6 @@ __global__ void k_finish(int32_t k, const typename T2<T>::type *__restrict__ Xp,
       Xc[i] = w;
     }
   }
-}
-
-template <typename TI, typename T>
-__global__ void k_load_x(int32_t k, const TI *__restrict__ x, typename T2<T>::type *__restrict__ Xp,
-                         int S) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= k) return;
-  typename T2<T>::type v;
-  v.x = (T)x[2 * i];
-  v.y = (T)x[2 * i + 1];
-  Xp[i] = v;
-  typename T2<T>::type z;
-  z.x = T(0);
-  z.y = T(0);
-  for (int s = 1; s < S; ++s) Xp[(int64_t)s * k + i] = z;
 }
 
 // ---------------------------------------------------------------------------
@@ -514,84 +397,60 @@ __global__ void k_convert(int64_t cnt, const TI *__restrict__ in, T *__restrict_
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename T>
-int gj_invert(pprviz_ctx *ctx, int32_t kp, T *A, T *Vt, T *P) {
-  constexpr int TM = sizeof(T) == 4 ? 128 : 64;
-  const size_t trail_smem = 2 * sizeof(T) * NB * TM;
-  const size_t panel_smem = 2 * sizeof(T) * NB * NB;
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_gj_trailing<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)trail_smem));
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_gj_rowpanel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)panel_smem));
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_gj_colpanel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)panel_smem));
-  const int nblk = kp / NB;
-  const unsigned tgrid = (unsigned)((kp + TM - 1) / TM);
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int K0 = kb * NB;
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_gj_diag<T><<<1, 256, 0, ctx->stream>>>(kp, K0, A, P); }
-    PPRVIZ_LAUNCHED(ctx);
-    if (nblk == 1) break;
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_gj_vt<T><<<dim3(kp / 32, NB / 32), dim3(32, 8), 0, ctx->stream>>>(kp, K0, A, Vt); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_gj_rowpanel<T><<<nblk, 256, panel_smem, ctx->stream>>>(kp, K0, A, P); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_gj_trailing<T, TM><<<dim3(tgrid, tgrid), 256, trail_smem, ctx->stream>>>(kp, K0, A, Vt); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_gj_colpanel<T><<<nblk, 256, panel_smem, ctx->stream>>>(kp, K0, A, Vt, P); }
-    PPRVIZ_LAUNCHED(ctx);
-  }
-  return PPRVIZ_OK;
-}
-
-int split_count(int32_t k, int32_t kp) {
-  // about eight resident 256-thread blocks per SM on 152 SMs; at most one
-  // 128-column band per split
-  const int rowblocks = (k + LWARPS * RPW - 1) / (LWARPS * RPW);
-  int S = (int)std::max(1, std::min(16, (8 * 152 + rowblocks - 1) / std::max(rowblocks, 1)));
-  return std::min(S, kp / 128);
-}
-
 template <typename T, typename TI, typename TO>
 int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int32_t iters, TO *x_out,
                  double *stress_h) {
   using V2 = typename T2<T>::type;
-  const int32_t kp = (k + 127) / 128 * 128;  // whole 128-column bands (and NB blocks)
-  const int S = split_count(k, kp);
+  const int32_t kp = (k + ST - 1) / ST * ST;  // whole symmetric tiles (and NB pivot blocks)
+  const int nbt = kp / ST;
   PPRVIZ_TRY(ws_ensure(ctx, WS_W1, sizeof(T) * (size_t)kp * kp));
   PPRVIZ_TRY(ws_ensure(ctx, WS_M, sizeof(T) * (size_t)kp * kp));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(T) * (size_t)(NB * kp + NB * NB)));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_X, sizeof(V2) * (size_t)S * k));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_B, sizeof(V2) * (size_t)S * k));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(T) * (size_t)(2 * NB * kp + NB * NB)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_X, sizeof(V2) * (size_t)kp * 2));            // X and b
+  PPRVIZ_TRY(ws_ensure(ctx, WS_B, sizeof(V2) * (size_t)nbt * kp));          // partial sums
   PPRVIZ_TRY(ws_ensure(ctx, WS_E, sizeof(V2) * (size_t)k + 64));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sizeof(double) * (size_t)(kp / 32) * kp));  // build row partials
   PPRVIZ_TRY(ws_ensure(ctx, WS_FLAG, 64));
   T *W1 = ctx->ws[WS_W1].as<T>(), *A = ctx->ws[WS_M].as<T>();
-  T *Vt = ctx->ws[WS_PIV].as<T>(), *P = Vt + (size_t)NB * kp;
-  V2 *Xp = ctx->ws[WS_X].as<V2>(), *Bp = ctx->ws[WS_B].as<V2>();
+  T *work = ctx->ws[WS_PIV].as<T>();
+  V2 *X = ctx->ws[WS_X].as<V2>(), *Bv = X + kp, *Part = ctx->ws[WS_B].as<V2>();
+  double *rowpart = ctx->ws[WS_RHS].as<double>();
   int *flag = ctx->ws[WS_FLAG].as<int>();
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_build<TI, T><<<(unsigned)((kp + 7) / 8), 256, 0, ctx->stream>>>(k, kp, pdist, W1, A, flag); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_build_sym<TI, T><<<dim3(kp / 32, kp / 32), dim3(32, 8), 0, ctx->stream>>>(k, kp, pdist, W1, A, rowpart, flag); }
+  PPRVIZ_LAUNCHED(ctx);
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_build_diag<T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(k, kp, rowpart, A); }
   PPRVIZ_LAUNCHED(ctx);
   int hf = 0;
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hf) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "pdist has a non-finite or non-positive off-diagonal entry");
-  if (iters > 0) PPRVIZ_TRY(gj_invert<T>(ctx, kp, A, Vt, P));
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<TI, T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(k, x0, Xp, S); }
+  if (iters > 0) {
+    if constexpr (std::is_same<T, float>::value) PPRVIZ_TRY(spd_inverse_f32(ctx, kp, A, work));
+    else PPRVIZ_TRY(spd_inverse_f64(ctx, kp, A, work));
+  }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<TI, T><<<(unsigned)((kp + 255) / 256), 256, 0, ctx->stream>>>(k, kp, x0, X); }
   PPRVIZ_LAUNCHED(ctx);
-  const dim3 grid((unsigned)((k + LWARPS * RPW - 1) / (LWARPS * RPW)), (unsigned)S);
+  const dim3 grid((unsigned)nbt, (unsigned)nbt);
+  const unsigned rgrid = (unsigned)((kp + 255) / 256);
   for (int it = 0; it < iters; ++it) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_pairpass<T, 0><<<grid, LWARPS * 32, 0, ctx->stream>>>(k, kp, W1, Xp, S, Bp); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass<T, 0><<<grid, 256, 0, ctx->stream>>>(kp, W1, X, Part); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_pairpass<T, 1><<<grid, LWARPS * 32, 0, ctx->stream>>>(k, kp, A, Bp, S, Xp); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, Bv); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass<T, 1><<<grid, 256, 0, ctx->stream>>>(kp, A, Bv, Part); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, X); }
     PPRVIZ_LAUNCHED(ctx);
   }
   V2 *Xc = ctx->ws[WS_E].as<V2>();
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_finish<T, TO><<<1, 1024, 0, ctx->stream>>>(k, Xp, S, x_out, Xc); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_finish<T, TO><<<1, 1024, 0, ctx->stream>>>(k, X, x_out, Xc); }
   PPRVIZ_LAUNCHED(ctx);
   ctx->stats.layout_iters = iters;
-  ctx->stats.bytes_ly = (double)sizeof(T) * k * (double)k * iters;
-  ctx->stats.bytes_apply = (double)sizeof(T) * k * (double)k * iters;
+  // algorithmic bytes: each pass reads the upper triangle of one k x k matrix
+  const double half = 0.5 * (double)k * ((double)k + 1.0) * sizeof(T);
+  ctx->stats.bytes_ly = half * iters;
+  ctx->stats.bytes_apply = half * iters;
   if (stress_h) {
     const unsigned eb = (unsigned)((k + LWARPS * RPW - 1) / (LWARPS * RPW));
     PPRVIZ_TRY(ws_ensure(ctx, WS_OUT1, sizeof(double) * (eb + 1)));
@@ -645,13 +504,16 @@ static int energy_typed(pprviz_ctx *ctx, const T *pdist, int32_t k, const T *x, 
   double *ep = ctx->ws[WS_OUT1].as<double>();
   int *flag = ctx->ws[WS_FLAG].as<int>();
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<T, T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(k, x, X, 1); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<T, T><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(k, k, x, X); }
   PPRVIZ_LAUNCHED(ctx);
   const T s = (T)scale;
-  if (gx && gD) { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_energy<T, true, true><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag); }
-  else if (gx) { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_energy<T, true, false><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag); }
-  else if (gD) { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_energy<T, false, true><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag); }
-  else { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_energy<T, false, false><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag); }
+  {
+    PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY);
+    if (gx && gD) k_energy<T, true, true><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag);
+    else if (gx) k_energy<T, true, false><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag);
+    else if (gD) k_energy<T, false, true><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag);
+    else k_energy<T, false, false><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist, X, s, ep, gx, gD, flag);
+  }
   PPRVIZ_LAUNCHED(ctx);
   { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_reduce_energy<<<1, 256, 0, ctx->stream>>>((int)eb, ep, ep + eb); }
   PPRVIZ_LAUNCHED(ctx);

@@ -39,6 +39,8 @@ namespace pprviz {
 
 constexpr int kWarps = 8;         // warps per block in the sweep kernels
 constexpr int kChunk = 128;       // group width granule (sources)
+constexpr int kMaxRefine = 6;     // refinement passes before E_NOT_CONVERGED
+constexpr int kMaxRefineSweeps = 32;  // Chebyshev sweeps per refinement pass
 
 template <typename T>
 struct Vec;  // 16-byte vector of T
@@ -120,6 +122,27 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
     float myw = 1.0f;
     if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
     int t = 0;
+    for (; t + 8 <= cnt; t += 8) {
+      T v[8][VEC];
+      float wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int32_t iq = __shfl_sync(0xffffffffu, myc, t + q);
+        if (WEIGHTED) wv[q] = __shfl_sync(0xffffffffu, myw, t + q);
+        Vec<T>::load(ycur + (int64_t)iq * ld + off, v[q]);
+      }
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        if (WEIGHTED) {
+          T s = T(0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) s += (T)wv[q] * v[q][u];
+          acc[u] += s;
+        } else {
+          acc[u] += ((v[0][u] + v[1][u]) + (v[2][u] + v[3][u])) + ((v[4][u] + v[5][u]) + (v[6][u] + v[7][u]));
+        }
+      }
+    }
     for (; t + 4 <= cnt; t += 4) {
       T v0[VEC], v1[VEC], v2[VEC], v3[VEC];
       const int32_t i0 = __shfl_sync(0xffffffffu, myc, t);
@@ -179,6 +202,27 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
   Vec<T>::store(yout + rowoff, out);
 }
 
+// v[u] = (double)(y_hi[u] + y_lo[u]), u < 4, with 16-byte loads (p is 4-aligned).
+__device__ __forceinline__ void load4(const float *hi, const float *lo, double (&v)[4]) {
+  float a[4];
+  Vec<float>::load(hi, a);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) v[u] = (double)a[u];
+  if (lo) {
+    float b[4];
+    Vec<float>::load(lo, b);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] += (double)b[u];
+  }
+}
+__device__ __forceinline__ void load4(const double *hi, const float *lo, double (&v)[4]) {
+  double a[2], b[2];
+  Vec<double>::load(hi, a);
+  Vec<double>::load(hi + 2, b);
+  v[0] = a[0]; v[1] = a[1]; v[2] = b[0]; v[3] = b[1];
+  (void)lo;  // the FP64 path keeps no low part
+}
+
 // FP64 residual of the computed rows x = dw * (y_hi + y_lo) against the
 // original system x (I - cP) = alpha e_s:
 //   res_jq = alpha [j == src[q]] - x_jq + c * sum_{i in N(j)} w_ij (y_hi + y_lo)[i][q]
@@ -186,7 +230,7 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
 // sum_j |res_jq| added into l1[q] (FP64).
 // Grid: (nchunks, row blocks); each warp walks rows with a stride so its
 // per-source partial sums are reduced once per block.
-template <typename T, bool WEIGHTED>
+template <typename T, bool WEIGHTED, bool EXACT>
 __global__ void __launch_bounds__(kWarps * 32)
 k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
            const float *__restrict__ w, const double *__restrict__ invdw,
@@ -210,29 +254,73 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
 #pragma unroll
     for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
     const int64_t b = rp[j], e = rp[j + 1];
-    for (int64_t base = b; base < e; base += 32) {
-      const int cnt = (int)min((int64_t)32, e - base);
-      int32_t myc = lane < cnt ? col[base + lane] : 0;
-      float myw = 1.0f;
-      if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
-      for (int t = 0; t < cnt; ++t) {
-        const int32_t i = __shfl_sync(0xffffffffu, myc, t);
-        const double wi = WEIGHTED ? (double)__shfl_sync(0xffffffffu, myw, t) : 1.0;
-        const int64_t p = (int64_t)i * ld + off;
+    if constexpr (std::is_same<T, float>::value && !EXACT) {
+      // Error-free FP32 accumulation of sum_i w_ij (y_hi + y_lo)_i: TwoSum
+      // (Knuth) keeps the exact rounding error of every addition of the high
+      // parts, FMA the exact error of every weighted product; the
+      // compensation is flushed into FP64 after every 32 edges and the sum is
+      // assembled in FP64. Relative error <= ~1e-12 per 32-edge batch.
+      float shi[VEC], sc[VEC], slo[VEC];
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) shi[u] = sc[u] = slo[u] = 0.0f;
+      for (int64_t base = b; base < e; base += 32) {
+        const int cnt = (int)min((int64_t)32, e - base);
+        int32_t myc = lane < cnt ? col[base + lane] : 0;
+        float myw = 1.0f;
+        if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
+        for (int t = 0; t < cnt; ++t) {
+          const int32_t i = __shfl_sync(0xffffffffu, myc, t);
+          const float wi = WEIGHTED ? __shfl_sync(0xffffffffu, myw, t) : 1.0f;
+          const int64_t p = (int64_t)i * ld + off;
+          float h[VEC], l[VEC];
+          Vec<float>::load(reinterpret_cast<const float *>(yhi) + p, h);
+          if (ylo) Vec<float>::load(ylo + p, l);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) {
+            float a = h[u], pe = 0.0f;
+            if (WEIGHTED) {
+              a = wi * h[u];
+              pe = fmaf(wi, h[u], -a);
+            }
+            const float s = shi[u] + a;
+            const float bb = s - shi[u];
+            sc[u] += ((shi[u] - (s - bb)) + (a - bb)) + pe;
+            shi[u] = s;
+            if (ylo) slo[u] = fmaf(wi, l[u], slo[u]);
+          }
+        }
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          double v = (double)yhi[p + u];
-          if (ylo) v += (double)ylo[p + u];
-          acc[u] += wi * v;
+          acc[u] += (double)sc[u];
+          sc[u] = 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[u] += (double)shi[u] + (double)slo[u];
+    } else {
+      for (int64_t base = b; base < e; base += 32) {
+        const int cnt = (int)min((int64_t)32, e - base);
+        int32_t myc = lane < cnt ? col[base + lane] : 0;
+        float myw = 1.0f;
+        if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
+        for (int t = 0; t < cnt; ++t) {
+          const int32_t i = __shfl_sync(0xffffffffu, myc, t);
+          const double wi = WEIGHTED ? (double)__shfl_sync(0xffffffffu, myw, t) : 1.0;
+          const int64_t p = (int64_t)i * ld + off;
+          double v[VEC];
+          load4(yhi + p, ylo ? ylo + p : nullptr, v);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) acc[u] += wi * v[u];
         }
       }
     }
     const int64_t rowoff = j * ld + off;
     const double dw = 1.0 / invdw[j];
+    double yrow[VEC];
+    load4(yhi + rowoff, ylo ? ylo + rowoff : nullptr, yrow);
 #pragma unroll
     for (int u = 0; u < VEC; ++u) {
-      double y = (double)yhi[rowoff + u];
-      if (ylo) y += (double)ylo[rowoff + u];
+      const double y = yrow[u];
       if (e == b) acc[u] += y;
       const double bq = (sq[u] == (int32_t)j) ? alpha : 0.0;
       const double r = bq - dw * y + c * acc[u];
@@ -334,7 +422,10 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
   return PPRVIZ_OK;
 }
 
-template <typename T>
+// EXACT selects FP64 accumulation of the neighbour sums; otherwise the FP32
+// path uses the error-free compensated sums (certificate floor ~1e-9 at the
+// largest degrees, so tighter eps needs EXACT).
+template <typename T, bool EXACT>
 int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha) {
   const int nchunks = (int)(ld / 128);
@@ -342,11 +433,11 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   dim3 grid(nchunks, rows_blocks);
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(l1, 0, sizeof(double) * (size_t)ld, ctx->stream));
   if (g->weighted)
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, true><<<grid, kWarps * 32, 0, ctx->stream>>>(
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, true, EXACT><<<grid, kWarps * 32, 0, ctx->stream>>>(
         g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), g->w.as<float>(), g->invdw_d.as<double>(),
         src, yhi, ylo, rhs_out, l1, alpha, 1.0 - alpha); }
   else
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, false><<<grid, kWarps * 32, 0, ctx->stream>>>(
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, false, EXACT><<<grid, kWarps * 32, 0, ctx->stream>>>(
         g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), nullptr, g->invdw_d.as<double>(), src,
         yhi, ylo, rhs_out, l1, alpha, 1.0 - alpha); }
   PPRVIZ_LAUNCHED(ctx);
@@ -425,6 +516,9 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   std::vector<double> cert;
   bool not_converged = false;
   const double rho = chebyshev_rate(c);
+  // the compensated FP32 residual resolves certificates down to ~1e-9; below
+  // that the neighbour sums are accumulated in FP64
+  const bool exact_res = eps < 1e-9;
 
   for (int32_t g0 = 0; g0 < k; g0 += (int32_t)ld) {
     const int32_t gvalid = (int32_t)std::min<int64_t>(ld, (int64_t)k - g0);
@@ -452,7 +546,7 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       }
       st.sweeps_main += T;
       st.bytes_sweep += 16.0 * (double)g->n * gvalid * T;
-      PPRVIZ_TRY(launch_residual<double>(ctx, g, ld, src, cur, nullptr, nullptr, l1, alpha));
+      PPRVIZ_TRY((launch_residual<double, true>(ctx, g, ld, src, cur, nullptr, nullptr, l1, alpha)));
       st.residual_passes++;
       PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
       yhi = cur;
@@ -460,8 +554,10 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       float *bufs[4] = {ctx->ws[WS_Y0].as<float>(), ctx->ws[WS_Y1].as<float>(), ctx->ws[WS_Y2].as<float>(),
                         ctx->ws[WS_Y3].as<float>()};
       float *rhs = ctx->ws[WS_RHS].as<float>();
-      // main solve: until FP32 rounding dominates (Chebyshev error ~ 2 rho^K <= 1e-7)
-      const int K1 = std::max(2, (int)ceil(log(0.5e-7) / log(rho)));
+      // main solve to a Chebyshev error bound 2 rho^K <= 1e-5: every further
+      // sweep here would only save one refinement sweep, and the refinement
+      // (driven by the exact FP64 residual) finishes the job
+      const int K1 = std::max(2, (int)ceil(log(0.5e-5) / log(rho)));
       float *hi = nullptr;
       PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, &hi));
       st.sweeps_main += K1;
@@ -469,16 +565,19 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       // free buffers for the correction solves; the first correction becomes x_lo
       float *fa = hi == bufs[0] ? bufs[1] : bufs[0], *fb = bufs[2], *fc = bufs[3];
       float *lo = nullptr;
-      PPRVIZ_TRY(launch_residual<float>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha));
+      PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha)
+                            : launch_residual<float, false>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha)));
       st.residual_passes++;
       PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
-      for (int pass = 0; pass < 4; ++pass) {
+      for (int pass = 0; pass < kMaxRefine; ++pass) {
         double cmax = 0.0;
         for (double v : cert) cmax = std::max(cmax, v);
         if (cmax <= eps) break;
-        // sweeps for the correction: its Chebyshev error must fall by eps / (4 cmax)
+        // sweeps for the correction: its Chebyshev error must fall by eps / (4 cmax),
+        // but an FP32 correction resolves only ~1e-7 of itself per pass, so
+        // sweeps past 2 rho^K ~ 3e-8 are left to the next pass
         int K2 = (int)ceil(log(0.25 * eps / cmax) / log(rho)) + 2;
-        K2 = std::min(std::max(K2, 4), 80);
+        K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
         float *delta = nullptr;
         PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, &delta));
         st.sweeps_refine += K2;
@@ -493,7 +592,8 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
           { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_axpy<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, delta, lo); }
           PPRVIZ_LAUNCHED(ctx);
         }
-        PPRVIZ_TRY(launch_residual<float>(ctx, g, ld, src, hi, lo, rhs, l1, alpha));
+        PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)
+                              : launch_residual<float, false>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)));
         st.residual_passes++;
         PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
       }

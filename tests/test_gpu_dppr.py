@@ -3,8 +3,8 @@ DPPR/PDist (P3) against the FP64 oracle, through the C ABI.
 
 Tolerances (derived in the design notes from the paper's definitions):
   DPPR:  |got - ref| <= 1e-6 * max(1, |ref|) per entry; certificate <= eps.
-  PDist: |got - ref| <= 1e-5 absolute (Lemma 1: dDelta = -dz / z on the
-         unclamped branch, so a 1e-6-relative z error moves Delta by ~1e-6).
+  PDist: 1e-5 plus the certified propagation bound of Eq. (1) (tests/_parity.py);
+         with a tight eps the flat 1e-5 gate holds everywhere.
   Degrees and other integer outputs: bit-exact.
 """
 import math
@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 import synth
+from _parity import check_dppr, check_pdist
 
 pytestmark = pytest.mark.gpu
 ALPHA = 0.15
@@ -40,13 +41,10 @@ def _oracle(g, view, alpha=ALPHA, direct=False):
     return D, d
 
 
-def _check_dppr(got, ref, tol=1e-6):
-    err = np.abs(got.astype(np.float64) - ref) / np.maximum(1.0, np.abs(ref))
-    assert err.max() <= tol, f"max rel-abs DPPR error {err.max():.3e}"
-    return err.max()
+_check_dppr = check_dppr
 
 
-def _check_pdist(got, ref, tol=1e-5):
+def _check_pdist_flat(got, ref, tol=1e-5):
     err = np.abs(got.astype(np.float64) - ref)
     assert err.max() <= tol, f"max PDist error {err.max():.3e}"
     return err.max()
@@ -138,7 +136,7 @@ def test_dppr_pdist_small_graphs(ctx, precision):
             assert st == 0, name
             assert cert.max() <= EPS
             _check_dppr(D, Dref)
-            _check_pdist(Delta, O.pdist_from_dppr(Dref, g.n))
+            check_pdist(Delta, Dref, cert, g.n)
 
 
 def test_dppr_fp64_outputs_and_closed_forms(ctx):
@@ -203,7 +201,7 @@ def test_config_small_chung_lu_1000_fp64(ctx):
     D, Delta, cert, st = ctx.dppr(G, view, ALPHA, EPS, P.FP64, out64=True)
     assert st == 0 and cert.max() <= EPS
     assert np.abs(D - Dref).max() <= EPS  # the FP64 path meets eps absolutely
-    _check_pdist(Delta, O.pdist_from_dppr(Dref, g.n), tol=1e-6)
+    check_pdist(Delta, Dref, cert, g.n, slack=1e-6)
 
 
 def test_fp32_multiple_groups_ragged_tail(ctx):
@@ -218,7 +216,22 @@ def test_fp32_multiple_groups_ragged_tail(ctx):
     assert stats["groups"] >= 2 and g.n % stats["source_group"] != 0
     assert st == 0 and cert.max() <= EPS
     _check_dppr(D, Dref)
-    _check_pdist(Delta, O.pdist_from_dppr(Dref, g.n))
+    check_pdist(Delta, Dref, cert, g.n)
+
+
+def test_tight_eps_gives_flat_pdist_gate(ctx):
+    """With eps = 1e-12 the certified PDist bound is below 1e-5 for every entry
+    above the clamp threshold, so the flat 1e-5 gate holds (FP32 refinement
+    passes continue on the x_hi + x_lo representation)."""
+    import paper_2112_14944_gb300 as P
+    for g in (synth.sbm([40, 50, 60, 7], 0.1, 0.004, seed=12), synth.chung_lu(500, 10, 2.5, seed=13)):
+        G = ctx.upload_graph(g)
+        view = np.arange(g.n, dtype=np.int32)
+        Dref, _ = _oracle(g, view, direct=True)
+        D, Delta, cert, st = ctx.dppr(G, view, ALPHA, 1e-12, P.FP32)
+        assert st == 0 and cert.max() <= 1e-12
+        _check_dppr(D, Dref, tol=2e-7)
+        _check_pdist_flat(Delta, O.pdist_from_dppr(Dref, g.n), tol=1e-5)
 
 
 def test_full_size_chung_lu_10k_fp32_sampled(ctx):
@@ -239,8 +252,10 @@ def test_full_size_chung_lu_10k_fp32_sampled(ctx):
     Drow = d[sample][:, None] * rows              # pi_d(s, .)
     Dcol = (d[:, None] * cols).T                  # pi_d(., s) as rows
     _check_dppr(D[sample], Drow)
-    _check_pdist(Delta[sample], np.where(np.arange(g.n)[None, :] == sample[:, None], 0.0,
-                                         O.pdist_from_z(Drow + Dcol, g.n)))
+    ref = np.where(np.arange(g.n)[None, :] == sample[:, None], 0.0, O.pdist_from_z(Drow + Dcol, g.n))
+    cc = cert[sample][:, None] + cert[None, :]
+    tol = 1e-5 + cc / np.maximum(Drow + Dcol - cc, math.e / g.n ** 2)
+    assert np.all(np.abs(Delta[sample].astype(np.float64) - ref) <= tol)
     asym = np.abs(D - D.T) / np.maximum(1.0, np.abs(D))
     assert asym.max() <= 2e-6
 
@@ -251,9 +266,9 @@ def test_pdist_standalone_matches_oracle(ctx):
     Dref[5, :] = 0.0
     Dref[:, 5] = 0.0                               # z = 0 entries
     for dt, tol in [(np.float32, 2e-6), (np.float64, 1e-12)]:
-        Din = Dref.astype(dt)
+        Din = np.ascontiguousarray(Dref, dtype=dt)
         ref = O.pdist_from_dppr(Din.astype(np.float64), 50)
         out = ctx.pdist(Din, 50)
         assert out.dtype == dt
-        _check_pdist(out, ref, tol=tol)
+        _check_pdist_flat(out, ref, tol=tol)
         assert out[5, 7] == np.float64(2 * math.log(50)).astype(dt)

@@ -19,6 +19,7 @@ import pytest
 
 import oracle as O
 import synth
+from _parity import check_pdist
 
 pytestmark = pytest.mark.gpu
 ALPHA = 0.15
@@ -175,7 +176,9 @@ def test_views_batch_matches_single_views(ctx):
         Dref = O.dppr_rows(O.ppr_direct(O.transition_matrix(n, g.row_ptr, g.col), ALPHA),
                            O.degrees(n, g.row_ptr, g.col), np.arange(n))
         Pd = pdb[sq:sq + n * n].reshape(n, n)
-        assert np.abs(Pd - O.pdist_from_dppr(Dref, n)).max() <= 1e-5
+        _, Pd1, cert, _ = ctx.dppr(G[v], np.arange(n, dtype=np.int32), ALPHA, 1e-6, P.FP32)
+        assert np.array_equal(Pd, Pd1)          # the batch runs the single-view kernels
+        check_pdist(Pd1, Dref, cert, n)
         X1, s1 = ctx.layout(Pd.copy(), x0[off[v]:off[v + 1]].copy(), 40, P.FP32)
         assert np.array_equal(X1, xb[off[v]:off[v + 1]])
         assert s1 == stress[v]
