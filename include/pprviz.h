@@ -224,6 +224,29 @@ int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *cons
                        const float *x0_packed, float *pdist_packed, float *x_packed,
                        double *stress_out, uint32_t mem_flags);
 
+/* Stress energy and gradients without allocating anything (no counterpart in
+ * the paper; a library convenience). Same results as pprviz_energy with FP32
+ * device buffers, for callers that may not allocate device memory when they
+ * call: code whose device memory is all owned by its own pool or a
+ * framework's allocator, code under a hard memory cap, or code that may only
+ * enqueue work on a stream it was handed.
+ * pdist, x:   device pointers (k*k and k*2 float), as in pprviz_energy.
+ * grad_x, grad_pdist: device outputs or NULL; e_out: host double or NULL.
+ * cuda_stream: the stream to run on (NULL = the legacy default stream); the
+ *             call waits for it before returning. No context is needed.
+ * Scratch: a fixed device array inside the library (about 528 KiB, held by
+ * every GPU that loads the library until the process exits), so k is limited
+ * to 65,536. The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture. Every call shares the array and the calls clear what
+ * must start at zero, but calls that overlap on the GPU (two streams, two
+ * threads) race on it and must be serialised by the caller.
+ * Returns PPRVIZ_OK, PPRVIZ_E_INVALID_ARG (NULL input, k outside [1, 65536],
+ * a non-positive off-diagonal distance) or PPRVIZ_E_CUDA; no error message is
+ * kept since there is no context. */
+int pprviz_energy_noalloc(const float *pdist, int32_t k, const float *x, double grad_scale, double *e_out,
+                          float *grad_x, float *grad_pdist, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

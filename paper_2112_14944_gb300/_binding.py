@@ -55,6 +55,7 @@ _SIGS = {
     "pprviz_energy": (C.c_int, [_VP, _VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, C.c_uint32]),
     "pprviz_views_batch": (C.c_int, [_VP, C.c_int32, _VP, _VP, C.c_double, C.c_double, C.c_int32, _VP, _VP, _VP,
                                      _VP, C.c_uint32]),
+    "pprviz_energy_noalloc": (C.c_int, [_VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -218,3 +219,15 @@ def pprviz_views_batch(ctx, graphs, offsets, alpha, eps, iters, x0_packed, pdist
                                                  float(eps), int(iters), _ptr(x0_packed)[0], _ptr(pdist_packed)[0],
                                                  _ptr(x_packed)[0], _ptr(stress_out)[0], mem_flags),
                   allow=(PPRVIZ_E_NOT_CONVERGED,))
+
+
+def pprviz_energy_noalloc(pdist, k, x, grad_scale=1.0, grad_x=None, grad_pdist=None, cuda_stream=None):
+    """Energy and gradients through the allocation-free entry point: device
+    (torch CUDA) buffers only, no context. Returns (status, energy)."""
+    for b in (pdist, x, grad_x, grad_pdist):
+        if b is not None and not _ptr(b)[1]:
+            raise ValueError("pprviz_energy_noalloc takes device buffers only")
+    e = C.c_double(0.0)
+    st = load().pprviz_energy_noalloc(_ptr(pdist)[0], int(k), _ptr(x)[0], float(grad_scale), C.byref(e),
+                                      _ptr(grad_x)[0], _ptr(grad_pdist)[0], cuda_stream)
+    return st, e.value

@@ -536,4 +536,94 @@ int energy_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x_d,
                              (float *)grad_pdist_d);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free energy entry point (pprviz_energy_noalloc).
+//
+// Some callers may not allocate device memory at the time they need the
+// energy: code that owns every byte of the device through its own pool or a
+// framework allocator (a cudaMalloc there fails or fragments the pool), code
+// running under a hard memory cap, or code that only enqueues work on a stream
+// it was handed. For them the scratch of the energy pass (the staged
+// coordinates, one FP64 partial per block and a status word) lives in the
+// fixed device array below, which every GPU that loads the library holds
+// until the process exits. The caller provides inputs and outputs.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxK = 65536;
+constexpr int kNoAllocBlocks = (kNoAllocMaxK + LWARPS * RPW - 1) / (LWARPS * RPW);
+constexpr size_t kNoAllocXBytes = sizeof(float2) * kNoAllocMaxK;             // 512 KiB
+constexpr size_t kNoAllocEBytes = sizeof(double) * (kNoAllocBlocks + 1);     // 16 KiB + 8 B
+constexpr size_t kNoAllocBytes = kNoAllocXBytes + kNoAllocEBytes + 256;       // + status word
+
+static __device__ __align__(256) unsigned char g_energy_scratch[kNoAllocBytes];
+
 }  // namespace pprviz
+
+#include <mutex>
+
+namespace {
+
+// Device address of g_energy_scratch, looked up once per device. In host code
+// the array's name is only a host-side stand-in for the device symbol, so the
+// kernels get this address instead.
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {nullptr};
+
+cudaError_t noalloc_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, pprviz::g_energy_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int pprviz_energy_noalloc(const float *pdist, int32_t k, const float *x, double grad_scale, double *e_out,
+                                     float *grad_x, float *grad_pdist, void *cuda_stream) {
+  using namespace pprviz;
+  if (!pdist || !x) return PPRVIZ_E_INVALID_ARG;
+  if (k < 1 || k > kNoAllocMaxK) return PPRVIZ_E_INVALID_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  void *base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) {
+    cudaGetLastError();
+    return PPRVIZ_E_CUDA;
+  }
+  float2 *X = reinterpret_cast<float2 *>(base);
+  double *eparts = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + kNoAllocXBytes);
+  int *flag = reinterpret_cast<int *>(static_cast<unsigned char *>(base) + kNoAllocXBytes + kNoAllocEBytes);
+  const unsigned eb = (unsigned)((k + LWARPS * RPW - 1) / (LWARPS * RPW));
+  // the status word keeps the previous call's value: clear it first
+  if (cudaMemsetAsync(flag, 0, sizeof(int), stream) != cudaSuccess) return PPRVIZ_E_CUDA;
+  k_load_x<float, float><<<(unsigned)((k + 255) / 256), 256, 0, stream>>>(k, k, x, X);
+  const float s = (float)grad_scale;
+  if (grad_x && grad_pdist)
+    k_energy<float, true, true><<<eb, LWARPS * 32, 0, stream>>>(k, pdist, X, s, eparts, grad_x, grad_pdist, flag);
+  else if (grad_x)
+    k_energy<float, true, false><<<eb, LWARPS * 32, 0, stream>>>(k, pdist, X, s, eparts, grad_x, grad_pdist, flag);
+  else if (grad_pdist)
+    k_energy<float, false, true><<<eb, LWARPS * 32, 0, stream>>>(k, pdist, X, s, eparts, grad_x, grad_pdist, flag);
+  else
+    k_energy<float, false, false><<<eb, LWARPS * 32, 0, stream>>>(k, pdist, X, s, eparts, grad_x, grad_pdist, flag);
+  k_reduce_energy<<<1, 256, 0, stream>>>((int)eb, eparts, eparts + eb);
+  if (cudaGetLastError() != cudaSuccess) return PPRVIZ_E_CUDA;
+  double e = 0.0;
+  int hf = 0;
+  if (cudaMemcpyAsync(&e, eparts + eb, sizeof(double), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    return PPRVIZ_E_CUDA;
+  }
+  if (hf) return PPRVIZ_E_INVALID_ARG;
+  if (e_out) *e_out = e;
+  return PPRVIZ_OK;
+}
