@@ -91,6 +91,11 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def fp32_simt_tflops(sm_max_mhz):
+    """FP32 FMA peak from unit counts: 152 SMs x 4 SMSPs x 32 lanes x 2 flop x clock."""
+    return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
 def config(args, n_gpus):
     return {"workload": WORKLOAD, "graph": "chung-lu", "n": args.n, "mean_degree": args.deg, "exponent": 2.5,
             "seed": 0, "view": "all nodes (k = n)", "alpha": ALPHA, "eps": EPS, "layout_iters": args.iters,
@@ -276,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
     sampler.start()
     step_ms, dppr_ms, layout_ms = [], [], []
     launches = 0
-    bytes_sweep = bytes_ly = bytes_apply = 0.0
+    bytes_sweep = bytes_ly = bytes_apply = flops_factor = 0.0
     sweeps = 0
     wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -289,6 +294,7 @@ def run_ours(args, rank, world, local_rank):
         sweeps += sd["sweeps_main"] + sd["sweeps_refine"]
         bytes_ly += sl["bytes_ly"]
         bytes_apply += sl["bytes_apply"]
+        flops_factor += sl["flops_factor"]
         ev[2].synchronize()
         dppr_ms.append(ev[0].elapsed_time(ev[1]))
         layout_ms.append(ev[1].elapsed_time(ev[2]))
@@ -354,11 +360,20 @@ def run_ours(args, rank, world, local_rank):
         kernels[cls] = {"kernel": label, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                         "frac": ach / hbm, "launches": cnt, "avg_launch_us": 1e3 * ms / cnt,
                         "alg_bytes_per_launch": alg / cnt, "traffic": measured_traffic(cls)}
+    ms, cnt = ktimes["factor"]
+    if cnt and ms > 0 and flops_factor > 0:
+        fp32_peak = fp32_simt_tflops(sm_max)
+        ach = flops_factor / (ms / 1e3) / 1e12
+        kernels["factor"] = {"kernel": "L^w inverse, symmetric block sweep (k_fac_*)", "bound": "alu",
+                             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                             "launches": cnt, "avg_launch_us": 1e3 * ms / cnt,
+                             "alg_flops_per_launch": flops_factor / cnt, "traffic": measured_traffic("factor"),
+                             "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x max SM clock"}
     share = {c: {"ms": ktimes[c][0] / args.steps, "launches": ktimes[c][1] // max(1, args.steps)}
              for c in ktimes if ktimes[c][1]}
     dom = max(kernels, key=lambda c: ktimes[c][0]) if kernels else None
     roof = dict(kernels[dom]) if dom else None
-    if roof is not None:
+    if roof is not None and roof["bound"] == "hbm":
         roof["peak_kind"] = f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

@@ -86,6 +86,9 @@ typedef struct pprviz_stats {
     double bytes_sweep;
     double bytes_ly;
     double bytes_apply;
+    /* Algorithmic FP flops of the L^w inverse (symmetric block sweep: pivot
+     * inverses, panels and the upper-triangle trailing updates). */
+    double flops_factor;
 } pprviz_stats;
 
 /* Kernel classes for per-class device timing (pprviz_profile). */
@@ -154,6 +157,8 @@ int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out
  *            iteration for the a-priori sweep count; the FP32 path runs
  *            Chebyshev sweeps and FP32 refinement passes until every source
  *            has cert(s) <= eps, or returns E_NOT_CONVERGED after 6 passes.
+ *            The FP32 path keeps each row as an exact sum of two floats, so it
+ *            certifies down to about d(s) * 1e-13; tighter eps needs PPRVIZ_FP64.
  *            Through Eq. (1) the certificates bound the PDist error too:
  *            |dDelta_ij| <= (c_i + c_j) / max(z_ij - c_i - c_j, e / n_clamp^2).
  * precision: PPRVIZ_FP64 or PPRVIZ_FP32.

@@ -63,7 +63,8 @@ class pprviz_stats(C.Structure):
     _fields_ = [("groups", C.c_int32), ("sweeps_main", C.c_int32), ("sweeps_refine", C.c_int32),
                 ("refine_passes", C.c_int32), ("residual_passes", C.c_int32), ("kernel_launches", C.c_int32),
                 ("max_cert", C.c_double), ("layout_iters", C.c_int32), ("source_group", C.c_int32),
-                ("bytes_sweep", C.c_double), ("bytes_ly", C.c_double), ("bytes_apply", C.c_double)]
+                ("bytes_sweep", C.c_double), ("bytes_ly", C.c_double), ("bytes_apply", C.c_double),
+                ("flops_factor", C.c_double)]
 
 
 _lib = None

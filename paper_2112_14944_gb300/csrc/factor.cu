@@ -139,15 +139,29 @@ k_fac_trailing(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ 
 #pragma unroll
       for (int c = 0; c < R; ++c) acc[r][c] += a[r] * b[c];
   }
+  // Epilogue: each row's SUB consecutive columns are one aligned vector; the
+  // masks (pivot block, lower blocks, kp) are uniform over it since blocks are
+  // 64-aligned and kp is a multiple of 128.
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i = I0 + (r / SUB) * HALF + ty * SUB + (r % SUB);
     if (i >= kp || (i >= K0 && i < K0 + FNB)) continue;
 #pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const int j = J0 + (c / SUB) * HALF + tx * SUB + (c % SUB);
+    for (int h = 0; h < 2; ++h) {
+      const int j = J0 + h * HALF + tx * SUB;
       if (j >= kp || (j >= K0 && j < K0 + FNB) || (i / FNB) > (j / FNB)) continue;
-      A[(int64_t)i * kp + j] -= acc[r][c];
+      T *p = A + (int64_t)i * kp + j;
+      if constexpr (sizeof(T) == 4 && SUB == 4) {
+        float4 v = *reinterpret_cast<float4 *>(p);
+        v.x -= acc[r][h * SUB + 0];
+        v.y -= acc[r][h * SUB + 1];
+        v.z -= acc[r][h * SUB + 2];
+        v.w -= acc[r][h * SUB + 3];
+        *reinterpret_cast<float4 *>(p) = v;
+      } else {
+#pragma unroll
+        for (int s = 0; s < SUB; ++s) p[s] -= acc[r][h * SUB + s];
+      }
     }
   }
 }
@@ -178,6 +192,11 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
                                         (int)trail_smem));
   const int nblk = kp / FNB;
   const unsigned tgrid = (unsigned)((kp + TM - 1) / TM);
+  // per pivot: the 64^3 pivot inverse, (nblk - 1) panel products of 2 * 64^3,
+  // and 2 * 64 flops for each of the (nblk - 1) nblk / 2 upper blocks of 64^2
+  const double b3 = (double)FNB * FNB * FNB;
+  const double nm1 = (double)(nblk - 1);
+  ctx->stats.flops_factor += (double)nblk * (2.0 * b3 + nm1 * 2.0 * b3 + nm1 * (nm1 + 1.0) / 2.0 * 2.0 * b3);
   for (int kb = 0; kb < nblk; ++kb) {
     const int K0 = kb * FNB;
     { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag<T><<<1, 512, diag_smem, ctx->stream>>>(kp, K0, A, P); }

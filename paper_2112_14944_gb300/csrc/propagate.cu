@@ -92,6 +92,19 @@ __global__ void k_axpy(int64_t count, const float *__restrict__ x, float *__rest
   if (idx < count) y[idx] += x[idx];
 }
 
+// Exact renormalisation of the two-float state: hi + lo is replaced by
+// s = fl(hi + lo) and the exact remainder lo - (s - hi) (Fast2Sum, Dekker
+// 1971; |hi| >= |lo| holds since lo is a correction of hi). Afterwards
+// |lo| <= ulp(hi) / 2, so later corrections keep ~48 significant bits.
+__global__ void k_renorm(int64_t count, float *__restrict__ hi, float *__restrict__ lo) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const float h = hi[idx], l = lo[idx];
+  const float s = h + l;
+  hi[idx] = s;
+  lo[idx] = l - (s - h);
+}
+
 // One sweep for the rows of a group.  For each node j and source column q:
 //   acc  = sum_{i in N(j)} w_ij y_cur[i][q]   (+ y_cur[j][q] if j has no edges)
 //   xnew = (b_jq + c * acc) / dw(j)           (y-scaled next iterate)
@@ -590,6 +603,11 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         } else {
           const int64_t cnt = g->n * ld;
           { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_axpy<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, delta, lo); }
+          PPRVIZ_LAUNCHED(ctx);
+        }
+        {
+          const int64_t cnt = g->n * ld;
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_renorm<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, hi, lo); }
           PPRVIZ_LAUNCHED(ctx);
         }
         PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)

@@ -220,18 +220,20 @@ def test_fp32_multiple_groups_ragged_tail(ctx):
 
 
 def test_tight_eps_gives_flat_pdist_gate(ctx):
-    """With eps = 1e-12 the certified PDist bound is below 1e-5 for every entry
-    above the clamp threshold, so the flat 1e-5 gate holds (FP32 refinement
-    passes continue on the x_hi + x_lo representation)."""
+    """With a tight eps the certified PDist bound falls below 1e-5 for every
+    entry above the clamp threshold, so the flat 1e-5 gate holds. The FP32
+    path refines on the renormalised x_hi + x_lo pair (certifiable to about
+    d_max * 1e-13); the FP64 path reaches 1e-12 directly."""
     import paper_2112_14944_gb300 as P
     for g in (synth.sbm([40, 50, 60, 7], 0.1, 0.004, seed=12), synth.chung_lu(500, 10, 2.5, seed=13)):
         G = ctx.upload_graph(g)
         view = np.arange(g.n, dtype=np.int32)
         Dref, _ = _oracle(g, view, direct=True)
-        D, Delta, cert, st = ctx.dppr(G, view, ALPHA, 1e-12, P.FP32)
-        assert st == 0 and cert.max() <= 1e-12
-        _check_dppr(D, Dref, tol=2e-7)
-        _check_pdist_flat(Delta, O.pdist_from_dppr(Dref, g.n), tol=1e-5)
+        for prec, eps in ((P.FP32, 1e-11), (P.FP64, 1e-12)):
+            D, Delta, cert, st = ctx.dppr(G, view, ALPHA, eps, prec)
+            assert st == 0 and cert.max() <= eps
+            _check_dppr(D, Dref, tol=2e-7)
+            _check_pdist_flat(Delta, O.pdist_from_dppr(Dref, g.n), tol=1e-5)
 
 
 def test_full_size_chung_lu_10k_fp32_sampled(ctx):
