@@ -156,17 +156,23 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- traffic
-def kernel_source_hash(files):
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, "paper_2112_14944_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+def kernel_source_hash(src):
+    """sha256 prefix of one kernel's source text: the part of `file` from the
+    first occurrence of `begin` up to the next occurrence of `end`."""
+    with open(os.path.join(ROOT, "paper_2112_14944_gb300", "csrc", src["file"])) as fh:
+        text = fh.read()
+    a = text.find(src["begin"])
+    if a < 0:
+        return None
+    b = text.find(src["end"], a + len(src["begin"]))
+    body = text[a:b if b > a else len(text)]
+    return hashlib.sha256(body.encode()).hexdigest()[:16]
 
 
 def measured_traffic(cls):
-    """DRAM bytes per launch of a kernel class from a committed ncu summary,
-    or None when absent or taken on a different version of the kernel source."""
+    """DRAM bytes per launch of a kernel class from the committed ncu summary
+    (profiles/traffic.json), or None when absent or when the kernel's source
+    text has changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -174,9 +180,9 @@ def measured_traffic(cls):
         d = json.load(f).get(cls)
     if not d:
         return None
-    if d.get("source_hash") != kernel_source_hash(d.get("files", [])):
+    if d.get("source_hash") != kernel_source_hash(d["src"]):
         return None
-    return d.get("dram_bytes_per_launch_full")
+    return d.get("dram_bytes_per_launch")
 
 
 # --------------------------------------------------------------------------- reference arm
