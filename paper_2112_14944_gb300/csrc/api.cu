@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -453,63 +454,73 @@ int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *cons
   if (!(alpha > 0.0 && alpha < 1.0) || !(eps > 0.0))
     return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1) and eps > 0");
   const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
-  int64_t sq_off = 0;
-  pprviz_stats total{};
-  int status = PPRVIZ_OK;
+  std::vector<int64_t> ks((size_t)nviews);
+  int64_t sq_total = 0, maxk = 0;
   for (int32_t v = 0; v < nviews; ++v) {
     const pprviz_graph *g = views[v];
     if (!g) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "NULL view graph");
     const int64_t nv = offsets[v + 1] - offsets[v];
-    if (nv != g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "offsets do not match the view sizes");
-    const int32_t k = (int32_t)nv;
-    std::vector<int32_t> view_h((size_t)k);
-    for (int32_t q = 0; q < k; ++q) view_h[q] = q;
-    PPRVIZ_TRY(ws_ensure(ctx, WS_VIEW, sizeof(int32_t) * (size_t)k));
-    int32_t *view_d = ctx->ws[WS_VIEW].as<int32_t>();
-    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_d, view_h.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, ctx->stream));
-    const size_t kk = (size_t)k * k;
-    PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, sizeof(float) * kk));
-    float *dppr_d = ctx->ws[WS_DPPR].as<float>();
-    float *pdist_d;
-    if (dev && pdist_packed) pdist_d = pdist_packed + sq_off;
-    else {
-      PPRVIZ_TRY(ws_ensure(ctx, WS_PDIST, sizeof(float) * kk));
-      pdist_d = ctx->ws[WS_PDIST].as<float>();
-    }
-    int s = dppr_solve(ctx, g, view_d, view_h, k, alpha, eps, PPRVIZ_FP32, dppr_d, false, nullptr);
+    if (nv != g->n || offsets[v] < 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "offsets do not match the view sizes");
+    ks[v] = nv;
+    sq_total += nv * nv;
+    maxk = std::max(maxk, nv);
+  }
+  const int64_t ntot = offsets[nviews];
+  // packed device buffers: all PDists, initial and final coordinates
+  float *pdist_all = nullptr, *x0_all = nullptr, *x_all = nullptr;
+  if (dev && pdist_packed) pdist_all = pdist_packed;
+  else {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_BPD, sizeof(float) * (size_t)sq_total));
+    pdist_all = ctx->ws[WS_BPD].as<float>();
+  }
+  const void *x0p = nullptr;
+  PPRVIZ_TRY(stage_in(ctx, x0_packed, sizeof(float) * 2 * (size_t)ntot, dev, WS_BXIN, &x0p));
+  x0_all = (float *)x0p;
+  if (dev) x_all = x_packed;
+  else {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_BXOUT, sizeof(float) * 2 * (size_t)ntot));
+    x_all = ctx->ws[WS_BXOUT].as<float>();
+  }
+  // DPPR and PDist view by view (each view's propagation fills the GPU)
+  PPRVIZ_TRY(ws_ensure(ctx, WS_VIEW, sizeof(int32_t) * (size_t)maxk));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, sizeof(float) * (size_t)maxk * maxk));
+  int32_t *view_d = ctx->ws[WS_VIEW].as<int32_t>();
+  float *dppr_d = ctx->ws[WS_DPPR].as<float>();
+  std::vector<int32_t> iota((size_t)maxk);
+  for (int64_t q = 0; q < maxk; ++q) iota[q] = (int32_t)q;
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_d, iota.data(), sizeof(int32_t) * maxk, cudaMemcpyHostToDevice, ctx->stream));
+  int status = PPRVIZ_OK;
+  pprviz_stats acc{};
+  int64_t sq_off = 0;
+  for (int32_t v = 0; v < nviews; ++v) {
+    const int32_t k = (int32_t)ks[v];
+    std::vector<int32_t> view_h(iota.begin(), iota.begin() + k);
+    int s = dppr_solve(ctx, views[v], view_d, view_h, k, alpha, eps, PPRVIZ_FP32, dppr_d, false, nullptr);
     if (s == PPRVIZ_E_NOT_CONVERGED) status = s;
     else if (s != PPRVIZ_OK) return finish(ctx, s);
-    PPRVIZ_TRY(pdist_launch(ctx, dppr_d, k, g->n, pdist_d, false));
-    const float *x0_d = nullptr;
-    if (dev) x0_d = x0_packed + 2 * offsets[v];
-    else {
-      PPRVIZ_TRY(ws_ensure(ctx, WS_IN1, sizeof(float) * 2 * k));
-      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ctx->ws[WS_IN1].p, x0_packed + 2 * offsets[v], sizeof(float) * 2 * k,
-                                       cudaMemcpyHostToDevice, ctx->stream));
-      x0_d = ctx->ws[WS_IN1].as<float>();
-    }
-    float *xo = dev ? x_packed + 2 * offsets[v] : nullptr;
-    if (!dev) {
-      PPRVIZ_TRY(ws_ensure(ctx, WS_OUT0, sizeof(float) * 2 * k));
-      xo = ctx->ws[WS_OUT0].as<float>();
-    }
-    double st = 0.0;
-    const pprviz_stats before = ctx->stats;
-    s = layout_run(ctx, pdist_d, k, x0_d, iters, PPRVIZ_FP32, false, xo, stress_out ? &st : nullptr);
-    if (s != PPRVIZ_OK) return finish(ctx, s);
-    if (stress_out) stress_out[v] = st;
-    (void)before;
-    if (!dev) {
-      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(x_packed + 2 * offsets[v], xo, sizeof(float) * 2 * k, cudaMemcpyDeviceToHost,
-                                       ctx->stream));
-      if (pdist_packed)
-        PPRVIZ_CUDA(ctx, cudaMemcpyAsync(pdist_packed + sq_off, pdist_d, sizeof(float) * kk, cudaMemcpyDeviceToHost,
-                                         ctx->stream));
-      PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    }
-    sq_off += (int64_t)kk;
+    PPRVIZ_TRY(pdist_launch(ctx, dppr_d, k, k, pdist_all + sq_off, false));
+    sq_off += (int64_t)k * k;
   }
-  (void)total;
+  acc = ctx->stats;
+  // all layouts together: one launch per pass over every view's tiles
+  int s = layout_batch_run(ctx, nviews, ks.data(), pdist_all, x0_all, iters, x_all, stress_out);
+  if (s != PPRVIZ_OK) return finish(ctx, s);
+  ctx->stats.groups = acc.groups;
+  ctx->stats.sweeps_main = acc.sweeps_main;
+  ctx->stats.sweeps_refine = acc.sweeps_refine;
+  ctx->stats.refine_passes = acc.refine_passes;
+  ctx->stats.residual_passes = acc.residual_passes;
+  ctx->stats.max_cert = acc.max_cert;
+  ctx->stats.bytes_sweep = acc.bytes_sweep;
+  if (!dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(x_packed, x_all, sizeof(float) * 2 * (size_t)ntot, cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    if (pdist_packed)
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(pdist_packed, pdist_all, sizeof(float) * (size_t)sq_total,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (status != PPRVIZ_OK) ctx->err = "a view's certificate stayed above eps after the refinement cap";
   return finish(ctx, status);
 }
 

@@ -38,7 +38,10 @@ struct DevBuf {
 enum Slot {
   WS_VIEW = 0, WS_SRC, WS_Y0, WS_Y1, WS_Y2, WS_Y3, WS_RHS, WS_CERT, WS_FLAG,
   WS_DPPR, WS_PDIST, WS_IN0, WS_IN1, WS_OUT0, WS_OUT1, WS_W1, WS_M, WS_PIV,
-  WS_B, WS_X, WS_E, WS_MISC, WS_COUNT
+  WS_B, WS_X, WS_E, WS_MISC,
+  // batched views
+  WS_BW1, WS_BM, WS_BX, WS_BPART, WS_BTAB, WS_BPD, WS_BXIN, WS_BXOUT,
+  WS_COUNT
 };
 
 }  // namespace pprviz
@@ -126,13 +129,19 @@ int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp
 // ---- factor (factor.cu) ----------------------------------------------------
 // In-place inverse of the SPD kp x kp matrix A (kp % 128 == 0); on return A
 // holds A^-1 on its upper 64-block triangle and on the 128 x 128 diagonal tiles.
-// `work` holds 2 * 64 * kp + 64 * 64 elements.
+// `work` holds 2 * 64 * kp + 64 * 64 + 64 elements (the last 64 hold a status
+// word). The FP32 version runs its trailing updates on the tensor cores and
+// returns PPRVIZ_E_TIMEOUT if an MMA completion wait expires.
 int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work);
 int spd_inverse_f64(pprviz_ctx *ctx, int32_t kp, double *A, double *work);
 
 // ---- layout (layout.cu) ----------------------------------------------------
 int layout_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x0_d, int32_t iters,
                int precision, bool io64, void *x_out_d, double *stress_h);
+// FP32 layouts of many views: pdist_d packs the k_v x k_v matrices in order,
+// x0_d / x_out_d the k_v x 2 coordinates; stress_h gets one value per view.
+int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const float *pdist_d,
+                     const float *x0_d, int32_t iters, float *x_out_d, double *stress_h);
 int energy_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x_d, double scale,
                bool f64, double *e_h, void *grad_x_d, void *grad_pdist_d);
 

@@ -148,13 +148,11 @@ __device__ __forceinline__ T lanes_transpose_sum(T (&v)[NV], int lane) {
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
-k_sympass(int32_t kp, const T *__restrict__ Mat, const typename T2<T>::type *__restrict__ V,
-          typename T2<T>::type *__restrict__ Part) {
+__device__ __forceinline__ void sympass_tile(const int I, const int J, int32_t kp, const T *__restrict__ Mat,
+                                             const typename T2<T>::type *__restrict__ V,
+                                             typename T2<T>::type *__restrict__ Part) {
   using V2 = typename T2<T>::type;
   constexpr int NV = 2 * SRPI;
-  const int I = blockIdx.y, J = blockIdx.x;
-  if (J < I) return;
   __shared__ V2 sVi[ST];
   __shared__ T colred[8][2 * ST];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -222,6 +220,51 @@ k_sympass(int32_t kp, const T *__restrict__ Mat, const typename T2<T>::type *__r
     for (int w = 0; w < 8; ++w) s += colred[w][threadIdx.x];
     part[((int64_t)I * kp + j0) * 2 + threadIdx.x] = s;
   }
+}
+
+// One view: block (J, I) of the tile grid; lower tiles exit at once.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+k_sympass(int32_t kp, const T *__restrict__ Mat, const typename T2<T>::type *__restrict__ V,
+          typename T2<T>::type *__restrict__ Part) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J < I) return;
+  sympass_tile<T, MODE>(I, J, kp, Mat, V, Part);
+}
+
+// Many views in one launch: block b takes tile tiles[b] = (view, I, J) and the
+// view's matrix, vector and partial-sum slices from its descriptor.
+struct BatchView {
+  int64_t mat_off;   // elements into the batched kp x kp matrices
+  int64_t vec_off;   // 2-vectors into the batched coordinate / b vectors (kp each)
+  int64_t part_off;  // 2-vectors into the batched partial sums (nbt x kp each)
+  int32_t kp, nbt, k, pad;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+k_sympass_batch(const int4 *__restrict__ tiles, const BatchView *__restrict__ views, const T *__restrict__ Mat,
+                const typename T2<T>::type *__restrict__ V, typename T2<T>::type *__restrict__ Part) {
+  const int4 t = tiles[blockIdx.x];
+  const BatchView bv = views[t.x];
+  sympass_tile<T, MODE>(t.y, t.z, bv.kp, Mat + bv.mat_off, V + bv.vec_off, Part + bv.part_off);
+}
+
+// V[row] = sum_{o < nbt} Part[o][row] for every view (blockIdx.y) in order.
+template <typename T>
+__global__ void k_reduce_parts_batch(const BatchView *__restrict__ views, const typename T2<T>::type *__restrict__ Part,
+                                     typename T2<T>::type *__restrict__ V) {
+  const BatchView bv = views[blockIdx.y];
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= bv.kp) return;
+  const typename T2<T>::type *p = Part + bv.part_off;
+  typename T2<T>::type s = p[r];
+  for (int o = 1; o < bv.nbt; ++o) {
+    const typename T2<T>::type u = p[(int64_t)o * bv.kp + r];
+    s.x += u.x;
+    s.y += u.y;
+  }
+  V[bv.vec_off + r] = s;
 }
 
 // V[row] = sum_{o < nb} Part[o][row], in order.
@@ -405,7 +448,7 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
   const int nbt = kp / ST;
   PPRVIZ_TRY(ws_ensure(ctx, WS_W1, sizeof(T) * (size_t)kp * kp));
   PPRVIZ_TRY(ws_ensure(ctx, WS_M, sizeof(T) * (size_t)kp * kp));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(T) * (size_t)(2 * NB * kp + NB * NB)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(T) * (size_t)(2 * NB * kp + NB * NB + 64)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_X, sizeof(V2) * (size_t)kp * 2));            // X and b
   PPRVIZ_TRY(ws_ensure(ctx, WS_B, sizeof(V2) * (size_t)nbt * kp));          // partial sums
   PPRVIZ_TRY(ws_ensure(ctx, WS_E, sizeof(V2) * (size_t)k + 64));
@@ -490,6 +533,116 @@ int layout_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x0_d
                                                (double *)x_out_d, stress_h);
   return layout_typed<float, float, float>(ctx, (const float *)pdist_d, k, (const float *)x0_d, iters,
                                            (float *)x_out_d, stress_h);
+}
+
+// Many views, FP32: each view's 1/Delta_s and (L^w + J/k)^-1 are built and
+// inverted into slices of two batched matrices, then every update runs as four
+// launches over all views together (L^Y pass, reduce, apply pass, reduce).
+int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const float *pdist_d,
+                     const float *x0_d, int32_t iters, float *x_out_d, double *stress_h) {
+  using V2 = float2;
+  std::vector<BatchView> bv((size_t)nviews);
+  std::vector<int4> tiles;
+  int64_t mat = 0, vec = 0, part = 0, maxkp = 0;
+  for (int32_t v = 0; v < nviews; ++v) {
+    const int32_t k = (int32_t)k_h[v];
+    const int32_t kp = (k + ST - 1) / ST * ST, nbt = kp / ST;
+    bv[v] = BatchView{mat, vec, part, kp, nbt, k, 0};
+    mat += (int64_t)kp * kp;
+    vec += kp;
+    part += (int64_t)nbt * kp;
+    maxkp = std::max<int64_t>(maxkp, kp);
+    for (int I = 0; I < nbt; ++I)
+      for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(v, I, J, 0));
+  }
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BW1, sizeof(float) * (size_t)mat));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BM, sizeof(float) * (size_t)mat));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BX, sizeof(V2) * (size_t)vec * 2));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BPART, sizeof(V2) * (size_t)part));
+  // the tile table (int4, 16-byte loads) starts at a 256-byte boundary after the descriptors
+  const size_t tab_off = (sizeof(BatchView) * (size_t)nviews + 255) & ~(size_t)255;
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BTAB, tab_off + sizeof(int4) * tiles.size()));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(float) * (size_t)(2 * NB * maxkp + NB * NB + 64)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sizeof(double) * (size_t)(maxkp / 32) * maxkp));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_FLAG, 64));
+  float *W1 = ctx->ws[WS_BW1].as<float>(), *M = ctx->ws[WS_BM].as<float>(), *work = ctx->ws[WS_PIV].as<float>();
+  V2 *X = ctx->ws[WS_BX].as<V2>(), *Bv = X + vec, *Part = ctx->ws[WS_BPART].as<V2>();
+  BatchView *views_d = reinterpret_cast<BatchView *>(ctx->ws[WS_BTAB].p);
+  int4 *tiles_d = reinterpret_cast<int4 *>(static_cast<unsigned char *>(ctx->ws[WS_BTAB].p) + tab_off);
+  double *rowpart = ctx->ws[WS_RHS].as<double>();
+  int *flag = ctx->ws[WS_FLAG].as<int>();
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(views_d, bv.data(), sizeof(BatchView) * bv.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(tiles_d, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  int64_t sq = 0, xo = 0;
+  for (int32_t v = 0; v < nviews; ++v) {
+    const int32_t k = bv[v].k, kp = bv[v].kp;
+    const float *Dv = pdist_d + sq;
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_build_sym<float, float><<<dim3(kp / 32, kp / 32), dim3(32, 8), 0, ctx->stream>>>(k, kp, Dv, W1 + bv[v].mat_off, M + bv[v].mat_off, rowpart, flag); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_build_diag<float><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(k, kp, rowpart, M + bv[v].mat_off); }
+    PPRVIZ_LAUNCHED(ctx);
+    if (iters > 0) PPRVIZ_TRY(spd_inverse_f32(ctx, kp, M + bv[v].mat_off, work));
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<float, float><<<(unsigned)((kp + 255) / 256), 256, 0, ctx->stream>>>(k, kp, x0_d + 2 * xo, X + bv[v].vec_off); }
+    PPRVIZ_LAUNCHED(ctx);
+    sq += (int64_t)k * k;
+    xo += k;
+  }
+  int hf = 0;
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hf) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "a view's pdist has a non-finite or non-positive entry");
+  const unsigned ntile = (unsigned)tiles.size();
+  const dim3 rgrid((unsigned)((maxkp + 255) / 256), (unsigned)nviews);
+  for (int it = 0; it < iters; ++it) {
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<float, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, W1, X, Part); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, Bv); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<float, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, M, Bv, Part); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, X); }
+    PPRVIZ_LAUNCHED(ctx);
+  }
+  ctx->stats.layout_iters = iters;
+  double half = 0.0;
+  for (int32_t v = 0; v < nviews; ++v) half += 0.5 * (double)bv[v].k * ((double)bv[v].k + 1.0) * sizeof(float);
+  ctx->stats.bytes_ly = half * iters;
+  ctx->stats.bytes_apply = half * iters;
+  // centre and emit each view; stress per view on its input pdist
+  int64_t maxk = 0;
+  for (int32_t v = 0; v < nviews; ++v) maxk = std::max<int64_t>(maxk, bv[v].k);
+  const unsigned eb_max = (unsigned)((maxk + LWARPS * RPW - 1) / (LWARPS * RPW));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_E, sizeof(V2) * (size_t)maxk + 64));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_OUT1, sizeof(double) * ((size_t)eb_max + 1) * nviews));
+  V2 *Xc = ctx->ws[WS_E].as<V2>();
+  double *ep = ctx->ws[WS_OUT1].as<double>();
+  sq = 0;
+  xo = 0;
+  for (int32_t v = 0; v < nviews; ++v) {
+    const int32_t k = bv[v].k;
+    const unsigned eb = (unsigned)((k + LWARPS * RPW - 1) / (LWARPS * RPW));
+    double *epv = ep + (size_t)v * (eb_max + 1);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_finish<float, float><<<1, 1024, 0, ctx->stream>>>(k, X + bv[v].vec_off, x_out_d + 2 * xo, Xc); }
+    PPRVIZ_LAUNCHED(ctx);
+    if (stress_h) {
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_energy<float, false, false><<<eb, LWARPS * 32, 0, ctx->stream>>>(k, pdist_d + sq, Xc, 1.0f, epv, nullptr, nullptr, flag); }
+      PPRVIZ_LAUNCHED(ctx);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_reduce_energy<<<1, 256, 0, ctx->stream>>>((int)eb, epv, epv + eb_max); }
+      PPRVIZ_LAUNCHED(ctx);
+    }
+    sq += (int64_t)k * k;
+    xo += k;
+  }
+  if (stress_h) {
+    std::vector<double> eh((size_t)(eb_max + 1) * nviews);
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(eh.data(), ep, sizeof(double) * eh.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int32_t v = 0; v < nviews; ++v) stress_h[v] = eh[(size_t)v * (eb_max + 1) + eb_max];
+  }
+  return PPRVIZ_OK;
 }
 
 template <typename T>

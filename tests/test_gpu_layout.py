@@ -183,3 +183,29 @@ def test_views_batch_matches_single_views(ctx):
         assert np.array_equal(X1, xb[off[v]:off[v + 1]])
         assert s1 == stress[v]
         sq += n * n
+
+
+def test_views_batch_sbm_sample_of_the_batched_workload(ctx):
+    """16 SBM views (sizes 50..1500, 4..16 blocks, p_in 0.1, p_out 0.002): the
+    batched workload at reduced size. Every view's layout equals a single-view
+    run bit for bit; sampled views' PDist match the oracle under the certified
+    gate; the final stresses equal the single-view stresses."""
+    import paper_2112_14944_gb300 as P
+    graphs = synth.sbm_views(16, seed=5, n_min=50, n_max=1500)
+    G = [ctx.upload_graph(g) for g in graphs]
+    x0 = np.concatenate([synth.uniform_x0(g.n, seed=100 + i) for i, g in enumerate(graphs)])
+    xb, pdb, stress, off = ctx.views_batch(G, x0, ALPHA, 1e-6, 200, want_pdist=True)
+    sq = np.concatenate([[0], np.cumsum([g.n * g.n for g in graphs])])
+    big = int(np.argmax([g.n for g in graphs]))
+    for v in sorted({0, big, len(graphs) - 1}):
+        g, n = graphs[v], graphs[v].n
+        Pd = pdb[sq[v]:sq[v + 1]].reshape(n, n)
+        _, Pd1, cert, _ = ctx.dppr(G[v], np.arange(n, dtype=np.int32), ALPHA, 1e-6, P.FP32)
+        assert np.array_equal(Pd, Pd1)
+        Dref = O.dppr_rows(O.ppr_direct(O.transition_matrix(n, g.row_ptr, g.col), ALPHA),
+                           O.degrees(n, g.row_ptr, g.col), np.arange(n))
+        check_pdist(Pd1, Dref, cert, n)
+    for v, g in enumerate(graphs):
+        X1, s1 = ctx.layout(pdb[sq[v]:sq[v + 1]].reshape(g.n, g.n).copy(), x0[off[v]:off[v + 1]].copy(), 200, P.FP32)
+        assert np.array_equal(X1, xb[off[v]:off[v + 1]])
+        assert s1 == stress[v]
