@@ -355,8 +355,8 @@ def run_ours(args, rank, world, local_rank):
         return
     hbm, sm_max, peak_kind = peaks()
     names = {"sweep": ("propagation sweep (k_sweep)", bytes_sweep),
-             "ly": ("all-pairs L^Y pass (k_pairpass<0>)", bytes_ly),
-             "apply": ("(L^w)^+ apply pass (k_pairpass<1>)", bytes_apply)}
+             "ly": ("all-pairs L^Y pass (k_sympass<0> + partial reduce)", bytes_ly),
+             "apply": ("(L^w)^+ apply pass (k_sympass<1> + partial reduce)", bytes_apply)}
     kernels = {}
     for cls, (label, alg) in names.items():
         ms, cnt = ktimes[cls]

@@ -479,11 +479,11 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
   for (int it = 0; it < iters; ++it) {
     { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass<T, 0><<<grid, 256, 0, ctx->stream>>>(kp, W1, X, Part); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, Bv); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, Bv); }
     PPRVIZ_LAUNCHED(ctx);
     { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass<T, 1><<<grid, 256, 0, ctx->stream>>>(kp, A, Bv, Part); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, X); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, X); }
     PPRVIZ_LAUNCHED(ctx);
   }
   V2 *Xc = ctx->ws[WS_E].as<V2>();
@@ -599,11 +599,11 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   for (int it = 0; it < iters; ++it) {
     { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<float, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, W1, X, Part); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, Bv); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, Bv); }
     PPRVIZ_LAUNCHED(ctx);
     { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<float, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, M, Bv, Part); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, X); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, X); }
     PPRVIZ_LAUNCHED(ctx);
   }
   ctx->stats.layout_iters = iters;
