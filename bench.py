@@ -14,6 +14,13 @@ DPPR, PDist, X out), copies inside the timed region.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm of this benchmark).
+
+`--workload dense` measures the dense-view propagation instead (not the
+default line): a dense clustered weighted view, n = 20,000, 20 blocks, 15 %
+density, lognormal(0, 1) weights, all nodes as the view; one step = all-pairs
+DPPR + PDist with the FP64 certificate, every sweep a 3xTF32 tensor-core
+contraction; the roofline is the tensor pipe's (TF32 peak = measured BF16
+peak x the nominal TF32/BF16 ratio 1.1/2.25).
 """
 from __future__ import annotations
 
@@ -44,13 +51,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--n", type=int, default=None, help="nodes (default 10000; 20000 with --workload dense)")
     ap.add_argument("--deg", type=float, default=20.0)
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", action="store_true",
                     help="one untimed pass of the hot path (for profiler command lines)")
+    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense"],
+                    help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000)")
     return ap.parse_args()
 
 
@@ -58,6 +67,9 @@ def run_case(args):
     """One pass of the hot path on the workload, untimed: ingest, FP32 DPPR +
     PDist with certificate, `--iters` layout updates, energy with gradient."""
     import torch
+    if args.workload == "dense":
+        run_dense_case(args)
+        return
 
     import paper_2112_14944_gb300 as P
     import synth
@@ -227,6 +239,125 @@ def run_reference(args, rank, world):
                          "sample": f"{n_src} seeded sources per step: DPPR rows and PDist rows by FP64 power "
                                    f"iteration to (1-alpha)^(t+1) <= 1e-15"},
         "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- dense views
+DENSE_WORKLOAD = "dense_clustered_weighted_n20000_d15"
+
+
+def dense_graph(n):
+    import synth
+    return synth.dense_clustered(n, blocks=20, density=0.15, seed=0)
+
+
+def run_dense_case(args):
+    """One untimed all-pairs DPPR + PDist on the dense weighted view."""
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    n = args.n
+    g = dense_graph(n)
+    ctx = P.Context(0, torch_stream=True)
+    dev = torch.device("cuda", 0)
+    G = ctx.upload(n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                   torch.from_numpy(g.weight).to(dev))
+    view = torch.arange(n, dtype=torch.int32, device=dev)
+    D = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Dl = torch.empty_like(D)
+    _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": DENSE_WORKLOAD, "n": n, "nnz": int(g.nnz), "status": status,
+                      "max_cert": float(cert.max()), "dppr_stats": ctx.stats()}))
+
+
+def run_dense(args, rank, world, local_rank):
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    g = dense_graph(n)
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    w = torch.from_numpy(g.weight).to(dev)
+    view = torch.arange(n, dtype=torch.int32, device=dev)
+    D = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Dl = torch.empty_like(D)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    G = ctx.upload(n, rp, col, w)
+
+    def step():
+        _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
+        assert status == 0 and cert.max() <= EPS, (status, cert.max())
+        return ctx.stats()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, flops, launches, sweeps, stats = [], 0.0, 0, 0, None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        flops += stats["flops_dense"]
+        launches += stats["kernel_launches"]
+        sweeps += stats["sweeps_main"] + stats["sweeps_refine"]
+    torch.cuda.synchronize()
+    sampler.stop()
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    total = sum(ms)
+    if world > 1:
+        t = torch.tensor([total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    if rank != 0:
+        return
+    entries = float(n) * n
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16, kind = 1900.0, "fallback"
+    if os.path.exists(pk):
+        with open(pk) as f:
+            bf16, kind = json.load(f)["bf16_tflops"], "measured"
+    tf32 = bf16 * 1.1 / 2.25
+    sw_ms, sw_n = ktimes["sweep"]
+    ach = flops / (sw_ms / 1e3) / 1e12
+    roof = {"kernel": "tensor-core sweep (k_dsweep_tc, 3xTF32 tcgen05.mma)", "bound": "tensor",
+            "achieved": ach, "peak": tf32, "unit": "TFLOP/s", "frac": ach / tf32,
+            "executed_tflops": 3 * ach, "executed_frac": 3 * ach / tf32,
+            "launches": sw_n, "avg_launch_us": 1e3 * sw_ms / max(1, sw_n),
+            "alg_flops_per_launch": flops / max(1, sw_n), "traffic": measured_traffic("dsweep"),
+            "peak_kind": f"{kind} bf16_tflops x 1.1/2.25 (nominal TF32/BF16), frac of {kind}"}
+    share = {c: {"ms": ktimes[c][0] / args.steps, "launches": ktimes[c][1] // max(1, args.steps)}
+             for c in ktimes if ktimes[c][1]}
+    line = {
+        "metric": "DPPR entries/s, dense weighted view n=20k, err<=1e-6 vs FP64 (tensor-core sweeps)",
+        "value": world * args.steps * entries / (total / 1e3), "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3/f32/f64", "data": "synthetic",
+        "config": {"workload": DENSE_WORKLOAD, "graph": "dense clustered SBM, lognormal(0,1) weights", "n": n,
+                   "nnz": int(g.nnz), "blocks": 20, "density": 0.15, "seed": 0, "view": "all nodes (k = n)",
+                   "alpha": ALPHA, "eps": EPS,
+                   "propagation": "fp32 chebyshev on 3xTF32 tensor-core sweeps + fp64 residual + refinement",
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "sweeps_per_step": sweeps / args.steps, "max_cert": stats["max_cert"] if stats else None,
+        "roofline": roof, "kernel_share": share, "gpu_launches": int(launches), "clocks": sampler.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -405,6 +536,8 @@ def run_ours(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.n is None:
+        args.n = 20000 if args.workload == "dense" else 10000
     if args.case:
         run_case(args)
         return
@@ -417,6 +550,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "dense":
+        run_dense(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

@@ -61,7 +61,14 @@ extern "C" {
 
 /* propagation precision (pprviz_dppr) and layout precision (pprviz_layout) */
 #define PPRVIZ_FP64 0            /* plain FP64: power iteration / FP64 layout arithmetic */
-#define PPRVIZ_FP32 1            /* FP32 Chebyshev sweeps + FP64 residual + refinement; FP32 layout */
+#define PPRVIZ_FP32 1            /* FP32 Chebyshev sweeps + FP64 residual + refinement; FP32 layout.
+                                  * pprviz_dppr picks the sweep kernel: dense tensor-core sweeps when
+                                  * n >= 512 and nnz >= n^2 / 20 (and the n x n matrix fits), CSR
+                                  * gather sweeps otherwise */
+#define PPRVIZ_FP32_CSR 2        /* pprviz_dppr only: PPRVIZ_FP32 with CSR gather sweeps always */
+#define PPRVIZ_FP32_TC 3         /* pprviz_dppr only: PPRVIZ_FP32 with every sweep a dense
+                                  * tensor-core contraction (3xTF32 tcgen05.mma); E_OOM if the
+                                  * n x n weight matrix does not fit */
 
 typedef struct pprviz_ctx pprviz_ctx;
 typedef struct pprviz_graph pprviz_graph;
@@ -89,6 +96,9 @@ typedef struct pprviz_stats {
     /* Algorithmic FP flops of the L^w inverse (symmetric block sweep: pivot
      * inverses, panels and the upper-triangle trailing updates). */
     double flops_factor;
+    /* Algorithmic flops of the dense tensor-core sweeps: 2 n^2 per (sweep,
+     * valid source); the 3xTF32 split executes three times as many. */
+    double flops_dense;
 } pprviz_stats;
 
 /* Kernel classes for per-class device timing (pprviz_profile). */
@@ -161,7 +171,12 @@ int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out
  *            certifies down to about d(s) * 1e-13; tighter eps needs PPRVIZ_FP64.
  *            Through Eq. (1) the certificates bound the PDist error too:
  *            |dDelta_ij| <= (c_i + c_j) / max(z_ij - c_i - c_j, e / n_clamp^2).
- * precision: PPRVIZ_FP64 or PPRVIZ_FP32.
+ * precision: PPRVIZ_FP64, PPRVIZ_FP32 (sweep kernel chosen by density),
+ *            PPRVIZ_FP32_CSR or PPRVIZ_FP32_TC (sweep kernel forced). The
+ *            tensor-core sweeps (P1d, Sec. 3.1 in matrix form: one sweep is the
+ *            dense product W Y of the n x n weights and the n x G state) change
+ *            only how a sweep is computed: the certificate and the refinement
+ *            are the same FP64 residual over the CSR.
  * dppr_out:  k*k DPPR, row q = pi_d(view[q], view[.]); may be NULL.
  * pdist_out: k*k PDist with Delta[q][r] from pi_d(q,r) + pi_d(r,q), the upper
  *            clamp 2 ln n_clamp (n_clamp = 0 means the graph's n) and a zero

@@ -29,6 +29,8 @@ PPRVIZ_DEVICE_PTRS = 1
 PPRVIZ_OUT_FP64 = 2
 PPRVIZ_FP64 = 0
 PPRVIZ_FP32 = 1
+PPRVIZ_FP32_CSR = 2
+PPRVIZ_FP32_TC = 3
 KERNEL_CLASSES = ["graph", "sweep", "residual", "extract", "pdist", "factor", "ly", "apply", "energy", "other"]
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID_ARG", 2: "E_BAD_GRAPH", 3: "E_OOM", 4: "E_CUDA",
@@ -64,7 +66,7 @@ class pprviz_stats(C.Structure):
                 ("refine_passes", C.c_int32), ("residual_passes", C.c_int32), ("kernel_launches", C.c_int32),
                 ("max_cert", C.c_double), ("layout_iters", C.c_int32), ("source_group", C.c_int32),
                 ("bytes_sweep", C.c_double), ("bytes_ly", C.c_double), ("bytes_apply", C.c_double),
-                ("flops_factor", C.c_double)]
+                ("flops_factor", C.c_double), ("flops_dense", C.c_double)]
 
 
 _lib = None

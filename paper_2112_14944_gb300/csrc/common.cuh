@@ -70,6 +70,9 @@ struct pprviz_graph {
   pprviz::DevBuf rp, col, w, deg, invdw_f, invdw_d;
   double m = 0.0;
   std::vector<double> h_deg;  // host copy of d(v), for per-group decisions
+  // dense weight matrix for the tensor-core sweeps, built on first use
+  mutable pprviz::DevBuf dense;
+  mutable int64_t dense_nw = 0;
 };
 
 namespace pprviz {
@@ -122,6 +125,19 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
                const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps,
                int precision, void *dppr_d, bool out64, double *cert_h);
 
+// ---- dense tensor-core sweeps (dense.cu) ----------------------------------
+// True when the graph holds enough of all pairs for a dense contraction to
+// beat the CSR gathers.
+bool dense_eligible(const pprviz_graph *g);
+// Source-group width of the dense path (multiple of 128).
+int64_t dense_group(int32_t k);
+// Builds g->dense (n x n weights, zero padded) if absent; E_OOM if it does not fit.
+int dense_prepare(pprviz_ctx *ctx, const pprviz_graph *g);
+// One Chebyshev sweep of a group with the semantics of the CSR sweep; yold is
+// overwritten with the new iterate; err gets bit 0 if an MMA wait expired.
+int dense_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src, const float *rhs,
+                const float *ycur, float *yold, double alpha, double om, int *err);
+
 // ---- pdist (pdist.cu) ------------------------------------------------------
 int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp,
                  void *pdist_d, bool f64);
@@ -129,9 +145,10 @@ int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp
 // ---- factor (factor.cu) ----------------------------------------------------
 // In-place inverse of the SPD kp x kp matrix A (kp % 128 == 0); on return A
 // holds A^-1 on its upper 64-block triangle and on the 128 x 128 diagonal tiles.
-// `work` holds 2 * 64 * kp + 64 * 64 + 64 elements (the last 64 hold a status
-// word). The FP32 version runs its trailing updates on the tensor cores and
+// `work` holds spd_inverse_work(kp) elements (2 * NB * kp + NB * NB + 64 with
+// NB = 128: the panels, the pivot inverse and a status word). The FP32 version runs its trailing updates on the tensor cores and
 // returns PPRVIZ_E_TIMEOUT if an MMA completion wait expires.
+size_t spd_inverse_work(int32_t kp);  // elements of `work` for either type
 int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work);
 int spd_inverse_f64(pprviz_ctx *ctx, int32_t kp, double *A, double *work);
 

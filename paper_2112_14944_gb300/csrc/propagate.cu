@@ -474,9 +474,11 @@ double chebyshev_rate(double c) { return (1.0 - sqrt(1.0 - c * c)) / c; }
 // Runs `sweeps` Chebyshev steps of x (I - cP) = b from x_0 = 0, x_1 = b.
 // On entry ya, yb are the two state buffers; returns the buffer holding the
 // last iterate.  b is the source delta (rhs == nullptr) or the dense rhs.
+// `tcerr` non-null selects the dense tensor-core sweeps (it receives their
+// error word); otherwise the CSR gather sweeps run.
 int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     int32_t gcount, const float *rhs, float *ya, float *yb, int sweeps,
-                    double alpha, float **result) {
+                    double alpha, int *tcerr, float **result) {
   const size_t bytes = sizeof(float) * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(ya, 0, bytes, ctx->stream));
@@ -495,7 +497,10 @@ int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   float *cur = yb, *old = ya;
   for (int s = 1; s < sweeps; ++s) {
     om = (s == 1) ? 1.0 / (1.0 - c * c / 2.0) : 1.0 / (1.0 - c * c * om / 4.0);
-    PPRVIZ_TRY(launch_sweep<float>(ctx, g, ld, true, rhs != nullptr, src, rhs, cur, old, old, alpha, om));
+    if (tcerr)
+      PPRVIZ_TRY(dense_sweep(ctx, g, ld, src, rhs, cur, old, alpha, om, tcerr));
+    else
+      PPRVIZ_TRY(launch_sweep<float>(ctx, g, ld, true, rhs != nullptr, src, rhs, cur, old, old, alpha, om));
     std::swap(cur, old);
   }
   *result = cur;
@@ -509,7 +514,17 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
                int precision, void *dppr_d, bool out64, double *cert_h) {
   const bool fp64 = precision == PPRVIZ_FP64;
   const size_t elem = fp64 ? sizeof(double) : sizeof(float);
-  const int64_t ld = choose_group(g->n, k, elem);
+  // sweep kernel: dense tensor-core contraction (forced, or chosen by density
+  // when the n x n matrix fits) or CSR gathers
+  bool dense = false;
+  if (precision == PPRVIZ_FP32_TC) {
+    PPRVIZ_TRY(dense_prepare(ctx, g));
+    dense = true;
+  } else if (precision == PPRVIZ_FP32 && dense_eligible(g)) {
+    dense = dense_prepare(ctx, g) == PPRVIZ_OK;
+    if (!dense) ctx->err.clear();
+  }
+  const int64_t ld = dense ? dense_group(k) : choose_group(g->n, k, elem);
   const size_t sbytes = elem * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
   PPRVIZ_TRY(ws_ensure(ctx, WS_Y0, sbytes));
@@ -523,6 +538,12 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, sizeof(double) * (size_t)ld));
   int32_t *src = ctx->ws[WS_SRC].as<int32_t>();
   double *l1 = ctx->ws[WS_CERT].as<double>();
+  int *tcerr = nullptr;
+  if (dense) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_FLAG, 64));
+    tcerr = ctx->ws[WS_FLAG].as<int>();
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(tcerr, 0, sizeof(int), ctx->stream));
+  }
   pprviz_stats &st = ctx->stats;
   st.source_group = (int32_t)ld;
   std::vector<int32_t> srch((size_t)ld);
@@ -572,9 +593,10 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       // (driven by the exact FP64 residual) finishes the job
       const int K1 = std::max(2, (int)ceil(log(0.5e-5) / log(rho)));
       float *hi = nullptr;
-      PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, &hi));
+      PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, tcerr, &hi));
       st.sweeps_main += K1;
-      st.bytes_sweep += 12.0 * (double)g->n * gvalid * (K1 - 1);
+      if (dense) st.flops_dense += 2.0 * (double)g->n * (double)g->n * gvalid * (K1 - 1);
+      else st.bytes_sweep += 12.0 * (double)g->n * gvalid * (K1 - 1);
       // free buffers for the correction solves; the first correction becomes x_lo
       float *fa = hi == bufs[0] ? bufs[1] : bufs[0], *fb = bufs[2], *fc = bufs[3];
       float *lo = nullptr;
@@ -592,9 +614,10 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         int K2 = (int)ceil(log(0.25 * eps / cmax) / log(rho)) + 2;
         K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
         float *delta = nullptr;
-        PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, &delta));
+        PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, tcerr, &delta));
         st.sweeps_refine += K2;
-        st.bytes_sweep += 16.0 * (double)g->n * gvalid * (K2 - 1);
+        if (dense) st.flops_dense += 2.0 * (double)g->n * (double)g->n * gvalid * (K2 - 1);
+        else st.bytes_sweep += 16.0 * (double)g->n * gvalid * (K2 - 1);
         st.refine_passes++;
         if (!lo) {
           lo = delta;
@@ -643,6 +666,12 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       }
       PPRVIZ_LAUNCHED(ctx);
     }
+  }
+  if (tcerr) {
+    int herr = 0;
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, tcerr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (herr) return set_err(ctx, PPRVIZ_E_TIMEOUT, "tensor-core sweep: an MMA completion wait expired");
   }
   if (not_converged)
     return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "certificate above eps after the refinement cap");
