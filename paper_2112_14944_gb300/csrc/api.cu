@@ -234,6 +234,7 @@ int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr, cons
   if ((e = g->deg.ensure(sizeof(double) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc deg"));
   if ((e = g->invdw_f.ensure(sizeof(float) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc invdw"));
   if ((e = g->invdw_d.ensure(sizeof(double) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc invdw"));
+  if ((e = g->dwff.ensure(sizeof(float2) * (size_t)n)) != cudaSuccess) return fail(cuda_err(ctx, e, "alloc dw"));
   if ((e = cudaMemcpyAsync(g->rp.p, row_ptr, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) != cudaSuccess)
     return fail(cuda_err(ctx, e, "copy row_ptr"));
   if (nnz && (e = cudaMemcpyAsync(g->col.p, col_idx, sizeof(int32_t) * (size_t)nnz, kind, ctx->stream)) != cudaSuccess)
@@ -256,6 +257,7 @@ void pprviz_graph_free(pprviz_graph *g) {
   g->deg.release();
   g->invdw_f.release();
   g->invdw_d.release();
+  g->dwff.release();
   delete g;
 }
 

@@ -41,6 +41,8 @@ enum Slot {
   WS_B, WS_X, WS_E, WS_MISC,
   // batched views
   WS_BW1, WS_BM, WS_BX, WS_BPART, WS_BTAB, WS_BPD, WS_BXIN, WS_BXOUT,
+  // deflated sweeps: spectral scratch, residual partials, per-source roots and coefficients
+  WS_SPEC, WS_RPART, WS_CSRC, WS_KAPPA,
   WS_COUNT
 };
 
@@ -68,11 +70,19 @@ struct pprviz_graph {
   bool weighted = false;
   uint32_t flags = 0;
   pprviz::DevBuf rp, col, w, deg, invdw_f, invdw_d;
+  pprviz::DevBuf dwff;  // walk degree as a float pair (hi, lo), hi + lo = dw to ~2^-48
   double m = 0.0;
   std::vector<double> h_deg;  // host copy of d(v), for per-group decisions
   // dense weight matrix for the tensor-core sweeps, built on first use
   mutable pprviz::DevBuf dense;
   mutable int64_t dense_nw = 0;
+  // component roots and spectral bound for the deflated sweeps, on first use
+  mutable pprviz::DevBuf comp;             // root (smallest id) of each node's component
+  mutable std::vector<int32_t> h_comp;     // host copy
+  mutable std::vector<double> h_mc;        // m_C = sum of walk degrees, indexed by root
+  mutable double spec_b = 1.0;             // |lambda| <= spec_b off the stationary modes (estimate + margin)
+  mutable bool spec_deflate = false;       // components resolved
+  mutable bool spec_ready = false;
 };
 
 namespace pprviz {
@@ -124,6 +134,10 @@ int view_check(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d, in
 int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
                const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps,
                int precision, void *dppr_d, bool out64, double *cert_h);
+
+// ---- graph analysis for the deflated sweeps (spectral.cu) ------------------
+// Fills g->comp / h_comp / h_mc / spec_b / spec_deflate once per graph.
+int graph_spectral(pprviz_ctx *ctx, const pprviz_graph *g);
 
 // ---- dense tensor-core sweeps (dense.cu) ----------------------------------
 // True when the graph holds enough of all pairs for a dense contraction to

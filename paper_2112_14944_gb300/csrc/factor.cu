@@ -4,10 +4,14 @@
 // With P = A_KK^-1 for pivot block K:
 //   A_KK -> -P,   A_IK -> A_IK P (and A_KI -> P A_KI),   A_IJ -> A_IJ - A_IK P A_KJ;
 // the matrix stays symmetric after every sweep and equals -A^-1 once every
-// block has been swept. Only the upper block triangle (64 x 64 blocks I <= J,
+// block has been swept. Only the upper block triangle (NB x NB blocks I <= J,
 // diagonal blocks in full) is stored and updated, which halves the O(k^3)
-// trailing work. A final pass negates it and mirrors the lower 64-blocks that
-// lie inside the 128 x 128 diagonal tiles read by the layout passes.
+// trailing work. A final pass negates it (and, with 64-blocks, mirrors the
+// lower 64-blocks inside the 128 x 128 diagonal tiles read by the layout).
+//
+// FP32: NB = 128, the trailing update on the tensor cores (3xTF32); every
+// sweep reads and writes the stored triangle once, so the wide block halves
+// that traffic against NB = 64. FP64: NB = 64 on the SIMT cores.
 #include <math.h>
 
 #include <algorithm>
@@ -17,27 +21,27 @@
 
 namespace pprviz {
 
-constexpr int FNB = 64;  // pivot block
+size_t spd_inverse_work(int32_t kp) { return (size_t)2 * 128 * kp + 128 * 128 + 64; }
 
-// P = A_KK^-1 by an in-place scalar sweep of the 64 x 64 block in shared memory
+// P = A_KK^-1 by an in-place scalar sweep of the NB x NB block in shared memory
 // (ping-pong buffers, one barrier per pivot); writes P to `P` and -P into A_KK.
-template <typename T>
+template <typename T, int NB>
 __global__ void __launch_bounds__(512) k_fac_diag(int32_t kp, int32_t K0, T *__restrict__ A, T *__restrict__ P) {
-  extern __shared__ unsigned char smem_raw[];
-  T *buf = reinterpret_cast<T *>(smem_raw);  // [2][FNB][FNB + 1]
-  constexpr int LD = FNB + 1, SZ = FNB * LD;
-  for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
-    const int r = e / FNB, c = e % FNB;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);  // [2][NB][NB + 1]
+  constexpr int LD = NB + 1, SZ = NB * LD;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
     buf[r * LD + c] = A[(int64_t)(K0 + r) * kp + K0 + c];
   }
   __syncthreads();
   int cur = 0;
-  for (int p = 0; p < FNB; ++p) {
+  for (int p = 0; p < NB; ++p) {
     const T *a = buf + cur * SZ;
     T *b = buf + (cur ^ 1) * SZ;
     const T piv = T(1) / a[p * LD + p];
-    for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
-      const int r = e / FNB, c = e % FNB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int r = e / NB, c = e % NB;
       const T arc = a[r * LD + c], arp = a[r * LD + p], apc = a[p * LD + c];
       T v;
       if (r == p && c == p) v = piv;
@@ -50,72 +54,222 @@ __global__ void __launch_bounds__(512) k_fac_diag(int32_t kp, int32_t K0, T *__r
     cur ^= 1;
   }
   const T *a = buf + cur * SZ;
-  for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
-    const int r = e / FNB, c = e % FNB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
     const T v = a[r * LD + c];
     P[e] = v;
     A[(int64_t)(K0 + r) * kp + K0 + c] = -v;
   }
 }
 
-// Panel of pivot block K for block I != K (64 rows): C_I = A_IK (from the
-// stored upper triangle: A[i][K0 + t] for I < K, A[K0 + t][i] for I > K),
-// U_I = C_I P. Writes Ct[t][i] = C_I, Ut[t][i] = U_I and stores U_I back as
-// the new panel (A_IK for I < K, A_KI = U_I^T for I > K).
+// The same sweep for a 128 x 128 FP32 block with the block in registers:
+// thread t owns row t / 8 and, with g = t % 8, the 16 columns 32 m + 4 g + w
+// (m, w < 4), so that the 8 threads of a row read a 128-byte run of the
+// published pivot row with each 16-byte load. Per pivot p the owners publish
+// row p, column p and 1 / a_pp through shared memory (double buffered by the
+// parity of p, so one barrier per pivot suffices).
+__global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A,
+                                                      float *__restrict__ P) {
+  __shared__ __align__(16) float sRow[2][128];
+  __shared__ float sCol[2][128];
+  __shared__ float sPiv[2];
+  const int r = threadIdx.x >> 3, g = threadIdx.x & 7;
+  float a[16];  // a[4 m + w] = column 32 m + 4 g + w
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const float4 v = *reinterpret_cast<const float4 *>(A + (int64_t)(K0 + r) * kp + K0 + 32 * m + 4 * g);
+    a[4 * m] = v.x; a[4 * m + 1] = v.y; a[4 * m + 2] = v.z; a[4 * m + 3] = v.w;
+  }
+  // pivot p = 4 q + w (w unrolled): column p is owned by g == q % 8 at
+  // register 4 (q / 8) + w, a 4-way choice instead of a 16-way search
+  for (int q = 0; q < 32; ++q) {
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const int p = 4 * q + w;
+    const int b = w & 1;
+    const bool col_owner = (q & 7) == g;
+    const int mq = q >> 3;
+    if (col_owner) {
+      const float colv = mq == 0 ? a[w] : mq == 1 ? a[4 + w] : mq == 2 ? a[8 + w] : a[12 + w];
+      sCol[b][r] = colv;
+      if (r == p) sPiv[b] = 1.0f / colv;
+    }
+    if (r == p) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        *reinterpret_cast<float4 *>(&sRow[b][32 * m + 4 * g]) =
+            make_float4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
+    }
+    __syncthreads();
+    const float piv = sPiv[b];
+    const float f = sCol[b][r] * piv;  // a_rp / a_pp
+    // every element: a_rc - (a_rp / a_pp) a_pc (one FMA); then row p and
+    // column p are overwritten with their own formulas
+    float4 rowv[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      rowv[m] = *reinterpret_cast<const float4 *>(&sRow[b][32 * m + 4 * g]);
+      a[4 * m + 0] = fmaf(-f, rowv[m].x, a[4 * m + 0]);
+      a[4 * m + 1] = fmaf(-f, rowv[m].y, a[4 * m + 1]);
+      a[4 * m + 2] = fmaf(-f, rowv[m].z, a[4 * m + 2]);
+      a[4 * m + 3] = fmaf(-f, rowv[m].w, a[4 * m + 3]);
+    }
+    if (r == p) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        a[4 * m + 0] = rowv[m].x * piv;
+        a[4 * m + 1] = rowv[m].y * piv;
+        a[4 * m + 2] = rowv[m].z * piv;
+        a[4 * m + 3] = rowv[m].w * piv;
+      }
+    }
+    if (col_owner) {
+      const float vcol = (r == p) ? piv : -f;
+      if (mq == 0) a[w] = vcol;
+      else if (mq == 1) a[4 + w] = vcol;
+      else if (mq == 2) a[8 + w] = vcol;
+      else a[12 + w] = vcol;
+    }
+  }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int c = 32 * m + 4 * g;
+    *reinterpret_cast<float4 *>(P + r * 128 + c) = make_float4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
+    *reinterpret_cast<float4 *>(A + (int64_t)(K0 + r) * kp + K0 + c) =
+        make_float4(-a[4 * m], -a[4 * m + 1], -a[4 * m + 2], -a[4 * m + 3]);
+  }
+}
+
 template <typename T>
+struct V4;  // 4-vector load/store of T
+template <>
+struct V4<float> {
+  __device__ static void ld(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ static void st(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct V4<double> {
+  __device__ static void ld(const double *p, double (&v)[4]) {
+    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+  }
+  __device__ static void st(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+// Panel of pivot block K for block I != K (NB rows): C_I = A_IK (from the
+// stored upper triangle: A[i][K0 + s] for I < K, A[K0 + s][i] for I > K),
+// U_I = C_I P. Writes C_I and U_I for the trailing update, transposed
+// (Ct[t][i], Ut[t][i], the SIMT update's layout) or, with KM, row-major
+// (Ct[i][t], Ut[i][t], row stride NB: K-major operands of the tensor-core
+// update), and stores U_I back as the new panel (A_IK for I < K, A_KI = U_I^T
+// for I > K). 256 threads on a 16 x 16 grid, each an R x R block of U
+// (R = NB / 16) accumulated in registers.
+template <typename T, int NB, bool KM>
 __global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ P,
                                                    T *__restrict__ Ct, T *__restrict__ Ut) {
-  const int I0 = blockIdx.x * FNB;
+  constexpr int R = NB / 16, LD = NB + 16 / (int)sizeof(T);
+  const int I0 = blockIdx.x * NB;
   if (I0 == K0) return;
-  extern __shared__ unsigned char smem_raw[];
-  T *sP = reinterpret_cast<T *>(smem_raw);  // [FNB][FNB]
-  T *sC = sP + FNB * FNB;                   // [FNB][FNB + 1]  sC[i][t]
-  constexpr int LD = FNB + 1;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T *sP = reinterpret_cast<T *>(smem_raw);  // [NB][NB]   sP[s][t]
+  T *sC = sP + NB * NB;                     // [NB][LD]   sC[s][i] = C[i][s]
   const bool above = I0 < K0;
-  for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     sP[e] = P[e];
-    const int r = e / FNB, c = e % FNB;
-    if (above) sC[r * LD + c] = A[(int64_t)(I0 + r) * kp + K0 + c];   // i = r, t = c
-    else sC[c * LD + r] = A[(int64_t)(K0 + r) * kp + I0 + c];         // t = r, i = c
+    const int r = e / NB, c = e % NB;
+    if (above) sC[c * LD + r] = A[(int64_t)(I0 + r) * kp + K0 + c];  // i = r, s = c
+    else sC[r * LD + c] = A[(int64_t)(K0 + r) * kp + I0 + c];         // s = r, i = c
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
-    const int t = e / FNB, i = e % FNB;  // consecutive threads: consecutive i
-    T u = T(0);
-#pragma unroll 8
-    for (int s = 0; s < FNB; ++s) u += sC[i * LD + s] * sP[s * FNB + t];
-    Ct[(int64_t)t * kp + I0 + i] = sC[i * LD + t];
-    Ut[(int64_t)t * kp + I0 + i] = u;
-    if (!above) A[(int64_t)(K0 + t) * kp + I0 + i] = u;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    if (KM) {  // Ct[I0 + i][t] = C[i][t]
+      const int i = e / NB, t = e % NB;
+      Ct[(int64_t)(I0 + i) * NB + t] = sC[t * LD + i];
+    } else {   // Ct[t][I0 + i] = C[i][t]
+      const int t = e / NB, i = e % NB;
+      Ct[(int64_t)t * kp + I0 + i] = sC[t * LD + i];
+    }
   }
-  if (above) {
-    __syncthreads();
-    // A[I0 + i][K0 + t] = U[i][t]: reuse sC for a coalesced row-major store
-    for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
-      const int i = e / FNB, t = e % FNB;
-      T u = T(0);
-#pragma unroll 8
-      for (int s = 0; s < FNB; ++s) u += sC[i * LD + s] * sP[s * FNB + t];
-      A[(int64_t)(I0 + i) * kp + K0 + t] = u;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T u[R][R];
+#pragma unroll
+  for (int x = 0; x < R; ++x)
+#pragma unroll
+    for (int y = 0; y < R; ++y) u[x][y] = T(0);
+#pragma unroll 4
+  for (int s = 0; s < NB; ++s) {
+    T av[R], bv[R];
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+      T tmp[4];
+      V4<T>::ld(sC + s * LD + ty * R + 4 * q, tmp);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) av[4 * q + w] = tmp[w];
+      V4<T>::ld(sP + s * NB + tx * R + 4 * q, tmp);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) bv[4 * q + w] = tmp[w];
+    }
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) u[x][y] += av[x] * bv[y];
+  }
+  // u[x][y] = U[i = ty R + x][t = tx R + y]
+  if (!KM || !above) {
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+      const int t = tx * R + y;
+#pragma unroll
+      for (int q = 0; q < R / 4; ++q) {
+        T tmp[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) tmp[w] = u[4 * q + w][y];
+        if (!KM) V4<T>::st(Ut + (int64_t)t * kp + I0 + ty * R + 4 * q, tmp);
+        if (!above) V4<T>::st(A + (int64_t)(K0 + t) * kp + I0 + ty * R + 4 * q, tmp);
+      }
+    }
+  }
+  if (KM || above) {
+#pragma unroll
+    for (int x = 0; x < R; ++x) {
+      const int i = ty * R + x;
+#pragma unroll
+      for (int q = 0; q < R / 4; ++q) {
+        T tmp[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) tmp[w] = u[x][4 * q + w];
+        if (KM) V4<T>::st(Ut + (int64_t)(I0 + i) * NB + tx * R + 4 * q, tmp);
+        if (above) V4<T>::st(A + (int64_t)(I0 + i) * kp + K0 + tx * R + 4 * q, tmp);
+      }
     }
   }
 }
 
-// Trailing update of the upper triangle: A[i][j] -= sum_t Ct[t][i] Ut[t][j] for
-// i, j outside the pivot block with block(i) <= block(j) (64-blocks). TM x TM
-// tiles over the upper tile triangle; R x R outputs per thread in two
-// SUB x SUB quadrants so that shared-memory reads are vectors.
-template <typename T, int TM>
+// SIMT trailing update of the upper triangle (FP64, NB = 64):
+// A[i][j] -= sum_t Ct[t][i] Ut[t][j] for i, j outside the pivot block with
+// block(i) <= block(j). TM x TM tiles over the upper tile triangle; R x R
+// outputs per thread in two SUB x SUB quadrants so that shared-memory reads
+// are vectors.
+template <typename T, int TM, int NB>
 __global__ void __launch_bounds__(256)
 k_fac_trailing(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ Ct, const T *__restrict__ Ut) {
   constexpr int R = TM / 16, SUB = R / 2, HALF = TM / 2;
   const int I0 = blockIdx.y * TM, J0 = blockIdx.x * TM;
   if (J0 < I0) return;  // lower tile triangle: not stored
-  if ((I0 >= K0 && I0 + TM <= K0 + FNB) || (J0 >= K0 && J0 + TM <= K0 + FNB)) return;
-  extern __shared__ unsigned char smem_raw[];
-  T *sA = reinterpret_cast<T *>(smem_raw);  // [FNB][TM]  sA[t][i] = Ct[t][I0 + i]
-  T *sB = sA + FNB * TM;                    // [FNB][TM]  sB[t][j] = Ut[t][J0 + j]
-  for (int e = threadIdx.x; e < FNB * TM; e += 256) {
+  if ((I0 >= K0 && I0 + TM <= K0 + NB) || (J0 >= K0 && J0 + TM <= K0 + NB)) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T *sA = reinterpret_cast<T *>(smem_raw);  // [NB][TM]  sA[t][i] = Ct[t][I0 + i]
+  T *sB = sA + NB * TM;                     // [NB][TM]  sB[t][j] = Ut[t][J0 + j]
+  for (int e = threadIdx.x; e < NB * TM; e += 256) {
     const int t = e / TM, x = e % TM;
     sA[e] = (I0 + x < kp) ? Ct[(int64_t)t * kp + I0 + x] : T(0);
     sB[e] = (J0 + x < kp) ? Ut[(int64_t)t * kp + J0 + x] : T(0);
@@ -128,7 +282,7 @@ k_fac_trailing(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ 
 #pragma unroll
     for (int c = 0; c < R; ++c) acc[r][c] = T(0);
 #pragma unroll 4
-  for (int t = 0; t < FNB; ++t) {
+  for (int t = 0; t < NB; ++t) {
     T a[R], b[R];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
@@ -142,52 +296,51 @@ k_fac_trailing(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ 
 #pragma unroll
       for (int c = 0; c < R; ++c) acc[r][c] += a[r] * b[c];
   }
-  // Epilogue: each row's SUB consecutive columns are one aligned vector; the
-  // masks (pivot block, lower blocks, kp) are uniform over it since blocks are
-  // 64-aligned and kp is a multiple of 128.
+  // Epilogue: each row's SUB consecutive columns lie in one block, so the
+  // masks (pivot block, lower blocks, kp) are uniform over them.
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i = I0 + (r / SUB) * HALF + ty * SUB + (r % SUB);
-    if (i >= kp || (i >= K0 && i < K0 + FNB)) continue;
+    if (i >= kp || (i >= K0 && i < K0 + NB)) continue;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int j = J0 + h * HALF + tx * SUB;
-      if (j >= kp || (j >= K0 && j < K0 + FNB) || (i / FNB) > (j / FNB)) continue;
+      if (j >= kp || (j >= K0 && j < K0 + NB) || (i / NB) > (j / NB)) continue;
       T *p = A + (int64_t)i * kp + j;
-      if constexpr (sizeof(T) == 4 && SUB == 4) {
-        float4 v = *reinterpret_cast<float4 *>(p);
-        v.x -= acc[r][h * SUB + 0];
-        v.y -= acc[r][h * SUB + 1];
-        v.z -= acc[r][h * SUB + 2];
-        v.w -= acc[r][h * SUB + 3];
-        *reinterpret_cast<float4 *>(p) = v;
-      } else {
 #pragma unroll
-        for (int s = 0; s < SUB; ++s) p[s] -= acc[r][h * SUB + s];
-      }
+      for (int s = 0; s < SUB; ++s) p[s] -= acc[r][h * SUB + s];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core trailing update (FP32 path): the same A[i][j] -= sum_t
-// Ct[t][i] Ut[t][j] on 128 x 128 tiles, as tcgen05.mma kind::tf32 products
-// with split operands (x = x_hi + x_lo, x_hi = x with the low 13 mantissa bits
-// cleared): C ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (error-compensated TF32,
-// Ootomo & Yokota 2022), FP32 accumulation in tensor memory.
-// Operands are staged by the CTA into the canonical no-swizzle K-major shared
-// layout (8-row x 16-byte core matrices, LBO = 128 B along K, SBO = 16 core
-// matrices per 8-row group); one thread issues the 24 MMAs and commits them to
-// an mbarrier, which every thread waits on with an iteration limit (on expiry
-// the CTA sets `err`, skips the update and still frees its tensor memory).
+// Tensor-core trailing update (FP32, NB = 128): A[i][j] -= sum_t Ct[t][i]
+// Ut[t][j] on the 128 x 128 tiles I <= J outside the pivot row and column, as
+// tcgen05.mma kind::tf32 products with split operands (x = x_hi + x_lo, x_hi =
+// x with the low 13 mantissa bits cleared): C ~ A_hi B_hi + A_hi B_lo + A_lo
+// B_hi (error-compensated TF32, Ootomo & Yokota 2022), FP32 accumulation in
+// tensor memory. The 128-deep inner dimension is streamed in 16-wide chunks
+// through two shared-memory stages in the canonical no-swizzle K-major layout
+// (8-row x 16-byte core matrices); the panels are stored row-major [x][t], so
+// each thread moves 16-byte runs of 4 consecutive t (8 lanes cover 8 rows at
+// one run, 4 lane octets the 4 runs of a chunk: 64 contiguous bytes per row,
+// and conflict-free canonical stores). The
+// global loads of chunk c + 1 are issued before the MMAs of chunk c are waited
+// on; every mbarrier wait has an iteration limit (on expiry the CTA sets `err`,
+// skips the update and still frees its tensor memory after a second bounded
+// wait). 64 KiB of shared memory, 128 tensor-memory columns and a small
+// register budget let three CTAs share an SM, so that one CTA's epilogue (the
+// read-modify-write of its C tile) overlaps the staging and MMAs of others.
 // ---------------------------------------------------------------------------
 namespace tc {
 constexpr int TM = 128;                       // tile edge (M = N = 128)
-constexpr int KD = FNB;                       // inner dimension (pivot block)
+constexpr int NB = 128;                       // pivot block = inner dimension
+constexpr int KC = 16;                        // inner chunk per stage
 constexpr uint32_t LBO = 128;                 // bytes to the next core matrix along K
-constexpr uint32_t SBO = (KD / 4) * 128;      // bytes to the next 8-row group
-constexpr int OPB = TM * KD * 4;              // bytes of one staged operand (32 KiB)
-constexpr int SMEM = 4 * OPB;                 // A_hi, A_lo, B_hi, B_lo
+constexpr uint32_t SBO = (KC / 4) * 128;      // bytes to the next 8-row group
+constexpr int OPB = TM * KC * 4;              // one staged operand part (8 KiB)
+constexpr int STAGE = 4 * OPB;                // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM = 2 * STAGE;               // two stages
 constexpr long WAIT_LIMIT = 1L << 22;         // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -206,125 +359,176 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ float hi_part(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < WAIT_LIMIT && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
+  float4 h, l;
+  h.x = hi_part(v.x); h.y = hi_part(v.y); h.z = hi_part(v.z); h.w = hi_part(v.w);
+  l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+  *reinterpret_cast<float4 *>(hi + off) = h;
+  *reinterpret_cast<float4 *>(lo + off) = l;
+}
+
+// 128 rows x (KC / 4) quads of one chunk: float4 per operand per thread
+constexpr int CH_ITEMS = TM * (KC / 4) / 256;
+struct Chunk {
+  float4 a[CH_ITEMS], b[CH_ITEMS];
+};
+
+// row x and quad kq of item `it` of thread `tid` (KC = 16: 4 quads per row)
+__device__ __forceinline__ void chunk_coords(int tid, int it, int &x, int &kq) {
+  const int lane = tid & 31, w = tid >> 5;
+  x = 8 * (w * CH_ITEMS + it) + (lane & 7);
+  kq = lane >> 3;
+}
+
+__device__ __forceinline__ void load_chunk(Chunk &ch, const float *__restrict__ Ct, const float *__restrict__ Ut,
+                                           int I0, int J0, int k0, int tid) {
+#pragma unroll
+  for (int it = 0; it < CH_ITEMS; ++it) {
+    int x, kq;
+    chunk_coords(tid, it, x, kq);
+    ch.a[it] = __ldg(reinterpret_cast<const float4 *>(Ct + (int64_t)(I0 + x) * NB + k0 + 4 * kq));
+    ch.b[it] = __ldg(reinterpret_cast<const float4 *>(Ut + (int64_t)(J0 + x) * NB + k0 + 4 * kq));
+  }
+}
+
+__device__ __forceinline__ void store_chunk(const Chunk &ch, unsigned char *st, int tid) {
+#pragma unroll
+  for (int it = 0; it < CH_ITEMS; ++it) {
+    int x, kq;
+    chunk_coords(tid, it, x, kq);
+    const uint32_t o = canon(x, 4 * kq);
+    put_split(st, st + OPB, o, ch.a[it]);
+    put_split(st + 2 * OPB, st + 3 * OPB, o, ch.b[it]);
+  }
+}
 }  // namespace tc
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_fac_trailing_tc(int32_t kp, int32_t K0, float *__restrict__ A, const float *__restrict__ Ct,
                   const float *__restrict__ Ut, int *__restrict__ err) {
   using namespace tc;
   const int I0 = blockIdx.y * TM, J0 = blockIdx.x * TM;
-  if (J0 < I0) return;  // lower tile triangle: not stored
+  if (J0 < I0 || I0 == K0 || J0 == K0) return;  // lower triangle, pivot row and column
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_sh;
-  unsigned char *sAh = smem_raw, *sAl = smem_raw + OPB, *sBh = smem_raw + 2 * OPB, *sBl = smem_raw + 3 * OPB;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // Epilogue ownership: warp w updates tile rows 32 (w % 4) + lane (its TMEM
-  // lanes) and columns 64 (w / 4) .. +63. Those 64 values of A are read from
-  // HBM first, so their latency overlaps the staging and the MMAs.
-  const int lg = warp & 3, ch = warp >> 2;
-  const int i_row = I0 + 32 * lg + lane;
-  const bool row_ok = !(i_row >= K0 && i_row < K0 + FNB);
-  float4 pre[16];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int j = J0 + 64 * ch + 8 * c;
-    const bool ok = row_ok && !(j >= K0 && j < K0 + FNB) && (i_row / FNB) <= (j / FNB);
-    const float4 *p = reinterpret_cast<const float4 *>(A + (int64_t)i_row * kp + j);
-    pre[2 * c] = ok ? p[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-    pre[2 * c + 1] = ok ? p[1] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  // stage: thread (row r, quad q of 4 inner indices) reads Ct[4q .. 4q+3][I0 + r]
-  // (coalesced across the warp) and writes one 16-byte chunk per operand part
-  static_assert((TM * (KD / 4)) % 256 == 0, "staging assumes 256 threads");
-#pragma unroll 4
-  for (int it = 0; it < TM * (KD / 4) / 256; ++it) {
-    const int idx = tid + 256 * it;
-    const int r = idx % TM, q = idx / TM;
-    float a[4], b[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      a[s] = Ct[(int64_t)(4 * q + s) * kp + I0 + r];
-      b[s] = Ut[(int64_t)(4 * q + s) * kp + J0 + r];
-    }
-    float4 ah, al, bh, bl;
-    ah.x = hi_part(a[0]); ah.y = hi_part(a[1]); ah.z = hi_part(a[2]); ah.w = hi_part(a[3]);
-    al.x = a[0] - ah.x; al.y = a[1] - ah.y; al.z = a[2] - ah.z; al.w = a[3] - ah.w;
-    bh.x = hi_part(b[0]); bh.y = hi_part(b[1]); bh.z = hi_part(b[2]); bh.w = hi_part(b[3]);
-    bl.x = b[0] - bh.x; bl.y = b[1] - bh.y; bl.z = b[2] - bh.z; bl.w = b[3] - bh.w;
-    const uint32_t o = canon(r, 4 * q);
-    *reinterpret_cast<float4 *>(sAh + o) = ah;
-    *reinterpret_cast<float4 *>(sAl + o) = al;
-    *reinterpret_cast<float4 *>(sBh + o) = bh;
-    *reinterpret_cast<float4 *>(sBl + o) = bl;
-  }
+  // TMEM read-out: warp w takes lanes (rows) 32 (w % 4) .. + 31 and columns
+  // 64 (w / 4) .. + 63 of the accumulator.
+  const int lg = warp & 3, chalf = warp >> 2;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)), "r"(TM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_sh;
-  if (tid == 0) {
-    int first = 1;
+  constexpr int NCH = NB / KC;
+  bool ok = true;
+  int issued = -1;
+  Chunk ch;
+  load_chunk(ch, Ct, Ut, I0, J0, 0, tid);
 #pragma unroll 1
-    for (int pass = 0; pass < 3; ++pass) {
-      const unsigned char *pa = (pass == 2) ? sAl : sAh;
-      const unsigned char *pb = (pass == 1) ? sBl : sBh;
-#pragma unroll 1
-      for (int ks = 0; ks < KD / 8; ++ks) {
-        const uint64_t da = desc(smem_u32(pa) + ks * 2 * LBO);
-        const uint64_t db = desc(smem_u32(pb) + ks * 2 * LBO);
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(IDESC), "r"(first ? 0u : 1u));
-        first = 0;
-      }
+  for (int cidx = 0; cidx < NCH; ++cidx) {
+    const int buf = cidx & 1;
+    unsigned char *st = smem_raw + buf * STAGE;
+    if (cidx >= 2 && !mbar_wait(&mbar[buf], (uint32_t)(((cidx - 2) >> 1) & 1))) ok = false;
+    if (__syncthreads_and(ok) == 0) {
+      ok = false;
+      break;
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
-  }
-  uint32_t done = 0;
-  for (long it = 0; it < WAIT_LIMIT && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(&mbar))
-        : "memory");
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done) {
-    if (lane == 0) atomicOr(err, 1);
-  } else {
-    // the warp's 32 lanes x 64 columns of the product, 4 x 16 columns per load
-    uint32_t v[64];
-    const uint32_t tbase = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * ch);
+    store_chunk(ch, st, tid);
+    if (cidx + 1 < NCH) load_chunk(ch, Ct, Ut, I0, J0, (cidx + 1) * KC, tid);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t base = smem_u32(st);
+#pragma unroll 1
+      for (int pass = 0; pass < 3; ++pass) {
+        const uint32_t pa = base + (pass == 2 ? OPB : 0);
+        const uint32_t pb = base + 2 * OPB + (pass == 1 ? OPB : 0);
 #pragma unroll
+        for (int ks = 0; ks < KC / 8; ++ks) {
+          const uint64_t da = desc(pa + ks * 2 * LBO);
+          const uint64_t db = desc(pb + ks * 2 * LBO);
+          const uint32_t acc = (cidx == 0 && pass == 0 && ks == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar[buf])));
+    }
+    issued = cidx;
+  }
+  if (ok && !mbar_wait(&mbar[issued & 1], (uint32_t)((issued >> 1) & 1))) ok = false;
+  ok = __syncthreads_and(ok) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(err, 1);
+      if (issued >= 0) (void)mbar_wait(&mbar[issued & 1], (uint32_t)((issued >> 1) & 1));
+    }
+  } else {
+    // The product goes through shared memory (the stages are free once the
+    // last MMA has completed) so that the read-modify-write of the C tile is
+    // row-contiguous: warp w writes its 32 rows x 64 columns (TMEM lane = row),
+    // 16-byte chunk c of row r at chunk slot c ^ (r % 32); then each warp
+    // updates whole 512-byte rows.
+    float *tile = reinterpret_cast<float *>(smem_raw);  // 128 x 128
+    const uint32_t tbase = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * chalf);
+    const int row = 32 * lg + lane;
+#pragma unroll 1
     for (int q = 0; q < 4; ++q) {
+      uint32_t v[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[16 * q + 0]), "=r"(v[16 * q + 1]), "=r"(v[16 * q + 2]), "=r"(v[16 * q + 3]), "=r"(v[16 * q + 4]),
-            "=r"(v[16 * q + 5]), "=r"(v[16 * q + 6]), "=r"(v[16 * q + 7]), "=r"(v[16 * q + 8]), "=r"(v[16 * q + 9]),
-            "=r"(v[16 * q + 10]), "=r"(v[16 * q + 11]), "=r"(v[16 * q + 12]), "=r"(v[16 * q + 13]),
-            "=r"(v[16 * q + 14]), "=r"(v[16 * q + 15])
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(tbase + (uint32_t)(16 * q)));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = J0 + 64 * ch + 8 * c;
-      if (!row_ok || (j >= K0 && j < K0 + FNB) || (i_row / FNB) > (j / FNB)) continue;
-      float4 *p = reinterpret_cast<float4 *>(A + (int64_t)i_row * kp + j);
-      float4 x = pre[2 * c], y = pre[2 * c + 1];
-      x.x -= __uint_as_float(v[8 * c + 0]); x.y -= __uint_as_float(v[8 * c + 1]);
-      x.z -= __uint_as_float(v[8 * c + 2]); x.w -= __uint_as_float(v[8 * c + 3]);
-      y.x -= __uint_as_float(v[8 * c + 4]); y.y -= __uint_as_float(v[8 * c + 5]);
-      y.z -= __uint_as_float(v[8 * c + 6]); y.w -= __uint_as_float(v[8 * c + 7]);
-      p[0] = x;
-      p[1] = y;
+      for (int c = 0; c < 4; ++c) {
+        const int c4 = 16 * chalf + 4 * q + c;
+        *reinterpret_cast<float4 *>(tile + row * TM + 4 * (c4 ^ (row & 31))) =
+            make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]), __uint_as_float(v[4 * c + 2]),
+                        __uint_as_float(v[4 * c + 3]));
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = warp; rr < TM; rr += 8) {
+      const float4 d = *reinterpret_cast<const float4 *>(tile + rr * TM + 4 * (lane ^ (rr & 31)));
+      float4 *p = reinterpret_cast<float4 *>(A + (int64_t)(I0 + rr) * kp + J0) + lane;
+      float4 x = *p;
+      x.x -= d.x;
+      x.y -= d.y;
+      x.z -= d.z;
+      x.w -= d.w;
+      *p = x;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -332,60 +536,68 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, float *__restrict__ A, const float *__
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM));
 }
 
-// A <- -A on the upper block triangle, and the lower 64-block of every 128 x 128
-// diagonal tile filled from its mirror, giving M = A^-1 where the layout reads it.
-template <typename T>
+// A <- -A on the upper block triangle; with NB = 64 also the lower 64-block of
+// every 128 x 128 diagonal tile filled from its mirror, giving M = A^-1 on the
+// upper tile triangle with full diagonal tiles (what the layout reads).
+template <typename T, int NB>
 __global__ void k_fac_finish(int32_t kp, T *__restrict__ A) {
   const int64_t i = blockIdx.y;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kp; j += (int64_t)gridDim.x * blockDim.x) {
-    if (i / FNB > j / FNB) continue;
+    if (i / NB > j / NB) continue;
     const T v = -A[i * kp + j];
     A[i * kp + j] = v;
-    if (i / 128 == j / 128 && i / FNB < j / FNB) A[j * kp + i] = v;
+    if (NB < 128 && i / 128 == j / 128 && i / NB < j / NB) A[j * kp + i] = v;
   }
 }
 
 template <typename T>
 static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
-  constexpr int TM = sizeof(T) == 4 ? 128 : 64;
-  constexpr bool TC = std::is_same<T, float>::value;  // FP32: tensor-core trailing update
-  T *Ct = work, *Ut = work + (size_t)FNB * kp, *P = work + (size_t)2 * FNB * kp;
-  int *err = reinterpret_cast<int *>(P + FNB * FNB);
-  const size_t diag_smem = 2 * sizeof(T) * FNB * (FNB + 1);
-  const size_t panel_smem = sizeof(T) * (FNB * FNB + FNB * (FNB + 1));
-  const size_t trail_smem = TC ? (size_t)tc::SMEM : 2 * sizeof(T) * FNB * TM;
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem));
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+  constexpr bool TC = std::is_same<T, float>::value;  // FP32: 128-blocks, tensor-core trailing update
+  constexpr int NB = TC ? 128 : 64;
+  constexpr int TM = 64;                               // SIMT trailing tile (FP64)
+  T *Ct = work, *Ut = work + (size_t)NB * kp, *P = work + (size_t)2 * NB * kp;
+  int *err = reinterpret_cast<int *>(P + NB * NB);
+  const size_t diag_smem = 2 * sizeof(T) * NB * (NB + 1);
+  const size_t panel_smem = sizeof(T) * (NB * NB + NB * (NB + 16 / sizeof(T)));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel<T, NB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)panel_smem));
   if constexpr (TC) {
     PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)trail_smem));
+                                          (int)tc::SMEM));
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   } else {
-    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)trail_smem));
+    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)diag_smem));
+    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing<T, TM, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(2 * sizeof(T) * NB * TM)));
   }
-  const int nblk = kp / FNB;
-  const unsigned tgrid = (unsigned)((kp + TM - 1) / TM);
-  // per pivot: the 64^3 pivot inverse, (nblk - 1) panel products of 2 * 64^3,
-  // and 2 * 64 flops for each of the (nblk - 1) nblk / 2 upper blocks of 64^2
-  const double b3 = (double)FNB * FNB * FNB;
+  const int nblk = kp / NB;
+  // per pivot: the NB^3 pivot inverse, (nblk - 1) panel products of 2 NB^3,
+  // and 2 NB^3 flops for each of the (nblk - 1) nblk / 2 upper blocks
+  const double b3 = (double)NB * NB * NB;
   const double nm1 = (double)(nblk - 1);
   ctx->stats.flops_factor += (double)nblk * (2.0 * b3 + nm1 * 2.0 * b3 + nm1 * (nm1 + 1.0) / 2.0 * 2.0 * b3);
   for (int kb = 0; kb < nblk; ++kb) {
-    const int K0 = kb * FNB;
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag<T><<<1, 512, diag_smem, ctx->stream>>>(kp, K0, A, P); }
+    const int K0 = kb * NB;
+    if constexpr (TC) {
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag128<<<1, 1024, 0, ctx->stream>>>(kp, K0, (float *)A, (float *)P); }
+    } else {
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag<T, NB><<<1, 512, diag_smem, ctx->stream>>>(kp, K0, A, P); }
+    }
     PPRVIZ_LAUNCHED(ctx);
     if (nblk == 1) break;
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_panel<T><<<nblk, 256, panel_smem, ctx->stream>>>(kp, K0, A, P, Ct, Ut); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, K0, A, P, Ct, Ut); }
     PPRVIZ_LAUNCHED(ctx);
     if constexpr (TC) {
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing_tc<<<dim3(tgrid, tgrid), 256, trail_smem, ctx->stream>>>(kp, K0, A, Ct, Ut, err); }
+      const unsigned tg = (unsigned)(kp / tc::TM);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing_tc<<<dim3(tg, tg), 256, tc::SMEM, ctx->stream>>>(kp, K0, A, Ct, Ut, err); }
     } else {
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing<T, TM><<<dim3(tgrid, tgrid), 256, trail_smem, ctx->stream>>>(kp, K0, A, Ct, Ut); }
+      const unsigned tg = (unsigned)((kp + TM - 1) / TM);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing<T, TM, NB><<<dim3(tg, tg), 256, 2 * sizeof(T) * NB * TM, ctx->stream>>>(kp, K0, A, Ct, Ut); }
     }
     PPRVIZ_LAUNCHED(ctx);
   }
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_finish<T><<<dim3((unsigned)std::min(8, (kp + 255) / 256), (unsigned)kp), 256, 0, ctx->stream>>>(kp, A); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_finish<T, NB><<<dim3((unsigned)std::min(8, (kp + 255) / 256), (unsigned)kp), 256, 0, ctx->stream>>>(kp, A); }
   PPRVIZ_LAUNCHED(ctx);
   if constexpr (TC) {
     int herr = 0;

@@ -63,7 +63,7 @@ __global__ void k_validate_csr(int64_t n, int64_t nnz, const int64_t *__restrict
 // node without edges (its self-loop).
 __global__ void k_degrees(int64_t n, const int64_t *__restrict__ rp, const float *__restrict__ w,
                           int count_only, double *__restrict__ deg, float *__restrict__ invdw_f,
-                          double *__restrict__ invdw_d) {
+                          double *__restrict__ invdw_d, float2 *__restrict__ dwff) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   int64_t b = rp[v], e = rp[v + 1];
@@ -77,6 +77,8 @@ __global__ void k_degrees(int64_t n, const int64_t *__restrict__ rp, const float
   double walk = (e > b) ? s : 1.0;
   invdw_d[v] = 1.0 / walk;
   invdw_f[v] = (float)(1.0 / walk);
+  const float hi = (float)walk;
+  dwff[v] = make_float2(hi, (float)(walk - (double)hi));
 }
 
 __global__ void k_view_check(int64_t n, int32_t k, const int32_t *__restrict__ view,
@@ -122,7 +124,7 @@ int graph_build(pprviz_ctx *ctx, pprviz_graph *g, uint32_t flags) {
   { PPRVIZ_PROF(ctx, PPRVIZ_K_GRAPH); k_degrees<<<blocks, threads, 0, ctx->stream>>>(
       n, g->rp.as<int64_t>(), g->weighted ? g->w.as<float>() : nullptr,
       (flags & PPRVIZ_DEGREE_COUNT) ? 1 : 0, g->deg.as<double>(), g->invdw_f.as<float>(),
-      g->invdw_d.as<double>()); }
+      g->invdw_d.as<double>(), g->dwff.as<float2>()); }
   PPRVIZ_LAUNCHED(ctx);
   g->h_deg.resize((size_t)n);
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(g->h_deg.data(), g->deg.p, sizeof(double) * (size_t)n,

@@ -147,10 +147,40 @@ __device__ __forceinline__ T lanes_transpose_sum(T (&v)[NV], int lane) {
   return r;
 }
 
+// sum_{o < nb} p[o * kp] in order o = 0, 1, ...; the loads (L2, since other
+// CTAs wrote them) are issued 16 at a time so that their latencies overlap,
+// the additions keep the order
+template <typename V2>
+__device__ __forceinline__ V2 sum_parts_in_order(const V2 *p, int64_t kp, int nb) {
+  V2 s = __ldcg(p);
+  for (int o0 = 1; o0 < nb; o0 += 16) {
+    V2 u[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (o0 + q < nb) u[q] = __ldcg(p + (int64_t)(o0 + q) * kp);
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (o0 + q < nb) {
+        s.x += u[q].x;
+        s.y += u[q].y;
+      }
+  }
+  return s;
+}
+
+// After its partial sums are written, the tile counts itself in for row
+// block I (and, off the diagonal, for row block J); every row block receives
+// exactly nbt partials (one per slot), so the CTA that brings a block's count
+// to nbt sums that block's partials in slot order into Vout and resets the
+// count for the next pass (a deterministic result, independent of which CTA
+// finishes last). One thread per CTA fences after the block barrier before
+// counting (release) and after a last count (acquire); the reducer reads
+// through L2.
 template <typename T, int MODE>
-__device__ __forceinline__ void sympass_tile(const int I, const int J, int32_t kp, const T *__restrict__ Mat,
+__device__ __forceinline__ void sympass_tile(const int I, const int J, int32_t kp, int nbt, const T *__restrict__ Mat,
                                              const typename T2<T>::type *__restrict__ V,
-                                             typename T2<T>::type *__restrict__ Part) {
+                                             typename T2<T>::type *__restrict__ Part, int *__restrict__ cnt,
+                                             typename T2<T>::type *__restrict__ Vout) {
   using V2 = typename T2<T>::type;
   constexpr int NV = 2 * SRPI;
   __shared__ V2 sVi[ST];
@@ -220,66 +250,46 @@ __device__ __forceinline__ void sympass_tile(const int I, const int J, int32_t k
     for (int w = 0; w < 8; ++w) s += colred[w][threadIdx.x];
     part[((int64_t)I * kp + j0) * 2 + threadIdx.x] = s;
   }
+  __shared__ int last[2];
+  __syncthreads();  // every thread's partials are written (CTA scope)
+  if (threadIdx.x == 0) {
+    __threadfence();  // release, cumulative over the barrier
+    last[0] = atomicAdd(&cnt[I], 1) == nbt - 1;
+    last[1] = (I != J) ? (atomicAdd(&cnt[J], 1) == nbt - 1) : 0;
+    if (last[0] || last[1]) __threadfence();  // acquire before the block reads other CTAs' partials
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    if (!last[side]) continue;
+    const int R = side ? J : I;
+    if (threadIdx.x < ST) {
+      const int64_t row = (int64_t)R * ST + threadIdx.x;
+      Vout[row] = sum_parts_in_order(Part + row, (int64_t)kp, nbt);
+    }
+    if (threadIdx.x == 0) cnt[R] = 0;
+  }
 }
 
-// One view: block (J, I) of the tile grid; lower tiles exit at once.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
-k_sympass(int32_t kp, const T *__restrict__ Mat, const typename T2<T>::type *__restrict__ V,
-          typename T2<T>::type *__restrict__ Part) {
-  const int I = blockIdx.y, J = blockIdx.x;
-  if (J < I) return;
-  sympass_tile<T, MODE>(I, J, kp, Mat, V, Part);
-}
-
-// Many views in one launch: block b takes tile tiles[b] = (view, I, J) and the
-// view's matrix, vector and partial-sum slices from its descriptor.
+// Views of a pass: block b takes tile tiles[b] = (view, I, J), I <= J, and the
+// view's matrix, vector, partial-sum and counter slices from its descriptor.
+// A single view is the case of one descriptor.
 struct BatchView {
   int64_t mat_off;   // elements into the batched kp x kp matrices
   int64_t vec_off;   // 2-vectors into the batched coordinate / b vectors (kp each)
   int64_t part_off;  // 2-vectors into the batched partial sums (nbt x kp each)
-  int32_t kp, nbt, k, pad;
+  int32_t kp, nbt, k, cnt_off;  // cnt_off: the view's nbt row-block counters
 };
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
 k_sympass_batch(const int4 *__restrict__ tiles, const BatchView *__restrict__ views, const T *__restrict__ Mat,
-                const typename T2<T>::type *__restrict__ V, typename T2<T>::type *__restrict__ Part) {
+                const typename T2<T>::type *__restrict__ V, typename T2<T>::type *__restrict__ Part,
+                int *__restrict__ cnt, typename T2<T>::type *__restrict__ Vout) {
   const int4 t = tiles[blockIdx.x];
   const BatchView bv = views[t.x];
-  sympass_tile<T, MODE>(t.y, t.z, bv.kp, Mat + bv.mat_off, V + bv.vec_off, Part + bv.part_off);
-}
-
-// V[row] = sum_{o < nbt} Part[o][row] for every view (blockIdx.y) in order.
-template <typename T>
-__global__ void k_reduce_parts_batch(const BatchView *__restrict__ views, const typename T2<T>::type *__restrict__ Part,
-                                     typename T2<T>::type *__restrict__ V) {
-  const BatchView bv = views[blockIdx.y];
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= bv.kp) return;
-  const typename T2<T>::type *p = Part + bv.part_off;
-  typename T2<T>::type s = p[r];
-  for (int o = 1; o < bv.nbt; ++o) {
-    const typename T2<T>::type u = p[(int64_t)o * bv.kp + r];
-    s.x += u.x;
-    s.y += u.y;
-  }
-  V[bv.vec_off + r] = s;
-}
-
-// V[row] = sum_{o < nb} Part[o][row], in order.
-template <typename T>
-__global__ void k_reduce_parts(int32_t kp, int nb, const typename T2<T>::type *__restrict__ Part,
-                               typename T2<T>::type *__restrict__ V) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= kp) return;
-  typename T2<T>::type s = Part[r];
-  for (int o = 1; o < nb; ++o) {
-    const typename T2<T>::type u = Part[(int64_t)o * kp + r];
-    s.x += u.x;
-    s.y += u.y;
-  }
-  V[r] = s;
+  sympass_tile<T, MODE>(t.y, t.z, bv.kp, bv.nbt, Mat + bv.mat_off, V + bv.vec_off, Part + bv.part_off,
+                        cnt + bv.cnt_off, Vout + bv.vec_off);
 }
 
 // X (kp x 2) = x0 for rows < k, zero on the padding.
@@ -448,7 +458,7 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
   const int nbt = kp / ST;
   PPRVIZ_TRY(ws_ensure(ctx, WS_W1, sizeof(T) * (size_t)kp * kp));
   PPRVIZ_TRY(ws_ensure(ctx, WS_M, sizeof(T) * (size_t)kp * kp));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(T) * (size_t)(2 * NB * kp + NB * NB + 64)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(T) * spd_inverse_work(kp)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_X, sizeof(V2) * (size_t)kp * 2));            // X and b
   PPRVIZ_TRY(ws_ensure(ctx, WS_B, sizeof(V2) * (size_t)nbt * kp));          // partial sums
   PPRVIZ_TRY(ws_ensure(ctx, WS_E, sizeof(V2) * (size_t)k + 64));
@@ -474,16 +484,26 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
   }
   { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<TI, T><<<(unsigned)((kp + 255) / 256), 256, 0, ctx->stream>>>(k, kp, x0, X); }
   PPRVIZ_LAUNCHED(ctx);
-  const dim3 grid((unsigned)nbt, (unsigned)nbt);
-  const unsigned rgrid = (unsigned)((kp + 255) / 256);
+  // one view descriptor, the upper tile triangle in row order, and the
+  // row-block counters of the fused reduce (zero between passes)
+  std::vector<int4> tiles;
+  for (int I = 0; I < nbt; ++I)
+    for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(0, I, J, 0));
+  const BatchView one{0, 0, 0, kp, nbt, k, 0};
+  const size_t tab_off = 256, cnt_off = (tab_off + sizeof(int4) * tiles.size() + 255) & ~(size_t)255;
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BTAB, cnt_off + sizeof(int) * (size_t)nbt));
+  BatchView *view_d = reinterpret_cast<BatchView *>(ctx->ws[WS_BTAB].p);
+  int4 *tiles_d = reinterpret_cast<int4 *>(static_cast<unsigned char *>(ctx->ws[WS_BTAB].p) + tab_off);
+  int *cnt = reinterpret_cast<int *>(static_cast<unsigned char *>(ctx->ws[WS_BTAB].p) + cnt_off);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_d, &one, sizeof(BatchView), cudaMemcpyHostToDevice, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(tiles_d, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)nbt, ctx->stream));
+  const unsigned ntile = (unsigned)tiles.size();
   for (int it = 0; it < iters; ++it) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass<T, 0><<<grid, 256, 0, ctx->stream>>>(kp, W1, X, Part); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<T, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, view_d, W1, X, Part, cnt, Bv); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, Bv); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass<T, 1><<<grid, 256, 0, ctx->stream>>>(kp, A, Bv, Part); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts<T><<<rgrid, 256, 0, ctx->stream>>>(kp, nbt, Part, X); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<T, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, view_d, A, Bv, Part, cnt, X); }
     PPRVIZ_LAUNCHED(ctx);
   }
   V2 *Xc = ctx->ws[WS_E].as<V2>();
@@ -536,21 +556,24 @@ int layout_run(pprviz_ctx *ctx, const void *pdist_d, int32_t k, const void *x0_d
 }
 
 // Many views, FP32: each view's 1/Delta_s and (L^w + J/k)^-1 are built and
-// inverted into slices of two batched matrices, then every update runs as four
-// launches over all views together (L^Y pass, reduce, apply pass, reduce).
+// inverted into slices of two batched matrices, then every update runs as two
+// launches over all views together (L^Y pass, apply pass, each with its fused
+// partial-sum reduce).
 int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const float *pdist_d,
                      const float *x0_d, int32_t iters, float *x_out_d, double *stress_h) {
   using V2 = float2;
   std::vector<BatchView> bv((size_t)nviews);
   std::vector<int4> tiles;
   int64_t mat = 0, vec = 0, part = 0, maxkp = 0;
+  int32_t cnts = 0;
   for (int32_t v = 0; v < nviews; ++v) {
     const int32_t k = (int32_t)k_h[v];
     const int32_t kp = (k + ST - 1) / ST * ST, nbt = kp / ST;
-    bv[v] = BatchView{mat, vec, part, kp, nbt, k, 0};
+    bv[v] = BatchView{mat, vec, part, kp, nbt, k, cnts};
     mat += (int64_t)kp * kp;
     vec += kp;
     part += (int64_t)nbt * kp;
+    cnts += nbt;
     maxkp = std::max<int64_t>(maxkp, kp);
     for (int I = 0; I < nbt; ++I)
       for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(v, I, J, 0));
@@ -559,18 +582,22 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   PPRVIZ_TRY(ws_ensure(ctx, WS_BM, sizeof(float) * (size_t)mat));
   PPRVIZ_TRY(ws_ensure(ctx, WS_BX, sizeof(V2) * (size_t)vec * 2));
   PPRVIZ_TRY(ws_ensure(ctx, WS_BPART, sizeof(V2) * (size_t)part));
-  // the tile table (int4, 16-byte loads) starts at a 256-byte boundary after the descriptors
+  // the tile table (int4, 16-byte loads) starts at a 256-byte boundary after the
+  // descriptors, the row-block counters at the next one after the table
   const size_t tab_off = (sizeof(BatchView) * (size_t)nviews + 255) & ~(size_t)255;
-  PPRVIZ_TRY(ws_ensure(ctx, WS_BTAB, tab_off + sizeof(int4) * tiles.size()));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(float) * (size_t)(2 * NB * maxkp + NB * NB + 64)));
+  const size_t cnt_off = (tab_off + sizeof(int4) * tiles.size() + 255) & ~(size_t)255;
+  PPRVIZ_TRY(ws_ensure(ctx, WS_BTAB, cnt_off + sizeof(int) * (size_t)cnts));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(float) * spd_inverse_work(maxkp)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sizeof(double) * (size_t)(maxkp / 32) * maxkp));
   PPRVIZ_TRY(ws_ensure(ctx, WS_FLAG, 64));
   float *W1 = ctx->ws[WS_BW1].as<float>(), *M = ctx->ws[WS_BM].as<float>(), *work = ctx->ws[WS_PIV].as<float>();
   V2 *X = ctx->ws[WS_BX].as<V2>(), *Bv = X + vec, *Part = ctx->ws[WS_BPART].as<V2>();
   BatchView *views_d = reinterpret_cast<BatchView *>(ctx->ws[WS_BTAB].p);
   int4 *tiles_d = reinterpret_cast<int4 *>(static_cast<unsigned char *>(ctx->ws[WS_BTAB].p) + tab_off);
+  int *cnt = reinterpret_cast<int *>(static_cast<unsigned char *>(ctx->ws[WS_BTAB].p) + cnt_off);
   double *rowpart = ctx->ws[WS_RHS].as<double>();
   int *flag = ctx->ws[WS_FLAG].as<int>();
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)cnts, ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(views_d, bv.data(), sizeof(BatchView) * bv.size(), cudaMemcpyHostToDevice,
                                    ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(tiles_d, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
@@ -595,15 +622,10 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hf) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "a view's pdist has a non-finite or non-positive entry");
   const unsigned ntile = (unsigned)tiles.size();
-  const dim3 rgrid((unsigned)((maxkp + 255) / 256), (unsigned)nviews);
   for (int it = 0; it < iters; ++it) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<float, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, W1, X, Part); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<float, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, W1, X, Part, cnt, Bv); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, Bv); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<float, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, M, Bv, Part); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_parts_batch<float><<<rgrid, 256, 0, ctx->stream>>>(views_d, Part, X); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<float, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, M, Bv, Part, cnt, X); }
     PPRVIZ_LAUNCHED(ctx);
   }
   ctx->stats.layout_iters = iters;

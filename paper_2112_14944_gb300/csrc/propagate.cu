@@ -21,6 +21,13 @@
 //    and the three-term Chebyshev recurrence converges with rate
 //    rho = (1 - sqrt(1 - c^2)) / c (0.557 at alpha = 0.15, vs 0.85 for the
 //    power iteration), needing no inner products.
+//  * Deflated start: the coefficient of a row on the stationary vector of its
+//    source's component is known exactly (1 for x (I - cP) = alpha e_s, and
+//    sum_j r_j / alpha for a correction system with right-hand side r), so
+//    every solve starts from that multiple of the stationary vector (uniform
+//    in y) and only the remaining modes, with |lambda| <= b (estimated per
+//    graph), are iterated: Chebyshev on [1 - cb, 1 + cb], rate
+//    (1 - sqrt(1 - (cb)^2)) / (cb), e.g. 0.21 instead of 0.557 at b = 0.48.
 //  * The certificate (Eq. (3)): with res = alpha e_s - x (I - cP) computed in
 //    FP64, the exact row is x + res Pi / alpha, so every DPPR entry of the row
 //    is within d(s) ||res||_1 / alpha. FP32 rows are refined: the FP32
@@ -85,6 +92,26 @@ __global__ void k_init_rhs(int64_t n, int64_t ld, const float *__restrict__ rhs,
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * ld) return;
   y[idx] = rhs[idx] * invdw[idx / ld];
+}
+
+// Deflated start of a solve for the sources of a group: on the component of
+// source q (root csrc[q], -1 for a padded column) y_0 = kappa[q], the
+// coefficient on the stationary vector (uniform in y); y_1 = c y_0 + b / dw,
+// the first Chebyshev step from y_0 (P fixes the stationary vector), with
+// b = alpha e_s, or the rhs of a correction system.
+__global__ void k_init_defl(int64_t n, int64_t ld, const int32_t *__restrict__ comp,
+                            const int32_t *__restrict__ csrc, const double *__restrict__ kappa,
+                            const int32_t *__restrict__ src, const float *__restrict__ rhs,
+                            const float *__restrict__ invdw, float alpha, float c, float *__restrict__ y0,
+                            float *__restrict__ y1) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * ld) return;
+  const int64_t j = idx / ld, q = idx - j * ld;
+  const int32_t cs = csrc[q];
+  const float v0 = (cs >= 0 && comp[j] == cs) ? (float)kappa[q] : 0.0f;
+  const float b = rhs ? rhs[idx] : ((src[q] == (int32_t)j) ? alpha : 0.0f);
+  y0[idx] = v0;
+  y1[idx] = c * v0 + b * invdw[j];
 }
 
 __global__ void k_axpy(int64_t count, const float *__restrict__ x, float *__restrict__ y) {
@@ -239,30 +266,42 @@ __device__ __forceinline__ void load4(const double *hi, const float *lo, double 
 // FP64 residual of the computed rows x = dw * (y_hi + y_lo) against the
 // original system x (I - cP) = alpha e_s:
 //   res_jq = alpha [j == src[q]] - x_jq + c * sum_{i in N(j)} w_ij (y_hi + y_lo)[i][q]
-// written (rounded to FP32) into rhs_out for the refinement, and
-// sum_j |res_jq| added into l1[q] (FP64).
-// Grid: (nchunks, row blocks); each warp walks rows with a stride so its
-// per-source partial sums are reduced once per block.
+// written (rounded to FP32) into rhs_out for the refinement; the block's
+// sums of |res_jq| and res_jq per source go to part[blockIdx.x][0 / 1][q]
+// (FP64), which k_res_reduce sums in a fixed order.
+// Grid: (row blocks, nchunks), row blocks fastest, so that the 128-source
+// chunks are processed roughly one after another and the state columns being
+// gathered stay resident in L2 even when the whole group does not fit; each
+// warp walks rows with a stride so its per-source partial sums are reduced
+// once per block.
 template <typename T, bool WEIGHTED, bool EXACT>
 __global__ void __launch_bounds__(kWarps * 32)
 k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-           const float *__restrict__ w, const double *__restrict__ invdw,
+           const float *__restrict__ w, const double *__restrict__ invdw, const float2 *__restrict__ dwff,
            const int32_t *__restrict__ src, const T *__restrict__ yhi, const float *__restrict__ ylo,
-           float *__restrict__ rhs_out, double *__restrict__ l1, double alpha, double c) {
+           float *__restrict__ rhs_out, double *__restrict__ part_out, double alpha, double c) {
   constexpr int VEC = 4;  // 128 sources per warp chunk for both state types
   __shared__ double red[kWarps][32 * VEC];
+  __shared__ double reds[kWarps][32 * VEC];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t chunk = blockIdx.x;
+  const int64_t chunk = blockIdx.y;
   const int64_t off = chunk * (32 * VEC) + lane * VEC;
   int32_t sq[VEC];
 #pragma unroll
   for (int u = 0; u < VEC; ++u) sq[u] = src[off + u];
-  double part[VEC];
+  // alpha and c as float-float pairs (float-float residual of the FP32 path)
+  const float alh = (float)alpha, all = (float)(alpha - (double)alh);
+  const float ch = (float)c, cl = (float)(c - (double)ch);
+  double part[VEC], psig[VEC];
+  float fpart[VEC], fpsig[VEC];  // the float-float path's per-lane sums
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) part[u] = 0.0;
-  const int64_t stride = (int64_t)gridDim.y * kWarps;
-  for (int64_t j = (int64_t)blockIdx.y * kWarps + warp; j < n; j += stride) {
+  for (int u = 0; u < VEC; ++u) {
+    part[u] = psig[u] = 0.0;
+    fpart[u] = fpsig[u] = 0.0f;
+  }
+  const int64_t stride = (int64_t)gridDim.x * kWarps;
+  for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < n; j += stride) {
     double acc[VEC];
 #pragma unroll
     for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
@@ -271,59 +310,121 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
       // Error-free FP32 accumulation of sum_i w_ij (y_hi + y_lo)_i: TwoSum
       // (Knuth) keeps the exact rounding error of every addition of the high
       // parts, FMA the exact error of every weighted product; the
-      // compensation is flushed into FP64 after every 32 edges and the sum is
-      // assembled in FP64. Relative error <= ~1e-12 per 32-edge batch.
-      float shi[VEC], sc[VEC], slo[VEC];
+      // compensation is flushed into a float-float accumulator (ah, al) after
+      // every 32 edges. The residual is then formed in float-float arithmetic
+      // (TwoProd by FMA, TwoSum), ~2^-48 relative to the row: GB300's FP64
+      // rate is too low to spend FP64 operations per (node, source).
+      float shi[VEC], sc[VEC], slo[VEC], ah[VEC], al[VEC];
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) shi[u] = sc[u] = slo[u] = 0.0f;
+      for (int u = 0; u < VEC; ++u) shi[u] = sc[u] = slo[u] = ah[u] = al[u] = 0.0f;
       for (int64_t base = b; base < e; base += 32) {
         const int cnt = (int)min((int64_t)32, e - base);
         int32_t myc = lane < cnt ? col[base + lane] : 0;
         float myw = 1.0f;
         if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
-        for (int t = 0; t < cnt; ++t) {
-          const int32_t i = __shfl_sync(0xffffffffu, myc, t);
-          const float wi = WEIGHTED ? __shfl_sync(0xffffffffu, myw, t) : 1.0f;
-          const int64_t p = (int64_t)i * ld + off;
-          float h[VEC], l[VEC];
-          Vec<float>::load(reinterpret_cast<const float *>(yhi) + p, h);
-          if (ylo) Vec<float>::load(ylo + p, l);
+        // GB neighbour rows in flight, then accumulated in edge order
+        constexpr int GB = WEIGHTED ? 4 : 8;
+        for (int t0 = 0; t0 < cnt; t0 += GB) {
+          float h[GB][VEC], l[GB][VEC], wv[GB];
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) {
-            float a = h[u], pe = 0.0f;
-            if (WEIGHTED) {
-              a = wi * h[u];
-              pe = fmaf(wi, h[u], -a);
+          for (int q = 0; q < GB; ++q) {
+            const int32_t i = __shfl_sync(0xffffffffu, myc, (t0 + q) & 31);
+            wv[q] = WEIGHTED ? __shfl_sync(0xffffffffu, myw, (t0 + q) & 31) : 1.0f;
+            if (t0 + q < cnt) {
+              const int64_t p = (int64_t)i * ld + off;
+              Vec<float>::load(reinterpret_cast<const float *>(yhi) + p, h[q]);
+              if (ylo) Vec<float>::load(ylo + p, l[q]);
             }
-            const float s = shi[u] + a;
-            const float bb = s - shi[u];
-            sc[u] += ((shi[u] - (s - bb)) + (a - bb)) + pe;
-            shi[u] = s;
-            if (ylo) slo[u] = fmaf(wi, l[u], slo[u]);
+          }
+#pragma unroll
+          for (int q = 0; q < GB; ++q) {
+            if (t0 + q >= cnt) break;
+            const float wi = wv[q];
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+              float a = h[q][u], pe = 0.0f;
+              if (WEIGHTED) {
+                a = wi * h[q][u];
+                pe = fmaf(wi, h[q][u], -a);
+              }
+              const float s = shi[u] + a;
+              const float bb = s - shi[u];
+              sc[u] += ((shi[u] - (s - bb)) + (a - bb)) + pe;
+              shi[u] = s;
+              if (ylo) slo[u] = fmaf(wi, l[q][u], slo[u]);
+            }
           }
         }
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          acc[u] += (double)sc[u];
+          const float t = ah[u] + sc[u];
+          const float bb = t - ah[u];
+          al[u] += (ah[u] - (t - bb)) + (sc[u] - bb);
+          ah[u] = t;
           sc[u] = 0.0f;
         }
       }
+      const int64_t rowoff = j * ld + off;
+      const float2 dwp = dwff[j];
+      const float dwh = dwp.x, dwl = dwp.y;
+      float hrow[VEC], lrow[VEC];
+      Vec<float>::load(reinterpret_cast<const float *>(yhi) + rowoff, hrow);
+      if (ylo) Vec<float>::load(ylo + rowoff, lrow);
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[u] += (double)shi[u] + (double)slo[u];
+      for (int u = 0; u < VEC; ++u) {
+        if (!ylo) lrow[u] = 0.0f;
+        // S = shi + ah + al + slo (the neighbour sum), as float-float
+        float Sh = shi[u] + ah[u];
+        const float bb = Sh - shi[u];
+        float Sl = ((shi[u] - (Sh - bb)) + (ah[u] - bb)) + (al[u] + slo[u]);
+        if (e == b) {  // no edges: the walk stays on j
+          Sh = hrow[u];
+          Sl = lrow[u];
+        }
+        // X = dw y and C = c S as unevaluated sums (TwoProd by FMA)
+        const float p1 = dwh * hrow[u];
+        const float t1 = fmaf(dwh, lrow[u], fmaf(dwl, hrow[u], fmaf(dwh, hrow[u], -p1)));
+        const float p2 = ch * Sh;
+        const float t2 = fmaf(ch, Sl, fmaf(cl, Sh, fmaf(ch, Sh, -p2)));
+        // r = b - X + C with the large terms combined by TwoSum
+        const float s1 = p2 - p1;
+        const float b1 = s1 - p2;
+        const float e1 = (p2 - (s1 - b1)) + (-p1 - b1);
+        const bool src_here = sq[u] == (int32_t)j;
+        const float bh = src_here ? alh : 0.0f, bl = src_here ? all : 0.0f;
+        const float s2 = s1 + bh;
+        const float b2 = s2 - s1;
+        const float e2 = (s1 - (s2 - b2)) + (bh - b2);
+        const float r = s2 + (((e1 + e2) + (t2 - t1)) + bl);
+        if (rhs_out) rhs_out[rowoff + u] = r;
+        fpart[u] += fabsf(r);
+        fpsig[u] += r;
+      }
+      continue;
     } else {
       for (int64_t base = b; base < e; base += 32) {
         const int cnt = (int)min((int64_t)32, e - base);
         int32_t myc = lane < cnt ? col[base + lane] : 0;
         float myw = 1.0f;
         if (WEIGHTED) myw = lane < cnt ? w[base + lane] : 0.0f;
-        for (int t = 0; t < cnt; ++t) {
-          const int32_t i = __shfl_sync(0xffffffffu, myc, t);
-          const double wi = WEIGHTED ? (double)__shfl_sync(0xffffffffu, myw, t) : 1.0;
-          const int64_t p = (int64_t)i * ld + off;
-          double v[VEC];
-          load4(yhi + p, ylo ? ylo + p : nullptr, v);
+        // 4 neighbour rows in flight, then accumulated in edge order
+        for (int t0 = 0; t0 < cnt; t0 += 4) {
+          double v[4][VEC], wv[4];
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) acc[u] += wi * v[u];
+          for (int q = 0; q < 4; ++q) {
+            const int32_t i = __shfl_sync(0xffffffffu, myc, (t0 + q) & 31);
+            wv[q] = WEIGHTED ? (double)__shfl_sync(0xffffffffu, myw, (t0 + q) & 31) : 1.0;
+            if (t0 + q < cnt) {
+              const int64_t p = (int64_t)i * ld + off;
+              load4(yhi + p, ylo ? ylo + p : nullptr, v[q]);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (t0 + q >= cnt) break;
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[u] += wv[q] * v[q][u];
+          }
         }
       }
     }
@@ -339,16 +440,47 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
       const double r = bq - dw * y + c * acc[u];
       if (rhs_out) rhs_out[rowoff + u] = (float)r;
       part[u] += fabs(r);
+      psig[u] += r;
     }
   }
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) red[warp][lane * VEC + u] = part[u];
+  for (int u = 0; u < VEC; ++u) {
+    red[warp][lane * VEC + u] = part[u] + (double)fpart[u];
+    reds[warp][lane * VEC + u] = psig[u] + (double)fpsig[u];
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
-    double s = 0.0;
+    double s = 0.0, ss = 0.0;
 #pragma unroll
-    for (int wv = 0; wv < kWarps; ++wv) s += red[wv][t];
-    atomicAdd(&l1[chunk * (32 * VEC) + t], s);
+    for (int wv = 0; wv < kWarps; ++wv) {
+      s += red[wv][t];
+      ss += reds[wv][t];
+    }
+    part_out[((int64_t)blockIdx.x * 2 + 0) * ld + chunk * (32 * VEC) + t] = s;
+    part_out[((int64_t)blockIdx.x * 2 + 1) * ld + chunk * (32 * VEC) + t] = ss;
+  }
+}
+
+// l1[q] = sum_b part[b][0][q], sig[q] = sum_b part[b][1][q] in a fixed order:
+// one warp per source, lane l sums blocks l, l + 32, ... in turn, then a
+// fixed butterfly over the lanes.
+__global__ void k_res_reduce(int64_t ld, int nblocks, const double *__restrict__ part, double *__restrict__ l1,
+                             double *__restrict__ sig) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= ld) return;
+  double s = 0.0, ss = 0.0;
+  for (int b = lane; b < nblocks; b += 32) {
+    s += part[((int64_t)b * 2 + 0) * ld + q];
+    ss += part[((int64_t)b * 2 + 1) * ld + q];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if (lane == 0) {
+    l1[q] = s;
+    sig[q] = ss;
   }
 }
 
@@ -441,46 +573,71 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
 template <typename T, bool EXACT>
 int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha) {
+  // l1 holds 2 * ld doubles: sum |res| per source, then sum res per source
   const int nchunks = (int)(ld / 128);
-  int rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps, std::max(1, 1216 / nchunks));
-  dim3 grid(nchunks, rows_blocks);
-  PPRVIZ_CUDA(ctx, cudaMemsetAsync(l1, 0, sizeof(double) * (size_t)ld, ctx->stream));
+  // ~1,216 CTAs in all when the group's state fits in L2; otherwise ~608 per
+  // chunk (about the resident CTAs of the GPU), so that the chunks run one
+  // after another and only ~one chunk's columns are gathered at a time
+  const bool fits_l2 = (double)g->n * (double)ld * 8.0 <= 64.0 * 1024 * 1024;
+  int rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps, fits_l2 ? std::max(1, 1216 / nchunks) : 608);
+  dim3 grid(rows_blocks, nchunks);
+  PPRVIZ_TRY(ws_ensure(ctx, WS_RPART, sizeof(double) * 2 * (size_t)rows_blocks * (size_t)ld));
+  double *part = ctx->ws[WS_RPART].as<double>();
   if (g->weighted)
     { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, true, EXACT><<<grid, kWarps * 32, 0, ctx->stream>>>(
         g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), g->w.as<float>(), g->invdw_d.as<double>(),
-        src, yhi, ylo, rhs_out, l1, alpha, 1.0 - alpha); }
+        g->dwff.as<float2>(), src, yhi, ylo, rhs_out, part, alpha, 1.0 - alpha); }
   else
     { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, false, EXACT><<<grid, kWarps * 32, 0, ctx->stream>>>(
-        g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), nullptr, g->invdw_d.as<double>(), src,
-        yhi, ylo, rhs_out, l1, alpha, 1.0 - alpha); }
+        g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), nullptr, g->invdw_d.as<double>(),
+        g->dwff.as<float2>(), src, yhi, ylo, rhs_out, part, alpha, 1.0 - alpha); }
+  PPRVIZ_LAUNCHED(ctx);
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_res_reduce<<<(unsigned)((ld * 32 + 255) / 256), 256, 0, ctx->stream>>>(ld, rows_blocks, part, l1, l1 + ld); }
   PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
 }
 
 // certificates of the group's sources: d(s) * ||res_s||_1 / alpha
+// (and the signed residual sums sigma_q = sum_j res_jq, which fix the
+// stationary coefficient of the next correction)
 int read_certs(pprviz_ctx *ctx, const pprviz_graph *g, const std::vector<int32_t> &view_h, int32_t g0,
-               int32_t gvalid, const double *l1_d, double alpha, std::vector<double> &cert) {
-  std::vector<double> l1((size_t)gvalid);
-  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(l1.data(), l1_d, sizeof(double) * (size_t)gvalid,
+               int32_t gvalid, int64_t ld, const double *l1_d, double alpha, std::vector<double> &cert,
+               std::vector<double> &sigma) {
+  std::vector<double> l1((size_t)2 * ld);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(l1.data(), l1_d, sizeof(double) * 2 * (size_t)ld,
                                    cudaMemcpyDeviceToHost, ctx->stream));
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   cert.resize((size_t)gvalid);
-  for (int32_t q = 0; q < gvalid; ++q) cert[q] = g->h_deg[view_h[g0 + q]] * l1[q] / alpha;
+  sigma.assign((size_t)ld, 0.0);
+  for (int32_t q = 0; q < gvalid; ++q) {
+    cert[q] = g->h_deg[view_h[g0 + q]] * l1[q] / alpha;
+    sigma[q] = l1[(size_t)ld + q];
+  }
   return PPRVIZ_OK;
 }
 
 double chebyshev_rate(double c) { return (1.0 - sqrt(1.0 - c * c)) / c; }
 
-// Runs `sweeps` Chebyshev steps of x (I - cP) = b from x_0 = 0, x_1 = b.
+// Runs `sweeps` Chebyshev steps of x (I - cP) = b for the interval
+// [1 - delta, 1 + delta] of the iterated modes. Without deflation (csrc ==
+// nullptr, delta = c) from x_0 = 0, x_1 = b; with it from the stationary
+// multiple x_0 = kappa (in y) and x_1 = c x_0 + b.
 // On entry ya, yb are the two state buffers; returns the buffer holding the
 // last iterate.  b is the source delta (rhs == nullptr) or the dense rhs.
 // `tcerr` non-null selects the dense tensor-core sweeps (it receives their
 // error word); otherwise the CSR gather sweeps run.
 int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     int32_t gcount, const float *rhs, float *ya, float *yb, int sweeps,
-                    double alpha, int *tcerr, float **result) {
+                    double alpha, int *tcerr, const int32_t *csrc, const double *kappa, double delta,
+                    float **result) {
   const size_t bytes = sizeof(float) * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
+  if (csrc) {
+    const int64_t cnt = g->n * ld;
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_defl<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(
+        g->n, ld, g->comp.as<int32_t>(), csrc, kappa, src, rhs, g->invdw_f.as<float>(), (float)alpha, (float)c, ya, yb); }
+    PPRVIZ_LAUNCHED(ctx);
+  } else {
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(ya, 0, bytes, ctx->stream));
   if (rhs) {
     const int64_t cnt = g->n * ld;
@@ -492,11 +649,13 @@ int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
                                                                       (float)alpha, yb); }
     PPRVIZ_LAUNCHED(ctx);
   }
-  // theta = 1, delta = c: omega_2 = 1 / (1 - c^2 / 2), omega_{k+1} = 1 / (1 - c^2 omega_k / 4)
+  }
+  // theta = 1: omega_2 = 1 / (1 - delta^2 / 2), omega_{k+1} = 1 / (1 - delta^2 omega_k / 4)
   double om = 1.0;
   float *cur = yb, *old = ya;
+  const double d2 = delta * delta;
   for (int s = 1; s < sweeps; ++s) {
-    om = (s == 1) ? 1.0 / (1.0 - c * c / 2.0) : 1.0 / (1.0 - c * c * om / 4.0);
+    om = (s == 1) ? 1.0 / (1.0 - d2 / 2.0) : 1.0 / (1.0 - d2 * om / 4.0);
     if (tcerr)
       PPRVIZ_TRY(dense_sweep(ctx, g, ld, src, rhs, cur, old, alpha, om, tcerr));
     else
@@ -535,9 +694,25 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
     PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sbytes));
   }
   PPRVIZ_TRY(ws_ensure(ctx, WS_SRC, sizeof(int32_t) * (size_t)ld));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, sizeof(double) * (size_t)ld));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, 2 * sizeof(double) * (size_t)ld));
   int32_t *src = ctx->ws[WS_SRC].as<int32_t>();
   double *l1 = ctx->ws[WS_CERT].as<double>();
+  // deflated sweeps (FP32): component roots and the spectral bound of the graph
+  bool defl = false;
+  double bsp = 1.0;
+  int32_t *csrc = nullptr;
+  double *kappa = nullptr;
+  if (!fp64) {
+    PPRVIZ_TRY(graph_spectral(ctx, g));
+    defl = g->spec_deflate;
+    bsp = defl ? g->spec_b : 1.0;
+    PPRVIZ_TRY(ws_ensure(ctx, WS_CSRC, sizeof(int32_t) * (size_t)ld));
+    PPRVIZ_TRY(ws_ensure(ctx, WS_KAPPA, sizeof(double) * (size_t)ld));
+    csrc = ctx->ws[WS_CSRC].as<int32_t>();
+    kappa = ctx->ws[WS_KAPPA].as<double>();
+  }
+  std::vector<int32_t> csrc_h((size_t)ld, -1);
+  std::vector<double> kappa_h((size_t)ld, 0.0), sigma;
   int *tcerr = nullptr;
   if (dense) {
     PPRVIZ_TRY(ws_ensure(ctx, WS_FLAG, 64));
@@ -549,7 +724,11 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   std::vector<int32_t> srch((size_t)ld);
   std::vector<double> cert;
   bool not_converged = false;
-  const double rho = chebyshev_rate(c);
+  // rate of the iterated modes on [1 - delta, 1 + delta]
+  auto rate = [](double delta) { return delta > 1e-12 ? chebyshev_rate(delta) : 0.0; };
+  auto sweeps_for = [](double factor, double r) {  // K with 2 r^K <= factor
+    return r > 0.0 ? (int)ceil(log(0.5 * factor) / log(r)) : 1;
+  };
   // the compensated FP32 residual resolves certificates down to ~1e-9; below
   // that the neighbour sums are accumulated in FP64
   const bool exact_res = eps < 1e-9;
@@ -582,18 +761,32 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       st.bytes_sweep += 16.0 * (double)g->n * gvalid * T;
       PPRVIZ_TRY((launch_residual<double, true>(ctx, g, ld, src, cur, nullptr, nullptr, l1, alpha)));
       st.residual_passes++;
-      PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
+      PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, ld, l1, alpha, cert, sigma));
       yhi = cur;
     } else {
       float *bufs[4] = {ctx->ws[WS_Y0].as<float>(), ctx->ws[WS_Y1].as<float>(), ctx->ws[WS_Y2].as<float>(),
                         ctx->ws[WS_Y3].as<float>()};
       float *rhs = ctx->ws[WS_RHS].as<float>();
+      // deflated start: the source's component root per column, and the
+      // stationary coefficient 1 / m_C of the main system
+      if (defl) {
+        for (int64_t q = 0; q < ld; ++q) {
+          csrc_h[q] = q < gvalid ? g->h_comp[view_h[g0 + q]] : -1;
+          kappa_h[q] = q < gvalid ? 1.0 / g->h_mc[(size_t)csrc_h[q]] : 0.0;
+        }
+        PPRVIZ_CUDA(ctx, cudaMemcpyAsync(csrc, csrc_h.data(), sizeof(int32_t) * (size_t)ld, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+        PPRVIZ_CUDA(ctx, cudaMemcpyAsync(kappa, kappa_h.data(), sizeof(double) * (size_t)ld,
+                                         cudaMemcpyHostToDevice, ctx->stream));
+      }
+      double delta_c = c * bsp;
       // main solve to a Chebyshev error bound 2 rho^K <= 1e-5: every further
       // sweep here would only save one refinement sweep, and the refinement
       // (driven by the exact FP64 residual) finishes the job
-      const int K1 = std::max(2, (int)ceil(log(0.5e-5) / log(rho)));
+      const int K1 = std::max(2, sweeps_for(1e-5, rate(delta_c)));
       float *hi = nullptr;
-      PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, tcerr, &hi));
+      PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, tcerr,
+                                 defl ? csrc : nullptr, kappa, delta_c, &hi));
       st.sweeps_main += K1;
       if (dense) st.flops_dense += 2.0 * (double)g->n * (double)g->n * gvalid * (K1 - 1);
       else st.bytes_sweep += 12.0 * (double)g->n * gvalid * (K1 - 1);
@@ -603,18 +796,30 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha)
                             : launch_residual<float, false>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha)));
       st.residual_passes++;
-      PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
+      PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, ld, l1, alpha, cert, sigma));
+      double cprev = 0.0;
       for (int pass = 0; pass < kMaxRefine; ++pass) {
         double cmax = 0.0;
         for (double v : cert) cmax = std::max(cmax, v);
         if (cmax <= eps) break;
+        // a pass that gained less than 10x means modes outside the estimated
+        // interval: iterate the full interval [1 - c, 1 + c] from here on
+        if (pass > 0 && cmax > 0.1 * cprev) delta_c = c;
+        cprev = cmax;
+        // correction's stationary coefficient: sum_j res_jq / alpha over m_C
+        if (defl) {
+          for (int64_t q = 0; q < gvalid; ++q) kappa_h[q] = sigma[q] / (alpha * g->h_mc[(size_t)csrc_h[q]]);
+          PPRVIZ_CUDA(ctx, cudaMemcpyAsync(kappa, kappa_h.data(), sizeof(double) * (size_t)ld,
+                                           cudaMemcpyHostToDevice, ctx->stream));
+        }
         // sweeps for the correction: its Chebyshev error must fall by eps / (4 cmax),
         // but an FP32 correction resolves only ~1e-7 of itself per pass, so
         // sweeps past 2 rho^K ~ 3e-8 are left to the next pass
-        int K2 = (int)ceil(log(0.25 * eps / cmax) / log(rho)) + 2;
+        int K2 = sweeps_for(0.5 * eps / cmax, rate(delta_c)) + 2;
         K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
         float *delta = nullptr;
-        PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, tcerr, &delta));
+        PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, tcerr,
+                                   defl ? csrc : nullptr, kappa, delta_c, &delta));
         st.sweeps_refine += K2;
         if (dense) st.flops_dense += 2.0 * (double)g->n * (double)g->n * gvalid * (K2 - 1);
         else st.bytes_sweep += 16.0 * (double)g->n * gvalid * (K2 - 1);
@@ -636,7 +841,7 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)
                               : launch_residual<float, false>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)));
         st.residual_passes++;
-        PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, l1, alpha, cert));
+        PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, ld, l1, alpha, cert, sigma));
       }
       yhi = hi;
       ylo = lo;
