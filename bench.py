@@ -486,8 +486,8 @@ def run_ours(args, rank, world, local_rank):
         return
     hbm, sm_max, peak_kind = peaks()
     names = {"sweep": ("propagation sweep (k_sweep)", bytes_sweep),
-             "ly": ("all-pairs L^Y pass (k_sympass_batch<0>, partial sums reduced in the same launch)", bytes_ly),
-             "apply": ("(L^w)^+ apply pass (k_sympass_batch<1>, partial sums reduced in the same launch)", bytes_apply)}
+             "ly": ("all-pairs L^Y pass (k_sympass_pipe<0>, persistent, TMA tile pipeline)", bytes_ly),
+             "apply": ("(L^w)^+ apply pass (k_sympass_pipe<1>, persistent, TMA tile pipeline)", bytes_apply)}
     kernels = {}
     for cls, (label, alg) in names.items():
         ms, cnt = ktimes[cls]

@@ -43,6 +43,8 @@ enum Slot {
   WS_BW1, WS_BM, WS_BX, WS_BPART, WS_BTAB, WS_BPD, WS_BXIN, WS_BXOUT,
   // deflated sweeps: spectral scratch, residual partials, per-source roots and coefficients
   WS_SPEC, WS_RPART, WS_CSRC, WS_KAPPA,
+  // tensor maps of the layout pass matrices, row-block table of the reduce
+  WS_TMAP, WS_TROWS, WS_TREC,
   WS_COUNT
 };
 

@@ -21,6 +21,7 @@
 //    per (tile, row) and added in a fixed order: no atomics, reproducible.
 //  * The energy and its gradients recompute every pair from X and Delta; no
 //    k x k intermediate is stored.
+#include <cuda.h>
 #include <math.h>
 
 #include <algorithm>
@@ -148,18 +149,18 @@ __device__ __forceinline__ T lanes_transpose_sum(T (&v)[NV], int lane) {
 }
 
 // sum_{o < nb} p[o * kp] in order o = 0, 1, ...; the loads (L2, since other
-// CTAs wrote them) are issued 16 at a time so that their latencies overlap,
+// CTAs wrote them) are issued 4 at a time so that their latencies overlap,
 // the additions keep the order
 template <typename V2>
 __device__ __forceinline__ V2 sum_parts_in_order(const V2 *p, int64_t kp, int nb) {
   V2 s = __ldcg(p);
-  for (int o0 = 1; o0 < nb; o0 += 16) {
-    V2 u[16];
+  for (int o0 = 1; o0 < nb; o0 += 4) {
+    V2 u[4];
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
+    for (int q = 0; q < 4; ++q)
       if (o0 + q < nb) u[q] = __ldcg(p + (int64_t)(o0 + q) * kp);
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
+    for (int q = 0; q < 4; ++q)
       if (o0 + q < nb) {
         s.x += u[q].x;
         s.y += u[q].y;
@@ -290,6 +291,281 @@ k_sympass_batch(const int4 *__restrict__ tiles, const BatchView *__restrict__ vi
   const BatchView bv = views[t.x];
   sympass_tile<T, MODE>(t.y, t.z, bv.kp, bv.nbt, Mat + bv.mat_off, V + bv.vec_off, Part + bv.part_off,
                         cnt + bv.cnt_off, Vout + bv.vec_off);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 symmetric pass, persistent and pipelined (the FP32 path of the single
+// and the batched layout). One CTA of 16 warps per SM takes a contiguous
+// chunk of the tile table. Each 128 x 128 tile (64 KiB) comes into shared
+// memory with one TMA tensor copy (cp.async.bulk.tensor.2d; a tensor map per
+// view and matrix) that completes on the stage's mbarrier; with PS stages the
+// copies of the next PS - 1 tiles are in flight while the warps work on the
+// current one, so the matrix streams from HBM at copy speed as long as a
+// tile's arithmetic takes less time than its copy. Nothing on the per-tile
+// path waits on global memory: the partial sums are plain stores and are
+// added up by a separate launch (k_reduce_rows), two CTA barriers per tile.
+// Warp w takes tile rows 8w..8w+7, lane l the columns 4l..4l+3 (one
+// conflict-free 16-byte shared-memory read per row). Per pair, as in
+// sympass_tile: row sums to Part[J][i], column sums of off-diagonal tiles to
+// Part[I][j].
+// Every mbarrier wait has an iteration limit: on expiry the CTA sets *err,
+// stops, waits (again bounded) for the copies it issued and returns.
+// ---------------------------------------------------------------------------
+namespace spipe {
+constexpr int PS = 3;                           // pipeline stages
+constexpr int WARPS = 16;
+constexpr int PRW = ST / WARPS;                 // tile rows per warp
+constexpr uint32_t TILE_BYTES = ST * ST * 4;    // one FP32 tile
+constexpr uint32_t VEC_BYTES = ST * 8;          // 128 coordinate pairs
+constexpr uint32_t STAGE_BYTES = TILE_BYTES + 2 * VEC_BYTES;  // tile, rows' and columns' vector slices
+constexpr int SMEM = PS * (int)STAGE_BYTES + 1024;  // stages + alignment slack
+constexpr long WAIT_LIMIT = 1L << 24;           // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < WAIT_LIMIT && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+// One thread: tile (I, J) of the matrix behind `map` and the vector slices
+// V[I 128 ..] and V[J 128 ..] (1 KiB each, plain bulk copies; V is the
+// view's vector) into the stage
+// at dst, all completing on bar (armed with their byte count first). The maps
+// sit in global memory, written by a host copy before the launch; the first
+// use of each map by a CTA is preceded by a tensor-map acquire fence
+// (`fenced` remembers the last map fenced).
+__device__ __forceinline__ void issue_tile(uint32_t dst, uint64_t *bar, const CUtensorMap *map, const float2 *V,
+                                           int I, int J, const CUtensorMap *&fenced) {
+  if (map != fenced) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+    fenced = map;
+  }
+  const uint32_t b = smem_u32(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(STAGE_BYTES) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(J * ST), "r"(I * ST), "r"(b)
+      : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst + TILE_BYTES),
+               "l"(V + (int64_t)I * ST), "r"(VEC_BYTES), "r"(b)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst + TILE_BYTES + VEC_BYTES),
+               "l"(V + (int64_t)J * ST), "r"(VEC_BYTES), "r"(b)
+               : "memory");
+}
+
+// 1/sqrt(max(d2, 2^-100)) on the special-function unit. For coincident points
+// (d2 = 0) the pair's dx, dy are 0, so its term is 0, as the L^Y definition
+// sets it; padding entries carry a zero matrix entry.
+__device__ __forceinline__ float rsqrt_clamped(float d2) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(d2, 0x1p-100f)));
+  return r;
+}
+}  // namespace spipe
+
+// A tile of the FP32 pass: view v, tile (I, J) of its kp x kp matrices, the
+// view's vector offset / 128 and its partial-sum offset (2-vectors).
+struct __align__(16) TileRec {
+  int32_t v, I, J, vblk;
+  int32_t kp, pad;
+  int64_t part_off;
+};
+
+// maps[2 v + MODE]: view v's 1/Delta_s (MODE 0) or M (MODE 1) as a kp x kp
+// FP32 tensor with 128 x 128 boxes. CTA b takes tiles b, b + G, b + 2G, ...
+// of the row-ordered table, so that the tiles in flight at any moment lie
+// side by side in the same 128 matrix rows (whole DRAM pages of each row
+// are read together). Per tile: wait for the stage, read the
+// warp's 8 rows and both vector slices into registers, one CTA barrier
+// (stage consumed), refill the stage with the tile PS ahead, then the
+// arithmetic, so that PS copies are in flight while the warps compute; the
+// tile records are loaded one step ahead. Lane l's four columns are processed
+// as two pairs with Blackwell's paired FP32 instructions (two lanes of work
+// per issue slot).
+template <int MODE>
+__global__ void __launch_bounds__(spipe::WARPS * 32, 1)
+k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *__restrict__ maps,
+               const float2 *__restrict__ V, float2 *__restrict__ Part, int *__restrict__ err) {
+  using namespace spipe;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[PS];
+  __shared__ __align__(16) float colred[WARPS][2 * ST];  // column partials per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = (int)gridDim.x, first = (int)blockIdx.x;
+  const int mine = ntile > first ? (ntile - 1 - first) / G + 1 : 0;
+  const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;  // TMA destinations 1024-byte aligned
+  const unsigned char *sgen = smem_raw + (sbase - smem_u32(smem_raw));
+  const CUtensorMap *fenced = nullptr;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PS; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int n = 0; n < PS && n < mine; ++n) {
+      const TileRec t = tiles[first + n * G];
+      issue_tile(sbase + (uint32_t)n * STAGE_BYTES, &full[n], maps + 2 * t.v + MODE, V + (int64_t)t.vblk * ST, t.I,
+                 t.J, fenced);
+    }
+  }
+  bool ok = true;
+  int waited = 0;  // local tiles whose stage has been waited on
+  TileRec t = mine > 0 ? tiles[first] : TileRec{};
+  const int rbase = warp * PRW;
+  const float sg = MODE == 0 ? -1.0f : 1.0f;
+#pragma unroll 1
+  for (int n = 0; n < mine; ++n) {
+    const int s = n % PS;
+    const TileRec tnext = (n + 1 < mine) ? tiles[first + (n + 1) * G] : t;
+    const TileRec tref = (threadIdx.x == 0 && n + PS < mine) ? tiles[first + (n + PS) * G] : t;  // the refill's record
+    if (!mbar_wait(&full[s], (uint32_t)((n / PS) & 1))) ok = false;
+    waited = n + 1;
+    const unsigned char *stage = sgen + (size_t)s * STAGE_BYTES;
+    const float *stile = reinterpret_cast<const float *>(stage) + rbase * ST + lane * 4;
+    const float2 *svi = reinterpret_cast<const float2 *>(stage + TILE_BYTES) + rbase;
+    const float4 *svj = reinterpret_cast<const float4 *>(stage + TILE_BYTES + VEC_BYTES) + lane * 2;
+    float4 m4[PRW];
+    float2 vi[PRW];
+#pragma unroll
+    for (int r = 0; r < PRW; ++r) {
+      m4[r] = *reinterpret_cast<const float4 *>(stile + r * ST);
+      vi[r] = svi[r];
+    }
+    const float4 c01 = svj[0], c23 = svj[1];  // (x0, y0, x1, y1), (x2, y2, x3, y3)
+    // stage s consumed by every warp; also orders the previous tile's
+    // column-sum reads of colred before this tile's writes
+    if (__syncthreads_and(ok) == 0) {
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0 && n + PS < mine) {
+      issue_tile(sbase + (uint32_t)s * STAGE_BYTES, &full[s], maps + 2 * tref.v + MODE, V + (int64_t)tref.vblk * ST,
+                 tref.I, tref.J, fenced);
+    }
+    // columns 4l..4l+3 as pairs A = (4l, 4l+1), B = (4l+2, 4l+3); MODE 0 keeps
+    // the column coordinates negated
+    const float2 xA = make_float2(sg * c01.x, sg * c01.z), yA = make_float2(sg * c01.y, sg * c01.w);
+    const float2 xB = make_float2(sg * c23.x, sg * c23.z), yB = make_float2(sg * c23.y, sg * c23.w);
+    float2 cxA = make_float2(0.0f, 0.0f), cxB = cxA, cyA = cxA, cyB = cxA;
+    float acc[2 * PRW];
+#pragma unroll
+    for (int r = 0; r < PRW; ++r) {
+      const float2 mA = make_float2(m4[r].x, m4[r].y), mB = make_float2(m4[r].z, m4[r].w);
+      const float2 vx = make_float2(vi[r].x, vi[r].x), vy = make_float2(vi[r].y, vi[r].y);
+      float2 ra, rb;
+      if (MODE == 0) {
+        // t_ij = M_ij (v_i - v_j) / |v_i - v_j|: row i gets +t, column j gets -t
+        const float2 dxA = __fadd2_rn(vx, xA), dyA = __fadd2_rn(vy, yA);
+        const float2 dxB = __fadd2_rn(vx, xB), dyB = __fadd2_rn(vy, yB);
+        const float2 qA = __ffma2_rn(dyA, dyA, __fmul2_rn(dxA, dxA));
+        const float2 qB = __ffma2_rn(dyB, dyB, __fmul2_rn(dxB, dxB));
+        const float2 kA = __fmul2_rn(mA, make_float2(rsqrt_clamped(qA.x), rsqrt_clamped(qA.y)));
+        const float2 kB = __fmul2_rn(mB, make_float2(rsqrt_clamped(qB.x), rsqrt_clamped(qB.y)));
+        ra = __ffma2_rn(kB, dxB, __fmul2_rn(kA, dxA));
+        rb = __ffma2_rn(kB, dyB, __fmul2_rn(kA, dyA));
+        cxA = __ffma2_rn(kA, dxA, cxA);  // sums of +t; negated when stored
+        cxB = __ffma2_rn(kB, dxB, cxB);
+        cyA = __ffma2_rn(kA, dyA, cyA);
+        cyB = __ffma2_rn(kB, dyB, cyB);
+      } else {
+        // row i gets M_ij v_j, column j gets M_ij v_i
+        ra = __ffma2_rn(mB, xB, __fmul2_rn(mA, xA));
+        rb = __ffma2_rn(mB, yB, __fmul2_rn(mA, yA));
+        cxA = __ffma2_rn(mA, vx, cxA);
+        cxB = __ffma2_rn(mB, vx, cxB);
+        cyA = __ffma2_rn(mA, vy, cyA);
+        cyB = __ffma2_rn(mB, vy, cyB);
+      }
+      acc[2 * r] = ra.x + ra.y;
+      acc[2 * r + 1] = rb.x + rb.y;
+    }
+    const int64_t kp = t.kp;
+    const int64_t i0 = (int64_t)t.I * ST, j0 = (int64_t)t.J * ST;
+    float *part = reinterpret_cast<float *>(Part + t.part_off);
+    const float tot = lanes_transpose_sum<2 * PRW, float>(acc, lane);
+    constexpr int REP = 32 / (2 * PRW);
+    if (lane % REP == 0) {
+      const int idx = lane / REP;
+      part[((int64_t)t.J * kp + i0 + rbase + (idx >> 1)) * 2 + (idx & 1)] = tot;
+    }
+    {
+      float4 *cr = reinterpret_cast<float4 *>(&colred[warp][lane * 8]);  // columns 4l..4l+3, (x, y) each
+      cr[0] = make_float4(sg * cxA.x, sg * cyA.x, sg * cxA.y, sg * cyA.y);
+      cr[1] = make_float4(sg * cxB.x, sg * cyB.x, sg * cxB.y, sg * cyB.y);
+    }
+    __syncthreads();  // column partials complete
+    if (t.I != t.J && threadIdx.x < 2 * ST) {
+      float c = 0.0f;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) c += colred[w][threadIdx.x];
+      part[((int64_t)t.I * kp + j0) * 2 + threadIdx.x] = c;
+    }
+    t = tnext;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      atomicOr(err, 1);
+      // the copies issued for local tiles waited - 1 .. waited + PS - 2 may still be landing
+      for (int n = waited - 1; n < mine && n < waited - 1 + PS; ++n)
+        (void)mbar_wait(&full[n % PS], (uint32_t)((n / PS) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+// Vout[R 128 + row] = sum over the nbt slots of Part[o][R 128 + row] for row
+// block R of view v, (v, R) = blocks[blockIdx.x]: thread (g, row) adds the
+// slots o = g, g + 8, ... in order (all its loads issued before the first
+// addition), then the eight group sums are added in order (a fixed order:
+// the same result on every run).
+__global__ void __launch_bounds__(1024)
+k_reduce_rows(const int2 *__restrict__ blocks, const BatchView *__restrict__ views, const float2 *__restrict__ Part,
+              float2 *__restrict__ Vout) {
+  constexpr int NG = 8, UN = 10;
+  __shared__ float2 red[NG][ST];
+  const int2 b = blocks[blockIdx.x];
+  const BatchView bv = views[b.x];
+  const int row = threadIdx.x & (ST - 1), g = threadIdx.x >> 7;
+  const int64_t r = (int64_t)b.y * ST + row;
+  const float2 *p = Part + bv.part_off + r;
+  float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+  for (int o0 = g; o0 < bv.nbt; o0 += NG * UN) {
+    float2 u[UN];
+#pragma unroll
+    for (int e = 0; e < UN; ++e)
+      if (o0 + NG * e < bv.nbt) u[e] = __ldcg(p + (int64_t)(o0 + NG * e) * bv.kp);
+#pragma unroll
+    for (int e = 0; e < UN; ++e)
+      if (o0 + NG * e < bv.nbt) {
+        acc.x += u[e].x;
+        acc.y += u[e].y;
+      }
+  }
+  red[g][row] = acc;
+  __syncthreads();
+  if (threadIdx.x < ST) {
+    float2 v = red[0][row];
+#pragma unroll
+    for (int e = 1; e < NG; ++e) {
+      v.x += red[e][row].x;
+      v.y += red[e][row].y;
+    }
+    Vout[bv.vec_off + r] = v;
+  }
 }
 
 // X (kp x 2) = x0 for rows < k, zero on the padding.
@@ -450,6 +726,96 @@ __global__ void k_convert(int64_t cnt, const TI *__restrict__ in, T *__restrict_
 // ---------------------------------------------------------------------------
 namespace {
 
+// Grid and shared-memory setup of the pipelined FP32 pass: one CTA per SM
+// (fewer when the table is shorter).
+int sympass_pipe_grid(pprviz_ctx *ctx, size_t ntile, unsigned *grid) {
+  int nsm = 0;
+  PPRVIZ_CUDA(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_sympass_pipe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, spipe::SMEM));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_sympass_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, spipe::SMEM));
+  *grid = (unsigned)std::min<size_t>(ntile, (size_t)std::max(nsm, 1));
+  return PPRVIZ_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the runtime).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The kp x kp row-major FP32 matrix at base as a 2-D tensor with 128 x 128
+// boxes, no swizzle (a box lands row-major in shared memory).
+int tile_map(pprviz_ctx *ctx, const float *base, int32_t kp, CUtensorMap *out) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return set_err(ctx, PPRVIZ_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)kp};
+  const cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)ST, (cuuint32_t)ST};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_err(ctx, PPRVIZ_E_CUDA, "cuTensorMapEncodeTiled failed for a layout matrix");
+  return PPRVIZ_OK;
+}
+
+// The upper-triangle tiles of every view, in view then row order, as tile
+// records in the device slot WS_TREC.
+int upload_tile_recs(pprviz_ctx *ctx, const std::vector<BatchView> &bv, const TileRec **recs_d, size_t *count) {
+  std::vector<TileRec> rec;
+  for (size_t v = 0; v < bv.size(); ++v)
+    for (int I = 0; I < bv[v].nbt; ++I)
+      for (int J = I; J < bv[v].nbt; ++J)
+        rec.push_back(TileRec{(int32_t)v, I, J, (int32_t)(bv[v].vec_off / ST), bv[v].kp, 0, bv[v].part_off});
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TREC, sizeof(TileRec) * rec.size()));
+  TileRec *d = ctx->ws[WS_TREC].as<TileRec>();
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d, rec.data(), sizeof(TileRec) * rec.size(), cudaMemcpyHostToDevice, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vector is released on return
+  *recs_d = d;
+  *count = rec.size();
+  return PPRVIZ_OK;
+}
+
+// The (view, row block) pairs of all views, one per k_reduce_rows block, into
+// the device slot WS_TROWS.
+int upload_row_blocks(pprviz_ctx *ctx, const std::vector<BatchView> &bv, const int2 **blocks_d) {
+  std::vector<int2> rb;
+  for (size_t v = 0; v < bv.size(); ++v)
+    for (int R = 0; R < bv[v].nbt; ++R) rb.push_back(make_int2((int)v, R));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TROWS, sizeof(int2) * rb.size()));
+  int2 *d = ctx->ws[WS_TROWS].as<int2>();
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d, rb.data(), sizeof(int2) * rb.size(), cudaMemcpyHostToDevice, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vector is released on return
+  *blocks_d = d;
+  return PPRVIZ_OK;
+}
+
+// Tensor maps of the two pass matrices of every view (maps[2 v] = 1/Delta_s,
+// maps[2 v + 1] = M) into the device slot WS_TMAP.
+int upload_maps(pprviz_ctx *ctx, const std::vector<BatchView> &bv, const float *W1, const float *M,
+                const CUtensorMap **maps_d) {
+  std::vector<CUtensorMap> maps(2 * bv.size());
+  for (size_t v = 0; v < bv.size(); ++v) {
+    PPRVIZ_TRY(tile_map(ctx, W1 + bv[v].mat_off, bv[v].kp, &maps[2 * v]));
+    PPRVIZ_TRY(tile_map(ctx, M + bv[v].mat_off, bv[v].kp, &maps[2 * v + 1]));
+  }
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TMAP, sizeof(CUtensorMap) * maps.size()));
+  CUtensorMap *d = reinterpret_cast<CUtensorMap *>(ctx->ws[WS_TMAP].p);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  // the host vector is released on return: wait for the copy
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *maps_d = d;
+  return PPRVIZ_OK;
+}
+
 template <typename T, typename TI, typename TO>
 int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int32_t iters, TO *x_out,
                  double *stress_h) {
@@ -488,7 +854,7 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
   // row-block counters of the fused reduce (zero between passes)
   std::vector<int4> tiles;
   for (int I = 0; I < nbt; ++I)
-    for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(0, I, J, 0));
+    for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(0, I, J, 0));  // w: vec_off / 128 = 0
   const BatchView one{0, 0, 0, kp, nbt, k, 0};
   const size_t tab_off = 256, cnt_off = (tab_off + sizeof(int4) * tiles.size() + 255) & ~(size_t)255;
   PPRVIZ_TRY(ws_ensure(ctx, WS_BTAB, cnt_off + sizeof(int) * (size_t)nbt));
@@ -500,11 +866,41 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
                                    ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)nbt, ctx->stream));
   const unsigned ntile = (unsigned)tiles.size();
-  for (int it = 0; it < iters; ++it) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<T, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, view_d, W1, X, Part, cnt, Bv); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<T, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, view_d, A, Bv, Part, cnt, X); }
-    PPRVIZ_LAUNCHED(ctx);
+  if constexpr (std::is_same<T, float>::value) {
+    unsigned pgrid = 0;
+    PPRVIZ_TRY(sympass_pipe_grid(ctx, tiles.size(), &pgrid));
+    const CUtensorMap *maps = nullptr;
+    PPRVIZ_TRY(upload_maps(ctx, std::vector<BatchView>{one}, W1, A, &maps));
+    const int2 *blocks = nullptr;
+    PPRVIZ_TRY(upload_row_blocks(ctx, std::vector<BatchView>{one}, &blocks));
+    const TileRec *recs = nullptr;
+    size_t nrec = 0;
+    PPRVIZ_TRY(upload_tile_recs(ctx, std::vector<BatchView>{one}, &recs, &nrec));
+    int *perr = flag + 1;
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
+    for (int it = 0; it < iters; ++it) {
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_pipe<0><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, X, Part, perr); }
+      PPRVIZ_LAUNCHED(ctx);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)nbt, 1024, 0, ctx->stream>>>(blocks, view_d, Part, Bv); }
+      PPRVIZ_LAUNCHED(ctx);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_pipe<1><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, Bv, Part, perr); }
+      PPRVIZ_LAUNCHED(ctx);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)nbt, 1024, 0, ctx->stream>>>(blocks, view_d, Part, X); }
+      PPRVIZ_LAUNCHED(ctx);
+    }
+    if (iters > 0) {
+      int herr = 0;
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      if (herr) return set_err(ctx, PPRVIZ_E_TIMEOUT, "layout pass: tile copy wait expired");
+    }
+  } else {
+    for (int it = 0; it < iters; ++it) {
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<T, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, view_d, W1, X, Part, cnt, Bv); }
+      PPRVIZ_LAUNCHED(ctx);
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<T, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, view_d, A, Bv, Part, cnt, X); }
+      PPRVIZ_LAUNCHED(ctx);
+    }
   }
   V2 *Xc = ctx->ws[WS_E].as<V2>();
   { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_finish<T, TO><<<1, 1024, 0, ctx->stream>>>(k, X, x_out, Xc); }
@@ -576,7 +972,7 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
     cnts += nbt;
     maxkp = std::max<int64_t>(maxkp, kp);
     for (int I = 0; I < nbt; ++I)
-      for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(v, I, J, 0));
+      for (int J = I; J < nbt; ++J) tiles.push_back(make_int4(v, I, J, (int)(bv[v].vec_off / ST)));
   }
   PPRVIZ_TRY(ws_ensure(ctx, WS_BW1, sizeof(float) * (size_t)mat));
   PPRVIZ_TRY(ws_ensure(ctx, WS_BM, sizeof(float) * (size_t)mat));
@@ -622,11 +1018,33 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hf) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "a view's pdist has a non-finite or non-positive entry");
   const unsigned ntile = (unsigned)tiles.size();
+  unsigned pgrid = 0;
+  PPRVIZ_TRY(sympass_pipe_grid(ctx, tiles.size(), &pgrid));
+  const CUtensorMap *maps = nullptr;
+  PPRVIZ_TRY(upload_maps(ctx, bv, W1, M, &maps));
+  const int2 *blocks = nullptr;
+  PPRVIZ_TRY(upload_row_blocks(ctx, bv, &blocks));
+  const TileRec *recs = nullptr;
+  size_t nrec = 0;
+  PPRVIZ_TRY(upload_tile_recs(ctx, bv, &recs, &nrec));
+  int *perr = flag + 1;
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
+  const unsigned nrb = (unsigned)cnts;  // row blocks of all views
   for (int it = 0; it < iters; ++it) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_batch<float, 0><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, W1, X, Part, cnt, Bv); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_pipe<0><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, X, Part, perr); }
     PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_batch<float, 1><<<ntile, 256, 0, ctx->stream>>>(tiles_d, views_d, M, Bv, Part, cnt, X); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<nrb, 1024, 0, ctx->stream>>>(blocks, views_d, Part, Bv); }
     PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_pipe<1><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, Bv, Part, perr); }
+    PPRVIZ_LAUNCHED(ctx);
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<nrb, 1024, 0, ctx->stream>>>(blocks, views_d, Part, X); }
+    PPRVIZ_LAUNCHED(ctx);
+  }
+  if (iters > 0) {
+    int herr = 0;
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (herr) return set_err(ctx, PPRVIZ_E_TIMEOUT, "layout pass: tile copy wait expired");
   }
   ctx->stats.layout_iters = iters;
   double half = 0.0;
