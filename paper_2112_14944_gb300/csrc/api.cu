@@ -141,7 +141,13 @@ void pprviz_destroy(pprviz_ctx *ctx) {
     cudaEventDestroy(p.second.second);
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
   for (auto &b : ctx->ws) b.release();
+  if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
+  if (ctx->ev_dp) cudaEventDestroy(ctx->ev_dp);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

@@ -44,7 +44,7 @@ enum Slot {
   // deflated sweeps: spectral scratch, residual partials, per-source roots and coefficients
   WS_SPEC, WS_RPART, WS_CSRC, WS_KAPPA,
   // tensor maps of the layout pass matrices, row-block table of the reduce
-  WS_TMAP, WS_TROWS, WS_TREC,
+  WS_TMAP, WS_TROWS, WS_TREC, WS_RUNP,
   WS_COUNT
 };
 
@@ -60,6 +60,9 @@ struct pprviz_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // second stream and events of the FP32 inverse's lookahead (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_t1 = nullptr, ev_dp = nullptr;
   std::string err;
   pprviz::DevBuf ws[pprviz::WS_COUNT];
   pprviz_stats stats{};
@@ -161,8 +164,8 @@ int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp
 // ---- factor (factor.cu) ----------------------------------------------------
 // In-place inverse of the SPD kp x kp matrix A (kp % 128 == 0); on return A
 // holds A^-1 on its upper 64-block triangle and on the 128 x 128 diagonal tiles.
-// `work` holds spd_inverse_work(kp) elements (2 * NB * kp + NB * NB + 64 with
-// NB = 128: the panels, the pivot inverse and a status word). The FP32 version runs its trailing updates on the tensor cores and
+// `work` holds spd_inverse_work(kp) elements (2 (2 * NB * kp + NB * NB) + 64
+// with NB = 128: two sets of panels and pivot inverse, and a status word). The FP32 version runs its trailing updates on the tensor cores and
 // returns PPRVIZ_E_TIMEOUT if an MMA completion wait expires.
 size_t spd_inverse_work(int32_t kp);  // elements of `work` for either type
 int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work);

@@ -21,7 +21,9 @@
 
 namespace pprviz {
 
-size_t spd_inverse_work(int32_t kp) { return (size_t)2 * 128 * kp + 128 * 128 + 64; }
+// two sets (the lookahead's parities) of panels Ct, Ut (NB x kp each) and
+// pivot inverse P (NB x NB), and a status word
+size_t spd_inverse_work(int32_t kp) { return (size_t)2 * (2 * 128 * (size_t)kp + 128 * 128) + 64; }
 
 // P = A_KK^-1 by an in-place scalar sweep of the NB x NB block in shared memory
 // (ping-pong buffers, one barrier per pivot); writes P to `P` and -P into A_KK.
@@ -416,11 +418,27 @@ __device__ __forceinline__ void store_chunk(const Chunk &ch, unsigned char *st, 
 }
 }  // namespace tc
 
+// Tiles of one launch: with k1 < 0, every upper tile outside the pivot block
+// row and column (grid tg x tg, the others exit at once); with k1 >= 0 and
+// !only_k1, the same without block row and column k1 (the next pivot's);
+// with only_k1, just the tiles of block row and column k1 (grid nblk x 1:
+// block b is tile (b, k1) for b < k1, else (k1, b)). The lookahead of the
+// driver updates block row and column k1 first, so that the next pivot's
+// inverse and panel overlap the rest of the update.
 __global__ void __launch_bounds__(256, 3)
-k_fac_trailing_tc(int32_t kp, int32_t K0, float *__restrict__ A, const float *__restrict__ Ct,
+k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict__ A, const float *__restrict__ Ct,
                   const float *__restrict__ Ut, int *__restrict__ err) {
   using namespace tc;
-  const int I0 = blockIdx.y * TM, J0 = blockIdx.x * TM;
+  int I0, J0;
+  if (only_k1) {
+    const int b = blockIdx.x;
+    I0 = (b < k1 ? b : k1) * TM;
+    J0 = (b < k1 ? k1 : b) * TM;
+  } else {
+    I0 = blockIdx.y * TM;
+    J0 = blockIdx.x * TM;
+    if (k1 >= 0 && (I0 == k1 * TM || J0 == k1 * TM)) return;  // the lookahead's tiles
+  }
   if (J0 < I0 || I0 == K0 || J0 == K0) return;  // lower triangle, pivot row and column
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -555,8 +573,14 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
   constexpr bool TC = std::is_same<T, float>::value;  // FP32: 128-blocks, tensor-core trailing update
   constexpr int NB = TC ? 128 : 64;
   constexpr int TM = 64;                               // SIMT trailing tile (FP64)
-  T *Ct = work, *Ut = work + (size_t)NB * kp, *P = work + (size_t)2 * NB * kp;
-  int *err = reinterpret_cast<int *>(P + NB * NB);
+  const size_t set = (size_t)2 * NB * kp + (size_t)NB * NB;  // one parity's Ct, Ut, P
+  T *Ct[2], *Ut[2], *P[2];
+  for (int q = 0; q < 2; ++q) {
+    Ct[q] = work + q * set;
+    Ut[q] = Ct[q] + (size_t)NB * kp;
+    P[q] = Ct[q] + (size_t)2 * NB * kp;
+  }
+  int *err = reinterpret_cast<int *>(work + 2 * set);
   const size_t diag_smem = 2 * sizeof(T) * NB * (NB + 1);
   const size_t panel_smem = sizeof(T) * (NB * NB + NB * (NB + 16 / sizeof(T)));
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel<T, NB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -577,28 +601,68 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
   const double b3 = (double)NB * NB * NB;
   const double nm1 = (double)(nblk - 1);
   ctx->stats.flops_factor += (double)nblk * (2.0 * b3 + nm1 * 2.0 * b3 + nm1 * (nm1 + 1.0) / 2.0 * 2.0 * b3);
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int K0 = kb * NB;
-    if constexpr (TC) {
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag128<<<1, 1024, 0, ctx->stream>>>(kp, K0, (float *)A, (float *)P); }
-    } else {
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag<T, NB><<<1, 512, diag_smem, ctx->stream>>>(kp, K0, A, P); }
+  if constexpr (TC) {
+    // Lookahead by one pivot on a second stream: step kb updates block row
+    // and column kb + 1 first (T1, main stream); the side stream then inverts
+    // pivot kb + 1 and forms its panel into the other parity's buffers while
+    // the main stream runs the rest of step kb's update (T2). One profiling
+    // interval covers the whole inverse on the main stream.
+    if (!ctx->side) {
+      // highest priority, so that the pivot's one-CTA inverse and the panel
+      // are dispatched as soon as an SM frees up instead of after the queued
+      // CTAs of the main stream's update
+      int lo = 0, hi = 0;
+      PPRVIZ_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      PPRVIZ_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
     }
+    if (!ctx->ev_t1) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_t1, cudaEventDisableTiming));
+    if (!ctx->ev_dp) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_dp, cudaEventDisableTiming));
+    PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
+    float *Af = (float *)A;
+    const unsigned tg = (unsigned)(kp / tc::TM);
+    k_fac_diag128<<<1, 1024, 0, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
     PPRVIZ_LAUNCHED(ctx);
-    if (nblk == 1) break;
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, K0, A, P, Ct, Ut); }
+    if (nblk > 1) {
+      k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, 0, A, P[0], Ct[0], Ut[0]);
+      PPRVIZ_LAUNCHED(ctx);
+    }
+    for (int kb = 0; nblk > 1 && kb < nblk; ++kb) {
+      const int q = kb & 1, K0 = kb * NB, k1 = kb + 1 < nblk ? kb + 1 : -1;
+      if (k1 >= 0) {
+        k_fac_trailing_tc<<<dim3((unsigned)nblk, 1), 256, tc::SMEM, ctx->stream>>>(kp, K0, k1, 1, Af, (float *)Ct[q],
+                                                                                 (float *)Ut[q], err);
+        PPRVIZ_LAUNCHED(ctx);
+        PPRVIZ_CUDA(ctx, cudaEventRecord(ctx->ev_t1, ctx->stream));
+        PPRVIZ_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_t1, 0));
+        k_fac_diag128<<<1, 1024, 0, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
+        PPRVIZ_LAUNCHED(ctx);
+        k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->side>>>(kp, k1 * NB, A, P[q ^ 1], Ct[q ^ 1], Ut[q ^ 1]);
+        PPRVIZ_LAUNCHED(ctx);
+        PPRVIZ_CUDA(ctx, cudaEventRecord(ctx->ev_dp, ctx->side));
+      }
+      k_fac_trailing_tc<<<dim3(tg, tg), 256, tc::SMEM, ctx->stream>>>(kp, K0, k1, 0, Af, (float *)Ct[q],
+                                                                    (float *)Ut[q], err);
+      PPRVIZ_LAUNCHED(ctx);
+      if (k1 >= 0) PPRVIZ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_dp, 0));
+      if (k1 < 0) break;
+    }
+    k_fac_finish<T, NB><<<dim3((unsigned)std::min(8, (kp + 255) / 256), (unsigned)kp), 256, 0, ctx->stream>>>(kp, A);
     PPRVIZ_LAUNCHED(ctx);
-    if constexpr (TC) {
-      const unsigned tg = (unsigned)(kp / tc::TM);
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing_tc<<<dim3(tg, tg), 256, tc::SMEM, ctx->stream>>>(kp, K0, A, Ct, Ut, err); }
-    } else {
+  } else {
+    for (int kb = 0; kb < nblk; ++kb) {
+      const int K0 = kb * NB;
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_diag<T, NB><<<1, 512, diag_smem, ctx->stream>>>(kp, K0, A, P[0]); }
+      PPRVIZ_LAUNCHED(ctx);
+      if (nblk == 1) break;
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, K0, A, P[0], Ct[0], Ut[0]); }
+      PPRVIZ_LAUNCHED(ctx);
       const unsigned tg = (unsigned)((kp + TM - 1) / TM);
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing<T, TM, NB><<<dim3(tg, tg), 256, 2 * sizeof(T) * NB * TM, ctx->stream>>>(kp, K0, A, Ct, Ut); }
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_trailing<T, TM, NB><<<dim3(tg, tg), 256, 2 * sizeof(T) * NB * TM, ctx->stream>>>(kp, K0, A, Ct[0], Ut[0]); }
+      PPRVIZ_LAUNCHED(ctx);
     }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_finish<T, NB><<<dim3((unsigned)std::min(8, (kp + 255) / 256), (unsigned)kp), 256, 0, ctx->stream>>>(kp, A); }
     PPRVIZ_LAUNCHED(ctx);
   }
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_fac_finish<T, NB><<<dim3((unsigned)std::min(8, (kp + 255) / 256), (unsigned)kp), 256, 0, ctx->stream>>>(kp, A); }
-  PPRVIZ_LAUNCHED(ctx);
   if constexpr (TC) {
     int herr = 0;
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

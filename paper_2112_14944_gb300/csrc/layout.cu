@@ -31,7 +31,6 @@
 
 namespace pprviz {
 
-constexpr int NB = 64;        // Gauss-Jordan pivot block
 constexpr int ST = 128;       // symmetric pass tile edge
 constexpr int SRPI = 8;       // rows per warp per sub-iteration in the symmetric pass
 constexpr int LWARPS = 8;     // warps per block in the energy pass
@@ -294,27 +293,36 @@ k_sympass_batch(const int4 *__restrict__ tiles, const BatchView *__restrict__ vi
 }
 
 // ---------------------------------------------------------------------------
-// FP32 symmetric pass, persistent and pipelined (the FP32 path of the single
-// and the batched layout). One CTA of 16 warps per SM takes a contiguous
-// chunk of the tile table. Each 128 x 128 tile (64 KiB) comes into shared
-// memory with one TMA tensor copy (cp.async.bulk.tensor.2d; a tensor map per
-// view and matrix) that completes on the stage's mbarrier; with PS stages the
-// copies of the next PS - 1 tiles are in flight while the warps work on the
-// current one, so the matrix streams from HBM at copy speed as long as a
-// tile's arithmetic takes less time than its copy. Nothing on the per-tile
-// path waits on global memory: the partial sums are plain stores and are
-// added up by a separate launch (k_reduce_rows), two CTA barriers per tile.
-// Warp w takes tile rows 8w..8w+7, lane l the columns 4l..4l+3 (one
-// conflict-free 16-byte shared-memory read per row). Per pair, as in
-// sympass_tile: row sums to Part[J][i], column sums of off-diagonal tiles to
-// Part[I][j].
-// Every mbarrier wait has an iteration limit: on expiry the CTA sets *err,
-// stops, waits (again bounded) for the copies it issued and returns.
+// FP32 symmetric pass, persistent, pipelined and warp-specialized (the FP32
+// path of the single and the batched layout). One CTA per SM: a producer warp
+// and 16 consumer warps. Each CTA takes a contiguous chunk of the tile table,
+// which lists every view's upper-triangle tiles column by column (J, then
+// I = 0..J). The producer brings each 128 x 128 tile (64 KiB) into a
+// shared-memory stage with one TMA tensor copy (cp.async.bulk.tensor.2d; a
+// tensor map per view and matrix), together with the two 1 KiB coordinate
+// slices it needs (plain bulk copies), all completing on the stage's "full"
+// mbarrier; it refills a stage once the stage's "empty" mbarrier has seen all
+// 16 consumer warps. With PS stages the copies of PS tiles are in flight.
+// The consumer warps never wait for each other: warp w takes tile rows
+// 8w..8w+7 (lane l the columns 4l..4l+3, one conflict-free 16-byte
+// shared-memory read per row), sums its rows across lanes and stores them per
+// tile (row block I, slot J), and keeps its column sums in registers while
+// consecutive tiles of the chunk share the column block J (a "run"); it
+// writes them once per run to the run's slot. A separate launch
+// (k_reduce_rows) adds slots and runs in a fixed order. Per pair:
+//   MODE 0 (L^Y): t_ij = Mat_ij (v_i - v_j) / |v_i - v_j|: row i +t, column j -t
+//   MODE 1 (apply M): row i gets Mat_ij v_j, column j gets Mat_ij v_i
+// (the diagonal tile adds its rows only: it is stored in full). Lane l's four
+// columns are processed as two pairs with Blackwell's paired FP32
+// instructions (two lanes of work per issue slot).
+// Every mbarrier wait has an iteration limit: on expiry the warp sets *err and
+// stops; the producer then waits (again bounded) for the copies it issued.
 // ---------------------------------------------------------------------------
 namespace spipe {
 constexpr int PS = 3;                           // pipeline stages
-constexpr int WARPS = 16;
-constexpr int PRW = ST / WARPS;                 // tile rows per warp
+constexpr int CWARPS = 16;                      // consumer warps
+constexpr int THREADS = (CWARPS + 1) * 32;      // + the producer warp
+constexpr int PRW = ST / CWARPS;                // tile rows per consumer warp
 constexpr uint32_t TILE_BYTES = ST * ST * 4;    // one FP32 tile
 constexpr uint32_t VEC_BYTES = ST * 8;          // 128 coordinate pairs
 constexpr uint32_t STAGE_BYTES = TILE_BYTES + 2 * VEC_BYTES;  // tile, rows' and columns' vector slices
@@ -336,12 +344,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // One thread: tile (I, J) of the matrix behind `map` and the vector slices
-// V[I 128 ..] and V[J 128 ..] (1 KiB each, plain bulk copies; V is the
-// view's vector) into the stage
-// at dst, all completing on bar (armed with their byte count first). The maps
-// sit in global memory, written by a host copy before the launch; the first
-// use of each map by a CTA is preceded by a tensor-map acquire fence
-// (`fenced` remembers the last map fenced).
+// V[I 128 ..] and V[J 128 ..] (V is the view's vector) into the stage at dst,
+// all completing on bar (armed with their byte count first). The maps sit in
+// global memory, written by a host copy before the launch; the first use of
+// each map by a CTA is preceded by a tensor-map acquire fence (`fenced`
+// remembers the last map fenced).
 __device__ __forceinline__ void issue_tile(uint32_t dst, uint64_t *bar, const CUtensorMap *map, const float2 *V,
                                            int I, int J, const CUtensorMap *&fenced) {
   if (map != fenced) {
@@ -377,97 +384,106 @@ __device__ __forceinline__ float rsqrt_clamped(float d2) {
 }  // namespace spipe
 
 // A tile of the FP32 pass: view v, tile (I, J) of its kp x kp matrices, the
-// view's vector offset / 128 and its partial-sum offset (2-vectors).
+// view's vector offset / 128, its row-sum slots (2-vectors) and the run slot
+// of its column sums (-1 for a diagonal tile).
 struct __align__(16) TileRec {
   int32_t v, I, J, vblk;
-  int32_t kp, pad;
+  int32_t kp, run;
   int64_t part_off;
 };
 
-// maps[2 v + MODE]: view v's 1/Delta_s (MODE 0) or M (MODE 1) as a kp x kp
-// FP32 tensor with 128 x 128 boxes. CTA b takes tiles b, b + G, b + 2G, ...
-// of the row-ordered table, so that the tiles in flight at any moment lie
-// side by side in the same 128 matrix rows (whole DRAM pages of each row
-// are read together). Per tile: wait for the stage, read the
-// warp's 8 rows and both vector slices into registers, one CTA barrier
-// (stage consumed), refill the stage with the tile PS ahead, then the
-// arithmetic, so that PS copies are in flight while the warps compute; the
-// tile records are loaded one step ahead. Lane l's four columns are processed
-// as two pairs with Blackwell's paired FP32 instructions (two lanes of work
-// per issue slot).
+// Run slot r holds, per consumer warp w, that warp's column sums of the run:
+// RunPart[(r CWARPS + w) 128 + c], c the column within block J.
 template <int MODE>
-__global__ void __launch_bounds__(spipe::WARPS * 32, 1)
+__global__ void __launch_bounds__(spipe::THREADS, 1)
 k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *__restrict__ maps,
-               const float2 *__restrict__ V, float2 *__restrict__ Part, int *__restrict__ err) {
+               const float2 *__restrict__ V, float2 *__restrict__ Part, float2 *__restrict__ RunPart,
+               int *__restrict__ err) {
   using namespace spipe;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[PS];
-  __shared__ __align__(16) float colred[WARPS][2 * ST];  // column partials per warp
+  __shared__ __align__(8) uint64_t full[PS], empty[PS];
+  __shared__ TileRec srec[PS];  // the record of the tile in each stage, written by the producer
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int G = (int)gridDim.x, first = (int)blockIdx.x;
-  const int mine = ntile > first ? (ntile - 1 - first) / G + 1 : 0;
+  const int first = (int)((int64_t)blockIdx.x * ntile / gridDim.x);
+  const int mine = (int)((int64_t)(blockIdx.x + 1) * ntile / gridDim.x) - first;
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;  // TMA destinations 1024-byte aligned
   const unsigned char *sgen = smem_raw + (sbase - smem_u32(smem_raw));
-  const CUtensorMap *fenced = nullptr;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < PS; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+    for (int s = 0; s < PS; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(CWARPS));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int n = 0; n < PS && n < mine; ++n) {
-      const TileRec t = tiles[first + n * G];
-      issue_tile(sbase + (uint32_t)n * STAGE_BYTES, &full[n], maps + 2 * t.v + MODE, V + (int64_t)t.vblk * ST, t.I,
-                 t.J, fenced);
+  __syncthreads();  // the only CTA-wide barrier
+  if (warp == CWARPS) {
+    // ---- producer
+    if (lane == 0) {
+      const CUtensorMap *fenced = nullptr;
+      int issued = 0;
+      bool ok = true;
+      for (int n = 0; n < mine; ++n) {
+        const int s = n % PS;
+        const TileRec t = tiles[first + n];
+        if (n >= PS && !mbar_wait(&empty[s], (uint32_t)(((n - PS) / PS) & 1))) {
+          ok = false;
+          break;
+        }
+        srec[s] = t;  // released to the consumers by the arrive below
+        issue_tile(sbase + (uint32_t)s * STAGE_BYTES, &full[s], maps + 2 * t.v + MODE, V + (int64_t)t.vblk * ST, t.I,
+                   t.J, fenced);
+        issued = n + 1;
+      }
+      if (!ok) {
+        atomicOr(err, 1);
+        // copies of the last PS issued tiles may still be landing
+        for (int n = issued > PS ? issued - PS : 0; n < issued; ++n)
+          (void)mbar_wait(&full[n % PS], (uint32_t)((n / PS) & 1));
+      }
     }
+    return;
   }
-  bool ok = true;
-  int waited = 0;  // local tiles whose stage has been waited on
-  TileRec t = mine > 0 ? tiles[first] : TileRec{};
+  // ---- consumers
   const int rbase = warp * PRW;
   const float sg = MODE == 0 ? -1.0f : 1.0f;
+  float2 rxA = make_float2(0.0f, 0.0f), rxB = rxA, ryA = rxA, ryB = rxA;  // column sums of the current run
+  int cur_run = -1;
 #pragma unroll 1
   for (int n = 0; n < mine; ++n) {
     const int s = n % PS;
-    const TileRec tnext = (n + 1 < mine) ? tiles[first + (n + 1) * G] : t;
-    const TileRec tref = (threadIdx.x == 0 && n + PS < mine) ? tiles[first + (n + PS) * G] : t;  // the refill's record
-    if (!mbar_wait(&full[s], (uint32_t)((n / PS) & 1))) ok = false;
-    waited = n + 1;
+    if (!mbar_wait(&full[s], (uint32_t)((n / PS) & 1))) {
+      if (lane == 0) atomicOr(err, 1);
+      return;
+    }
+    const TileRec t = srec[s];
+    if (t.run != cur_run) {
+      if (cur_run >= 0) {
+        float4 *o = reinterpret_cast<float4 *>(RunPart + ((int64_t)cur_run * CWARPS + warp) * ST + lane * 4);
+        o[0] = make_float4(sg * rxA.x, sg * ryA.x, sg * rxA.y, sg * ryA.y);
+        o[1] = make_float4(sg * rxB.x, sg * ryB.x, sg * rxB.y, sg * ryB.y);
+      }
+      rxA = rxB = ryA = ryB = make_float2(0.0f, 0.0f);
+      cur_run = t.run;
+    }
     const unsigned char *stage = sgen + (size_t)s * STAGE_BYTES;
     const float *stile = reinterpret_cast<const float *>(stage) + rbase * ST + lane * 4;
     const float2 *svi = reinterpret_cast<const float2 *>(stage + TILE_BYTES) + rbase;
     const float4 *svj = reinterpret_cast<const float4 *>(stage + TILE_BYTES + VEC_BYTES) + lane * 2;
-    float4 m4[PRW];
-    float2 vi[PRW];
-#pragma unroll
-    for (int r = 0; r < PRW; ++r) {
-      m4[r] = *reinterpret_cast<const float4 *>(stile + r * ST);
-      vi[r] = svi[r];
-    }
-    const float4 c01 = svj[0], c23 = svj[1];  // (x0, y0, x1, y1), (x2, y2, x3, y3)
-    // stage s consumed by every warp; also orders the previous tile's
-    // column-sum reads of colred before this tile's writes
-    if (__syncthreads_and(ok) == 0) {
-      ok = false;
-      break;
-    }
-    if (threadIdx.x == 0 && n + PS < mine) {
-      issue_tile(sbase + (uint32_t)s * STAGE_BYTES, &full[s], maps + 2 * tref.v + MODE, V + (int64_t)tref.vblk * ST,
-                 tref.I, tref.J, fenced);
-    }
     // columns 4l..4l+3 as pairs A = (4l, 4l+1), B = (4l+2, 4l+3); MODE 0 keeps
     // the column coordinates negated
+    const float4 c01 = svj[0], c23 = svj[1];  // (x0, y0, x1, y1), (x2, y2, x3, y3)
     const float2 xA = make_float2(sg * c01.x, sg * c01.z), yA = make_float2(sg * c01.y, sg * c01.w);
     const float2 xB = make_float2(sg * c23.x, sg * c23.z), yB = make_float2(sg * c23.y, sg * c23.w);
     float2 cxA = make_float2(0.0f, 0.0f), cxB = cxA, cyA = cxA, cyB = cxA;
     float acc[2 * PRW];
 #pragma unroll
     for (int r = 0; r < PRW; ++r) {
-      const float2 mA = make_float2(m4[r].x, m4[r].y), mB = make_float2(m4[r].z, m4[r].w);
-      const float2 vx = make_float2(vi[r].x, vi[r].x), vy = make_float2(vi[r].y, vi[r].y);
+      const float4 m4 = *reinterpret_cast<const float4 *>(stile + r * ST);
+      const float2 vi = svi[r];
+      const float2 mA = make_float2(m4.x, m4.y), mB = make_float2(m4.z, m4.w);
+      const float2 vx = make_float2(vi.x, vi.x), vy = make_float2(vi.y, vi.y);
       float2 ra, rb;
       if (MODE == 0) {
-        // t_ij = M_ij (v_i - v_j) / |v_i - v_j|: row i gets +t, column j gets -t
         const float2 dxA = __fadd2_rn(vx, xA), dyA = __fadd2_rn(vy, yA);
         const float2 dxB = __fadd2_rn(vx, xB), dyB = __fadd2_rn(vy, yB);
         const float2 qA = __ffma2_rn(dyA, dyA, __fmul2_rn(dxA, dxA));
@@ -481,7 +497,6 @@ k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *
         cyA = __ffma2_rn(kA, dyA, cyA);
         cyB = __ffma2_rn(kB, dyB, cyB);
       } else {
-        // row i gets M_ij v_j, column j gets M_ij v_i
         ra = __ffma2_rn(mB, xB, __fmul2_rn(mA, xA));
         rb = __ffma2_rn(mB, yB, __fmul2_rn(mA, yA));
         cxA = __ffma2_rn(mA, vx, cxA);
@@ -492,47 +507,41 @@ k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *
       acc[2 * r] = ra.x + ra.y;
       acc[2 * r + 1] = rb.x + rb.y;
     }
-    const int64_t kp = t.kp;
-    const int64_t i0 = (int64_t)t.I * ST, j0 = (int64_t)t.J * ST;
-    float *part = reinterpret_cast<float *>(Part + t.part_off);
+    // every lane's reads of stage s (and of srec[s]) are done (their values
+    // are in use above)
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+    if (t.run >= 0) {
+      rxA = __fadd2_rn(rxA, cxA);
+      rxB = __fadd2_rn(rxB, cxB);
+      ryA = __fadd2_rn(ryA, cyA);
+      ryB = __fadd2_rn(ryB, cyB);
+    }
     const float tot = lanes_transpose_sum<2 * PRW, float>(acc, lane);
     constexpr int REP = 32 / (2 * PRW);
     if (lane % REP == 0) {
       const int idx = lane / REP;
-      part[((int64_t)t.J * kp + i0 + rbase + (idx >> 1)) * 2 + (idx & 1)] = tot;
+      float *part = reinterpret_cast<float *>(Part + t.part_off);
+      part[((int64_t)t.J * t.kp + (int64_t)t.I * ST + rbase + (idx >> 1)) * 2 + (idx & 1)] = tot;
     }
-    {
-      float4 *cr = reinterpret_cast<float4 *>(&colred[warp][lane * 8]);  // columns 4l..4l+3, (x, y) each
-      cr[0] = make_float4(sg * cxA.x, sg * cyA.x, sg * cxA.y, sg * cyA.y);
-      cr[1] = make_float4(sg * cxB.x, sg * cyB.x, sg * cxB.y, sg * cyB.y);
-    }
-    __syncthreads();  // column partials complete
-    if (t.I != t.J && threadIdx.x < 2 * ST) {
-      float c = 0.0f;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) c += colred[w][threadIdx.x];
-      part[((int64_t)t.I * kp + j0) * 2 + threadIdx.x] = c;
-    }
-    t = tnext;
   }
-  if (!ok) {
-    if (threadIdx.x == 0) {
-      atomicOr(err, 1);
-      // the copies issued for local tiles waited - 1 .. waited + PS - 2 may still be landing
-      for (int n = waited - 1; n < mine && n < waited - 1 + PS; ++n)
-        (void)mbar_wait(&full[n % PS], (uint32_t)((n / PS) & 1));
-    }
-    __syncthreads();
+  if (cur_run >= 0) {
+    float4 *o = reinterpret_cast<float4 *>(RunPart + ((int64_t)cur_run * CWARPS + warp) * ST + lane * 4);
+    o[0] = make_float4(sg * rxA.x, sg * ryA.x, sg * rxA.y, sg * ryA.y);
+    o[1] = make_float4(sg * rxB.x, sg * ryB.x, sg * rxB.y, sg * ryB.y);
   }
 }
 
-// Vout[R 128 + row] = sum over the nbt slots of Part[o][R 128 + row] for row
-// block R of view v, (v, R) = blocks[blockIdx.x]: thread (g, row) adds the
-// slots o = g, g + 8, ... in order (all its loads issued before the first
-// addition), then the eight group sums are added in order (a fixed order:
+// Row block R of view v, (v, R) = blocks[blockIdx.x]:
+//   Vout[R 128 + row] = sum_{J = R}^{nbt - 1} Part[J][R 128 + row]        (row sums of tiles (R, J))
+//                     + sum over the runs of column block R and their warps
+//                       of RunPart[(r CWARPS + w) 128 + row]                (column sums of tiles (I < R, R))
+// The items are numbered in that order; thread (g, row) adds items g, g + 8,
+// ... in order, then the eight group sums are added in order (a fixed order:
 // the same result on every run).
 __global__ void __launch_bounds__(1024)
-k_reduce_rows(const int2 *__restrict__ blocks, const BatchView *__restrict__ views, const float2 *__restrict__ Part,
+k_reduce_rows(const int2 *__restrict__ blocks, const BatchView *__restrict__ views, const int *__restrict__ run_ptr,
+              const int *__restrict__ run_idx, const float2 *__restrict__ Part, const float2 *__restrict__ RunPart,
               float2 *__restrict__ Vout) {
   constexpr int NG = 8, UN = 10;
   __shared__ float2 red[NG][ST];
@@ -540,17 +549,26 @@ k_reduce_rows(const int2 *__restrict__ blocks, const BatchView *__restrict__ vie
   const BatchView bv = views[b.x];
   const int row = threadIdx.x & (ST - 1), g = threadIdx.x >> 7;
   const int64_t r = (int64_t)b.y * ST + row;
-  const float2 *p = Part + bv.part_off + r;
+  const int nrow = bv.nbt - b.y;
+  const int r0 = run_ptr[blockIdx.x], nitem = nrow + (run_ptr[blockIdx.x + 1] - r0) * spipe::CWARPS;
   float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll 1
-  for (int o0 = g; o0 < bv.nbt; o0 += NG * UN) {
+  for (int i0 = g; i0 < nitem; i0 += NG * UN) {
     float2 u[UN];
 #pragma unroll
-    for (int e = 0; e < UN; ++e)
-      if (o0 + NG * e < bv.nbt) u[e] = __ldcg(p + (int64_t)(o0 + NG * e) * bv.kp);
+    for (int e = 0; e < UN; ++e) {
+      const int i = i0 + NG * e;
+      if (i < nrow) {
+        u[e] = __ldcg(Part + bv.part_off + (int64_t)(b.y + i) * bv.kp + r);
+      } else if (i < nitem) {
+        const int q = i - nrow;
+        const int run = run_idx[r0 + q / spipe::CWARPS];
+        u[e] = __ldcg(RunPart + ((int64_t)run * spipe::CWARPS + q % spipe::CWARPS) * ST + row);
+      }
+    }
 #pragma unroll
     for (int e = 0; e < UN; ++e)
-      if (o0 + NG * e < bv.nbt) {
+      if (i0 + NG * e < nitem) {
         acc.x += u[e].x;
         acc.y += u[e].y;
       }
@@ -766,34 +784,100 @@ int tile_map(pprviz_ctx *ctx, const float *base, int32_t kp, CUtensorMap *out) {
   return PPRVIZ_OK;
 }
 
-// The upper-triangle tiles of every view, in view then row order, as tile
-// records in the device slot WS_TREC.
-int upload_tile_recs(pprviz_ctx *ctx, const std::vector<BatchView> &bv, const TileRec **recs_d, size_t *count) {
+// Tables of the pipelined FP32 pass for a grid of G CTAs (device slots
+// WS_TREC, WS_TROWS):
+//  * tile records of every view's upper-triangle tiles, view by view, column
+//    by column (J, then I = 0..J), with the run slot of each off-diagonal
+//    tile: consecutive tiles of one column block in one CTA's chunk
+//    [b ntile / G, (b + 1) ntile / G) share a run;
+//  * the (view, row block) pairs, one per k_reduce_rows block (view order,
+//    then R), and for each the runs of column block R (CSR: run_ptr, run_idx).
+struct PassTables {
+  const TileRec *recs = nullptr;
+  int ntile = 0;
+  const int2 *blocks = nullptr;
+  const int *run_ptr = nullptr, *run_idx = nullptr;
+  int nblocks = 0, nruns = 0;
+};
+
+int upload_pass_tables(pprviz_ctx *ctx, const std::vector<BatchView> &bv, unsigned G, PassTables *pt) {
   std::vector<TileRec> rec;
+  std::vector<int> rb_base(bv.size());
+  int nrb = 0;
+  for (size_t v = 0; v < bv.size(); ++v) {
+    rb_base[v] = nrb;
+    nrb += bv[v].nbt;
+    for (int J = 0; J < bv[v].nbt; ++J)
+      for (int I = 0; I <= J; ++I)
+        rec.push_back(TileRec{(int32_t)v, I, J, (int32_t)(bv[v].vec_off / ST), bv[v].kp, -1, bv[v].part_off});
+  }
+  const int64_t ntile = (int64_t)rec.size();
+  if (ntile >= INT32_MAX) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "too many layout tiles");
+  std::vector<std::vector<int>> runs_of(nrb);
+  int nruns = 0, cur = -1, prev_v = -1, prev_J = -1;
+  int64_t b = 0;  // CTA of position p: first(b) <= p < first(b + 1)
+  for (int64_t p = 0; p < ntile; ++p) {
+    while (b + 1 < (int64_t)G && (b + 1) * ntile / G <= p) ++b;
+    TileRec &r = rec[p];
+    const bool chunk_start = (b * ntile / G) == p;
+    if (r.I == r.J) {  // diagonal: its column sums are not taken
+      cur = -1;
+      continue;
+    }
+    if (cur < 0 || chunk_start || r.v != prev_v || r.J != prev_J) {
+      cur = nruns++;
+      runs_of[rb_base[r.v] + r.J].push_back(cur);
+    }
+    r.run = cur;
+    prev_v = r.v;
+    prev_J = r.J;
+  }
+  std::vector<int2> blocks;
+  std::vector<int> run_ptr(1, 0), run_idx;
   for (size_t v = 0; v < bv.size(); ++v)
-    for (int I = 0; I < bv[v].nbt; ++I)
-      for (int J = I; J < bv[v].nbt; ++J)
-        rec.push_back(TileRec{(int32_t)v, I, J, (int32_t)(bv[v].vec_off / ST), bv[v].kp, 0, bv[v].part_off});
+    for (int R = 0; R < bv[v].nbt; ++R) {
+      blocks.push_back(make_int2((int)v, R));
+      for (int q : runs_of[rb_base[v] + R]) run_idx.push_back(q);
+      run_ptr.push_back((int)run_idx.size());
+    }
+  if (run_idx.empty()) run_idx.push_back(0);  // keep the device pointer valid
+  const size_t o_blocks = 0, o_ptr = (sizeof(int2) * blocks.size() + 255) & ~(size_t)255;
+  const size_t o_idx = (o_ptr + sizeof(int) * run_ptr.size() + 255) & ~(size_t)255;
+  const size_t bytes = o_idx + sizeof(int) * run_idx.size();
   PPRVIZ_TRY(ws_ensure(ctx, WS_TREC, sizeof(TileRec) * rec.size()));
-  TileRec *d = ctx->ws[WS_TREC].as<TileRec>();
-  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d, rec.data(), sizeof(TileRec) * rec.size(), cudaMemcpyHostToDevice, ctx->stream));
-  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vector is released on return
-  *recs_d = d;
-  *count = rec.size();
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TROWS, bytes));
+  unsigned char *d = static_cast<unsigned char *>(ctx->ws[WS_TROWS].p);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ctx->ws[WS_TREC].p, rec.data(), sizeof(TileRec) * rec.size(),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d + o_blocks, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d + o_ptr, run_ptr.data(), sizeof(int) * run_ptr.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d + o_idx, run_idx.data(), sizeof(int) * run_idx.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vectors are released on return
+  pt->recs = ctx->ws[WS_TREC].as<TileRec>();
+  pt->ntile = (int)ntile;
+  pt->blocks = reinterpret_cast<const int2 *>(d + o_blocks);
+  pt->run_ptr = reinterpret_cast<const int *>(d + o_ptr);
+  pt->run_idx = reinterpret_cast<const int *>(d + o_idx);
+  pt->nblocks = (int)blocks.size();
+  pt->nruns = nruns;
   return PPRVIZ_OK;
 }
 
-// The (view, row block) pairs of all views, one per k_reduce_rows block, into
-// the device slot WS_TROWS.
-int upload_row_blocks(pprviz_ctx *ctx, const std::vector<BatchView> &bv, const int2 **blocks_d) {
-  std::vector<int2> rb;
-  for (size_t v = 0; v < bv.size(); ++v)
-    for (int R = 0; R < bv[v].nbt; ++R) rb.push_back(make_int2((int)v, R));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_TROWS, sizeof(int2) * rb.size()));
-  int2 *d = ctx->ws[WS_TROWS].as<int2>();
-  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(d, rb.data(), sizeof(int2) * rb.size(), cudaMemcpyHostToDevice, ctx->stream));
-  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vector is released on return
-  *blocks_d = d;
+// One layout update of all views in the tables: L^Y pass over W1 from X into
+// Bv, apply pass over M from Bv into X, each followed by its reduce.
+int pass_pair(pprviz_ctx *ctx, unsigned grid, const PassTables &pt, const CUtensorMap *maps, const BatchView *views_d,
+              float2 *X, float2 *Bv, float2 *Part, float2 *RunPart, int *perr) {
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_pipe<0><<<grid, spipe::THREADS, spipe::SMEM, ctx->stream>>>(pt.ntile, pt.recs, maps, X, Part, RunPart, perr); }
+  PPRVIZ_LAUNCHED(ctx);
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)pt.nblocks, 1024, 0, ctx->stream>>>(pt.blocks, views_d, pt.run_ptr, pt.run_idx, Part, RunPart, Bv); }
+  PPRVIZ_LAUNCHED(ctx);
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_pipe<1><<<grid, spipe::THREADS, spipe::SMEM, ctx->stream>>>(pt.ntile, pt.recs, maps, Bv, Part, RunPart, perr); }
+  PPRVIZ_LAUNCHED(ctx);
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)pt.nblocks, 1024, 0, ctx->stream>>>(pt.blocks, views_d, pt.run_ptr, pt.run_idx, Part, RunPart, X); }
+  PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
 }
 
@@ -869,25 +953,16 @@ int layout_typed(pprviz_ctx *ctx, const TI *pdist, int32_t k, const TI *x0, int3
   if constexpr (std::is_same<T, float>::value) {
     unsigned pgrid = 0;
     PPRVIZ_TRY(sympass_pipe_grid(ctx, tiles.size(), &pgrid));
+    const std::vector<BatchView> one_v{one};
     const CUtensorMap *maps = nullptr;
-    PPRVIZ_TRY(upload_maps(ctx, std::vector<BatchView>{one}, W1, A, &maps));
-    const int2 *blocks = nullptr;
-    PPRVIZ_TRY(upload_row_blocks(ctx, std::vector<BatchView>{one}, &blocks));
-    const TileRec *recs = nullptr;
-    size_t nrec = 0;
-    PPRVIZ_TRY(upload_tile_recs(ctx, std::vector<BatchView>{one}, &recs, &nrec));
+    PPRVIZ_TRY(upload_maps(ctx, one_v, W1, A, &maps));
+    PassTables pt;
+    PPRVIZ_TRY(upload_pass_tables(ctx, one_v, pgrid, &pt));
+    PPRVIZ_TRY(ws_ensure(ctx, WS_RUNP, sizeof(V2) * ((size_t)pt.nruns * spipe::CWARPS * ST + 1)));
+    V2 *RunPart = ctx->ws[WS_RUNP].as<V2>();
     int *perr = flag + 1;
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
-    for (int it = 0; it < iters; ++it) {
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_pipe<0><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, X, Part, perr); }
-      PPRVIZ_LAUNCHED(ctx);
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)nbt, 1024, 0, ctx->stream>>>(blocks, view_d, Part, Bv); }
-      PPRVIZ_LAUNCHED(ctx);
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_pipe<1><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, Bv, Part, perr); }
-      PPRVIZ_LAUNCHED(ctx);
-      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)nbt, 1024, 0, ctx->stream>>>(blocks, view_d, Part, X); }
-      PPRVIZ_LAUNCHED(ctx);
-    }
+    for (int it = 0; it < iters; ++it) PPRVIZ_TRY(pass_pair(ctx, pgrid, pt, maps, view_d, X, Bv, Part, RunPart, perr));
     if (iters > 0) {
       int herr = 0;
       PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1022,24 +1097,13 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   PPRVIZ_TRY(sympass_pipe_grid(ctx, tiles.size(), &pgrid));
   const CUtensorMap *maps = nullptr;
   PPRVIZ_TRY(upload_maps(ctx, bv, W1, M, &maps));
-  const int2 *blocks = nullptr;
-  PPRVIZ_TRY(upload_row_blocks(ctx, bv, &blocks));
-  const TileRec *recs = nullptr;
-  size_t nrec = 0;
-  PPRVIZ_TRY(upload_tile_recs(ctx, bv, &recs, &nrec));
+  PassTables pt;
+  PPRVIZ_TRY(upload_pass_tables(ctx, bv, pgrid, &pt));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_RUNP, sizeof(V2) * ((size_t)pt.nruns * spipe::CWARPS * ST + 1)));
+  V2 *RunPart = ctx->ws[WS_RUNP].as<V2>();
   int *perr = flag + 1;
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
-  const unsigned nrb = (unsigned)cnts;  // row blocks of all views
-  for (int it = 0; it < iters; ++it) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_pipe<0><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, X, Part, perr); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<nrb, 1024, 0, ctx->stream>>>(blocks, views_d, Part, Bv); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_pipe<1><<<pgrid, spipe::WARPS * 32, spipe::SMEM, ctx->stream>>>((int)nrec, recs, maps, Bv, Part, perr); }
-    PPRVIZ_LAUNCHED(ctx);
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<nrb, 1024, 0, ctx->stream>>>(blocks, views_d, Part, X); }
-    PPRVIZ_LAUNCHED(ctx);
-  }
+  for (int it = 0; it < iters; ++it) PPRVIZ_TRY(pass_pair(ctx, pgrid, pt, maps, views_d, X, Bv, Part, RunPart, perr));
   if (iters > 0) {
     int herr = 0;
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -11,6 +11,13 @@ Tolerances:
                plus trajectory properties: non-increasing stress, centred
                output, final stress within 1e-3 of the oracle's.
   Energy: relative 1e-12 (FP64), 1e-5 (FP32); gradients likewise.
+  Batched vs single-view FP32 layout: the batched passes group a view's
+               column sums by the CTA chunks of the whole batch, so they add
+               the same FP32 terms in another order; one update agrees within
+               1e-5 * max(1, |X|_max), 40-200 updates within 2e-3 * max(1,
+               |X|_max) (the same amplification) and final stresses within
+               1e-4 relative. PDist is computed by the same kernels and is
+               compared bit for bit.
 """
 import math
 
@@ -44,6 +51,14 @@ def _pdist_for(ctx, n, mean_deg, seed, out64):
 
 def _rel(a, b):
     return np.abs(np.asarray(a, np.float64) - b) / np.maximum(1.0, np.abs(b))
+
+
+def _same_layout(X1, Xb, s1, sb, tol):
+    """Batched and single-view FP32 layouts of one view: the same trajectory up to
+    FP32 summation order."""
+    scale = max(1.0, float(np.abs(X1).max()))
+    assert np.abs(np.asarray(Xb, np.float64) - X1).max() <= tol * scale
+    assert abs(sb - s1) <= 1e-4 * abs(s1)
 
 
 def test_layout_fp64_config_small_full_trajectory(ctx):
@@ -180,16 +195,24 @@ def test_views_batch_matches_single_views(ctx):
         assert np.array_equal(Pd, Pd1)          # the batch runs the single-view kernels
         check_pdist(Pd1, Dref, cert, n)
         X1, s1 = ctx.layout(Pd.copy(), x0[off[v]:off[v + 1]].copy(), 40, P.FP32)
-        assert np.array_equal(X1, xb[off[v]:off[v + 1]])
-        assert s1 == stress[v]
+        _same_layout(X1, xb[off[v]:off[v + 1]], s1, stress[v], 2e-3)
+        sq += n * n
+    # one update: only the summation order differs
+    xb1, _, stress1, _ = ctx.views_batch(G, x0, ALPHA, 1e-6, 1, want_pdist=False)
+    sq = 0
+    for v, g in enumerate(graphs):
+        n = g.n
+        X1, s1 = ctx.layout(pdb[sq:sq + n * n].reshape(n, n).copy(), x0[off[v]:off[v + 1]].copy(), 1, P.FP32)
+        _same_layout(X1, xb1[off[v]:off[v + 1]], s1, stress1[v], 1e-5)
         sq += n * n
 
 
 def test_views_batch_sbm_sample_of_the_batched_workload(ctx):
     """16 SBM views (sizes 50..1500, 4..16 blocks, p_in 0.1, p_out 0.002): the
-    batched workload at reduced size. Every view's layout equals a single-view
-    run bit for bit; sampled views' PDist match the oracle under the certified
-    gate; the final stresses equal the single-view stresses."""
+    batched workload at reduced size. Every view's PDist equals a single-view
+    run bit for bit and, for sampled views, matches the oracle under the
+    certified gate; every view's layout and final stress equal a single-view
+    run's up to FP32 summation order."""
     import paper_2112_14944_gb300 as P
     graphs = synth.sbm_views(16, seed=5, n_min=50, n_max=1500)
     G = [ctx.upload_graph(g) for g in graphs]
@@ -207,5 +230,4 @@ def test_views_batch_sbm_sample_of_the_batched_workload(ctx):
         check_pdist(Pd1, Dref, cert, n)
     for v, g in enumerate(graphs):
         X1, s1 = ctx.layout(pdb[sq[v]:sq[v + 1]].reshape(g.n, g.n).copy(), x0[off[v]:off[v + 1]].copy(), 200, P.FP32)
-        assert np.array_equal(X1, xb[off[v]:off[v + 1]])
-        assert s1 == stress[v]
+        _same_layout(X1, xb[off[v]:off[v + 1]], s1, stress[v], 2e-3)
