@@ -264,6 +264,8 @@ void pprviz_graph_free(pprviz_graph *g) {
   g->invdw_f.release();
   g->invdw_d.release();
   g->dwff.release();
+  g->dense.release();
+  g->comp.release();
   delete g;
 }
 
