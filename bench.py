@@ -45,6 +45,22 @@ WORKLOAD = "chung_lu_n10000_deg20"
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
 
 
+# One launch in PROF_EVERY of the classes launched hundreds of times per step
+# is bracketed by CUDA events (every launch of the others): events between all
+# launches would serialise them and slow the step being measured.
+PROF_EVERY = 16
+
+
+def class_share(ktimes, steps):
+    """Per class and step: device ms (the timed launches' mean duration x all
+    launches) and launches."""
+    out = {}
+    for c, (ms, cnt, timed) in ktimes.items():
+        if cnt and timed:
+            out[c] = {"ms": ms / timed * cnt / steps, "launches": cnt / steps, "timed_launches": timed / steps}
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,7 +318,7 @@ def run_dense(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ctx.profile(True)
+    ctx.profile(PROF_EVERY)
     sampler = ClockSampler(local_rank)
     sampler.start()
     ms, flops, launches, sweeps, stats = [], 0.0, 0, 0, None
@@ -336,16 +352,15 @@ def run_dense(args, rank, world, local_rank):
         with open(pk) as f:
             bf16, kind = json.load(f)["bf16_tflops"], "measured"
     tf32 = bf16 * 1.1 / 2.25
-    sw_ms, sw_n = ktimes["sweep"]
-    ach = flops / (sw_ms / 1e3) / 1e12
+    sw_ms, sw_all, sw_n = ktimes["sweep"]
+    ach = flops / sw_all * sw_n / (sw_ms / 1e3) / 1e12  # flops of the timed launches / their time
     roof = {"kernel": "tensor-core sweep (k_dsweep_tc, 3xTF32 tcgen05.mma)", "bound": "tensor",
             "achieved": ach, "peak": tf32, "unit": "TFLOP/s", "frac": ach / tf32,
             "executed_tflops": 3 * ach, "executed_frac": 3 * ach / tf32,
-            "launches": sw_n, "avg_launch_us": 1e3 * sw_ms / max(1, sw_n),
-            "alg_flops_per_launch": flops / max(1, sw_n), "traffic": measured_traffic("dsweep"),
+            "launches": sw_all, "timed_launches": sw_n, "avg_launch_us": 1e3 * sw_ms / max(1, sw_n),
+            "alg_flops_per_launch": flops / max(1, sw_all), "traffic": measured_traffic("dsweep"),
             "peak_kind": f"{kind} bf16_tflops x 1.1/2.25 (nominal TF32/BF16), frac of {kind}"}
-    share = {c: {"ms": ktimes[c][0] / args.steps, "launches": ktimes[c][1] // max(1, args.steps)}
-             for c in ktimes if ktimes[c][1]}
+    share = class_share(ktimes, args.steps)
     line = {
         "metric": "DPPR entries/s, dense weighted view n=20k, err<=1e-6 vs FP64 (tensor-core sweeps)",
         "value": world * args.steps * entries / (total / 1e3), "unit": "entries/s", "n_gpus": world,
@@ -413,7 +428,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ctx.profile(True)
+    ctx.profile(PROF_EVERY)
     sampler = ClockSampler(local_rank)
     sampler.start()
     step_ms, dppr_ms, layout_ms = [], [], []
@@ -489,26 +504,32 @@ def run_ours(args, rank, world, local_rank):
              "ly": ("all-pairs L^Y pass (k_sympass_pipe<0>, persistent, TMA tile pipeline)", bytes_ly),
              "apply": ("(L^w)^+ apply pass (k_sympass_pipe<1>, persistent, TMA tile pipeline)", bytes_apply)}
     kernels = {}
+    # algorithmic bytes per launch = the class's bytes over all its launches in
+    # the timed steps / those launches; achieved = that / the average duration
+    # of its timed launches
     for cls, (label, alg) in names.items():
-        ms, cnt = ktimes[cls]
-        if cnt == 0 or ms <= 0:
+        ms, cnt, timed = ktimes[cls]
+        if timed == 0 or ms <= 0:
             continue
-        ach = alg / (ms / 1e3) / 1e9
+        per = alg / cnt
+        ach = per / (ms / timed / 1e3) / 1e9
         kernels[cls] = {"kernel": label, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                        "frac": ach / hbm, "launches": cnt, "avg_launch_us": 1e3 * ms / cnt,
-                        "alg_bytes_per_launch": alg / cnt, "traffic": measured_traffic(cls)}
-    ms, cnt = ktimes["factor"]
-    if cnt and ms > 0 and flops_factor > 0:
+                        "frac": ach / hbm, "launches": cnt, "timed_launches": timed,
+                        "avg_launch_us": 1e3 * ms / timed, "alg_bytes_per_launch": per,
+                        "traffic": measured_traffic(cls)}
+    ms, cnt, timed = ktimes["factor"]
+    if timed and ms > 0 and flops_factor > 0:
         fp32_peak = fp32_simt_tflops(sm_max)
-        ach = flops_factor / (ms / 1e3) / 1e12
-        kernels["factor"] = {"kernel": "L^w inverse, symmetric block sweep (k_fac_*)", "bound": "alu",
-                             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                             "launches": cnt, "avg_launch_us": 1e3 * ms / cnt,
-                             "alg_flops_per_launch": flops_factor / cnt, "traffic": measured_traffic("factor"),
+        per = flops_factor / cnt
+        ach = per / (ms / timed / 1e3) / 1e12
+        kernels["factor"] = {"kernel": "L^w build + inverse: symmetric block sweep with lookahead (k_fac_*)",
+                             "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": ach / fp32_peak, "launches": cnt, "timed_launches": timed,
+                             "avg_launch_us": 1e3 * ms / timed, "alg_flops_per_launch": per,
+                             "traffic": measured_traffic("factor"),
                              "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x max SM clock"}
-    share = {c: {"ms": ktimes[c][0] / args.steps, "launches": ktimes[c][1] // max(1, args.steps)}
-             for c in ktimes if ktimes[c][1]}
-    dom = max(kernels, key=lambda c: ktimes[c][0]) if kernels else None
+    share = class_share(ktimes, args.steps)
+    dom = max(kernels, key=lambda c: share[c]["ms"]) if kernels else None
     roof = dict(kernels[dom]) if dom else None
     if roof is not None and roof["bound"] == "hbm":
         roof["peak_kind"] = f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"

@@ -123,14 +123,19 @@ const char *pprviz_last_error(const pprviz_ctx *ctx);
 /* Wait for all work enqueued on the context stream. */
 int pprviz_sync(pprviz_ctx *ctx);
 int pprviz_get_stats(const pprviz_ctx *ctx, pprviz_stats *out);
-/* Device timing per kernel class. With `enable` != 0, every kernel launch of
- * the context is bracketed by CUDA events on the context stream; the totals
- * accumulate until read. pprviz_profile resets the totals. */
+/* Device timing per kernel class, by CUDA events on the context stream
+ * around launches. enable = 0: off; 1: every launch is timed; N > 1: every
+ * launch of the classes launched a few times per call, and one launch in N
+ * of the sweep, L^Y, apply and other classes (launched hundreds of times per
+ * call; events between every launch would serialise them). The totals
+ * accumulate until read; pprviz_profile resets them. */
 int pprviz_profile(pprviz_ctx *ctx, int enable);
-/* Waits for the context stream, then writes PPRVIZ_NKCLASS entries of total
- * device milliseconds and launch counts per class since the last reset (NULL
- * arrays are skipped). Launch counts are kept even when timing is off. */
-int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out);
+/* Waits for the context stream, then writes, per class (PPRVIZ_NKCLASS
+ * entries; NULL arrays are skipped) since the last reset: the total device
+ * milliseconds of the timed launches, the number of launches, and the number
+ * of timed launches (the ones in ms_out). Launch counts are kept even when
+ * timing is off. */
+int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, int64_t *timed_out);
 
 /* P0 - graph ingest (Sec. 2.1; Table 1: n nodes, out-degree d(v)).
  * row_ptr: n+1 int64, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.

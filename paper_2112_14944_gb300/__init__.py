@@ -107,12 +107,13 @@ class Context:
     def sync(self):
         B.pprviz_sync(self.h)
 
-    def profile(self, enable: bool = True):
-        """Reset the per-kernel-class counters; time every launch if `enable`."""
+    def profile(self, enable=True):
+        """Reset the per-kernel-class counters; enable: False off, True every launch,
+        N > 1 one in N launches of the hot classes (sweep, L^Y, apply, other)."""
         B.pprviz_profile(self.h, enable)
 
     def kernel_times(self) -> dict:
-        """{class: (device ms, launches)} since the last profile() call."""
+        """{class: (device ms of the timed launches, launches, timed launches)} since the last profile() call."""
         return B.pprviz_kernel_times(self.h)
 
     def upload(self, n, row_ptr, col, weights=None, validate=True, degree_count=False) -> Graph:

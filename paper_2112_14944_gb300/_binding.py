@@ -45,7 +45,7 @@ _SIGS = {
     "pprviz_sync": (C.c_int, [_VP]),
     "pprviz_get_stats": (C.c_int, [_VP, _VP]),
     "pprviz_profile": (C.c_int, [_VP, C.c_int]),
-    "pprviz_kernel_times": (C.c_int, [_VP, _VP, _VP]),
+    "pprviz_kernel_times": (C.c_int, [_VP, _VP, _VP, _VP]),
     "pprviz_graph_upload": (C.c_int, [_VP, C.c_int64, _VP, _VP, _VP, C.c_uint32, C.c_uint32, C.POINTER(_VP)]),
     "pprviz_graph_free": (None, [_VP]),
     "pprviz_graph_degrees": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -162,16 +162,18 @@ def pprviz_get_stats(ctx: int) -> dict:
     return {name: getattr(s, name) for name, _ in s._fields_}
 
 
-def pprviz_profile(ctx: int, enable: bool) -> None:
-    _check(ctx, load().pprviz_profile(ctx, 1 if enable else 0))
+def pprviz_profile(ctx: int, enable) -> None:
+    """enable: False/0 off, True/1 every launch, N > 1 one in N launches of the hot classes."""
+    _check(ctx, load().pprviz_profile(ctx, int(enable)))
 
 
 def pprviz_kernel_times(ctx: int) -> dict:
-    """{class: (total device ms, launches)} since the last pprviz_profile."""
+    """{class: (device ms of the timed launches, launches, timed launches)} since the last pprviz_profile."""
     ms = np.zeros(len(KERNEL_CLASSES), dtype=np.float64)
     cnt = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
-    _check(ctx, load().pprviz_kernel_times(ctx, ms.ctypes.data, cnt.ctypes.data))
-    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(KERNEL_CLASSES)}
+    timed = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+    _check(ctx, load().pprviz_kernel_times(ctx, ms.ctypes.data, cnt.ctypes.data, timed.ctypes.data))
+    return {name: (float(ms[i]), int(cnt[i]), int(timed[i])) for i, name in enumerate(KERNEL_CLASSES)}
 
 
 def pprviz_graph_upload(ctx, n, row_ptr, col_idx, weights=None, flags=PPRVIZ_UNDIRECTED | PPRVIZ_VALIDATE) -> int:

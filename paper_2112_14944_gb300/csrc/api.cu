@@ -47,8 +47,11 @@ static cudaEvent_t ev_get(pprviz_ctx *ctx) {
 }
 
 ProfScope::ProfScope(pprviz_ctx *ctx, int k) : c(ctx), cls(k) {
-  c->class_launches[cls]++;
-  if (c->profiling) {
+  const int64_t nth = c->class_launches[cls]++;
+  // the classes launched hundreds of times per call are sampled: one launch in prof_every
+  const bool hot = cls == PPRVIZ_K_SWEEP || cls == PPRVIZ_K_LY || cls == PPRVIZ_K_APPLY || cls == PPRVIZ_K_OTHER;
+  if (c->profiling && (!hot || nth % c->prof_every == 0)) {
+    c->class_timed[cls]++;
     a = ev_get(c);
     b = ev_get(c);
     if (a && b) cudaEventRecord(a, c->stream);
@@ -179,12 +182,14 @@ int pprviz_profile(pprviz_ctx *ctx, int enable) {
   for (int i = 0; i < PPRVIZ_NKCLASS; ++i) {
     ctx->class_ms[i] = 0.0;
     ctx->class_launches[i] = 0;
+    ctx->class_timed[i] = 0;
   }
   ctx->profiling = enable != 0;
+  ctx->prof_every = enable > 1 ? enable : 1;
   return PPRVIZ_OK;
 }
 
-int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out) {
+int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, int64_t *timed_out) {
   if (!ctx) return PPRVIZ_E_INVALID_ARG;
   PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -199,6 +204,7 @@ int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out) 
   for (int i = 0; i < PPRVIZ_NKCLASS; ++i) {
     if (ms_out) ms_out[i] = ctx->class_ms[i];
     if (launches_out) launches_out[i] = ctx->class_launches[i];
+    if (timed_out) timed_out[i] = ctx->class_timed[i];
   }
   return PPRVIZ_OK;
 }

@@ -57,6 +57,8 @@ struct pprviz_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double class_ms[PPRVIZ_NKCLASS] = {0};
   int64_t class_launches[PPRVIZ_NKCLASS] = {0};
+  int64_t class_timed[PPRVIZ_NKCLASS] = {0};  // launches whose device time is in class_ms
+  int prof_every = 1;                         // sampling period of the hot classes
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -416,16 +416,56 @@ k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();  // the only CTA-wide barrier
+  // the launch that follows (the reduce) may be scheduled from now on; it
+  // waits for this grid's completion itself
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (warp == CWARPS) {
     // ---- producer
     if (lane == 0) {
       const CUtensorMap *fenced = nullptr;
-      int issued = 0;
+      // The matrix tiles do not depend on the previous launch: the first PS
+      // are requested before waiting for it (expect_tx without the arrival,
+      // so the stage cannot complete early); their vector slices, which the
+      // previous launch writes, after it.
+      const int npre = mine < PS ? mine : PS;
+      for (int n = 0; n < npre; ++n) {
+        const TileRec t = tiles[first + n];
+        const CUtensorMap *map = maps + 2 * t.v + MODE;
+        if (map != fenced) {
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                       : "memory");
+          fenced = map;
+        }
+        const uint32_t b = smem_u32(&full[n]);
+        asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(TILE_BYTES) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(sbase + (uint32_t)n * STAGE_BYTES),
+            "l"(reinterpret_cast<uint64_t>(map)), "r"(t.J * ST), "r"(t.I * ST), "r"(b)
+            : "memory");
+      }
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      for (int n = 0; n < npre; ++n) {
+        const TileRec t = tiles[first + n];
+        const float2 *Vv = V + (int64_t)t.vblk * ST;
+        const uint32_t dst = sbase + (uint32_t)n * STAGE_BYTES, b = smem_u32(&full[n]);
+        srec[n] = t;  // released to the consumers by the arrive below
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(2 * VEC_BYTES) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         dst + TILE_BYTES),
+                     "l"(Vv + (int64_t)t.I * ST), "r"(VEC_BYTES), "r"(b)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         dst + TILE_BYTES + VEC_BYTES),
+                     "l"(Vv + (int64_t)t.J * ST), "r"(VEC_BYTES), "r"(b)
+                     : "memory");
+      }
+      int issued = npre;
       bool ok = true;
-      for (int n = 0; n < mine; ++n) {
+      for (int n = npre; n < mine; ++n) {
         const int s = n % PS;
         const TileRec t = tiles[first + n];
-        if (n >= PS && !mbar_wait(&empty[s], (uint32_t)(((n - PS) / PS) & 1))) {
+        if (!mbar_wait(&empty[s], (uint32_t)(((n - PS) / PS) & 1))) {
           ok = false;
           break;
         }
@@ -545,6 +585,10 @@ k_reduce_rows(const int2 *__restrict__ blocks, const BatchView *__restrict__ vie
               float2 *__restrict__ Vout) {
   constexpr int NG = 8, UN = 10;
   __shared__ float2 red[NG][ST];
+  // launched as a programmatic dependent of the pass: wait for it to complete
+  // (its partial sums visible); the next pass may be scheduled meanwhile
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int2 b = blocks[blockIdx.x];
   const BatchView bv = views[b.x];
   const int row = threadIdx.x & (ST - 1), g = threadIdx.x >> 7;
@@ -868,15 +912,36 @@ int upload_pass_tables(pprviz_ctx *ctx, const std::vector<BatchView> &bv, unsign
 
 // One layout update of all views in the tables: L^Y pass over W1 from X into
 // Bv, apply pass over M from Bv into X, each followed by its reduce.
+// Launch on the context stream as a programmatic dependent of the previous
+// launch (the kernel itself waits for it with griddepcontrol.wait), so that
+// its blocks are scheduled, and the pass requests its first tiles, while the
+// previous launch finishes.
+template <typename... P, typename... A>
+cudaError_t launch_dependent(pprviz_ctx *ctx, void (*kernel)(P...), unsigned grid, unsigned block, size_t smem,
+                             A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 int pass_pair(pprviz_ctx *ctx, unsigned grid, const PassTables &pt, const CUtensorMap *maps, const BatchView *views_d,
               float2 *X, float2 *Bv, float2 *Part, float2 *RunPart, int *perr) {
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); k_sympass_pipe<0><<<grid, spipe::THREADS, spipe::SMEM, ctx->stream>>>(pt.ntile, pt.recs, maps, X, Part, RunPart, perr); }
+  const unsigned nb = (unsigned)pt.nblocks;
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<0>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, pt.recs, maps, (const float2 *)X, Part, RunPart, perr)); }
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)pt.nblocks, 1024, 0, ctx->stream>>>(pt.blocks, views_d, pt.run_ptr, pt.run_idx, Part, RunPart, Bv); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, nb, 1024, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, Bv)); }
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); k_sympass_pipe<1><<<grid, spipe::THREADS, spipe::SMEM, ctx->stream>>>(pt.ntile, pt.recs, maps, Bv, Part, RunPart, perr); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<1>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, pt.recs, maps, (const float2 *)Bv, Part, RunPart, perr)); }
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_reduce_rows<<<(unsigned)pt.nblocks, 1024, 0, ctx->stream>>>(pt.blocks, views_d, pt.run_ptr, pt.run_idx, Part, RunPart, X); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, nb, 1024, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, X)); }
   PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
 }
