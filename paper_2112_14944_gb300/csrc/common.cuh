@@ -166,8 +166,9 @@ int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp
 // ---- factor (factor.cu) ----------------------------------------------------
 // In-place inverse of the SPD kp x kp matrix A (kp % 128 == 0); on return A
 // holds A^-1 on its upper 64-block triangle and on the 128 x 128 diagonal tiles.
-// `work` holds spd_inverse_work(kp) elements (2 (2 * NB * kp + NB * NB) + 64
-// with NB = 128: two sets of panels and pivot inverse, and a status word). The FP32 version runs its trailing updates on the tensor cores and
+// `work` holds spd_inverse_work(kp) elements: two sets (the lookahead's
+// parities) of panels (2 x 2 NB x kp: Ct and Ut split into high and low
+// parts, NB = 128) and pivot inverse (NB x NB), and a status word. The FP32 version runs its trailing updates on the tensor cores and
 // returns PPRVIZ_E_TIMEOUT if an MMA completion wait expires.
 size_t spd_inverse_work(int32_t kp);  // elements of `work` for either type
 int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work);

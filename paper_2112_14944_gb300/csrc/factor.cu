@@ -21,9 +21,9 @@
 
 namespace pprviz {
 
-// two sets (the lookahead's parities) of panels Ct, Ut (NB x kp each) and
-// pivot inverse P (NB x NB), and a status word
-size_t spd_inverse_work(int32_t kp) { return (size_t)2 * (2 * 128 * (size_t)kp + 128 * 128) + 64; }
+// two sets (the lookahead's parities) of panels Ct, Ut (2 NB x kp each: the
+// split high and low parts) and pivot inverse P (NB x NB), and a status word
+size_t spd_inverse_work(int32_t kp) { return (size_t)2 * (2 * 256 * (size_t)kp + 128 * 128) + 64; }
 
 // P = A_KK^-1 by an in-place scalar sweep of the NB x NB block in shared memory
 // (ping-pong buffers, one barrier per pivot); writes P to `P` and -P into A_KK.
@@ -167,13 +167,38 @@ struct V4<double> {
   }
 };
 
+// Operand layout of the tensor-core trailing update ("split canonical"): for
+// a 128-row block B and a 16-wide chunk c of the inner dimension, the TF32
+// high parts (x with its low 13 mantissa bits cleared) and the remainders
+// (x - high) of the 128 x 16 chunk are two consecutive 8 KiB runs in the
+// canonical no-swizzle K-major layout of tcgen05 (8-row x 16-byte core
+// matrices: byte (r / 8) 512 + (k / 4) 128 + (r % 8) 16 + (k % 4) 4), at
+// float offset (B 8 + c) 4096. A chunk's operands are then one contiguous
+// 16 KiB copy. Four consecutive k (k % 4 == 0) are contiguous, so the writer
+// stores float4s.
+__device__ __forceinline__ void store_split4(float *X, int row, int k, const float (&v)[4]) {
+  const int B = row >> 7, r = row & 127, c = k >> 4, kk = k & 15;
+  float *blk = X + (int64_t)(B * 8 + c) * 4096;
+  const int o = ((r >> 3) * 512 + (kk >> 2) * 128 + (r & 7) * 16) >> 2;
+  float4 h, l;
+  h.x = __uint_as_float(__float_as_uint(v[0]) & 0xFFFFE000u);
+  h.y = __uint_as_float(__float_as_uint(v[1]) & 0xFFFFE000u);
+  h.z = __uint_as_float(__float_as_uint(v[2]) & 0xFFFFE000u);
+  h.w = __uint_as_float(__float_as_uint(v[3]) & 0xFFFFE000u);
+  l.x = v[0] - h.x; l.y = v[1] - h.y; l.z = v[2] - h.z; l.w = v[3] - h.w;
+  *reinterpret_cast<float4 *>(blk + o) = h;
+  *reinterpret_cast<float4 *>(blk + 2048 + o) = l;
+}
+template <typename T>
+__device__ __forceinline__ void store_split4(T *, int, int, const T (&)[4]) {}  // FP64: unused
+
 // Panel of pivot block K for block I != K (NB rows): C_I = A_IK (from the
 // stored upper triangle: A[i][K0 + s] for I < K, A[K0 + s][i] for I > K),
 // U_I = C_I P. Writes C_I and U_I for the trailing update, transposed
-// (Ct[t][i], Ut[t][i], the SIMT update's layout) or, with KM, row-major
-// (Ct[i][t], Ut[i][t], row stride NB: K-major operands of the tensor-core
-// update), and stores U_I back as the new panel (A_IK for I < K, A_KI = U_I^T
-// for I > K). 256 threads on a 16 x 16 grid, each an R x R block of U
+// (Ct[t][i], Ut[t][i], the SIMT update's layout) or, with KM, in the split
+// canonical layout of the tensor-core update (rows i of block I, inner index
+// t), and stores U_I back as the new panel (A_IK for I < K, A_KI = U_I^T for
+// I > K). 256 threads on a 16 x 16 grid, each an R x R block of U
 // (R = NB / 16) accumulated in registers.
 template <typename T, int NB, bool KM>
 __global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ P,
@@ -192,11 +217,15 @@ __global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__
     else sC[r * LD + c] = A[(int64_t)(K0 + r) * kp + I0 + c];         // s = r, i = c
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    if (KM) {  // Ct[I0 + i][t] = C[i][t]
-      const int i = e / NB, t = e % NB;
-      Ct[(int64_t)(I0 + i) * NB + t] = sC[t * LD + i];
-    } else {   // Ct[t][I0 + i] = C[i][t]
+  if (KM) {  // C[i][t .. t + 3], split
+    for (int e = threadIdx.x; e < NB * NB / 4; e += blockDim.x) {
+      const int i = e / (NB / 4), t = (e % (NB / 4)) * 4;
+      const T v[4] = {sC[t * LD + i], sC[(t + 1) * LD + i], sC[(t + 2) * LD + i], sC[(t + 3) * LD + i]};
+      store_split4(Ct, I0 + i, t, v);
+    }
+  }
+  for (int e = threadIdx.x; e < NB * NB && !KM; e += blockDim.x) {
+    {          // Ct[t][I0 + i] = C[i][t]
       const int t = e / NB, i = e % NB;
       Ct[(int64_t)t * kp + I0 + i] = sC[t * LD + i];
     }
@@ -249,7 +278,7 @@ __global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__
         T tmp[4];
 #pragma unroll
         for (int w = 0; w < 4; ++w) tmp[w] = u[x][4 * q + w];
-        if (KM) V4<T>::st(Ut + (int64_t)(I0 + i) * NB + tx * R + 4 * q, tmp);
+        if (KM) store_split4(Ut, I0 + i, tx * R + 4 * q, tmp);
         if (above) V4<T>::st(A + (int64_t)(I0 + i) * kp + K0 + tx * R + 4 * q, tmp);
       }
     }
@@ -316,23 +345,10 @@ k_fac_trailing(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core trailing update (FP32, NB = 128): A[i][j] -= sum_t Ct[t][i]
-// Ut[t][j] on the 128 x 128 tiles I <= J outside the pivot row and column, as
-// tcgen05.mma kind::tf32 products with split operands (x = x_hi + x_lo, x_hi =
-// x with the low 13 mantissa bits cleared): C ~ A_hi B_hi + A_hi B_lo + A_lo
-// B_hi (error-compensated TF32, Ootomo & Yokota 2022), FP32 accumulation in
-// tensor memory. The 128-deep inner dimension is streamed in 16-wide chunks
-// through two shared-memory stages in the canonical no-swizzle K-major layout
-// (8-row x 16-byte core matrices); the panels are stored row-major [x][t], so
-// each thread moves 16-byte runs of 4 consecutive t (8 lanes cover 8 rows at
-// one run, 4 lane octets the 4 runs of a chunk: 64 contiguous bytes per row,
-// and conflict-free canonical stores). The
-// global loads of chunk c + 1 are issued before the MMAs of chunk c are waited
-// on; every mbarrier wait has an iteration limit (on expiry the CTA sets `err`,
-// skips the update and still frees its tensor memory after a second bounded
-// wait). 64 KiB of shared memory, 128 tensor-memory columns and a small
-// register budget let three CTAs share an SM, so that one CTA's epilogue (the
-// read-modify-write of its C tile) overlaps the staging and MMAs of others.
+// Tensor-core trailing update (FP32 inverse): C_IJ -= A_I^T B_J with the
+// 3xTF32 split (Ootomo & Yokota 2022; hi = x with the low 13 mantissa bits
+// cleared): C ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in
+// tensor memory, 128 x 128 tiles, inner dimension 128 in 16-wide chunks.
 // ---------------------------------------------------------------------------
 namespace tc {
 constexpr int TM = 128;                       // tile edge (M = N = 128)
@@ -342,14 +358,11 @@ constexpr uint32_t LBO = 128;                 // bytes to the next core matrix a
 constexpr uint32_t SBO = (KC / 4) * 128;      // bytes to the next 8-row group
 constexpr int OPB = TM * KC * 4;              // one staged operand part (8 KiB)
 constexpr int STAGE = 4 * OPB;                // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM = 2 * STAGE;               // two stages
+constexpr int NST = 3;                        // stages
+constexpr int SMEM = NST * STAGE + 1024;      // stages (+ alignment); the epilogue reuses 64 KiB of them
 constexpr long WAIT_LIMIT = 1L << 22;         // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t canon(int r, int k) {
-  return (uint32_t)((r >> 3) * SBO + (k >> 2) * LBO + (r & 7) * 16 + (k & 3) * 4);
-}
 
 // shared-memory matrix descriptor: start >> 4, LBO >> 4, SBO >> 4, version 1, no swizzle
 __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
@@ -359,8 +372,6 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
 
 // instruction descriptor, kind::tf32: F32 accumulate, TF32 A and B, both K-major
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-
-__device__ __forceinline__ float hi_part(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   uint32_t done = 0;
@@ -374,47 +385,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
-__device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
-  float4 h, l;
-  h.x = hi_part(v.x); h.y = hi_part(v.y); h.z = hi_part(v.z); h.w = hi_part(v.w);
-  l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-  *reinterpret_cast<float4 *>(hi + off) = h;
-  *reinterpret_cast<float4 *>(lo + off) = l;
-}
-
-// 128 rows x (KC / 4) quads of one chunk: float4 per operand per thread
-constexpr int CH_ITEMS = TM * (KC / 4) / 256;
-struct Chunk {
-  float4 a[CH_ITEMS], b[CH_ITEMS];
-};
-
-// row x and quad kq of item `it` of thread `tid` (KC = 16: 4 quads per row)
-__device__ __forceinline__ void chunk_coords(int tid, int it, int &x, int &kq) {
-  const int lane = tid & 31, w = tid >> 5;
-  x = 8 * (w * CH_ITEMS + it) + (lane & 7);
-  kq = lane >> 3;
-}
-
-__device__ __forceinline__ void load_chunk(Chunk &ch, const float *__restrict__ Ct, const float *__restrict__ Ut,
-                                           int I0, int J0, int k0, int tid) {
-#pragma unroll
-  for (int it = 0; it < CH_ITEMS; ++it) {
-    int x, kq;
-    chunk_coords(tid, it, x, kq);
-    ch.a[it] = __ldg(reinterpret_cast<const float4 *>(Ct + (int64_t)(I0 + x) * NB + k0 + 4 * kq));
-    ch.b[it] = __ldg(reinterpret_cast<const float4 *>(Ut + (int64_t)(J0 + x) * NB + k0 + 4 * kq));
-  }
-}
-
-__device__ __forceinline__ void store_chunk(const Chunk &ch, unsigned char *st, int tid) {
-#pragma unroll
-  for (int it = 0; it < CH_ITEMS; ++it) {
-    int x, kq;
-    chunk_coords(tid, it, x, kq);
-    const uint32_t o = canon(x, 4 * kq);
-    put_split(st, st + OPB, o, ch.a[it]);
-    put_split(st + 2 * OPB, st + 3 * OPB, o, ch.b[it]);
-  }
+// Chunk c of the operands of tile (I0, J0) into stage st: the 16 KiB split
+// runs of Ct block I0 / 128 and Ut block J0 / 128, completing on bar.
+__device__ __forceinline__ void issue_chunk(uint32_t st, uint64_t *bar, const float *Ct, const float *Ut, int I0,
+                                            int J0, int c) {
+  const uint32_t b = smem_u32(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(STAGE) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(st),
+               "l"(Ct + (int64_t)((I0 / TM) * (NB / KC) + c) * 4096), "r"(2 * OPB), "r"(b)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   st + 2 * OPB),
+               "l"(Ut + (int64_t)((J0 / TM) * (NB / KC) + c) * 4096), "r"(2 * OPB), "r"(b)
+               : "memory");
 }
 }  // namespace tc
 
@@ -425,7 +408,16 @@ __device__ __forceinline__ void store_chunk(const Chunk &ch, unsigned char *st, 
 // block b is tile (b, k1) for b < k1, else (k1, b)). The lookahead of the
 // driver updates block row and column k1 first, so that the next pivot's
 // inverse and panel overlap the rest of the update.
-__global__ void __launch_bounds__(256, 3)
+// One thread streams the 8 inner chunks of the tile's operands (already
+// split by the panel kernel) through NST shared-memory stages with bulk
+// copies and issues the 3 x 2 MMAs of each chunk; a stage is refilled once
+// the MMAs of the chunk before it have completed. 96 KiB of shared memory,
+// 128 tensor-memory columns: two CTAs per SM, so that one CTA's epilogue
+// (the read-modify-write of its C tile) overlaps the other's MMAs. Every
+// mbarrier wait has an iteration limit (on expiry the CTA sets `err`, skips
+// the update and still frees its tensor memory after bounded waits for its
+// copies and MMAs).
+__global__ void __launch_bounds__(256, 2)
 k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict__ A, const float *__restrict__ Ct,
                   const float *__restrict__ Ut, int *__restrict__ err) {
   using namespace tc;
@@ -441,9 +433,12 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
   }
   if (J0 < I0 || I0 == K0 || J0 == K0) return;  // lower triangle, pivot row and column
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[NST], mmad[NST];
   __shared__ uint32_t tmem_sh;
+  __shared__ int ok_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char *sbuf = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // 1024-byte aligned
+  const uint32_t sb = smem_u32(sbuf);
   // TMEM read-out: warp w takes lanes (rows) 32 (w % 4) .. + 31 and columns
   // 64 (w / 4) .. + 63 of the accumulator.
   const int lg = warp & 3, chalf = warp >> 2;
@@ -452,8 +447,10 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    for (int q = 0; q < NST; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mmad[q])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -461,27 +458,19 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_sh;
   constexpr int NCH = NB / KC;
-  bool ok = true;
-  int issued = -1;
-  Chunk ch;
-  load_chunk(ch, Ct, Ut, I0, J0, 0, tid);
-#pragma unroll 1
-  for (int cidx = 0; cidx < NCH; ++cidx) {
-    const int buf = cidx & 1;
-    unsigned char *st = smem_raw + buf * STAGE;
-    if (cidx >= 2 && !mbar_wait(&mbar[buf], (uint32_t)(((cidx - 2) >> 1) & 1))) ok = false;
-    if (__syncthreads_and(ok) == 0) {
-      ok = false;
-      break;
-    }
-    store_chunk(ch, st, tid);
-    if (cidx + 1 < NCH) load_chunk(ch, Ct, Ut, I0, J0, (cidx + 1) * KC, tid);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
-      const uint32_t base = smem_u32(st);
+  if (tid == 0) {
+    bool ok = true;
+    int issued = 0, done = -1;  // chunks copied; last chunk whose MMAs were seen complete
+    for (int c = 0; c < NST && c < NCH; ++c) issue_chunk(sb + c * STAGE, &full[c], Ct, Ut, I0, J0, c);
+    issued = NST < NCH ? NST : NCH;
+    int mmad_last = -1;
+    for (int c = 0; c < NCH && ok; ++c) {
+      const int s = c % NST;
+      if (!mbar_wait(&full[s], (uint32_t)((c / NST) & 1))) {
+        ok = false;
+        break;
+      }
+      const uint32_t base = sb + s * STAGE;
 #pragma unroll 1
       for (int pass = 0; pass < 3; ++pass) {
         const uint32_t pa = base + (pass == 2 ? OPB : 0);
@@ -490,7 +479,7 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
         for (int ks = 0; ks < KC / 8; ++ks) {
           const uint64_t da = desc(pa + ks * 2 * LBO);
           const uint64_t db = desc(pb + ks * 2 * LBO);
-          const uint32_t acc = (cidx == 0 && pass == 0 && ks == 0) ? 0u : 1u;
+          const uint32_t acc = (c == 0 && pass == 0 && ks == 0) ? 0u : 1u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
@@ -498,25 +487,40 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&mbar[buf])));
+          smem_u32(&mmad[s])));
+      mmad_last = c;
+      // refill the stage of chunk c - 1 once its MMAs are done
+      if (c >= 1 && c - 1 + NST < NCH) {
+        const int sp = (c - 1) % NST;
+        if (!mbar_wait(&mmad[sp], (uint32_t)(((c - 1) / NST) & 1))) {
+          ok = false;
+          break;
+        }
+        done = c - 1;
+        issue_chunk(sb + sp * STAGE, &full[sp], Ct, Ut, I0, J0, c - 1 + NST);
+        issued = c - 1 + NST + 1;
+      }
     }
-    issued = cidx;
-  }
-  if (ok && !mbar_wait(&mbar[issued & 1], (uint32_t)((issued >> 1) & 1))) ok = false;
-  ok = __syncthreads_and(ok) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok) {
-    if (tid == 0) {
+    // all MMAs complete (they complete in order)
+    if (ok && !mbar_wait(&mmad[(NCH - 1) % NST], (uint32_t)(((NCH - 1) / NST) & 1))) ok = false;
+    if (!ok) {
       atomicOr(err, 1);
-      if (issued >= 0) (void)mbar_wait(&mbar[issued & 1], (uint32_t)((issued >> 1) & 1));
+      // bounded waits for the copies and MMAs this CTA issued
+      for (int c = done + 1; c < issued; ++c) (void)mbar_wait(&full[c % NST], (uint32_t)((c / NST) & 1));
+      for (int c = done + 1; c <= mmad_last; ++c) (void)mbar_wait(&mmad[c % NST], (uint32_t)((c / NST) & 1));
     }
-  } else {
+    ok_sh = ok ? 1 : 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok_sh) {
     // The product goes through shared memory (the stages are free once the
     // last MMA has completed) so that the read-modify-write of the C tile is
     // row-contiguous: warp w writes its 32 rows x 64 columns (TMEM lane = row),
     // 16-byte chunk c of row r at chunk slot c ^ (r % 32); then each warp
     // updates whole 512-byte rows.
-    float *tile = reinterpret_cast<float *>(smem_raw);  // 128 x 128
+    float *tile = reinterpret_cast<float *>(sbuf);  // 128 x 128
     const uint32_t tbase = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * chalf);
     const int row = 32 * lg + lane;
 #pragma unroll 1
@@ -573,12 +577,13 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
   constexpr bool TC = std::is_same<T, float>::value;  // FP32: 128-blocks, tensor-core trailing update
   constexpr int NB = TC ? 128 : 64;
   constexpr int TM = 64;                               // SIMT trailing tile (FP64)
-  const size_t set = (size_t)2 * NB * kp + (size_t)NB * NB;  // one parity's Ct, Ut, P
+  const size_t pan = (TC ? 2 : 1) * (size_t)NB * kp;         // one panel (split into high and low parts with TC)
+  const size_t set = 2 * pan + (size_t)NB * NB;               // one parity's Ct, Ut, P
   T *Ct[2], *Ut[2], *P[2];
   for (int q = 0; q < 2; ++q) {
     Ct[q] = work + q * set;
-    Ut[q] = Ct[q] + (size_t)NB * kp;
-    P[q] = Ct[q] + (size_t)2 * NB * kp;
+    Ut[q] = Ct[q] + pan;
+    P[q] = Ct[q] + 2 * pan;
   }
   int *err = reinterpret_cast<int *>(work + 2 * set);
   const size_t diag_smem = 2 * sizeof(T) * NB * (NB + 1);
