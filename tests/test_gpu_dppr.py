@@ -274,3 +274,44 @@ def test_pdist_standalone_matches_oracle(ctx):
         assert out.dtype == dt
         _check_pdist_flat(out, ref, tol=tol)
         assert out[5, 7] == np.float64(2 * math.log(50)).astype(dt)
+
+
+def test_full_size_view_of_2m_graph_sampled(ctx):
+    """Chung-Lu n=2,000,000, mean degree 10, a view of 8,192 nodes drawn
+    uniformly (the differentiable-layout workload): FP32 DPPR/PDist among the
+    view with n_clamp = n. Sampled view rows against the oracle's power
+    iteration on the whole graph (rows and columns of the sampled sources),
+    every certificate, DPPR symmetry, and the stress energy and gradient of a
+    layout of the whole view on sampled rows."""
+    import paper_2112_14944_gb300 as P
+    g = synth.chung_lu(2_000_000, 10, 2.5, seed=0)
+    k = 8192
+    view = synth.sample_view(g.n, k, seed=0)
+    G = ctx.upload_graph(g)
+    D, Delta, cert, st = ctx.dppr(G, view, ALPHA, EPS, P.FP32)
+    assert st == 0 and cert.shape == (k,) and cert.max() <= EPS
+    pos = np.array([0, 1, 2345, k - 1])             # sampled positions in the view
+    src = view[pos]
+    Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    rows = O.ppr_rows(Pm, src, ALPHA)               # pi(s, .) over the graph
+    cols = O.ppr_cols(Pm, src, ALPHA)               # pi(., s)
+    Drow = d[src][:, None] * rows[:, view]          # pi_d(s, t), t in the view
+    Dcol = (d[view][:, None] * cols[view, :]).T     # pi_d(t, s) as rows
+    _check_dppr(D[pos], Drow)
+    z = Drow + Dcol
+    ref = O.pdist_from_z(z, g.n)
+    ref[np.arange(len(pos)), pos] = 0.0
+    cc = cert[pos][:, None] + cert[None, :]
+    tol = 1e-5 + cc / np.maximum(z - cc, math.e / float(g.n) ** 2)
+    assert np.all(np.abs(Delta[pos].astype(np.float64) - ref) <= tol)
+    asym = np.abs(D - D.T) / np.maximum(1.0, np.abs(D))
+    assert asym.max() <= 2e-6
+    # energy and gradient of a layout of the whole view (pair recomputation)
+    X = synth.uniform_x0(k, seed=0) * 8.0
+    e, gx, _ = ctx.energy(Delta, X, grad_scale=1.0, grad_x=True)
+    Dd, Xd = Delta.astype(np.float64), X.astype(np.float64)
+    e_ref = O.stress(Xd, Dd)
+    assert abs(e - e_ref) <= 2e-5 * e_ref
+    g_ref = O.stress_grad(Xd, Dd)[pos]
+    assert np.abs(gx[pos] - g_ref).max() <= 2e-4 * max(1.0, np.abs(g_ref).max())

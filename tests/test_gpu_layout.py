@@ -231,3 +231,32 @@ def test_views_batch_sbm_sample_of_the_batched_workload(ctx):
     for v, g in enumerate(graphs):
         X1, s1 = ctx.layout(pdb[sq[v]:sq[v + 1]].reshape(g.n, g.n).copy(), x0[off[v]:off[v + 1]].copy(), 200, P.FP32)
         _same_layout(X1, xb[off[v]:off[v + 1]], s1, stress[v], 2e-3)
+
+
+def test_views_batch_full_size_sbm_workload_sampled(ctx):
+    """The batched-views workload at full size: 256 SBM views, n_v ~ U{50..5000},
+    4..16 blocks, p_in 0.1, p_out 0.002 (seed 0), DPPR, PDist and 200 FP32
+    layout updates of every view in one call. For sampled views (the smallest,
+    the largest and two more) the single-view PDist matches the oracle's
+    direct solve under the certified gate, and the batched layout and final
+    stress equal the single-view run's up to FP32 summation order; every view's
+    output is finite and centred."""
+    import paper_2112_14944_gb300 as P
+    graphs = synth.sbm_views(256, seed=0)
+    G = [ctx.upload_graph(g) for g in graphs]
+    x0 = np.concatenate([synth.uniform_x0(g.n, seed=1000 + i) for i, g in enumerate(graphs)])
+    xb, _, stress, off = ctx.views_batch(G, x0, ALPHA, 1e-6, 200, want_pdist=False)
+    assert np.all(np.isfinite(xb)) and np.all(np.isfinite(stress)) and np.all(stress > 0)
+    for v in range(len(graphs)):
+        assert np.abs(xb[off[v]:off[v + 1]].astype(np.float64).mean(0)).max() <= 1e-3
+    sizes = np.array([g.n for g in graphs])
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 200})
+    for v in pick:
+        g, n = graphs[v], graphs[v].n
+        _, Pd1, cert, st = ctx.dppr(G[v], np.arange(n, dtype=np.int32), ALPHA, 1e-6, P.FP32)
+        assert st == 0 and cert.max() <= 1e-6
+        Dref = O.dppr_rows(O.ppr_direct(O.transition_matrix(n, g.row_ptr, g.col), ALPHA),
+                           O.degrees(n, g.row_ptr, g.col), np.arange(n))
+        check_pdist(Pd1, Dref, cert, n)
+        X1, s1 = ctx.layout(Pd1, x0[off[v]:off[v + 1]].copy(), 200, P.FP32)
+        _same_layout(X1, xb[off[v]:off[v + 1]], s1, stress[v], 2e-3)
