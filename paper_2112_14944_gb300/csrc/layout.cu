@@ -349,8 +349,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // global memory, written by a host copy before the launch; the first use of
 // each map by a CTA is preceded by a tensor-map acquire fence (`fenced`
 // remembers the last map fenced).
+__device__ __forceinline__ void tile_copy(uint32_t dst, uint32_t b, const CUtensorMap *map, int I, int J,
+                                          uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(J * ST), "r"(I * ST), "r"(b), "l"(policy)
+      : "memory");
+}
+
 __device__ __forceinline__ void issue_tile(uint32_t dst, uint64_t *bar, const CUtensorMap *map, const float2 *V,
-                                           int I, int J, const CUtensorMap *&fenced) {
+                                           int I, int J, const CUtensorMap *&fenced, uint64_t policy) {
   if (map != fenced) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
                  : "memory");
@@ -358,11 +367,7 @@ __device__ __forceinline__ void issue_tile(uint32_t dst, uint64_t *bar, const CU
   }
   const uint32_t b = smem_u32(bar);
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(STAGE_BYTES) : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(J * ST), "r"(I * ST), "r"(b)
-      : "memory");
+  tile_copy(dst, b, map, I, J, policy);
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    dst + TILE_BYTES),
                "l"(V + (int64_t)I * ST), "r"(VEC_BYTES), "r"(b)
@@ -396,7 +401,7 @@ struct __align__(16) TileRec {
 // RunPart[(r CWARPS + w) 128 + c], c the column within block J.
 template <int MODE>
 __global__ void __launch_bounds__(spipe::THREADS, 1)
-k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *__restrict__ maps,
+k_sympass_pipe(int ntile, int npin /* per CTA */, const TileRec *__restrict__ tiles, const CUtensorMap *__restrict__ maps,
                const float2 *__restrict__ V, float2 *__restrict__ Part, float2 *__restrict__ RunPart,
                int *__restrict__ err) {
   using namespace spipe;
@@ -423,6 +428,12 @@ k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *
     // ---- producer
     if (lane == 0) {
       const CUtensorMap *fenced = nullptr;
+      // L2 policies: the first npin tiles of every CTA's chunk stay resident
+      // across passes (evict_last), so that each CTA reads the same share
+      // from L2; the rest stream through (evict_first)
+      uint64_t keep, stream;
+      asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
       // The matrix tiles do not depend on the previous launch: the first PS
       // are requested before waiting for it (expect_tx without the arrival,
       // so the stage cannot complete early); their vector slices, which the
@@ -438,11 +449,7 @@ k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *
         }
         const uint32_t b = smem_u32(&full[n]);
         asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(TILE_BYTES) : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-            "[%4];" ::"r"(sbase + (uint32_t)n * STAGE_BYTES),
-            "l"(reinterpret_cast<uint64_t>(map)), "r"(t.J * ST), "r"(t.I * ST), "r"(b)
-            : "memory");
+        tile_copy(sbase + (uint32_t)n * STAGE_BYTES, b, map, t.I, t.J, n < npin ? keep : stream);
       }
       asm volatile("griddepcontrol.wait;" ::: "memory");
       for (int n = 0; n < npre; ++n) {
@@ -471,7 +478,7 @@ k_sympass_pipe(int ntile, const TileRec *__restrict__ tiles, const CUtensorMap *
         }
         srec[s] = t;  // released to the consumers by the arrive below
         issue_tile(sbase + (uint32_t)s * STAGE_BYTES, &full[s], maps + 2 * t.v + MODE, V + (int64_t)t.vblk * ST, t.I,
-                   t.J, fenced);
+                   t.J, fenced, n < npin ? keep : stream);
         issued = n + 1;
       }
       if (!ok) {
@@ -932,14 +939,20 @@ cudaError_t launch_dependent(pprviz_ctx *ctx, void (*kernel)(P...), unsigned gri
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// L2 bytes of each pass matrix kept resident across updates (evict_last):
+// the two matrices together stay well inside the 126 MB L2 next to the
+// partial sums and coordinates; the rest of each matrix streams from HBM
+constexpr double kPinBytes = 40.0 * 1024 * 1024;
+
 int pass_pair(pprviz_ctx *ctx, unsigned grid, const PassTables &pt, const CUtensorMap *maps, const BatchView *views_d,
               float2 *X, float2 *Bv, float2 *Part, float2 *RunPart, int *perr) {
   const unsigned nb = (unsigned)pt.nblocks;
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<0>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, pt.recs, maps, (const float2 *)X, Part, RunPart, perr)); }
+  const int npin = (int)(kPinBytes / spipe::TILE_BYTES / grid);  // tiles per CTA
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<0>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, npin, pt.recs, maps, (const float2 *)X, Part, RunPart, perr)); }
   PPRVIZ_LAUNCHED(ctx);
   { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, nb, 1024, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, Bv)); }
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<1>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, pt.recs, maps, (const float2 *)Bv, Part, RunPart, perr)); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<1>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, npin, pt.recs, maps, (const float2 *)Bv, Part, RunPart, perr)); }
   PPRVIZ_LAUNCHED(ctx);
   { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, nb, 1024, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, X)); }
   PPRVIZ_LAUNCHED(ctx);
