@@ -15,6 +15,10 @@ DPPR, PDist, X out), copies inside the timed region.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm of this benchmark).
 
+`--workload views` measures the batched-views workload instead (not the
+default line): 256 SBM views of 50..5,000 nodes, one pprviz_views_batch call
+per step (DPPR + PDist + 200 layout updates of every view).
+
 `--workload dense` measures the dense-view propagation instead (not the
 default line): a dense clustered weighted view, n = 20,000, 20 blocks, 15 %
 density, lognormal(0, 1) weights, all nodes as the view; one step = all-pairs
@@ -74,8 +78,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", action="store_true",
                     help="one untimed pass of the hot path (for profiler command lines)")
-    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense"],
-                    help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000)")
+    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views"],
+                    help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000); "
+                         "views: the 256 batched SBM views")
     return ap.parse_args()
 
 
@@ -377,6 +382,84 @@ def run_dense(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- batched views
+VIEWS_WORKLOAD = "sbm_views_256_n50_5000"
+
+
+def run_views(args, rank, world, local_rank):
+    """The batched-views workload: 256 SBM views (n_v ~ U{50..5000}, 4..16
+    blocks, p_in 0.1, p_out 0.002, seed 0); one step = one pprviz_views_batch
+    call on device buffers: all-pairs DPPR + PDist of every view (certified to
+    eps) and 200 FP32 layout updates of every view."""
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    graphs = synth.sbm_views(256, seed=0)
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    G = [ctx.upload_graph(g) for g in graphs]
+    x0 = torch.from_numpy(np.concatenate([synth.uniform_x0(g.n, seed=1000 + i)
+                                          for i, g in enumerate(graphs)])).to(dev)
+    entries = float(sum(g.n * g.n for g in graphs))
+    iters = 200
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        _, _, _, _, cert = ctx.views_batch(G, x0, ALPHA, EPS, iters, want_pdist=True, want_cert=True)
+        assert np.all(cert <= EPS), cert.max()
+        return ctx.stats()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(PROF_EVERY)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, launches, stats = [], 0, None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        launches += stats["kernel_launches"]
+    torch.cuda.synchronize()
+    sampler.stop()
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    total = sum(ms)
+    if world > 1:
+        t = torch.tensor([total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    if rank != 0:
+        return
+    line = {
+        "metric": "DPPR entries/s, 256 batched SBM views (DPPR + PDist + 200 layout updates each)",
+        "value": world * args.steps * entries / (total / 1e3), "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": VIEWS_WORKLOAD, "views": 256, "n_range": [50, 5000], "blocks": [4, 16],
+                   "p_in": 0.1, "p_out": 0.002, "seed": 0, "sum_n": int(sum(g.n for g in graphs)),
+                   "sum_n2": int(entries), "alpha": ALPHA, "eps": EPS, "layout_iters": iters,
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "views_stats": {k: stats[k] for k in ("groups", "sweeps_main", "sweeps_refine", "residual_passes",
+                                              "max_cert", "source_group")} if stats else None,
+        "kernel_share": class_share(ktimes, args.steps), "gpu_launches": int(launches),
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -573,6 +656,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "dense":
         run_dense(args, rank, world, local_rank)
+    elif args.workload == "views":
+        run_views(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

@@ -235,19 +235,27 @@ int pprviz_energy(pprviz_ctx *ctx, const void *pdist, int32_t k, const void *x,
 /* P7 - many independent views in one call (Sec. 2.2: the multi-level
  * mechanism visits the children of many supernodes). View v is its own
  * undirected graph (uploaded with pprviz_graph_upload); every node of it is a
- * source (k_v = n_v, n_clamp = n_v). For each view: DPPR (FP32 path, eps),
- * PDist, then `iters` FP32 stress-majorization updates from its x0.
+ * source (k_v = n_v, n_clamp = n_v). For each view: DPPR (FP32 path, eps, the
+ * same certificate as pprviz_dppr), PDist, then `iters` FP32
+ * stress-majorization updates from its x0.
+ * The propagation runs the views, largest first, as the disjoint union of
+ * their graphs: consecutive views of similar size form a wave whose sources
+ * advance together in every sweep launch; the layouts of all views share one
+ * launch per pass.
+ * nviews:      1 .. 65,535; the views hold at most 2^31 - 1 nodes in all.
  * offsets:     nviews+1 int64 prefix sums of n_v (host).
  * x0_packed:   sum n_v * 2 floats (view v at offsets[v]*2).
  * pdist_packed: sum n_v^2 floats (view v at the prefix sum of n_u^2, u < v);
  *              may be NULL.
  * x_packed:    sum n_v * 2 floats, the final layouts.
  * stress_out:  nviews doubles (host), final stress per view; may be NULL.
+ * cert_out:    sum n_v doubles (host, packed like offsets): the DPPR
+ *              certificate of each view's source rows; may be NULL.
  * Errors: as pprviz_dppr and pprviz_layout. */
 int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views,
                        const int64_t *offsets, double alpha, double eps, int32_t iters,
                        const float *x0_packed, float *pdist_packed, float *x_packed,
-                       double *stress_out, uint32_t mem_flags);
+                       double *stress_out, double *cert_out, uint32_t mem_flags);
 
 /* Stress energy and gradients without allocating anything (no counterpart in
  * the paper; a library convenience). Same results as pprviz_energy with FP32

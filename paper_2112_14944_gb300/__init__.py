@@ -201,16 +201,31 @@ class Context:
         self._leave(dev, pdist, x, gx_out, gd_out)
         return float(e[0]), (gx_out if grad_x else None), (gd_out if grad_pdist else None)
 
-    def views_batch(self, graphs, x0_packed, alpha=0.15, eps=1e-6, iters=200, want_pdist=False):
-        """Batched views (numpy host buffers). Returns (x_packed, pdist_packed, stress, offsets)."""
+    def views_batch(self, graphs, x0_packed, alpha=0.15, eps=1e-6, iters=200, want_pdist=False, want_cert=False):
+        """Batched views. x0_packed is a numpy array (host buffers) or a torch
+        CUDA tensor (device buffers: the packed layouts and PDists come back as
+        CUDA tensors). Returns (x_packed, pdist_packed, stress, offsets), plus
+        the packed per-source certificates when want_cert is set."""
         sizes = np.array([g.n for g in graphs], dtype=np.int64)
         offsets = np.zeros(len(graphs) + 1, dtype=np.int64)
         np.cumsum(sizes, out=offsets[1:])
-        x_packed = np.empty_like(x0_packed)
-        pd = np.empty(int((sizes ** 2).sum()), dtype=np.float32) if want_pdist else None
+        nsq = int((sizes ** 2).sum())
+        dev = B._is_torch(x0_packed)
+        if dev:
+            import torch
+            x_packed = torch.empty_like(x0_packed)
+            pd = torch.empty(nsq, dtype=torch.float32, device=x0_packed.device) if want_pdist else None
+        else:
+            x_packed = np.empty_like(x0_packed)
+            pd = np.empty(nsq, dtype=np.float32) if want_pdist else None
         stress = np.zeros(len(graphs), dtype=np.float64)
+        cert = np.full(int(offsets[-1]), np.nan, dtype=np.float64) if want_cert else None
+        self._enter(dev)
         B.pprviz_views_batch(self.h, [g.h for g in graphs], offsets, alpha, eps, iters, x0_packed, pd, x_packed,
-                             stress, 0)
+                             stress, cert, B.PPRVIZ_DEVICE_PTRS if dev else 0)
+        self._leave(dev, x0_packed, pd, x_packed)
+        if want_cert:
+            return x_packed, pd, stress, offsets, cert
         return x_packed, pd, stress, offsets
 
 

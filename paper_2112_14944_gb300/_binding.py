@@ -56,7 +56,7 @@ _SIGS = {
     "pprviz_layout": (C.c_int, [_VP, _VP, C.c_int32, _VP, C.c_int32, C.c_int, _VP, _VP, C.c_uint32]),
     "pprviz_energy": (C.c_int, [_VP, _VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, C.c_uint32]),
     "pprviz_views_batch": (C.c_int, [_VP, C.c_int32, _VP, _VP, C.c_double, C.c_double, C.c_int32, _VP, _VP, _VP,
-                                     _VP, C.c_uint32]),
+                                     _VP, _VP, C.c_uint32]),
     "pprviz_energy_noalloc": (C.c_int, [_VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, _VP]),
 }
 
@@ -218,11 +218,12 @@ def pprviz_energy(ctx, pdist, k, x, grad_scale, e_out, grad_x, grad_pdist, mem_f
 
 
 def pprviz_views_batch(ctx, graphs, offsets, alpha, eps, iters, x0_packed, pdist_packed, x_packed, stress_out,
-                       mem_flags):
+                       cert_out, mem_flags):
     arr = (_VP * len(graphs))(*graphs)
     return _check(ctx, load().pprviz_views_batch(ctx, len(graphs), C.addressof(arr), _ptr(offsets)[0], float(alpha),
                                                  float(eps), int(iters), _ptr(x0_packed)[0], _ptr(pdist_packed)[0],
-                                                 _ptr(x_packed)[0], _ptr(stress_out)[0], mem_flags),
+                                                 _ptr(x_packed)[0], _ptr(stress_out)[0], _ptr(cert_out)[0],
+                                                 mem_flags),
                   allow=(PPRVIZ_E_NOT_CONVERGED,))
 
 

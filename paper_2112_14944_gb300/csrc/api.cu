@@ -462,7 +462,7 @@ int pprviz_energy(pprviz_ctx *ctx, const void *pdist, int32_t k, const void *x, 
 
 int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views, const int64_t *offsets,
                        double alpha, double eps, int32_t iters, const float *x0_packed, float *pdist_packed,
-                       float *x_packed, double *stress_out, uint32_t mem_flags) {
+                       float *x_packed, double *stress_out, double *cert_out, uint32_t mem_flags) {
   if (!ctx) return PPRVIZ_E_INVALID_ARG;
   PPRVIZ_TRY(begin(ctx));
   if (nviews < 1 || !views || !offsets || !x0_packed || !x_packed)
@@ -498,27 +498,18 @@ int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *cons
     PPRVIZ_TRY(ws_ensure(ctx, WS_BXOUT, sizeof(float) * 2 * (size_t)ntot));
     x_all = ctx->ws[WS_BXOUT].as<float>();
   }
-  // DPPR and PDist view by view (each view's propagation fills the GPU)
+  // DPPR and PDist of all views: waves of similar-size views share every launch
   PPRVIZ_TRY(ws_ensure(ctx, WS_VIEW, sizeof(int32_t) * (size_t)maxk));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, sizeof(float) * (size_t)maxk * maxk));
   int32_t *view_d = ctx->ws[WS_VIEW].as<int32_t>();
-  float *dppr_d = ctx->ws[WS_DPPR].as<float>();
   std::vector<int32_t> iota((size_t)maxk);
   for (int64_t q = 0; q < maxk; ++q) iota[q] = (int32_t)q;
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_d, iota.data(), sizeof(int32_t) * maxk, cudaMemcpyHostToDevice, ctx->stream));
-  int status = PPRVIZ_OK;
-  pprviz_stats acc{};
-  int64_t sq_off = 0;
-  for (int32_t v = 0; v < nviews; ++v) {
-    const int32_t k = (int32_t)ks[v];
-    std::vector<int32_t> view_h(iota.begin(), iota.begin() + k);
-    int s = dppr_solve(ctx, views[v], view_d, view_h, k, alpha, eps, PPRVIZ_FP32, dppr_d, false, nullptr);
-    if (s == PPRVIZ_E_NOT_CONVERGED) status = s;
-    else if (s != PPRVIZ_OK) return finish(ctx, s);
-    PPRVIZ_TRY(pdist_launch(ctx, dppr_d, k, k, pdist_all + sq_off, false));
-    sq_off += (int64_t)k * k;
-  }
-  acc = ctx->stats;
+  std::vector<int64_t> sq_off((size_t)nviews + 1, 0);
+  for (int32_t v = 0; v < nviews; ++v) sq_off[v + 1] = sq_off[v] + ks[v] * ks[v];
+  int status = dppr_views_solve(ctx, nviews, views, offsets, sq_off.data(), alpha, eps, view_d, pdist_all, cert_out);
+  if (status != PPRVIZ_OK && status != PPRVIZ_E_NOT_CONVERGED) return finish(ctx, status);
+  const std::string dppr_err = ctx->err;
+  pprviz_stats acc = ctx->stats;
   // all layouts together: one launch per pass over every view's tiles
   int s = layout_batch_run(ctx, nviews, ks.data(), pdist_all, x0_all, iters, x_all, stress_out);
   if (s != PPRVIZ_OK) return finish(ctx, s);
@@ -537,7 +528,7 @@ int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *cons
                                        cudaMemcpyDeviceToHost, ctx->stream));
   }
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (status != PPRVIZ_OK) ctx->err = "a view's certificate stayed above eps after the refinement cap";
+  if (status != PPRVIZ_OK) ctx->err = dppr_err;
   return finish(ctx, status);
 }
 

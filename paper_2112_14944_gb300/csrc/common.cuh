@@ -45,6 +45,9 @@ enum Slot {
   WS_SPEC, WS_RPART, WS_CSRC, WS_KAPPA,
   // tensor maps of the layout pass matrices, row-block table of the reduce
   WS_TMAP, WS_TROWS, WS_TREC, WS_RUNP,
+  // batched propagation: the union graph of the views and its tables
+  WS_URP, WS_UCOL, WS_UW, WS_UDEG, WS_UINVD, WS_UINVF, WS_UDWFF, WS_ULIDX, WS_UNV, WS_UCOMP, WS_UKAP,
+  WS_UDESC, WS_UBROWS, WS_UBPTR,
   WS_COUNT
 };
 
@@ -141,6 +144,14 @@ int view_check(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d, in
 int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
                const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps,
                int precision, void *dppr_d, bool out64, double *cert_h);
+
+// All-pairs DPPR and PDist of many views (each view: every node a source,
+// n_clamp = its size) in shared launches. node_off: nviews + 1 prefix sums
+// of the sizes (cert_h order); sq_off: prefix sums of the squared sizes
+// (pdist_all order, device FP32); iota_d: 0 .. max n - 1 on the device.
+int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views, const int64_t *node_off,
+                     const int64_t *sq_off, double alpha, double eps, const int32_t *iota_d, float *pdist_all,
+                     double *cert_h);
 
 // ---- graph analysis for the deflated sweeps (spectral.cu) ------------------
 // Fills g->comp / h_comp / h_mc / spec_b / spec_deflate once per graph.

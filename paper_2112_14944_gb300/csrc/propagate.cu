@@ -139,23 +139,30 @@ __global__ void k_renorm(int64_t count, float *__restrict__ hi, float *__restric
 //   else: y_out = xnew                         (power iteration)
 // b_jq = alpha [j == src[q]] unless RHS, then b_jq = rhs[j][q].
 // One warp per (row j, 32*VEC-source chunk); lanes own VEC consecutive sources.
-template <typename T, bool WEIGHTED, bool CHEB, bool RHS>
+// Batched views (BATCH): the graph is the disjoint union of the views and the
+// state covers its rows [row0, row0 + n); column q is, for every row, the
+// source g0 + q of that row's own view, and src holds each node's index within
+// its view, so b_jq = alpha [src[row0 + j] == g0 + q]. Neighbours stay inside
+// their view, hence inside the state's row range.
+template <typename T, bool WEIGHTED, bool CHEB, bool RHS, bool BATCH>
 __global__ void __launch_bounds__(kWarps * 32)
 k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
         const int32_t *__restrict__ col, const float *__restrict__ w, const T *__restrict__ invdw,
         const int32_t *__restrict__ src, const float *__restrict__ rhs, const T *__restrict__ ycur,
-        const T *yold, T *yout, T alpha, T c, T om, T om1) {
+        const T *yold, T *yout, T alpha, T c, T om, T om1, int64_t row0, int32_t g0) {
   constexpr int VEC = Vec<T>::N;
   const int lane = threadIdx.x & 31;
   const int64_t item = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (item >= n * nchunks) return;
   const int64_t chunk = item / n;
-  const int64_t j = item - chunk * n;
+  const int64_t j = item - chunk * n;  // row within the state
+  const int64_t jg = j + row0;         // row of the graph
   const int64_t off = chunk * (32 * VEC) + lane * VEC;
+  const int64_t rb = BATCH ? row0 : 0;  // state row of graph node i: i - rb
   T acc[VEC];
 #pragma unroll
   for (int u = 0; u < VEC; ++u) acc[u] = T(0);
-  const int64_t b = rp[j], e = rp[j + 1];
+  const int64_t b = rp[jg], e = rp[jg + 1];
   for (int64_t base = b; base < e; base += 32) {
     const int cnt = (int)min((int64_t)32, e - base);
     int32_t myc = lane < cnt ? col[base + lane] : 0;
@@ -169,7 +176,7 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
       for (int q = 0; q < 8; ++q) {
         const int32_t iq = __shfl_sync(0xffffffffu, myc, t + q);
         if (WEIGHTED) wv[q] = __shfl_sync(0xffffffffu, myw, t + q);
-        Vec<T>::load(ycur + (int64_t)iq * ld + off, v[q]);
+        Vec<T>::load(ycur + ((int64_t)iq - rb) * ld + off, v[q]);
       }
 #pragma unroll
       for (int u = 0; u < VEC; ++u) {
@@ -189,10 +196,10 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
       const int32_t i1 = __shfl_sync(0xffffffffu, myc, t + 1);
       const int32_t i2 = __shfl_sync(0xffffffffu, myc, t + 2);
       const int32_t i3 = __shfl_sync(0xffffffffu, myc, t + 3);
-      Vec<T>::load(ycur + (int64_t)i0 * ld + off, v0);
-      Vec<T>::load(ycur + (int64_t)i1 * ld + off, v1);
-      Vec<T>::load(ycur + (int64_t)i2 * ld + off, v2);
-      Vec<T>::load(ycur + (int64_t)i3 * ld + off, v3);
+      Vec<T>::load(ycur + ((int64_t)i0 - rb) * ld + off, v0);
+      Vec<T>::load(ycur + ((int64_t)i1 - rb) * ld + off, v1);
+      Vec<T>::load(ycur + ((int64_t)i2 - rb) * ld + off, v2);
+      Vec<T>::load(ycur + ((int64_t)i3 - rb) * ld + off, v3);
       if (WEIGHTED) {
         const T w0 = (T)__shfl_sync(0xffffffffu, myw, t);
         const T w1 = (T)__shfl_sync(0xffffffffu, myw, t + 1);
@@ -208,7 +215,7 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
     for (; t < cnt; ++t) {
       T v0[VEC];
       const int32_t i0 = __shfl_sync(0xffffffffu, myc, t);
-      Vec<T>::load(ycur + (int64_t)i0 * ld + off, v0);
+      Vec<T>::load(ycur + ((int64_t)i0 - rb) * ld + off, v0);
       const T w0 = WEIGHTED ? (T)__shfl_sync(0xffffffffu, myw, t) : T(1);
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[u] += w0 * v0[u];
@@ -221,14 +228,18 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
 #pragma unroll
     for (int u = 0; u < VEC; ++u) acc[u] += v0[u];
   }
-  const T invd = invdw[j];
+  const T invd = invdw[jg];
   T bq[VEC];
   if (RHS) {
 #pragma unroll
     for (int u = 0; u < VEC; ++u) bq[u] = (T)rhs[rowoff + u];
+  } else if (BATCH) {
+    const int32_t lj = src[jg] - g0 - (int32_t)off;
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) bq[u] = (lj == u) ? alpha : T(0);
   } else {
 #pragma unroll
-    for (int u = 0; u < VEC; ++u) bq[u] = (src[off + u] == (int32_t)j) ? alpha : T(0);
+    for (int u = 0; u < VEC; ++u) bq[u] = (src[off + u] == (int32_t)jg) ? alpha : T(0);
   }
   T out[VEC];
 #pragma unroll
@@ -274,12 +285,16 @@ __device__ __forceinline__ void load4(const double *hi, const float *lo, double 
 // gathered stay resident in L2 even when the whole group does not fit; each
 // warp walks rows with a stride so its per-source partial sums are reduced
 // once per block.
-template <typename T, bool WEIGHTED, bool EXACT>
+// Batched views (BATCH, see k_sweep): block b covers the state rows
+// brows[b] = [x, y), all of one view, so its partial sums belong to that view;
+// graph node i is state row i - row0 and the source test is src[i] == g0 + q.
+template <typename T, bool WEIGHTED, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(kWarps * 32)
 k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
            const float *__restrict__ w, const double *__restrict__ invdw, const float2 *__restrict__ dwff,
            const int32_t *__restrict__ src, const T *__restrict__ yhi, const float *__restrict__ ylo,
-           float *__restrict__ rhs_out, double *__restrict__ part_out, double alpha, double c) {
+           float *__restrict__ rhs_out, double *__restrict__ part_out, double alpha, double c,
+           const int2 *__restrict__ brows, int64_t row0, int32_t g0) {
   constexpr int VEC = 4;  // 128 sources per warp chunk for both state types
   __shared__ double red[kWarps][32 * VEC];
   __shared__ double reds[kWarps][32 * VEC];
@@ -289,7 +304,8 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
   const int64_t off = chunk * (32 * VEC) + lane * VEC;
   int32_t sq[VEC];
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) sq[u] = src[off + u];
+  for (int u = 0; u < VEC; ++u) sq[u] = BATCH ? 0 : src[off + u];
+  const int64_t rb = BATCH ? row0 : 0;  // state row of graph node i: i - rb
   // alpha and c as float-float pairs (float-float residual of the FP32 path)
   const float alh = (float)alpha, all = (float)(alpha - (double)alh);
   const float ch = (float)c, cl = (float)(c - (double)ch);
@@ -300,12 +316,28 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
     part[u] = psig[u] = 0.0;
     fpart[u] = fpsig[u] = 0.0f;
   }
-  const int64_t stride = (int64_t)gridDim.x * kWarps;
-  for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < n; j += stride) {
+  int64_t jfirst, jend, stride;
+  if (BATCH) {
+    const int2 br = brows[blockIdx.x];
+    jfirst = br.x + warp;
+    jend = br.y;
+    stride = kWarps;
+  } else {
+    jfirst = (int64_t)blockIdx.x * kWarps + warp;
+    jend = n;
+    stride = (int64_t)gridDim.x * kWarps;
+  }
+  for (int64_t j = jfirst; j < jend; j += stride) {
+    const int64_t jg = j + row0;  // row of the graph
+    if (BATCH) {
+      const int32_t lj = src[jg] - g0 - (int32_t)off;
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) sq[u] = (lj == u) ? (int32_t)jg : -1;
+    }
     double acc[VEC];
 #pragma unroll
     for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
-    const int64_t b = rp[j], e = rp[j + 1];
+    const int64_t b = rp[jg], e = rp[jg + 1];
     if constexpr (std::is_same<T, float>::value && !EXACT) {
       // Error-free FP32 accumulation of sum_i w_ij (y_hi + y_lo)_i: TwoSum
       // (Knuth) keeps the exact rounding error of every addition of the high
@@ -331,7 +363,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
             const int32_t i = __shfl_sync(0xffffffffu, myc, (t0 + q) & 31);
             wv[q] = WEIGHTED ? __shfl_sync(0xffffffffu, myw, (t0 + q) & 31) : 1.0f;
             if (t0 + q < cnt) {
-              const int64_t p = (int64_t)i * ld + off;
+              const int64_t p = ((int64_t)i - rb) * ld + off;
               Vec<float>::load(reinterpret_cast<const float *>(yhi) + p, h[q]);
               if (ylo) Vec<float>::load(ylo + p, l[q]);
             }
@@ -365,7 +397,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
         }
       }
       const int64_t rowoff = j * ld + off;
-      const float2 dwp = dwff[j];
+      const float2 dwp = dwff[jg];
       const float dwh = dwp.x, dwl = dwp.y;
       float hrow[VEC], lrow[VEC];
       Vec<float>::load(reinterpret_cast<const float *>(yhi) + rowoff, hrow);
@@ -390,7 +422,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
         const float s1 = p2 - p1;
         const float b1 = s1 - p2;
         const float e1 = (p2 - (s1 - b1)) + (-p1 - b1);
-        const bool src_here = sq[u] == (int32_t)j;
+        const bool src_here = sq[u] == (int32_t)jg;
         const float bh = src_here ? alh : 0.0f, bl = src_here ? all : 0.0f;
         const float s2 = s1 + bh;
         const float b2 = s2 - s1;
@@ -415,7 +447,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
             const int32_t i = __shfl_sync(0xffffffffu, myc, (t0 + q) & 31);
             wv[q] = WEIGHTED ? (double)__shfl_sync(0xffffffffu, myw, (t0 + q) & 31) : 1.0;
             if (t0 + q < cnt) {
-              const int64_t p = (int64_t)i * ld + off;
+              const int64_t p = ((int64_t)i - rb) * ld + off;
               load4(yhi + p, ylo ? ylo + p : nullptr, v[q]);
             }
           }
@@ -429,14 +461,14 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
       }
     }
     const int64_t rowoff = j * ld + off;
-    const double dw = 1.0 / invdw[j];
+    const double dw = 1.0 / invdw[jg];
     double yrow[VEC];
     load4(yhi + rowoff, ylo ? ylo + rowoff : nullptr, yrow);
 #pragma unroll
     for (int u = 0; u < VEC; ++u) {
       const double y = yrow[u];
       if (e == b) acc[u] += y;
-      const double bq = (sq[u] == (int32_t)j) ? alpha : 0.0;
+      const double bq = (sq[u] == (int32_t)jg) ? alpha : 0.0;
       const double r = bq - dw * y + c * acc[u];
       if (rhs_out) rhs_out[rowoff + u] = (float)r;
       part[u] += fabs(r);
@@ -482,6 +514,56 @@ __global__ void k_res_reduce(int64_t ld, int nblocks, const double *__restrict__
     l1[q] = s;
     sig[q] = ss;
   }
+}
+
+// Batched views: out[w][0][q] = sum over the blocks b of view w (bptr[w] <=
+// b < bptr[w + 1]) of part[b][0][q], out[w][1][q] likewise, in the fixed
+// order of k_res_reduce. One warp per (view, source).
+__global__ void k_res_reduce_batch(int64_t ld, int nviews, const int *__restrict__ bptr,
+                                   const double *__restrict__ part, double *__restrict__ out) {
+  const int64_t wq = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wq >= (int64_t)nviews * ld) return;
+  const int64_t v = wq / ld, q = wq - v * ld;
+  double s = 0.0, ss = 0.0;
+  for (int b = bptr[v] + lane; b < bptr[v + 1]; b += 32) {
+    s += part[((int64_t)b * 2 + 0) * ld + q];
+    ss += part[((int64_t)b * 2 + 1) * ld + q];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if (lane == 0) {
+    out[(v * 2 + 0) * ld + q] = s;
+    out[(v * 2 + 1) * ld + q] = ss;
+  }
+}
+
+// Batched views: the deflated start of k_init_defl for a wave. The source of
+// column q for state row j (graph node jg = row0 + j) is node
+// s = jg - lidx[jg] + g0 + q of the same view when g0 + q < nv[jg] (nv: the
+// size of the node's view); kap[s] is that source's stationary coefficient
+// (NULL: no deflation, y_0 = 0).
+__global__ void k_init_defl_batch(int64_t nrows, int64_t ld, int64_t row0, int32_t g0, const int32_t *__restrict__ lidx,
+                                  const int32_t *__restrict__ nv, const int32_t *__restrict__ comp,
+                                  const double *__restrict__ kap, const float *__restrict__ rhs,
+                                  const float *__restrict__ invdw, float alpha, float c, float *__restrict__ y0,
+                                  float *__restrict__ y1) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nrows * ld) return;
+  const int64_t j = idx / ld, q = idx - j * ld;
+  const int64_t jg = row0 + j;
+  const int32_t lj = lidx[jg];
+  const int64_t colq = (int64_t)g0 + q;
+  float v0 = 0.0f;
+  if (kap && colq < nv[jg]) {
+    const int64_t s = jg - lj + colq;
+    if (comp[jg] == comp[s]) v0 = (float)kap[s];
+  }
+  const float b = rhs ? rhs[idx] : ((colq == lj) ? alpha : 0.0f);
+  y0[idx] = v0;
+  y1[idx] = c * v0 + b * invdw[jg];
 }
 
 // out[(g0 + q) * k + r] = d(view[g0+q]) * dw(view[r]) * (y_hi + y_lo)[view[r]][q]
@@ -538,29 +620,56 @@ int64_t choose_group(int64_t n, int32_t k, size_t elem) {
   return g;
 }
 
+// A wave of batched views (see k_sweep): the state covers the union-graph
+// rows [row0, row0 + nrows), column q is source g0 + q of every row's view;
+// lidx[i] is node i's index within its view. The residual's blocks each cover
+// the state rows brows[b] of one view; the blocks of the wave's view w are
+// [bptr[w], bptr[w + 1]).
+struct Wave {
+  const int32_t *lidx = nullptr;
+  int64_t row0 = 0, nrows = 0;
+  int32_t g0 = 0;
+  const int2 *brows = nullptr;
+  const int *bptr = nullptr;
+  const int32_t *nv = nullptr;  // size of each node's view
+  int nblocks = 0, nviews = 0;
+};
+
 template <typename T>
 int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, bool rhs,
                  const int32_t *src, const float *rhsbuf, const T *ycur, const T *yold, T *yout,
-                 double alpha, double om) {
+                 double alpha, double om, const Wave *wv = nullptr) {
   constexpr int VEC = Vec<T>::N;
   const int nchunks = (int)(ld / (32 * VEC));
-  const int64_t items = g->n * nchunks;
+  const int64_t nrows = wv ? wv->nrows : g->n;
+  const int64_t items = nrows * nchunks;
   const unsigned blocks = (unsigned)((items + kWarps - 1) / kWarps);
   const T *invdw = std::is_same<T, float>::value ? (const T *)g->invdw_f.p : (const T *)g->invdw_d.p;
   const T a = (T)alpha, c = (T)(1.0 - alpha), o = (T)om, o1 = (T)(1.0 - om);
   const float *w = g->weighted ? g->w.as<float>() : nullptr;
   const int64_t *rp = g->rp.as<int64_t>();
   const int32_t *col = g->col.as<int32_t>();
+  const int64_t row0 = wv ? wv->row0 : 0;
+  const int32_t g0 = wv ? wv->g0 : 0;
+  if (wv) src = wv->lidx;
   PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
-#define PPRVIZ_SWEEP(W, C, R)                                                                   \
-  k_sweep<T, W, C, R><<<blocks, kWarps * 32, 0, ctx->stream>>>(g->n, ld, nchunks, rp, col, w, invdw, \
-                                                               src, rhsbuf, ycur, yold, yout, a, c, o, o1)
-  if (g->weighted) {
-    if (cheb) { if (rhs) PPRVIZ_SWEEP(true, true, true); else PPRVIZ_SWEEP(true, true, false); }
-    else { if (rhs) PPRVIZ_SWEEP(true, false, true); else PPRVIZ_SWEEP(true, false, false); }
+#define PPRVIZ_SWEEP(W, C, R, B)                                                                   \
+  k_sweep<T, W, C, R, B><<<blocks, kWarps * 32, 0, ctx->stream>>>(nrows, ld, nchunks, rp, col, w, invdw, \
+                                                                  src, rhsbuf, ycur, yold, yout, a, c, o, o1, row0, g0)
+  if (wv) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (!cheb) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "batched sweeps are Chebyshev sweeps");
+      if (g->weighted) { if (rhs) PPRVIZ_SWEEP(true, true, true, true); else PPRVIZ_SWEEP(true, true, false, true); }
+      else { if (rhs) PPRVIZ_SWEEP(false, true, true, true); else PPRVIZ_SWEEP(false, true, false, true); }
+    } else {
+      return set_err(ctx, PPRVIZ_E_INVALID_ARG, "batched sweeps are FP32");
+    }
+  } else if (g->weighted) {
+    if (cheb) { if (rhs) PPRVIZ_SWEEP(true, true, true, false); else PPRVIZ_SWEEP(true, true, false, false); }
+    else { if (rhs) PPRVIZ_SWEEP(true, false, true, false); else PPRVIZ_SWEEP(true, false, false, false); }
   } else {
-    if (cheb) { if (rhs) PPRVIZ_SWEEP(false, true, true); else PPRVIZ_SWEEP(false, true, false); }
-    else { if (rhs) PPRVIZ_SWEEP(false, false, true); else PPRVIZ_SWEEP(false, false, false); }
+    if (cheb) { if (rhs) PPRVIZ_SWEEP(false, true, true, false); else PPRVIZ_SWEEP(false, true, false, false); }
+    else { if (rhs) PPRVIZ_SWEEP(false, false, true, false); else PPRVIZ_SWEEP(false, false, false, false); }
   }
 #undef PPRVIZ_SWEEP
   PPRVIZ_LAUNCHED(ctx);
@@ -570,29 +679,50 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
 // EXACT selects FP64 accumulation of the neighbour sums; otherwise the FP32
 // path uses the error-free compensated sums (certificate floor ~1e-9 at the
 // largest degrees, so tighter eps needs EXACT).
+// l1 receives, per view of the group (one view unless batched), 2 * ld
+// doubles: sum |res| per source, then sum res per source.
 template <typename T, bool EXACT>
 int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
-                    const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha) {
-  // l1 holds 2 * ld doubles: sum |res| per source, then sum res per source
+                    const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha,
+                    const Wave *wv = nullptr) {
   const int nchunks = (int)(ld / 128);
-  // ~1,216 CTAs in all when the group's state fits in L2; otherwise ~608 per
-  // chunk (about the resident CTAs of the GPU), so that the chunks run one
-  // after another and only ~one chunk's columns are gathered at a time
-  const bool fits_l2 = (double)g->n * (double)ld * 8.0 <= 64.0 * 1024 * 1024;
-  int rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps, fits_l2 ? std::max(1, 1216 / nchunks) : 608);
+  int rows_blocks;
+  if (wv) {
+    rows_blocks = wv->nblocks;
+  } else {
+    // ~1,216 CTAs in all when the group's state fits in L2; otherwise ~608 per
+    // chunk (about the resident CTAs of the GPU), so that the chunks run one
+    // after another and only ~one chunk's columns are gathered at a time
+    const bool fits_l2 = (double)g->n * (double)ld * 8.0 <= 64.0 * 1024 * 1024;
+    rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps, fits_l2 ? std::max(1, 1216 / nchunks) : 608);
+  }
   dim3 grid(rows_blocks, nchunks);
   PPRVIZ_TRY(ws_ensure(ctx, WS_RPART, sizeof(double) * 2 * (size_t)rows_blocks * (size_t)ld));
   double *part = ctx->ws[WS_RPART].as<double>();
-  if (g->weighted)
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, true, EXACT><<<grid, kWarps * 32, 0, ctx->stream>>>(
-        g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), g->w.as<float>(), g->invdw_d.as<double>(),
-        g->dwff.as<float2>(), src, yhi, ylo, rhs_out, part, alpha, 1.0 - alpha); }
-  else
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_residual<T, false, EXACT><<<grid, kWarps * 32, 0, ctx->stream>>>(
-        g->n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), nullptr, g->invdw_d.as<double>(),
-        g->dwff.as<float2>(), src, yhi, ylo, rhs_out, part, alpha, 1.0 - alpha); }
+  const float *w = g->weighted ? g->w.as<float>() : nullptr;
+  const int64_t n = wv ? wv->nrows : g->n;
+  const int2 *brows = wv ? wv->brows : nullptr;
+  const int64_t row0 = wv ? wv->row0 : 0;
+  const int32_t g0 = wv ? wv->g0 : 0;
+  if (wv) src = wv->lidx;
+#define PPRVIZ_RES(W, B)                                                                                  \
+  k_residual<T, W, EXACT, B><<<grid, kWarps * 32, 0, ctx->stream>>>(                                        \
+      n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), w, g->invdw_d.as<double>(), g->dwff.as<float2>(), src, \
+      yhi, ylo, rhs_out, part, alpha, 1.0 - alpha, brows, row0, g0)
+  {
+    PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL);
+    if (wv) { if (g->weighted) PPRVIZ_RES(true, true); else PPRVIZ_RES(false, true); }
+    else { if (g->weighted) PPRVIZ_RES(true, false); else PPRVIZ_RES(false, false); }
+  }
+#undef PPRVIZ_RES
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_res_reduce<<<(unsigned)((ld * 32 + 255) / 256), 256, 0, ctx->stream>>>(ld, rows_blocks, part, l1, l1 + ld); }
+  if (wv) {
+    const int64_t warps = (int64_t)wv->nviews * ld;
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_res_reduce_batch<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, ctx->stream>>>(
+        ld, wv->nviews, wv->bptr, part, l1); }
+  } else {
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL); k_res_reduce<<<(unsigned)((ld * 32 + 255) / 256), 256, 0, ctx->stream>>>(ld, rows_blocks, part, l1, l1 + ld); }
+  }
   PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
 }
@@ -629,10 +759,17 @@ double chebyshev_rate(double c) { return (1.0 - sqrt(1.0 - c * c)) / c; }
 int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     int32_t gcount, const float *rhs, float *ya, float *yb, int sweeps,
                     double alpha, int *tcerr, const int32_t *csrc, const double *kappa, double delta,
-                    float **result) {
+                    float **result, const Wave *wv = nullptr) {
   const size_t bytes = sizeof(float) * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
-  if (csrc) {
+  if (wv) {
+    // kappa: the sources' stationary coefficients by graph node, or NULL
+    const int64_t cnt = wv->nrows * ld;
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_defl_batch<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(
+        wv->nrows, ld, wv->row0, wv->g0, wv->lidx, wv->nv, g->comp.as<int32_t>(), kappa, rhs, g->invdw_f.as<float>(),
+        (float)alpha, (float)c, ya, yb); }
+    PPRVIZ_LAUNCHED(ctx);
+  } else if (csrc) {
     const int64_t cnt = g->n * ld;
     { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_defl<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(
         g->n, ld, g->comp.as<int32_t>(), csrc, kappa, src, rhs, g->invdw_f.as<float>(), (float)alpha, (float)c, ya, yb); }
@@ -659,7 +796,7 @@ int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
     if (tcerr)
       PPRVIZ_TRY(dense_sweep(ctx, g, ld, src, rhs, cur, old, alpha, om, tcerr));
     else
-      PPRVIZ_TRY(launch_sweep<float>(ctx, g, ld, true, rhs != nullptr, src, rhs, cur, old, old, alpha, om));
+      PPRVIZ_TRY(launch_sweep<float>(ctx, g, ld, true, rhs != nullptr, src, rhs, cur, old, old, alpha, om, wv));
     std::swap(cur, old);
   }
   *result = cur;
@@ -880,6 +1017,345 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   }
   if (not_converged)
     return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "certificate above eps after the refinement cap");
+  return PPRVIZ_OK;
+}
+
+
+// --------------------------------------------------------------------------
+// Batched views (P7): many views of uneven size in shared launches.
+//
+// The views are laid out, largest first, as the disjoint union of their
+// graphs (node ids offset, CSR concatenated; lidx = index within the view,
+// nv = the view's size). Consecutive views of similar size form a wave, a
+// contiguous row range of the union; column q of a wave's state is source q
+// of every view in it at once (k_sweep, BATCH), so one sweep launch advances
+// all sources of all views of the wave. Per-view results (certificates, DPPR
+// rows, PDist) are separated again by row range.
+// --------------------------------------------------------------------------
+namespace {
+
+struct UnionDesc {
+  const int64_t *rp;
+  const int32_t *col;
+  const float *w;
+  const double *deg, *invd;
+  const float *invf;
+  const float2 *dwff;
+  int64_t n, off, nnzoff;
+};
+
+__global__ void k_union_build(const UnionDesc *__restrict__ d, int64_t *__restrict__ rp, int32_t *__restrict__ col,
+                              float *__restrict__ w, double *__restrict__ deg, float *__restrict__ invf,
+                              double *__restrict__ invd, float2 *__restrict__ dwff, int32_t *__restrict__ lidx,
+                              int32_t *__restrict__ nv) {
+  const UnionDesc v = d[blockIdx.y];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.n) return;
+  const int64_t gi = v.off + i;
+  const int64_t b = v.rp[i], e = v.rp[i + 1];
+  rp[gi] = b + v.nnzoff;
+  if (i == v.n - 1) rp[gi + 1] = e + v.nnzoff;  // equals the next view's first entry
+  for (int64_t k = b; k < e; ++k) {
+    col[v.nnzoff + k] = v.col[k] + (int32_t)v.off;
+    if (w) w[v.nnzoff + k] = v.w ? v.w[k] : 1.0f;
+  }
+  deg[gi] = v.deg[i];
+  invf[gi] = v.invf[i];
+  invd[gi] = v.invd[i];
+  dwff[gi] = v.dwff[i];
+  lidx[gi] = (int32_t)i;
+  nv[gi] = (int32_t)v.n;
+}
+
+// a workspace slot seen as a graph buffer (released with the context)
+pprviz::DevBuf slot_view(pprviz_ctx *ctx, int slot) { return ctx->ws[slot]; }
+
+}  // namespace
+
+int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views, const int64_t *node_off,
+                     const int64_t *sq_off, double alpha, double eps, const int32_t *iota_d, float *pdist_all,
+                     double *cert_h) {
+  const double c = 1.0 - alpha;
+  // processing order: largest view first (stable)
+  std::vector<int32_t> order((size_t)nviews);
+  for (int32_t v = 0; v < nviews; ++v) order[v] = v;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return views[a]->n > views[b]->n; });
+  std::vector<int64_t> uoff((size_t)nviews), unnz((size_t)nviews);
+  int64_t N = 0, NNZ = 0, maxn = 0;
+  bool weighted = false;
+  for (int32_t i = 0; i < nviews; ++i) {
+    const pprviz_graph *g = views[order[i]];
+    uoff[order[i]] = N;
+    unnz[order[i]] = NNZ;
+    N += g->n;
+    NNZ += g->nnz;
+    maxn = std::max(maxn, g->n);
+    weighted = weighted || g->weighted;
+  }
+  if (N > INT32_MAX) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "the views hold more than 2^31 - 1 nodes in all");
+  if (nviews > 65535) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "at most 65,535 views per batch");
+  // ---- the union graph, in workspace slots
+  PPRVIZ_TRY(ws_ensure(ctx, WS_URP, sizeof(int64_t) * (size_t)(N + 1)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UCOL, sizeof(int32_t) * (size_t)std::max<int64_t>(NNZ, 1)));
+  if (weighted) PPRVIZ_TRY(ws_ensure(ctx, WS_UW, sizeof(float) * (size_t)std::max<int64_t>(NNZ, 1)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UDEG, sizeof(double) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UINVD, sizeof(double) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UINVF, sizeof(float) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UDWFF, sizeof(float2) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_ULIDX, sizeof(int32_t) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UNV, sizeof(int32_t) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UCOMP, sizeof(int32_t) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UKAP, 2 * sizeof(double) * (size_t)N));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UDESC, sizeof(UnionDesc) * (size_t)nviews));
+  std::vector<UnionDesc> desc((size_t)nviews);
+  for (int32_t v = 0; v < nviews; ++v) {
+    const pprviz_graph *g = views[v];
+    desc[v] = UnionDesc{g->rp.as<int64_t>(), g->col.as<int32_t>(), g->weighted ? g->w.as<float>() : nullptr,
+                        g->deg.as<double>(), g->invdw_d.as<double>(), g->invdw_f.as<float>(), g->dwff.as<float2>(),
+                        g->n, uoff[v], unnz[v]};
+  }
+  UnionDesc *desc_d = ctx->ws[WS_UDESC].as<UnionDesc>();
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(desc_d, desc.data(), sizeof(UnionDesc) * (size_t)nviews, cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  {
+    dim3 grid((unsigned)((maxn + 255) / 256), (unsigned)nviews);
+    PPRVIZ_PROF(ctx, PPRVIZ_K_GRAPH);
+    k_union_build<<<grid, 256, 0, ctx->stream>>>(desc_d, ctx->ws[WS_URP].as<int64_t>(), ctx->ws[WS_UCOL].as<int32_t>(),
+                                                 weighted ? ctx->ws[WS_UW].as<float>() : nullptr,
+                                                 ctx->ws[WS_UDEG].as<double>(), ctx->ws[WS_UINVF].as<float>(),
+                                                 ctx->ws[WS_UINVD].as<double>(), ctx->ws[WS_UDWFF].as<float2>(),
+                                                 ctx->ws[WS_ULIDX].as<int32_t>(), ctx->ws[WS_UNV].as<int32_t>());
+  }
+  PPRVIZ_LAUNCHED(ctx);
+  pprviz_graph U;
+  U.ctx = ctx;
+  U.n = N;
+  U.nnz = NNZ;
+  U.weighted = weighted;
+  U.rp = slot_view(ctx, WS_URP);
+  U.col = slot_view(ctx, WS_UCOL);
+  if (weighted) U.w = slot_view(ctx, WS_UW);
+  U.deg = slot_view(ctx, WS_UDEG);
+  U.invdw_d = slot_view(ctx, WS_UINVD);
+  U.invdw_f = slot_view(ctx, WS_UINVF);
+  U.dwff = slot_view(ctx, WS_UDWFF);
+  U.comp = slot_view(ctx, WS_UCOMP);  // large enough: graph_spectral allocates nothing for it
+  U.h_deg.resize((size_t)N);
+  for (int32_t v = 0; v < nviews; ++v)
+    std::copy(views[v]->h_deg.begin(), views[v]->h_deg.end(), U.h_deg.begin() + uoff[v]);
+  const int32_t *lidx = ctx->ws[WS_ULIDX].as<int32_t>();
+  const int32_t *nvr = ctx->ws[WS_UNV].as<int32_t>();
+  // components and the spectral bound (the largest over the views)
+  PPRVIZ_TRY(graph_spectral(ctx, &U));
+  const bool defl = U.spec_deflate;
+  const double bsp = defl ? U.spec_b : 1.0;
+  double *kap_main = ctx->ws[WS_UKAP].as<double>(), *kap_corr = kap_main + N;
+  std::vector<double> kap_h((size_t)N, 0.0);
+  if (defl) {
+    for (int64_t sidx = 0; sidx < N; ++sidx) kap_h[sidx] = 1.0 / U.h_mc[(size_t)U.h_comp[sidx]];
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(kap_main, kap_h.data(), sizeof(double) * (size_t)N, cudaMemcpyHostToDevice,
+                                     ctx->stream));
+  }
+
+  // ---- waves: consecutive views (largest first) whose state of full width
+  // keeps ~3 live buffers within ~64 MB of L2; a view too large for that
+  // alone gets its own wave and a narrower source group
+  struct WaveDef {
+    int32_t first, last;  // positions in `order`, inclusive first, exclusive last
+    int64_t row0, nrows, width, ld;
+  };
+  std::vector<WaveDef> waves;
+  const double budget = 64.0 * 1024 * 1024;
+  for (int32_t i = 0; i < nviews;) {
+    const int64_t n0 = views[order[i]]->n;
+    const int64_t width = (n0 + kChunk - 1) / kChunk * kChunk;
+    WaveDef wd{i, i + 1, uoff[order[i]], n0, width, width};
+    while (wd.last < nviews && (double)(wd.nrows + views[order[wd.last]]->n) * (double)width * 12.0 <= budget)
+      wd.nrows += views[order[wd.last++]]->n;
+    int64_t ld = (int64_t)(budget / (12.0 * (double)wd.nrows)) / kChunk * kChunk;
+    wd.ld = std::min(width, std::max<int64_t>(kChunk, std::min<int64_t>(ld, 4096)));
+    waves.push_back(wd);
+    i = wd.last;
+  }
+  // buffers: five states of the largest wave x group, the wave's DPPR
+  // matrices, the residual's row blocks
+  size_t smax = 0, dmax = 0;
+  int nbmax = 0;
+  for (const WaveDef &wd : waves) {
+    smax = std::max(smax, sizeof(float) * (size_t)(wd.nrows * wd.ld));
+    size_t dd = 0;
+    for (int32_t i = wd.first; i < wd.last; ++i) dd += (size_t)views[order[i]]->n * (size_t)views[order[i]]->n;
+    dmax = std::max(dmax, dd);
+    nbmax = std::max(nbmax, (int)(wd.last - wd.first) + 1216);
+  }
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y0, smax));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y1, smax));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y2, smax));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y3, smax));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, smax));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, sizeof(float) * std::max<size_t>(dmax, 1)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UBROWS, sizeof(int2) * (size_t)nbmax));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UBPTR, sizeof(int) * (size_t)(nviews + 1)));
+  int64_t ldmax = 0;
+  for (const WaveDef &wd : waves) ldmax = std::max(ldmax, wd.ld);
+  PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, 2 * sizeof(double) * (size_t)ldmax * (size_t)nviews));
+  float *dppr_w = ctx->ws[WS_DPPR].as<float>();
+  int2 *brows_d = ctx->ws[WS_UBROWS].as<int2>();
+  int *bptr_d = ctx->ws[WS_UBPTR].as<int>();
+  double *l1 = ctx->ws[WS_CERT].as<double>();
+  pprviz_stats &st = ctx->stats;
+  const bool exact_res = eps < 1e-9;
+  auto rate = [](double delta) { return delta > 1e-12 ? chebyshev_rate(delta) : 0.0; };
+  auto sweeps_for = [](double factor, double r) { return r > 0.0 ? (int)ceil(log(0.5 * factor) / log(r)) : 1; };
+  bool not_converged = false;
+
+  for (const WaveDef &wd : waves) {
+    const int nvw = (int)(wd.last - wd.first);
+    // residual row blocks: ~1,216 blocks of the wave shared in proportion to
+    // the views' sizes (at least one each), never straddling two views
+    std::vector<int2> brows;
+    std::vector<int> bptr((size_t)nvw + 1, 0);
+    const int nchunks = (int)(wd.ld / 128);
+    const double share = std::max(1.0, 1216.0 / nchunks) / (double)wd.nrows;
+    for (int w = 0; w < nvw; ++w) {
+      const pprviz_graph *g = views[order[wd.first + w]];
+      const int64_t r0 = uoff[order[wd.first + w]] - wd.row0;
+      int64_t nb = std::max<int64_t>(1, (int64_t)(share * (double)g->n));
+      nb = std::min<int64_t>(nb, (g->n + kWarps - 1) / kWarps);
+      const int64_t per = (g->n + nb - 1) / nb;
+      for (int64_t r = 0; r < g->n; r += per) brows.push_back(make_int2((int)(r0 + r), (int)(r0 + std::min(g->n, r + per))));
+      bptr[w + 1] = (int)brows.size();
+    }
+    PPRVIZ_TRY(ws_ensure(ctx, WS_UBROWS, sizeof(int2) * brows.size()));
+    brows_d = ctx->ws[WS_UBROWS].as<int2>();
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(brows_d, brows.data(), sizeof(int2) * brows.size(), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(bptr_d, bptr.data(), sizeof(int) * bptr.size(), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    Wave wv;
+    wv.lidx = lidx;
+    wv.nv = nvr;
+    wv.row0 = wd.row0;
+    wv.nrows = wd.nrows;
+    wv.brows = brows_d;
+    wv.bptr = bptr_d;
+    wv.nblocks = (int)brows.size();
+    wv.nviews = nvw;
+    const int64_t ld = wd.ld;
+    const int64_t cnt = wd.nrows * ld;
+    // DPPR matrices of the wave's views, packed in wave order
+    std::vector<size_t> doff((size_t)nvw + 1, 0);
+    for (int w = 0; w < nvw; ++w) {
+      const int64_t n = views[order[wd.first + w]]->n;
+      doff[w + 1] = doff[w] + (size_t)n * (size_t)n;
+    }
+    for (int64_t g0 = 0; g0 < wd.width; g0 += ld) {
+      wv.g0 = (int32_t)g0;
+      st.groups++;
+      float *bufs[4] = {ctx->ws[WS_Y0].as<float>(), ctx->ws[WS_Y1].as<float>(), ctx->ws[WS_Y2].as<float>(),
+                        ctx->ws[WS_Y3].as<float>()};
+      float *rhs = ctx->ws[WS_RHS].as<float>();
+      double delta_c = c * bsp;
+      const int K1 = std::max(2, sweeps_for(1e-5, rate(delta_c)));
+      float *hi = nullptr;
+      PPRVIZ_TRY(chebyshev_solve(ctx, &U, ld, nullptr, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, nullptr,
+                                 nullptr, defl ? kap_main : nullptr, delta_c, &hi, &wv));
+      st.sweeps_main += K1;
+      st.bytes_sweep += 12.0 * (double)cnt * (K1 - 1);
+      float *fa = hi == bufs[0] ? bufs[1] : bufs[0], *fb = bufs[2], *fc = bufs[3];
+      float *lo = nullptr;
+      // certificates: cert of source (view w, column q) = d(s) ||res||_1 / alpha
+      std::vector<double> l1h((size_t)2 * ld * nvw), cert;
+      double cmax = 0.0;
+      auto certs = [&]() -> int {
+        PPRVIZ_CUDA(ctx, cudaMemcpyAsync(l1h.data(), l1, sizeof(double) * l1h.size(), cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+        PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cmax = 0.0;
+        for (int w = 0; w < nvw; ++w) {
+          const int32_t v = order[wd.first + w];
+          const int64_t gv = std::min<int64_t>(ld, views[v]->n - g0);
+          for (int64_t q = 0; q < gv; ++q) {
+            const double cq = views[v]->h_deg[(size_t)(g0 + q)] * l1h[(size_t)(w * 2) * ld + q] / alpha;
+            cmax = std::max(cmax, cq);
+          }
+        }
+        return PPRVIZ_OK;
+      };
+      PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, &U, ld, nullptr, hi, nullptr, rhs, l1, alpha, &wv)
+                            : launch_residual<float, false>(ctx, &U, ld, nullptr, hi, nullptr, rhs, l1, alpha, &wv)));
+      st.residual_passes++;
+      PPRVIZ_TRY(certs());
+      double cprev = 0.0;
+      for (int pass = 0; pass < kMaxRefine && cmax > eps; ++pass) {
+        if (pass > 0 && cmax > 0.1 * cprev) delta_c = c;
+        cprev = cmax;
+        if (defl) {
+          // the corrections' stationary coefficients, by source node
+          for (int w = 0; w < nvw; ++w) {
+            const int32_t v = order[wd.first + w];
+            const int64_t gv = std::min<int64_t>(ld, views[v]->n - g0);
+            for (int64_t q = 0; q < gv; ++q) {
+              const int64_t sn = uoff[v] + g0 + q;
+              kap_h[(size_t)sn] = l1h[(size_t)(w * 2 + 1) * ld + q] / (alpha * U.h_mc[(size_t)U.h_comp[(size_t)sn]]);
+            }
+          }
+          PPRVIZ_CUDA(ctx, cudaMemcpyAsync(kap_corr + wd.row0, kap_h.data() + wd.row0, sizeof(double) * (size_t)wd.nrows,
+                                           cudaMemcpyHostToDevice, ctx->stream));
+        }
+        int K2 = sweeps_for(0.5 * eps / cmax, rate(delta_c)) + 2;
+        K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
+        float *dl = nullptr;
+        PPRVIZ_TRY(chebyshev_solve(ctx, &U, ld, nullptr, (int32_t)ld, rhs, fa, fb, K2, alpha, nullptr, nullptr,
+                                   defl ? kap_corr : nullptr, delta_c, &dl, &wv));
+        st.sweeps_refine += K2;
+        st.bytes_sweep += 16.0 * (double)cnt * (K2 - 1);
+        st.refine_passes++;
+        if (!lo) {
+          lo = dl;
+          fa = (dl == fa) ? fb : fa;
+          fb = fc;
+        } else {
+          { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_axpy<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, dl, lo); }
+          PPRVIZ_LAUNCHED(ctx);
+        }
+        { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_renorm<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, hi, lo); }
+        PPRVIZ_LAUNCHED(ctx);
+        PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, &U, ld, nullptr, hi, lo, rhs, l1, alpha, &wv)
+                              : launch_residual<float, false>(ctx, &U, ld, nullptr, hi, lo, rhs, l1, alpha, &wv)));
+        st.residual_passes++;
+        PPRVIZ_TRY(certs());
+      }
+      // per view: certificates and the DPPR rows g0 .. g0 + gvalid
+      for (int w = 0; w < nvw; ++w) {
+        const int32_t v = order[wd.first + w];
+        const pprviz_graph *g = views[v];
+        const int64_t gv = std::min<int64_t>(ld, g->n - g0);
+        if (gv <= 0) continue;
+        for (int64_t q = 0; q < gv; ++q) {
+          const double cq = g->h_deg[(size_t)(g0 + q)] * l1h[(size_t)(w * 2) * ld + q] / alpha;
+          st.max_cert = std::max(st.max_cert, cq);
+          if (cq > eps) not_converged = true;
+          if (cert_h) cert_h[node_off[v] + g0 + q] = cq;
+        }
+        const int64_t rs = uoff[v] - wd.row0;  // first state row of the view
+        dim3 grid((unsigned)((gv + 31) / 32), (unsigned)((g->n + 31) / 32));
+        dim3 block(32, 8);
+        { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<float, float><<<grid, block, 0, ctx->stream>>>(
+            (int32_t)g->n, (int32_t)g0, (int32_t)gv, ld, iota_d, U.deg.as<double>() + uoff[v],
+            U.invdw_d.as<double>() + uoff[v], hi + rs * ld, lo ? lo + rs * ld : nullptr, dppr_w + doff[w]); }
+        PPRVIZ_LAUNCHED(ctx);
+      }
+    }
+    for (int w = 0; w < nvw; ++w) {
+      const int32_t v = order[wd.first + w];
+      const int64_t n = views[v]->n;
+      PPRVIZ_TRY(pdist_launch(ctx, dppr_w + doff[w], (int32_t)n, n, pdist_all + sq_off[v], false));
+    }
+  }
+  st.source_group = (int32_t)ldmax;
+  if (not_converged)
+    return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "a view's certificate stayed above eps after the refinement cap");
   return PPRVIZ_OK;
 }
 
