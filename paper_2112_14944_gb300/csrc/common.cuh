@@ -48,6 +48,8 @@ enum Slot {
   // batched propagation: the union graph of the views and its tables
   WS_URP, WS_UCOL, WS_UW, WS_UDEG, WS_UINVD, WS_UINVF, WS_UDWFF, WS_ULIDX, WS_UNV, WS_UCOMP, WS_UKAP,
   WS_UDESC, WS_UBROWS, WS_UBPTR,
+  // batched inverses: panels and pivot inverses of every view, job and step tables
+  WS_FACB, WS_FACT,
   WS_COUNT
 };
 
@@ -183,6 +185,11 @@ int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp
 // returns PPRVIZ_E_TIMEOUT if an MMA completion wait expires.
 size_t spd_inverse_work(int32_t kp);  // elements of `work` for either type
 int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work);
+// FP32 inverses of many SPD matrices at once (A[v]: kp[v] x kp[v] device,
+// kp[v] % 128 == 0), in place as spd_inverse_f32; `work` holds
+// spd_inverse_batch_work(nviews, kp) floats.
+size_t spd_inverse_batch_work(int32_t nviews, const int32_t *kp);
+int spd_inverse_batch_f32(pprviz_ctx *ctx, int32_t nviews, const int32_t *kp, float *const *A, float *work);
 int spd_inverse_f64(pprviz_ctx *ctx, int32_t kp, double *A, double *work);
 
 // ---- layout (layout.cu) ----------------------------------------------------

@@ -70,8 +70,7 @@ __global__ void __launch_bounds__(512) k_fac_diag(int32_t kp, int32_t K0, T *__r
 // published pivot row with each 16-byte load. Per pivot p the owners publish
 // row p, column p and 1 / a_pp through shared memory (double buffered by the
 // parity of p, so one barrier per pivot suffices).
-__global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A,
-                                                      float *__restrict__ P) {
+__device__ __forceinline__ void fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A, float *__restrict__ P) {
   __shared__ __align__(16) float sRow[2][128];
   __shared__ float sCol[2][128];
   __shared__ float sPiv[2];
@@ -143,6 +142,11 @@ __global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, fl
   }
 }
 
+__global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A,
+                                                      float *__restrict__ P) {
+  fac_diag128(kp, K0, A, P);
+}
+
 template <typename T>
 struct V4;  // 4-vector load/store of T
 template <>
@@ -201,10 +205,9 @@ __device__ __forceinline__ void store_split4(T *, int, int, const T (&)[4]) {}  
 // I > K). 256 threads on a 16 x 16 grid, each an R x R block of U
 // (R = NB / 16) accumulated in registers.
 template <typename T, int NB, bool KM>
-__global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ P,
-                                                   T *__restrict__ Ct, T *__restrict__ Ut) {
+__device__ __forceinline__ void fac_panel(int32_t kp, int32_t K0, int I0, T *__restrict__ A, const T *__restrict__ P,
+                                          T *__restrict__ Ct, T *__restrict__ Ut) {
   constexpr int R = NB / 16, LD = NB + 16 / (int)sizeof(T);
-  const int I0 = blockIdx.x * NB;
   if (I0 == K0) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   T *sP = reinterpret_cast<T *>(smem_raw);  // [NB][NB]   sP[s][t]
@@ -283,6 +286,12 @@ __global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__
       }
     }
   }
+}
+
+template <typename T, int NB, bool KM>
+__global__ void __launch_bounds__(256) k_fac_panel(int32_t kp, int32_t K0, T *__restrict__ A, const T *__restrict__ P,
+                                                   T *__restrict__ Ct, T *__restrict__ Ut) {
+  fac_panel<T, NB, KM>(kp, K0, (int)blockIdx.x * NB, A, P, Ct, Ut);
 }
 
 // SIMT trailing update of the upper triangle (FP64, NB = 64):
@@ -417,21 +426,11 @@ __device__ __forceinline__ void issue_chunk(uint32_t st, uint64_t *bar, const fl
 // mbarrier wait has an iteration limit (on expiry the CTA sets `err`, skips
 // the update and still frees its tensor memory after bounded waits for its
 // copies and MMAs).
-__global__ void __launch_bounds__(256, 2)
-k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict__ A, const float *__restrict__ Ct,
-                  const float *__restrict__ Ut, int *__restrict__ err) {
+// C tile (I0, J0) -= Ct_I^T Ut_J (the whole CTA; see k_fac_trailing_tc).
+__device__ __forceinline__ void trailing_tc_tile(int32_t kp, int I0, int J0, float *__restrict__ A,
+                                                 const float *__restrict__ Ct, const float *__restrict__ Ut,
+                                                 int *__restrict__ err) {
   using namespace tc;
-  int I0, J0;
-  if (only_k1) {
-    const int b = blockIdx.x;
-    I0 = (b < k1 ? b : k1) * TM;
-    J0 = (b < k1 ? k1 : b) * TM;
-  } else {
-    I0 = blockIdx.y * TM;
-    J0 = blockIdx.x * TM;
-    if (k1 >= 0 && (I0 == k1 * TM || J0 == k1 * TM)) return;  // the lookahead's tiles
-  }
-  if (J0 < I0 || I0 == K0 || J0 == K0) return;  // lower triangle, pivot row and column
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[NST], mmad[NST];
   __shared__ uint32_t tmem_sh;
@@ -558,6 +557,24 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM));
 }
 
+__global__ void __launch_bounds__(256, 2)
+k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict__ A, const float *__restrict__ Ct,
+                  const float *__restrict__ Ut, int *__restrict__ err) {
+  using namespace tc;
+  int I0, J0;
+  if (only_k1) {
+    const int b = blockIdx.x;
+    I0 = (b < k1 ? b : k1) * TM;
+    J0 = (b < k1 ? k1 : b) * TM;
+  } else {
+    I0 = blockIdx.y * TM;
+    J0 = blockIdx.x * TM;
+    if (k1 >= 0 && (I0 == k1 * TM || J0 == k1 * TM)) return;  // the lookahead's tiles
+  }
+  if (J0 < I0 || I0 == K0 || J0 == K0) return;  // lower triangle, pivot row and column
+  trailing_tc_tile(kp, I0, J0, A, Ct, Ut, err);
+}
+
 // A <- -A on the upper block triangle; with NB = 64 also the lower 64-block of
 // every 128 x 128 diagonal tile filled from its mirror, giving M = A^-1 on the
 // upper tile triangle with full diagonal tiles (what the layout reads).
@@ -680,6 +697,159 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
 int spd_inverse_f32(pprviz_ctx *ctx, int32_t kp, float *A, float *work) { return spd_inverse<float>(ctx, kp, A, work); }
 int spd_inverse_f64(pprviz_ctx *ctx, int32_t kp, double *A, double *work) {
   return spd_inverse<double>(ctx, kp, A, work);
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched FP32 inverses (the views of one batch): the same block sweep, pivot
+// step by pivot step, each launch covering that step's work in every view that
+// still has the pivot: one CTA per view for the pivot inverse, one per block
+// for the panels, one per upper tile for the trailing update (the views'
+// blocks and tiles concatenated; a CTA finds its view by binary search over
+// the launch's offsets). No lookahead: the batch's views fill the GPU.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FacJob {
+  float *A, *Ct, *Ut, *P;
+  int32_t kp, nblk;
+};
+
+// largest i < n with off[i] <= b (off non-decreasing, off[0] <= b)
+__device__ __forceinline__ int find_slot(const int *__restrict__ off, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(1024) k_fac_diag128_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
+                                                            int32_t K0) {
+  const FacJob j = jobs[act[blockIdx.x]];
+  fac_diag128(j.kp, K0, j.A, j.P);
+}
+
+__global__ void __launch_bounds__(256) k_fac_panel_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
+                                                         const int *__restrict__ off, int nact, int32_t K0) {
+  const int s = find_slot(off, nact, (int)blockIdx.x);
+  const FacJob j = jobs[act[s]];
+  fac_panel<float, 128, true>(j.kp, K0, ((int)blockIdx.x - off[s]) * 128, j.A, j.P, j.Ct, j.Ut);
+}
+
+// tile t of a view's upper tile triangle, row by row: (I, J), I <= J
+__global__ void __launch_bounds__(256, 2)
+k_fac_trailing_tc_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act, const int *__restrict__ off,
+                        int nact, int kb, int *__restrict__ err) {
+  const int s = find_slot(off, nact, (int)blockIdx.x);
+  const FacJob j = jobs[act[s]];
+  int t = (int)blockIdx.x - off[s], I = 0;
+  while (I < j.nblk && t >= j.nblk - I) {
+    t -= j.nblk - I;
+    ++I;
+  }
+  const int J = I + t;
+  if (I >= j.nblk || J >= j.nblk || I == kb || J == kb) return;
+  trailing_tc_tile(j.kp, I * tc::TM, J * tc::TM, j.A, j.Ct, j.Ut, err);
+}
+
+}  // namespace
+
+size_t spd_inverse_batch_work(int32_t nviews, const int32_t *kp) {
+  size_t total = 0;
+  for (int32_t v = 0; v < nviews; ++v) total += (size_t)512 * kp[v] + 128 * 128;
+  return total + 64;
+}
+
+int spd_inverse_batch_f32(pprviz_ctx *ctx, int32_t nviews, const int32_t *kp, float *const *A, float *work) {
+  using namespace tc;
+  std::vector<FacJob> jobs((size_t)nviews);
+  size_t o = 0;
+  int maxnb = 0;
+  double flops = 0.0;
+  for (int32_t v = 0; v < nviews; ++v) {
+    const int nblk = kp[v] / 128;
+    jobs[v] = FacJob{A[v], work + o, work + o + (size_t)256 * kp[v], work + o + (size_t)512 * kp[v], kp[v], nblk};
+    o += (size_t)512 * kp[v] + 128 * 128;
+    maxnb = std::max(maxnb, nblk);
+    const double b3 = 128.0 * 128.0 * 128.0, nm1 = nblk - 1.0;
+    flops += nblk * (2.0 * b3 + nm1 * 2.0 * b3 + nm1 * (nm1 + 1.0) / 2.0 * 2.0 * b3);
+  }
+  ctx->stats.flops_factor += flops;
+  int *err = reinterpret_cast<int *>(work + o);
+  // per step: the views with the pivot (all), those with panels and a trailing
+  // update (more than one block), and the launches' offsets
+  struct StepTab { size_t act_all, act_multi, pan, trl; int nall, nmulti, npan, ntrl; };
+  std::vector<StepTab> steps((size_t)maxnb);
+  std::vector<int> tab;
+  for (int kb = 0; kb < maxnb; ++kb) {
+    StepTab &st = steps[kb];
+    st.act_all = tab.size();
+    for (int32_t v = 0; v < nviews; ++v)
+      if (jobs[v].nblk > kb) tab.push_back(v);
+    st.nall = (int)(tab.size() - st.act_all);
+    st.act_multi = tab.size();
+    for (int32_t v = 0; v < nviews; ++v)
+      if (jobs[v].nblk > kb && jobs[v].nblk > 1) tab.push_back(v);
+    st.nmulti = (int)(tab.size() - st.act_multi);
+    st.pan = tab.size();
+    int acc = 0;
+    for (int q = 0; q < st.nmulti; ++q) {
+      tab.push_back(acc);
+      acc += jobs[tab[st.act_multi + q]].nblk;
+    }
+    tab.push_back(acc);
+    st.npan = acc;
+    st.trl = tab.size();
+    acc = 0;
+    for (int q = 0; q < st.nmulti; ++q) {
+      tab.push_back(acc);
+      const int nb = jobs[tab[st.act_multi + q]].nblk;
+      acc += nb * (nb + 1) / 2;
+    }
+    tab.push_back(acc);
+    st.ntrl = acc;
+  }
+  const size_t jb = (sizeof(FacJob) * jobs.size() + 255) & ~(size_t)255;
+  PPRVIZ_TRY(ws_ensure(ctx, WS_FACT, jb + sizeof(int) * tab.size()));
+  FacJob *jobs_d = ctx->ws[WS_FACT].as<FacJob>();
+  int *tab_d = reinterpret_cast<int *>(static_cast<unsigned char *>(ctx->ws[WS_FACT].p) + jb);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(jobs_d, jobs.data(), sizeof(FacJob) * jobs.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+  const size_t panel_smem = sizeof(float) * (128 * 128 + 128 * (128 + 4));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM));
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  {
+    PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
+    for (int kb = 0; kb < maxnb; ++kb) {
+      const StepTab &st = steps[kb];
+      const int32_t K0 = kb * 128;
+      k_fac_diag128_batch<<<(unsigned)st.nall, 1024, 0, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
+      PPRVIZ_LAUNCHED(ctx);
+      if (st.nmulti == 0) continue;
+      k_fac_panel_batch<<<(unsigned)st.npan, 256, panel_smem, ctx->stream>>>(jobs_d, tab_d + st.act_multi,
+                                                                              tab_d + st.pan, st.nmulti, K0);
+      PPRVIZ_LAUNCHED(ctx);
+      k_fac_trailing_tc_batch<<<(unsigned)st.ntrl, 256, SMEM, ctx->stream>>>(jobs_d, tab_d + st.act_multi,
+                                                                             tab_d + st.trl, st.nmulti, kb, err);
+      PPRVIZ_LAUNCHED(ctx);
+    }
+    for (int32_t v = 0; v < nviews; ++v) {
+      k_fac_finish<float, 128><<<dim3((unsigned)std::min(8, (kp[v] + 255) / 256), (unsigned)kp[v]), 256, 0,
+                                 ctx->stream>>>(kp[v], A[v]);
+      PPRVIZ_LAUNCHED(ctx);
+    }
+  }
+  int herr = 0;
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (herr) return set_err(ctx, PPRVIZ_E_TIMEOUT, "tensor-core trailing update: MMA completion wait expired");
+  return PPRVIZ_OK;
 }
 
 }  // namespace pprviz

@@ -1136,10 +1136,9 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   const size_t tab_off = (sizeof(BatchView) * (size_t)nviews + 255) & ~(size_t)255;
   const size_t cnt_off = (tab_off + sizeof(int4) * tiles.size() + 255) & ~(size_t)255;
   PPRVIZ_TRY(ws_ensure(ctx, WS_BTAB, cnt_off + sizeof(int) * (size_t)cnts));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_PIV, sizeof(float) * spd_inverse_work(maxkp)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sizeof(double) * (size_t)(maxkp / 32) * maxkp));
   PPRVIZ_TRY(ws_ensure(ctx, WS_FLAG, 64));
-  float *W1 = ctx->ws[WS_BW1].as<float>(), *M = ctx->ws[WS_BM].as<float>(), *work = ctx->ws[WS_PIV].as<float>();
+  float *W1 = ctx->ws[WS_BW1].as<float>(), *M = ctx->ws[WS_BM].as<float>();
   V2 *X = ctx->ws[WS_BX].as<V2>(), *Bv = X + vec, *Part = ctx->ws[WS_BPART].as<V2>();
   BatchView *views_d = reinterpret_cast<BatchView *>(ctx->ws[WS_BTAB].p);
   int4 *tiles_d = reinterpret_cast<int4 *>(static_cast<unsigned char *>(ctx->ws[WS_BTAB].p) + tab_off);
@@ -1153,6 +1152,8 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
                                    ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
   int64_t sq = 0, xo = 0;
+  std::vector<int32_t> kps((size_t)nviews);
+  std::vector<float *> mats((size_t)nviews);
   for (int32_t v = 0; v < nviews; ++v) {
     const int32_t k = bv[v].k, kp = bv[v].kp;
     const float *Dv = pdist_d + sq;
@@ -1160,11 +1161,17 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
     PPRVIZ_LAUNCHED(ctx);
     { PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR); k_build_diag<float><<<(unsigned)((k + 255) / 256), 256, 0, ctx->stream>>>(k, kp, rowpart, M + bv[v].mat_off); }
     PPRVIZ_LAUNCHED(ctx);
-    if (iters > 0) PPRVIZ_TRY(spd_inverse_f32(ctx, kp, M + bv[v].mat_off, work));
     { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_load_x<float, float><<<(unsigned)((kp + 255) / 256), 256, 0, ctx->stream>>>(k, kp, x0_d + 2 * xo, X + bv[v].vec_off); }
     PPRVIZ_LAUNCHED(ctx);
+    kps[v] = kp;
+    mats[v] = M + bv[v].mat_off;
     sq += (int64_t)k * k;
     xo += k;
+  }
+  // every view's (L^w + J/k)^-1 together, pivot step by pivot step
+  if (iters > 0) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_FACB, sizeof(float) * spd_inverse_batch_work(nviews, kps.data())));
+    PPRVIZ_TRY(spd_inverse_batch_f32(ctx, nviews, kps.data(), mats.data(), ctx->ws[WS_FACB].as<float>()));
   }
   int hf = 0;
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -1029,8 +1029,9 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
 // nv = the view's size). Consecutive views of similar size form a wave, a
 // contiguous row range of the union; column q of a wave's state is source q
 // of every view in it at once (k_sweep, BATCH), so one sweep launch advances
-// all sources of all views of the wave. Per-view results (certificates, DPPR
-// rows, PDist) are separated again by row range.
+// all sources of all views of the wave. Each wave iterates its Chebyshev
+// sweeps on the largest spectral bound of its views. Per-view results
+// (certificates, DPPR rows, PDist) are separated again by row range.
 // --------------------------------------------------------------------------
 namespace {
 
@@ -1139,16 +1140,30 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
   U.invdw_d = slot_view(ctx, WS_UINVD);
   U.invdw_f = slot_view(ctx, WS_UINVF);
   U.dwff = slot_view(ctx, WS_UDWFF);
-  U.comp = slot_view(ctx, WS_UCOMP);  // large enough: graph_spectral allocates nothing for it
+  U.comp = slot_view(ctx, WS_UCOMP);  // component roots, filled from the views below
   U.h_deg.resize((size_t)N);
   for (int32_t v = 0; v < nviews; ++v)
     std::copy(views[v]->h_deg.begin(), views[v]->h_deg.end(), U.h_deg.begin() + uoff[v]);
   const int32_t *lidx = ctx->ws[WS_ULIDX].as<int32_t>();
   const int32_t *nvr = ctx->ws[WS_UNV].as<int32_t>();
-  // components and the spectral bound (the largest over the views)
-  PPRVIZ_TRY(graph_spectral(ctx, &U));
-  const bool defl = U.spec_deflate;
-  const double bsp = defl ? U.spec_b : 1.0;
+  // components and spectral bound of every view (computed once per graph and
+  // kept with it); the union's component roots are the views' roots offset
+  bool defl = true;
+  for (int32_t v = 0; v < nviews; ++v) {
+    PPRVIZ_TRY(graph_spectral(ctx, views[v]));
+    defl = defl && views[v]->spec_deflate;
+  }
+  U.h_comp.resize((size_t)N);
+  U.h_mc.assign((size_t)N, 0.0);
+  for (int32_t v = 0; v < nviews; ++v) {
+    const pprviz_graph *g = views[v];
+    for (int64_t i = 0; i < g->n; ++i) {
+      U.h_comp[(size_t)(uoff[v] + i)] = (int32_t)(uoff[v] + g->h_comp[(size_t)i]);
+      U.h_mc[(size_t)(uoff[v] + i)] = g->h_mc[(size_t)i];
+    }
+  }
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(U.comp.p, U.h_comp.data(), sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice,
+                                   ctx->stream));
   double *kap_main = ctx->ws[WS_UKAP].as<double>(), *kap_corr = kap_main + N;
   std::vector<double> kap_h((size_t)N, 0.0);
   if (defl) {
@@ -1243,6 +1258,10 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
     wv.nviews = nvw;
     const int64_t ld = wd.ld;
     const int64_t cnt = wd.nrows * ld;
+    // the wave's iterated modes: |lambda| <= the largest bound of its views
+    double bsp = 0.0;
+    for (int w = 0; w < nvw; ++w) bsp = std::max(bsp, views[order[wd.first + w]]->spec_b);
+    if (!defl) bsp = 1.0;
     // DPPR matrices of the wave's views, packed in wave order
     std::vector<size_t> doff((size_t)nvw + 1, 0);
     for (int w = 0; w < nvw; ++w) {
