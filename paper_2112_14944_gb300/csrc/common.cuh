@@ -74,6 +74,8 @@ struct pprviz_ctx {
   pprviz::DevBuf ws[pprviz::WS_COUNT];
   pprviz_stats stats{};
   int launches = 0;  // kernels launched in the current call
+  // source-group widths chosen by the sweep autotuner, by graph size class
+  std::vector<std::pair<uint64_t, int64_t>> tuned_groups;
 };
 
 struct pprviz_graph {

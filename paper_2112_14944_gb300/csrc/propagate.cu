@@ -44,7 +44,9 @@
 
 namespace pprviz {
 
-constexpr int kWarps = 8;         // warps per block in the sweep kernels
+constexpr int kWarps = 8;         // warps per block in the residual kernels
+constexpr int kSweepWarps = 1;    // warps per block in k_sweep: one-warp blocks retire with their own
+                                  // row, so a hub row does not hold seven finished warps' slots
 constexpr int kChunk = 128;       // group width granule (sources)
 constexpr int kMaxRefine = 6;     // refinement passes before E_NOT_CONVERGED
 constexpr int kMaxRefineSweeps = 32;  // Chebyshev sweeps per refinement pass
@@ -145,14 +147,14 @@ __global__ void k_renorm(int64_t count, float *__restrict__ hi, float *__restric
 // its view, so b_jq = alpha [src[row0 + j] == g0 + q]. Neighbours stay inside
 // their view, hence inside the state's row range.
 template <typename T, bool WEIGHTED, bool CHEB, bool RHS, bool BATCH>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kSweepWarps * 32)
 k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
         const int32_t *__restrict__ col, const float *__restrict__ w, const T *__restrict__ invdw,
         const int32_t *__restrict__ src, const float *__restrict__ rhs, const T *__restrict__ ycur,
         const T *yold, T *yout, T alpha, T c, T om, T om1, int64_t row0, int32_t g0) {
   constexpr int VEC = Vec<T>::N;
   const int lane = threadIdx.x & 31;
-  const int64_t item = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t item = (int64_t)blockIdx.x * kSweepWarps + (threadIdx.x >> 5);
   if (item >= n * nchunks) return;
   const int64_t chunk = item / n;
   const int64_t j = item - chunk * n;  // row within the state
@@ -643,7 +645,7 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
   const int nchunks = (int)(ld / (32 * VEC));
   const int64_t nrows = wv ? wv->nrows : g->n;
   const int64_t items = nrows * nchunks;
-  const unsigned blocks = (unsigned)((items + kWarps - 1) / kWarps);
+  const unsigned blocks = (unsigned)((items + kSweepWarps - 1) / kSweepWarps);
   const T *invdw = std::is_same<T, float>::value ? (const T *)g->invdw_f.p : (const T *)g->invdw_d.p;
   const T a = (T)alpha, c = (T)(1.0 - alpha), o = (T)om, o1 = (T)(1.0 - om);
   const float *w = g->weighted ? g->w.as<float>() : nullptr;
@@ -654,7 +656,7 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
   if (wv) src = wv->lidx;
   PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
 #define PPRVIZ_SWEEP(W, C, R, B)                                                                   \
-  k_sweep<T, W, C, R, B><<<blocks, kWarps * 32, 0, ctx->stream>>>(nrows, ld, nchunks, rp, col, w, invdw, \
+  k_sweep<T, W, C, R, B><<<blocks, kSweepWarps * 32, 0, ctx->stream>>>(nrows, ld, nchunks, rp, col, w, invdw, \
                                                                   src, rhsbuf, ycur, yold, yout, a, c, o, o1, row0, g0)
   if (wv) {
     if constexpr (std::is_same<T, float>::value) {
@@ -725,6 +727,75 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   }
   PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
+}
+
+// Autotuner of the source-group width G of the FP32 CSR sweeps. The
+// candidates are 128, 256, ... up to the width whose ~3 live [n][G] buffers
+// fill ~64 MB of L2 (choose_group); each runs three timed Chebyshev sweeps on
+// the graph (after one untimed), and the width with the least time per source
+// and sweep wins. The choice is kept in the context per size class (bit
+// lengths of n, nnz and k, weighted or not), so the cost (a few milliseconds)
+// is paid on the first call of each class.
+int64_t tuned_group(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int *status) {
+  *status = PPRVIZ_OK;
+  auto bits = [](uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return (uint64_t)b; };
+  const uint64_t key = (bits((uint64_t)g->n) << 40) | (bits((uint64_t)g->nnz) << 32) | (bits((uint64_t)k) << 8) |
+                       (g->weighted ? 1u : 0u);
+  for (const auto &e : ctx->tuned_groups)
+    if (e.first == key) return e.second;
+  const int64_t gmax = choose_group(g->n, k, sizeof(float));
+  std::vector<int64_t> cands;
+  for (int64_t c = kChunk; c < gmax; c *= 2) cands.push_back(c);
+  cands.push_back(gmax);
+  int64_t best = gmax;
+  if (cands.size() > 1) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      cudaGetLastError();
+      if (e0) cudaEventDestroy(e0);
+      *status = set_err(ctx, PPRVIZ_E_CUDA, "autotuner: event creation failed");
+      return gmax;
+    }
+    double best_score = 0.0;
+    int st = PPRVIZ_OK;
+    for (int64_t G : cands) {
+      const size_t bytes = sizeof(float) * (size_t)(g->n * G);
+      if ((st = ws_ensure(ctx, WS_Y0, bytes)) != PPRVIZ_OK) break;
+      if ((st = ws_ensure(ctx, WS_Y1, bytes)) != PPRVIZ_OK) break;
+      if ((st = ws_ensure(ctx, WS_SRC, sizeof(int32_t) * (size_t)G)) != PPRVIZ_OK) break;
+      float *ya = ctx->ws[WS_Y0].as<float>(), *yb = ctx->ws[WS_Y1].as<float>();
+      const int32_t *src = ctx->ws[WS_SRC].as<int32_t>();
+      cudaError_t ce = cudaMemsetAsync(ya, 0, bytes, ctx->stream);
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(yb, 0, bytes, ctx->stream);
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(ctx->ws[WS_SRC].p, 0xFF, sizeof(int32_t) * (size_t)G, ctx->stream);
+      if (ce != cudaSuccess) { st = cuda_err(ctx, ce, "autotuner"); break; }
+      float ms = 0.0f;
+      for (int rep = 0; rep < 4 && st == PPRVIZ_OK; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, ctx->stream);
+        st = launch_sweep<float>(ctx, g, G, true, false, src, nullptr, (rep & 1) ? yb : ya, (rep & 1) ? ya : yb,
+                                 (rep & 1) ? ya : yb, 0.15, 1.0);
+      }
+      if (st != PPRVIZ_OK) break;
+      cudaEventRecord(e1, ctx->stream);
+      if ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        st = cuda_err(ctx, ce, "autotuner timing");
+        break;
+      }
+      const double score = (double)ms / (double)G;
+      if (best_score == 0.0 || score < best_score) {
+        best_score = score;
+        best = G;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PPRVIZ_OK) {
+      *status = st;
+      return gmax;
+    }
+  }
+  ctx->tuned_groups.push_back({key, best});
+  return best;
 }
 
 // certificates of the group's sources: d(s) * ||res_s||_1 / alpha
@@ -820,7 +891,16 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
     dense = dense_prepare(ctx, g) == PPRVIZ_OK;
     if (!dense) ctx->err.clear();
   }
-  const int64_t ld = dense ? dense_group(k) : choose_group(g->n, k, elem);
+  int64_t ld = 0;
+  if (dense) {
+    ld = dense_group(k);
+  } else if (fp64) {
+    ld = choose_group(g->n, k, elem);
+  } else {
+    int ts = PPRVIZ_OK;
+    ld = tuned_group(ctx, g, k, &ts);
+    PPRVIZ_TRY(ts);
+  }
   const size_t sbytes = elem * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
   PPRVIZ_TRY(ws_ensure(ctx, WS_Y0, sbytes));
