@@ -367,7 +367,7 @@ constexpr uint32_t LBO = 128;                 // bytes to the next core matrix a
 constexpr uint32_t SBO = (KC / 4) * 128;      // bytes to the next 8-row group
 constexpr int OPB = TM * KC * 4;              // one staged operand part (8 KiB)
 constexpr int STAGE = 4 * OPB;                // A_hi, A_lo, B_hi, B_lo
-constexpr int NST = 3;                        // stages
+constexpr int NST = 2;                        // stages (64 KiB: also the epilogue's tile)
 constexpr int SMEM = NST * STAGE + 1024;      // stages (+ alignment); the epilogue reuses 64 KiB of them
 constexpr long WAIT_LIMIT = 1L << 22;         // mbarrier polls before giving up
 
@@ -420,8 +420,8 @@ __device__ __forceinline__ void issue_chunk(uint32_t st, uint64_t *bar, const fl
 // One thread streams the 8 inner chunks of the tile's operands (already
 // split by the panel kernel) through NST shared-memory stages with bulk
 // copies and issues the 3 x 2 MMAs of each chunk; a stage is refilled once
-// the MMAs of the chunk before it have completed. 96 KiB of shared memory,
-// 128 tensor-memory columns: two CTAs per SM, so that one CTA's epilogue
+// the MMAs of the chunk before it have completed. 65 KiB of shared memory,
+// 128 tensor-memory columns: three CTAs per SM, so that one CTA's epilogue
 // (the read-modify-write of its C tile) overlaps the other's MMAs. Every
 // mbarrier wait has an iteration limit (on expiry the CTA sets `err`, skips
 // the update and still frees its tensor memory after bounded waits for its
@@ -557,7 +557,7 @@ __device__ __forceinline__ void trailing_tc_tile(int32_t kp, int I0, int J0, flo
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM));
 }
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict__ A, const float *__restrict__ Ct,
                   const float *__restrict__ Ut, int *__restrict__ err) {
   using namespace tc;
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(256) k_fac_panel_batch(const FacJob *__restric
 }
 
 // tile t of a view's upper tile triangle, row by row: (I, J), I <= J
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 k_fac_trailing_tc_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act, const int *__restrict__ off,
                         int nact, int kb, int *__restrict__ err) {
   const int s = find_slot(off, nact, (int)blockIdx.x);

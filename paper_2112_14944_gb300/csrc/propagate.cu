@@ -686,17 +686,19 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
 template <typename T, bool EXACT>
 int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha,
-                    const Wave *wv = nullptr) {
+                    const Wave *wv = nullptr, int total_blocks = 1216) {
   const int nchunks = (int)(ld / 128);
   int rows_blocks;
   if (wv) {
     rows_blocks = wv->nblocks;
   } else {
-    // ~1,216 CTAs in all when the group's state fits in L2; otherwise ~608 per
-    // chunk (about the resident CTAs of the GPU), so that the chunks run one
-    // after another and only ~one chunk's columns are gathered at a time
+    // `total_blocks` CTAs in all when the group's state fits in L2 (1,216
+    // unless tuned); otherwise ~608 per chunk (about the resident CTAs of the
+    // GPU), so that the chunks run one after another and only ~one chunk's
+    // columns are gathered at a time
     const bool fits_l2 = (double)g->n * (double)ld * 8.0 <= 64.0 * 1024 * 1024;
-    rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps, fits_l2 ? std::max(1, 1216 / nchunks) : 608);
+    rows_blocks = (int)std::min<int64_t>((g->n + kWarps - 1) / kWarps,
+                                         fits_l2 ? std::max(1, total_blocks / nchunks) : 608);
   }
   dim3 grid(rows_blocks, nchunks);
   PPRVIZ_TRY(ws_ensure(ctx, WS_RPART, sizeof(double) * 2 * (size_t)rows_blocks * (size_t)ld));
@@ -729,36 +731,47 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   return PPRVIZ_OK;
 }
 
-// Autotuner of the source-group width G of the FP32 CSR sweeps. The
-// candidates are 128, 256, ... up to the width whose ~3 live [n][G] buffers
-// fill ~64 MB of L2 (choose_group); each runs three timed Chebyshev sweeps on
-// the graph (after one untimed), and the width with the least time per source
-// and sweep wins. The choice is kept in the context per size class (bit
-// lengths of n, nnz and k, weighted or not), so the cost (a few milliseconds)
-// is paid on the first call of each class.
-int64_t tuned_group(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int *status) {
+// Autotuner of the FP32 CSR path's launch shapes, per size class (bit
+// lengths of n, nnz and k, weighted or not), kept in the context so that its
+// cost (a few milliseconds) is paid on the first call of each class:
+//  * the source-group width G: candidates 128, 256, ... up to the width whose
+//    ~3 live [n][G] buffers fill ~64 MB of L2 (choose_group); each runs three
+//    timed Chebyshev sweeps on the graph (after one untimed), and the width
+//    with the least time per source and sweep wins;
+//  * then, at that width, the residual's CTA count (608 .. 4,864 in all): three
+//    timed residual passes with a low part each, the fastest wins.
+// The values of the state do not change the work of either kernel, so both
+// are timed on zeroed buffers.
+struct TunedShape {
+  int64_t group;
+  int res_blocks;
+};
+
+TunedShape tuned_shape(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int *status) {
   *status = PPRVIZ_OK;
   auto bits = [](uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return (uint64_t)b; };
   const uint64_t key = (bits((uint64_t)g->n) << 40) | (bits((uint64_t)g->nnz) << 32) | (bits((uint64_t)k) << 8) |
                        (g->weighted ? 1u : 0u);
   for (const auto &e : ctx->tuned_groups)
-    if (e.first == key) return e.second;
+    if (e.first == key) return TunedShape{e.second >> 16, (int)(e.second & 0xFFFF)};
   const int64_t gmax = choose_group(g->n, k, sizeof(float));
   std::vector<int64_t> cands;
   for (int64_t c = kChunk; c < gmax; c *= 2) cands.push_back(c);
   cands.push_back(gmax);
   int64_t best = gmax;
-  if (cands.size() > 1) {
+  int best_res = 1216;
+  {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
       cudaGetLastError();
       if (e0) cudaEventDestroy(e0);
       *status = set_err(ctx, PPRVIZ_E_CUDA, "autotuner: event creation failed");
-      return gmax;
+      return TunedShape{gmax, 1216};
     }
     double best_score = 0.0;
     int st = PPRVIZ_OK;
     for (int64_t G : cands) {
+      if (cands.size() == 1) break;
       const size_t bytes = sizeof(float) * (size_t)(g->n * G);
       if ((st = ws_ensure(ctx, WS_Y0, bytes)) != PPRVIZ_OK) break;
       if ((st = ws_ensure(ctx, WS_Y1, bytes)) != PPRVIZ_OK) break;
@@ -787,15 +800,52 @@ int64_t tuned_group(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int *stat
         best = G;
       }
     }
+    // the residual's CTA count at the chosen width (only where its state fits in L2)
+    const bool fits_l2 = (double)g->n * (double)best * 8.0 <= 64.0 * 1024 * 1024;
+    if (st == PPRVIZ_OK && fits_l2 && g->n >= 8 * 608) {
+      const size_t bytes = sizeof(float) * (size_t)(g->n * best);
+      if (st == PPRVIZ_OK) st = ws_ensure(ctx, WS_Y0, bytes);
+      if (st == PPRVIZ_OK) st = ws_ensure(ctx, WS_Y1, bytes);
+      if (st == PPRVIZ_OK) st = ws_ensure(ctx, WS_RHS, bytes);
+      if (st == PPRVIZ_OK) st = ws_ensure(ctx, WS_SRC, sizeof(int32_t) * (size_t)best);
+      if (st == PPRVIZ_OK) st = ws_ensure(ctx, WS_CERT, 2 * sizeof(double) * (size_t)best);
+      cudaError_t ce = cudaSuccess;
+      if (st == PPRVIZ_OK) ce = cudaMemsetAsync(ctx->ws[WS_Y0].p, 0, bytes, ctx->stream);
+      if (st == PPRVIZ_OK && ce == cudaSuccess) ce = cudaMemsetAsync(ctx->ws[WS_Y1].p, 0, bytes, ctx->stream);
+      if (st == PPRVIZ_OK && ce == cudaSuccess)
+        ce = cudaMemsetAsync(ctx->ws[WS_SRC].p, 0xFF, sizeof(int32_t) * (size_t)best, ctx->stream);
+      if (st == PPRVIZ_OK && ce != cudaSuccess) st = cuda_err(ctx, ce, "autotuner");
+      double best_t = 0.0;
+      for (int total : {608, 1216, 2432, 4864}) {
+        if (st != PPRVIZ_OK) break;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 4 && st == PPRVIZ_OK; ++rep) {
+          if (rep == 1) cudaEventRecord(e0, ctx->stream);
+          st = launch_residual<float, false>(ctx, g, best, ctx->ws[WS_SRC].as<int32_t>(), ctx->ws[WS_Y0].as<float>(),
+                                             ctx->ws[WS_Y1].as<float>(), ctx->ws[WS_RHS].as<float>(),
+                                             ctx->ws[WS_CERT].as<double>(), 0.15, nullptr, total);
+        }
+        if (st != PPRVIZ_OK) break;
+        cudaEventRecord(e1, ctx->stream);
+        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+          st = cuda_err(ctx, ce, "autotuner timing");
+          break;
+        }
+        if (best_t == 0.0 || ms < best_t) {
+          best_t = ms;
+          best_res = total;
+        }
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != PPRVIZ_OK) {
       *status = st;
-      return gmax;
+      return TunedShape{gmax, 1216};
     }
   }
-  ctx->tuned_groups.push_back({key, best});
-  return best;
+  ctx->tuned_groups.push_back({key, (best << 16) | best_res});
+  return TunedShape{best, best_res};
 }
 
 // certificates of the group's sources: d(s) * ||res_s||_1 / alpha
@@ -892,14 +942,17 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
     if (!dense) ctx->err.clear();
   }
   int64_t ld = 0;
+  int res_blocks = 1216;
   if (dense) {
     ld = dense_group(k);
   } else if (fp64) {
     ld = choose_group(g->n, k, elem);
   } else {
     int ts = PPRVIZ_OK;
-    ld = tuned_group(ctx, g, k, &ts);
+    const TunedShape sh = tuned_shape(ctx, g, k, &ts);
     PPRVIZ_TRY(ts);
+    ld = sh.group;
+    res_blocks = sh.res_blocks;
   }
   const size_t sbytes = elem * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
@@ -1010,8 +1063,8 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       // free buffers for the correction solves; the first correction becomes x_lo
       float *fa = hi == bufs[0] ? bufs[1] : bufs[0], *fb = bufs[2], *fc = bufs[3];
       float *lo = nullptr;
-      PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha)
-                            : launch_residual<float, false>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha)));
+      PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha, nullptr, res_blocks)
+                            : launch_residual<float, false>(ctx, g, ld, src, hi, nullptr, rhs, l1, alpha, nullptr, res_blocks)));
       st.residual_passes++;
       PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, ld, l1, alpha, cert, sigma));
       double cprev = 0.0;
@@ -1055,8 +1108,8 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
           { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_renorm<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, hi, lo); }
           PPRVIZ_LAUNCHED(ctx);
         }
-        PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)
-                              : launch_residual<float, false>(ctx, g, ld, src, hi, lo, rhs, l1, alpha)));
+        PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, src, hi, lo, rhs, l1, alpha, nullptr, res_blocks)
+                              : launch_residual<float, false>(ctx, g, ld, src, hi, lo, rhs, l1, alpha, nullptr, res_blocks)));
         st.residual_passes++;
         PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, ld, l1, alpha, cert, sigma));
       }
