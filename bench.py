@@ -55,6 +55,30 @@ L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
 PROF_EVERY = 16
 
 
+def max_over_ranks(x, device):
+    """The largest x over the ranks of the process group (x itself when there
+    is no group or a single rank): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier_if_group():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def whole_job_rate(units_per_rank_step, steps, world, max_ms):
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time (weak scaling: each rank runs its own replica)."""
+    return world * steps * units_per_rank_step / (max_ms / 1e3)
+
+
 def class_share(ktimes, steps):
     """Per class and step: device ms (the timed launches' mean duration x all
     launches) and launches."""
@@ -71,7 +95,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=None, help="nodes (default 10000; 20000 with --workload dense)")
+    ap.add_argument("--n", "--num-nodes", dest="n", type=int, default=None,
+                    help="nodes (default 10000; 20000 with --workload dense); under torchrun use --num-nodes")
     ap.add_argument("--deg", type=float, default=20.0)
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -320,8 +345,7 @@ def run_dense(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_if_group()
     torch.cuda.synchronize()
     ctx.profile(PROF_EVERY)
     sampler = ClockSampler(local_rank)
@@ -344,10 +368,7 @@ def run_dense(args, rank, world, local_rank):
     ktimes = ctx.kernel_times()
     ctx.profile(False)
     total = sum(ms)
-    if world > 1:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, dev)
     if rank != 0:
         return
     entries = float(n) * n
@@ -368,7 +389,7 @@ def run_dense(args, rank, world, local_rank):
     share = class_share(ktimes, args.steps)
     line = {
         "metric": "DPPR entries/s, dense weighted view n=20k, err<=1e-6 vs FP64 (tensor-core sweeps)",
-        "value": world * args.steps * entries / (total / 1e3), "unit": "entries/s", "n_gpus": world,
+        "value": whole_job_rate(entries, args.steps, world, total), "unit": "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3/f32/f64", "data": "synthetic",
         "config": {"workload": DENSE_WORKLOAD, "graph": "dense clustered SBM, lognormal(0,1) weights", "n": n,
@@ -415,8 +436,7 @@ def run_views(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_if_group()
     torch.cuda.synchronize()
     ctx.profile(PROF_EVERY)
     sampler = ClockSampler(local_rank)
@@ -437,15 +457,12 @@ def run_views(args, rank, world, local_rank):
     ktimes = ctx.kernel_times()
     ctx.profile(False)
     total = sum(ms)
-    if world > 1:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, dev)
     if rank != 0:
         return
     line = {
         "metric": "DPPR entries/s, 256 batched SBM views (DPPR + PDist + 200 layout updates each)",
-        "value": world * args.steps * entries / (total / 1e3), "unit": "entries/s", "n_gpus": world,
+        "value": whole_job_rate(entries, args.steps, world, total), "unit": "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": VIEWS_WORKLOAD, "views": 256, "n_range": [50, 5000], "blocks": [4, 16],
@@ -508,8 +525,7 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_if_group()
     torch.cuda.synchronize()
     ctx.profile(PROF_EVERY)
     sampler = ClockSampler(local_rank)
@@ -536,19 +552,15 @@ def run_ours(args, rank, world, local_rank):
         step_ms.append(ev[0].elapsed_time(ev[2]))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_if_group()
     torch.cuda.synchronize()
     sampler.stop()
     ktimes = ctx.kernel_times()
     ctx.profile(False)
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     entries = float(n) * n
-    value = world * args.steps * entries / (total_ms / 1e3)
+    value = whole_job_rate(entries, args.steps, world, total_ms)
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -570,13 +582,10 @@ def run_ours(args, rank, world, local_rank):
             G.free()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         tot = sum(e2e_ms)
-        if world > 1:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(tot, dev)
         h2d = rp_h.nbytes + col_h.nbytes + view_h.nbytes + Dl_h.nbytes + x0_p.nbytes
         d2h = D_h.nbytes + Dl_h.nbytes + X_h.nbytes + 8 * n
-        e2e = {"value": world * args.e2e_steps * entries / (tot / 1e3), "unit": "entries/s",
+        e2e = {"value": whole_job_rate(entries, args.e2e_steps, world, tot), "unit": "entries/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": tot / args.e2e_steps}
 
