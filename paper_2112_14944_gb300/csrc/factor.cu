@@ -415,7 +415,7 @@ __device__ __forceinline__ void issue_chunk(uint32_t st, uint64_t *bar, const fl
 // !only_k1, the same without block row and column k1 (the next pivot's);
 // with only_k1, just the tiles of block row and column k1 (grid nblk x 1:
 // block b is tile (b, k1) for b < k1, else (k1, b)). The lookahead of the
-// driver updates block row and column k1 first, so that the next pivot's
+// host loop updates block row and column k1 first, so that the next pivot's
 // inverse and panel overlap the rest of the update.
 // One thread streams the 8 inner chunks of the tile's operands (already
 // split by the panel kernel) through NST shared-memory stages with bulk

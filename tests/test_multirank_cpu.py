@@ -78,7 +78,7 @@ def test_reference_arm_prints_one_line():
 
 
 def test_reference_arm_under_torchrun_two_ranks():
-    """The driver's launch form for N = 2: rank 0 alone prints the line."""
+    """The torchrun launch form for N = 2: rank 0 alone prints the line."""
     pytest.importorskip("torch")
     port = _free_port()
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
