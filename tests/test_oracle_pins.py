@@ -96,6 +96,81 @@ def test_single_edge_closed_form():
     assert abs(Pi[0, 1] - C / (1 + C)) < 1e-15
 
 
+def _weighted_csr_from_edges(n, wedges):
+    """Symmetric weighted CSR from (a, b, w) undirected edges."""
+    pairs = sorted({(a, b): w for a, b, w in wedges}.items() | {(b, a): w for a, b, w in wedges}.items())
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    for (a, _), _ in pairs:
+        row_ptr[a + 1] += 1
+    row_ptr = np.cumsum(row_ptr)
+    col = np.array([b for (_, b), _ in pairs], dtype=np.int32)
+    w = np.array([x for _, x in pairs], dtype=np.float32)
+    return row_ptr, col, w
+
+
+def test_weighted_star_closed_form():
+    # Weighted reading of Sec. 3.1 / Definition 1: a walk at v steps to u with
+    # probability w_vu / s_v and d(v) = s_v (the strength). Star: centre 0,
+    # leaves j with edge weights w_j, W = sum_j w_j. From the recursion
+    # pi(s, t) = alpha [s = t] + c sum_u P(s, u) pi(u, t):
+    #   pi(centre, centre) = 1 / (1 + c),  pi(leaf_j, centre) = c / (1 + c),
+    #   pi(centre, leaf_j) = c w_j / (W (1 + c)),
+    #   pi(leaf_i, leaf_j) = alpha [i = j] + c^2 w_j / (W (1 + c)),
+    # so pi_d(centre, leaf_j) = pi_d(leaf_j, centre) = c w_j / (1 + c) and
+    # pi_d(leaf_i, leaf_j) = c^2 w_i w_j / (W (1 + c)). With d = edge count
+    # or P normalised by the count instead, these values (and the symmetry)
+    # do not hold, since the weights below differ.
+    wts = [0.5, 1.0, 2.0, 3.5, 7.25]
+    L = len(wts)
+    n = L + 1
+    rp, col, w = _weighted_csr_from_edges(n, [(0, j + 1, wts[j]) for j in range(L)])
+    W = float(sum(wts))
+    d = O.degrees(n, rp, col, w)
+    assert abs(d[0] - W) < 1e-12 and np.allclose(d[1:], wts, atol=1e-12, rtol=0)
+    P = O.transition_matrix(n, rp, col, w)
+    Pi = O.ppr_rows(P, np.arange(n), ALPHA)
+    assert abs(Pi[0, 0] - 1 / (1 + C)) < 1e-14
+    for j in range(L):
+        assert abs(Pi[j + 1, 0] - C / (1 + C)) < 1e-14
+        assert abs(Pi[0, j + 1] - C * wts[j] / (W * (1 + C))) < 1e-14
+        for i in range(L):
+            exp = (ALPHA if i == j else 0.0) + C * C * wts[j] / (W * (1 + C))
+            assert abs(Pi[i + 1, j + 1] - exp) < 1e-14
+    D = O.dppr_rows(Pi, d, np.arange(n))
+    for j in range(L):
+        assert abs(D[0, j + 1] - C * wts[j] / (1 + C)) < 1e-13
+        assert abs(D[j + 1, 0] - C * wts[j] / (1 + C)) < 1e-13
+    assert abs(D[1, 4] - C * C * wts[0] * wts[3] / (W * (1 + C))) < 1e-14
+    # the same star read with d = edge count breaks the symmetry of pi_d
+    dc = O.degrees(n, rp, col)
+    Dc = O.dppr_rows(Pi, dc, np.arange(n))
+    assert np.abs(Dc - Dc.T).max() > 1e-2
+
+
+def test_weighted_graph_invariants():
+    # On a symmetric weighted graph the strength-weighted walk is reversible
+    # (s_v P(v, u) = w_vu = s_u P(u, v)), so pi_d is symmetric, every PPR row
+    # is a distribution, and sum_{s,t} pi_d(s, t) = sum_s d(s) = sum of all
+    # stored weights (Eq. (11) with m = sum_v d(v)).
+    g = synth.dense_clustered(120, blocks=4, density=0.2, seed=6)
+    assert g.weight is not None and np.ptp(g.weight) > 1.0
+    P = _graph_P(g)
+    d = O.degrees(g.n, g.row_ptr, g.col, g.weight)
+    Pi = O.ppr_direct(P, ALPHA)
+    D = O.dppr_rows(Pi, d, np.arange(g.n))
+    assert np.abs(Pi.sum(axis=1) - 1).max() < 1e-13
+    assert np.abs(D - D.T).max() < 1e-12 * max(1.0, np.abs(D).max())
+    m = float(np.asarray(g.weight, dtype=np.float64).sum())
+    assert abs(D.sum() - m) < 1e-11 * m
+    # P[i, j] = w_ij / s_i row by row
+    Pd = P.toarray()
+    for v in (0, 7, 63, 119):
+        lo, hi = g.row_ptr[v], g.row_ptr[v + 1]
+        if hi > lo:
+            ww = np.asarray(g.weight[lo:hi], dtype=np.float64)
+            assert np.allclose(Pd[v, g.col[lo:hi]], ww / ww.sum(), atol=1e-15, rtol=0)
+
+
 def test_invariants_on_random_graph():
     g = synth.chung_lu(300, 10, 2.5, seed=1)
     P = _graph_P(g)
