@@ -101,6 +101,10 @@ def parse():
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="also time the oracle sample on every host core (1) or not (0)")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the plain FP64 GPU path on the same workload (0 = skip)")
     ap.add_argument("--case", action="store_true",
                     help="one untimed pass of the hot path (for profiler command lines)")
     ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views"],
@@ -149,9 +153,15 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-def fp32_simt_tflops(sm_max_mhz):
-    """FP32 FMA peak from unit counts: 152 SMs x 4 SMSPs x 32 lanes x 2 flop x clock."""
-    return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+def tf32_tflops():
+    """Dense TF32 tensor peak: the measured BF16 peak (burst) x the nominal
+    TF32/BF16 ratio 1.1/2.25. Returns (TFLOP/s, how it was derived)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16, kind = 1900.0, "fallback"
+    if os.path.exists(p):
+        with open(p) as f:
+            bf16, kind = json.load(f)["bf16_tflops"], "measured"
+    return bf16 * 1.1 / 2.25, f"{kind} bf16_tflops x 1.1/2.25 (nominal TF32/BF16), frac of {kind}"
 
 
 def config(args, n_gpus):
@@ -244,21 +254,130 @@ def measured_traffic(cls):
 
 
 # --------------------------------------------------------------------------- reference arm
-def cpu_oracle_sample(g, n_src, seed=1):
-    """FP64 oracle on a bounded sample: DPPR rows of n_src sources and the
-    PDist rows they fix. Returns (entries, seconds)."""
+def cpu_oracle_rows(g, src, n_clamp=None):
+    """FP64 oracle on a bounded sample: the DPPR rows pi_d(s, .) of the
+    sources `src` and the PDist rows they fix (power iteration to
+    (1 - alpha)^(t+1) <= 1e-15 for rows and columns). Returns (DPPR rows,
+    PDist rows, z rows, seconds)."""
     import oracle as O
-    import synth
-    src = synth.sample_view(g.n, n_src, seed=seed)
     t0 = time.perf_counter()
-    Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
-    d = O.degrees(g.n, g.row_ptr, g.col)
+    Pm = O.transition_matrix(g.n, g.row_ptr, g.col, g.weight)
+    d = O.degrees(g.n, g.row_ptr, g.col, g.weight)
     rows = O.ppr_rows(Pm, src, ALPHA)
     cols = O.ppr_cols(Pm, src, ALPHA)
     D = O.dppr_rows(rows, d, src)
     Dc = (d[:, None] * cols).T
-    O.pdist_from_z(D + Dc, g.n)
-    return n_src * g.n, time.perf_counter() - t0
+    z = D + Dc
+    Dl = O.pdist_from_z(z, g.n if n_clamp is None else n_clamp)
+    Dl[np.arange(len(src)), src] = 0.0
+    return D, Dl, z, time.perf_counter() - t0
+
+
+def cpu_oracle_sample(g, n_src, seed=1):
+    """The oracle's DPPR rows of n_src seeded sources and the PDist rows they
+    fix, on one thread. Returns (entries, seconds)."""
+    import synth
+    src = synth.sample_view(g.n, n_src, seed=seed)
+    _, _, _, t = cpu_oracle_rows(g, src)
+    return n_src * g.n, t
+
+
+def _oracle_worker(args):
+    n, row_ptr, col, weight, src = args
+    import synth
+    g = synth.Graph(n, row_ptr, col, weight)
+    _, _, _, t = cpu_oracle_rows(g, src)
+    return len(src) * n, t
+
+
+def cpu_oracle_all_cores(g, n_src_per_core, seed=7):
+    """The same oracle sample on every host core: one process per core
+    (spawned, so it is safe after CUDA is initialised), each computing the
+    rows of its own n_src_per_core seeded sources. Returns (entries, wall
+    seconds of the parallel part, cores)."""
+    import multiprocessing as mp
+
+    import synth
+    cores = os.cpu_count() or 1
+    src = synth.sample_view(g.n, min(g.n, cores * n_src_per_core), seed=seed)
+    chunks = [src[i::cores] for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_pool_init) as pool:
+        pool.map(_pool_ping, range(cores))  # workers started and imported before the clock
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(g.n, g.row_ptr, g.col, g.weight, c) for c in chunks if len(c)])
+        wall = time.perf_counter() - t0
+    return sum(e for e, _ in res), wall, cores
+
+
+def _pool_init():
+    # one BLAS thread per worker: the pool itself is the parallelism
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    sys.path.insert(0, ROOT)
+    import oracle  # noqa: F401
+    import synth  # noqa: F401
+
+
+def _pool_ping(i):
+    return i
+
+
+def oracle_errors(g, src, D, Dl, cert):
+    """Per-result error of the GPU outputs against the oracle's rows of the
+    sampled sources (the CPU-baseline sample): DPPR max-abs and
+    max-abs / max(1, |ref|), PDist max-abs and the largest excess over the
+    certified PDist tolerance (<= 0 when every entry passes)."""
+    import math
+    Dref, Dlref, z, _ = cpu_oracle_rows(g, src)
+    Dg = np.asarray(D, dtype=np.float64)
+    Dlg = np.asarray(Dl, dtype=np.float64)
+    e_d = np.abs(Dg - Dref)
+    e_l = np.abs(Dlg - Dlref)
+    # the certified PDist tolerance of Eq. (1): 1e-5 + (c_s + c_t) / max(z - c_s - c_t, e / n^2)
+    # with z = pi_d(s, t) + pi_d(t, s) from the oracle's rows and columns
+    c = np.asarray(cert, dtype=np.float64)
+    cc = c[src][:, None] + c[None, :]
+    tol = 1e-5 + cc / np.maximum(z - cc, math.e / float(g.n) ** 2)
+    tol[np.arange(len(src)), src] = 1e-5
+    return {"sample_sources": len(src), "dppr_max_abs": float(e_d.max()),
+            "dppr_max_abs_over_max1": float((e_d / np.maximum(1.0, np.abs(Dref))).max()),
+            "pdist_max_abs": float(e_l.max()), "pdist_certified_gate_excess": float((e_l - tol).max()),
+            "max_cert": float(c.max())}
+
+
+def layout_update_error_bound(Dl, X0, X1):
+    """A bound on the error of one GPU stress-majorization update that needs
+    no oracle: with b = L^Y(X0) X0 and r = L^w X1 - b (both in FP64 on the
+    host, from the GPU's PDist), the exact centred update X* satisfies
+    |X1 - X*|_F <= |r|_F / lambda_2(L^w), and lambda_2(L^w) >= k w_min for
+    the complete-graph Laplacian L^w with weights w_ij = 1 / Delta_ij^2 >= w_min
+    (Appendix A.1, Eq. (10)). Returns (that bound, and the first Jacobi
+    estimate max_i |r_i| / L^w_ii of the error), both over max(1, max|X1|)."""
+    D = np.asarray(Dl, dtype=np.float64)
+    k = D.shape[0]
+    X0 = np.asarray(X0, dtype=np.float64)
+    X1 = np.asarray(X1, dtype=np.float64)
+    r = np.zeros((k, 2))
+    diag = np.zeros(k)
+    wmin = np.inf
+    for a in range(0, k, 1024):
+        Db = D[a:a + 1024]
+        off = np.ones_like(Db, dtype=bool)
+        off[np.arange(len(Db)), np.arange(a, a + len(Db))] = False
+        W = np.where(off, 1.0 / np.where(off, Db, 1.0) ** 2, 0.0)
+        wmin = min(wmin, float(W[off].min()))
+        diff0 = X0[a:a + len(Db), None, :] - X0[None, :, :]
+        d0 = np.sqrt((diff0 ** 2).sum(-1))
+        LY = np.where(off & (d0 > 0), 1.0 / (np.where(off, Db, 1.0) * np.where(d0 > 0, d0, 1.0)), 0.0)
+        b = (LY[:, :, None] * diff0).sum(1)
+        lw = (W[:, :, None] * (X1[a:a + len(Db), None, :] - X1[None, :, :])).sum(1)
+        r[a:a + len(Db)] = lw - b
+        diag[a:a + len(Db)] = W.sum(1)
+    scale = max(1.0, float(np.abs(X1).max()))
+    bound = float(np.sqrt((r ** 2).sum()) / (k * wmin))
+    jac = float((np.abs(r) / diag[:, None]).max())
+    return bound / scale, jac / scale
 
 
 def run_reference(args, rank, world):
@@ -518,12 +637,12 @@ def run_ours(args, rank, world, local_rank):
         if rec is not None:
             rec[2].record(stream)
         G.free()
-        assert status == 0 and cert.max() <= EPS, (status, cert.max())
-        return launches, sd, sl, s
+        return launches, sd, sl, s, status, cert
 
     for _ in range(args.warmup):
         flush.zero_()
-        step()
+        _, _, _, _, status, cert = step()
+        assert status == 0 and cert.max() <= EPS, (status, cert.max())
     torch.cuda.synchronize()
     barrier_if_group()
     torch.cuda.synchronize()
@@ -534,12 +653,15 @@ def run_ours(args, rank, world, local_rank):
     launches = 0
     bytes_sweep = bytes_ly = bytes_apply = flops_factor = 0.0
     sweeps = 0
+    statuses, certs = [], []
     wall0 = time.perf_counter()
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()  # outside the step's events
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        nl, sd, sl, stress = step(ev)
+        nl, sd, sl, stress, status, last_cert = step(ev)
+        statuses.append(status)
+        certs.append(float(last_cert.max()))
         launches += nl
         bytes_sweep += sd["bytes_sweep"]
         sweeps += sd["sweeps_main"] + sd["sweeps_refine"]
@@ -557,6 +679,8 @@ def run_ours(args, rank, world, local_rank):
     sampler.stop()
     ktimes = ctx.kernel_times()
     ctx.profile(False)
+    # every timed step converged and is certified within eps (checked after the clock)
+    assert all(st == 0 for st in statuses) and max(certs) <= EPS, (statuses, max(certs))
     total_ms = sum(step_ms)
     total_ms = max_over_ranks(total_ms, dev)
     entries = float(n) * n
@@ -571,23 +695,64 @@ def run_ours(args, rank, world, local_rank):
         D_h = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
         Dl_h = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
         X_h = torch.empty((n, 2), dtype=torch.float32).pin_memory().numpy()
-        e2e_ms = []
+        e2e_ms, e2e_st, e2e_cert = [], [], []
         for _ in range(args.e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             G = ctx.upload(n, rp_h, col_h)
-            ctx.dppr(G, view_h, ALPHA, EPS, P.FP32, dppr_out=D_h, pdist_out=Dl_h, cert=True)
+            _, _, cert_h, st_h = ctx.dppr(G, view_h, ALPHA, EPS, P.FP32, dppr_out=D_h, pdist_out=Dl_h, cert=True)
             ctx.layout(Dl_h, x0_p, args.iters, P.FP32, x_out=X_h, stress=True)
             G.free()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            e2e_st.append(st_h)
+            e2e_cert.append(float(cert_h.max()))
+        assert all(st == 0 for st in e2e_st) and max(e2e_cert) <= EPS, (e2e_st, max(e2e_cert))
         tot = sum(e2e_ms)
         tot = max_over_ranks(tot, dev)
         h2d = rp_h.nbytes + col_h.nbytes + view_h.nbytes + Dl_h.nbytes + x0_p.nbytes
         d2h = D_h.nbytes + Dl_h.nbytes + X_h.nbytes + 8 * n
         e2e = {"value": whole_job_rate(entries, args.e2e_steps, world, tot), "unit": "entries/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": tot / args.e2e_steps}
+               "ms_per_step": tot / args.e2e_steps, "max_cert": max(e2e_cert)}
+
+    # ---- the plain FP64 GPU path on the same workload and eps: FP64 power
+    # iteration (PPRVIZ_FP64) and the FP64 layout, device buffers, one step
+    fp64 = None
+    if args.fp64_steps > 0:
+        D64 = torch.empty((n, n), dtype=torch.float64, device=dev)
+        Dl64 = torch.empty((n, n), dtype=torch.float64, device=dev)
+        x64 = x0.double()
+        xo64 = torch.empty_like(x64)
+
+        def step64():
+            G = ctx.upload(n, rp, col)
+            _, _, c64, st64 = ctx.dppr(G, view, ALPHA, EPS, P.FP64, dppr_out=D64, pdist_out=Dl64, cert=True,
+                                       out64=True)
+            ctx.layout(Dl64, x64, args.iters, P.FP64, x_out=xo64, stress=True)
+            G.free()
+            return st64, float(c64.max())
+
+        step64()  # warm-up (workspace, first-use allocations)
+        ms64, st64s, c64s = [], [], []
+        for _ in range(args.fp64_steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st64, c64 = step64()
+            e1.record(stream)
+            e1.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+            st64s.append(st64)
+            c64s.append(c64)
+        assert all(st == 0 for st in st64s) and max(c64s) <= EPS, (st64s, max(c64s))
+        t64 = max_over_ranks(sum(ms64), dev) / len(ms64)
+        fp64 = {"value": whole_job_rate(entries, 1, world, t64), "unit": "entries/s", "ms_per_step": t64,
+                "steps": len(ms64), "max_cert": max(c64s), "speedup_of_fp32_step": t64 / (total_ms / args.steps),
+                "path": "FP64 power iteration (a-priori sweep count) + FP64 residual certificate; FP64 PDist; "
+                        "FP64 L^w inverse and layout passes; same graph, view, eps, iterations"}
+        del D64, Dl64
 
     if rank != 0:
         return
@@ -611,25 +776,41 @@ def run_ours(args, rank, world, local_rank):
                         "traffic": measured_traffic(cls)}
     ms, cnt, timed = ktimes["factor"]
     if timed and ms > 0 and flops_factor > 0:
-        fp32_peak = fp32_simt_tflops(sm_max)
+        tf32, tf_kind = tf32_tflops()
         per = flops_factor / cnt
         ach = per / (ms / timed / 1e3) / 1e12
-        kernels["factor"] = {"kernel": "L^w build + inverse: symmetric block sweep with lookahead (k_fac_*)",
-                             "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                             "frac": ach / fp32_peak, "launches": cnt, "timed_launches": timed,
+        kernels["factor"] = {"kernel": "L^w build + inverse: symmetric block sweep with lookahead (k_fac_*); "
+                                       "trailing update on tcgen05.mma kind::tf32 (3xTF32)",
+                             "bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
+                             "frac": ach / tf32, "issued_frac_3xtf32": 3 * ach / tf32,
+                             "launches": cnt, "timed_launches": timed,
                              "avg_launch_us": 1e3 * ms / timed, "alg_flops_per_launch": per,
-                             "traffic": measured_traffic("factor"),
-                             "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+                             "traffic": measured_traffic("factor"), "peak_kind": tf_kind}
     share = class_share(ktimes, args.steps)
     dom = max(kernels, key=lambda c: share[c]["ms"]) if kernels else None
     roof = dict(kernels[dom]) if dom else None
     if roof is not None and roof["bound"] == "hbm":
         roof["peak_kind"] = f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"
-    cpu = None
+    cpu, errors = None, None
     if world == 1 and not args.no_cpu_baseline:
         e, t = cpu_oracle_sample(g, 16)
         cpu = {"value": e / t, "unit": "entries/s", "cores": 1, "kind": "oracle",
                "sample": "16 seeded sources: FP64 DPPR rows + PDist rows by power iteration (scipy sparse, 1 thread)"}
+        if args.cpu_all_cores:
+            ea, ta, cores = cpu_oracle_all_cores(g, 16)
+            cpu["all_cores"] = {"value": ea / ta, "unit": "entries/s", "cores": cores,
+                                "sample": f"{cores} x 16 seeded sources, one spawned process per core"}
+        # per-result error of the last timed step's outputs against the oracle's rows
+        src = synth.sample_view(n, 16, seed=1)
+        errors = oracle_errors(g, src, D[torch.from_numpy(src).to(dev).long()].cpu().numpy(),
+                               Dl[torch.from_numpy(src).to(dev).long()].cpu().numpy(), last_cert)
+        # one layout update from X0 on the step's PDist: error bound of the exact update
+        x1 = torch.empty_like(x0)
+        ctx.layout(Dl, x0, 1, P.FP32, x_out=x1, stress=False)
+        bnd, jac = layout_update_error_bound(Dl.cpu().numpy(), x0_h, x1.cpu().numpy())
+        errors["layout_one_update_err_bound"] = bnd
+        errors["layout_one_update_err_jacobi_estimate"] = jac
+        errors["max_cert_timed_steps"] = max(certs)
     line = {
         "metric": "DPPR entries/s at n=10k, err<=1e-6 vs FP64; layout iters/s; % HBM roofline",
         "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -641,7 +822,7 @@ def run_ours(args, rank, world, local_rank):
                    "sweeps_per_step": sweeps / args.steps, "final_stress": stress,
                    "wall_s_timed_region": wall},
         "roofline": roof, "roofline_kernels": kernels, "kernel_share": share,
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches), "errors": errors, "vs_fp64_gpu": fp64,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": sampler.summary(),
     }
     print(json.dumps(line), flush=True)

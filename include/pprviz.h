@@ -266,14 +266,18 @@ int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *cons
  * pdist, x:   device pointers (k*k and k*2 float), as in pprviz_energy.
  * grad_x, grad_pdist: device outputs or NULL; e_out: host double or NULL.
  * cuda_stream: the stream to run on (NULL = the legacy default stream); the
- *             call waits for it before returning. No context is needed.
+ *             call waits for that stream before it returns, to read back the
+ *             energy and the status word. No context is needed: the call runs
+ *             on the current device, in its primary context (the one the CUDA
+ *             runtime API uses).
  * Scratch: a fixed device array inside the library (about 528 KiB, held by
  * every GPU that loads the library until the process exits), so k is limited
  * to 65,536. The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture. Every call shares the array and the calls clear what
- * must start at zero, but calls that overlap on the GPU (two streams, two
- * threads) race on it and must be serialised by the caller.
+ * in that device's primary context (once per device, with that device
+ * current); make that first call on each device before any stream capture.
+ * Every call shares the array and the calls clear what must start at zero,
+ * but calls that overlap on the GPU (two streams, two threads) race on it
+ * and must be serialised by the caller.
  * Returns PPRVIZ_OK, PPRVIZ_E_INVALID_ARG (NULL input, k outside [1, 65536],
  * a non-positive off-diagonal distance) or PPRVIZ_E_CUDA; no error message is
  * kept since there is no context. */

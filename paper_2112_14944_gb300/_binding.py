@@ -227,12 +227,41 @@ def pprviz_views_batch(ctx, graphs, offsets, alpha, eps, iters, x0_packed, pdist
                   allow=(PPRVIZ_E_NOT_CONVERGED,))
 
 
+def _check_noalloc_buffers(k, pdist, x, grad_x, grad_pdist):
+    """The C entry point has no context and sees only pointers, so the sizes,
+    element type and device of its buffers are checked here: float32 torch
+    tensors holding at least k*k (pdist, grad_pdist) or k*2 (x, grad_x)
+    elements, all on the current CUDA device. k outside [1, 65536] is left to
+    the library, which rejects it with PPRVIZ_E_INVALID_ARG."""
+    if pdist is None or x is None:
+        raise ValueError("pprviz_energy_noalloc needs pdist and x")
+    k = int(k)
+    need = {"pdist": (pdist, k * k), "x": (x, 2 * k), "grad_x": (grad_x, 2 * k), "grad_pdist": (grad_pdist, k * k)}
+    given = [(name, b, n) for name, (b, n) in need.items() if b is not None]
+    for name, b, _ in given:
+        if not _is_torch(b):
+            raise ValueError(f"pprviz_energy_noalloc: {name} must be a torch CUDA tensor")
+        if str(b.dtype) != "torch.float32":
+            raise ValueError(f"pprviz_energy_noalloc: {name} must be float32, got {b.dtype}")
+        if not b.is_contiguous():
+            raise ValueError(f"pprviz_energy_noalloc: {name} must be contiguous")
+    for name, b, n in given:
+        if k >= 1 and b.numel() < n:
+            raise ValueError(f"pprviz_energy_noalloc: {name} holds {b.numel()} elements, needs {n}")
+    for name, b, _ in given:
+        if not b.is_cuda:
+            raise ValueError(f"pprviz_energy_noalloc: {name} must be a device buffer")
+        import torch
+        if b.device.index != torch.cuda.current_device():
+            raise ValueError(f"pprviz_energy_noalloc: {name} is on cuda:{b.device.index}, "
+                             f"the current device is cuda:{torch.cuda.current_device()}")
+
+
 def pprviz_energy_noalloc(pdist, k, x, grad_scale=1.0, grad_x=None, grad_pdist=None, cuda_stream=None):
-    """Energy and gradients through the allocation-free entry point: device
-    (torch CUDA) buffers only, no context. Returns (status, energy)."""
-    for b in (pdist, x, grad_x, grad_pdist):
-        if b is not None and not _ptr(b)[1]:
-            raise ValueError("pprviz_energy_noalloc takes device buffers only")
+    """Energy and gradients through the allocation-free entry point: float32
+    device (torch CUDA) buffers on the current device only, no context.
+    Returns (status, energy)."""
+    _check_noalloc_buffers(k, pdist, x, grad_x, grad_pdist)
     e = C.c_double(0.0)
     st = load().pprviz_energy_noalloc(_ptr(pdist)[0], int(k), _ptr(x)[0], float(grad_scale), C.byref(e),
                                       _ptr(grad_x)[0], _ptr(grad_pdist)[0], cuda_stream)

@@ -45,3 +45,17 @@ def check_dppr(got, ref, tol=1e-6):
     err = np.abs(np.asarray(got, dtype=np.float64) - ref) / np.maximum(1.0, np.abs(ref))
     assert err.max() <= tol, f"max rel-abs DPPR error {err.max():.3e}"
     return float(err.max())
+
+
+def oracle_dppr(g, alpha=0.15):
+    """All-pairs DPPR of a graph by the oracle's direct solve (Sec. 3.1,
+    Definition 1): Pi = alpha (I - (1 - alpha) P)^-1, rows scaled by d(s)."""
+    P = O.transition_matrix(g.n, g.row_ptr, g.col, g.weight)
+    d = O.degrees(g.n, g.row_ptr, g.col, g.weight)
+    return O.dppr_rows(O.ppr_direct(P, alpha), d, np.arange(g.n))
+
+
+def oracle_pdist(g, alpha=0.15, n_clamp=None):
+    """The oracle's all-pairs PDist of a graph (Eq. (1)), FP64: the input of
+    the layout parity tests, so that no oracle input comes from the GPU."""
+    return O.pdist_from_dppr(oracle_dppr(g, alpha), g.n if n_clamp is None else n_clamp)

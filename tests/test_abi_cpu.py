@@ -81,3 +81,31 @@ def test_product_path_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_noalloc_binding_rejects_bad_buffers_before_the_call():
+    """The allocation-free entry point has no context to check buffers
+    against, so its binding rejects wrong types, short buffers and host
+    buffers before any C call (the C call is never reached here)."""
+    torch = pytest.importorskip("torch")
+    from paper_2112_14944_gb300 import _binding as B
+    k = 8
+    ok_d, ok_x = torch.zeros(k * k), torch.zeros(k * 2)
+    with pytest.raises(ValueError, match="float32"):
+        B._check_noalloc_buffers(k, torch.zeros(k * k, dtype=torch.float64), ok_x, None, None)
+    with pytest.raises(ValueError, match="float32"):
+        B._check_noalloc_buffers(k, ok_d, ok_x, torch.zeros(k * 2, dtype=torch.float16), None)
+    with pytest.raises(ValueError, match="needs 64"):
+        B._check_noalloc_buffers(k, torch.zeros(k * k - 1), ok_x, None, None)
+    with pytest.raises(ValueError, match="needs 16"):
+        B._check_noalloc_buffers(k, ok_d, torch.zeros(15), None, None)
+    with pytest.raises(ValueError, match="needs 16"):
+        B._check_noalloc_buffers(k, ok_d, ok_x, torch.zeros(3), None)
+    with pytest.raises(ValueError, match="needs 64"):
+        B._check_noalloc_buffers(k, ok_d, ok_x, None, torch.zeros(10))
+    with pytest.raises(ValueError, match="device buffer"):
+        B._check_noalloc_buffers(k, ok_d, ok_x, None, None)       # host tensors
+    with pytest.raises(ValueError, match="torch CUDA tensor"):
+        B._check_noalloc_buffers(k, np.zeros(k * k, np.float32), ok_x, None, None)
+    with pytest.raises(ValueError, match="needs pdist and x"):
+        B._check_noalloc_buffers(k, None, ok_x, None, None)

@@ -308,9 +308,15 @@ def test_full_size_view_of_2m_graph_sampled(ctx):
     asym = np.abs(D - D.T) / np.maximum(1.0, np.abs(D))
     assert asym.max() <= 2e-6
     # energy and gradient of a layout of the whole view (pair recomputation)
+    # on a seeded symmetric target in the PDist range [2, 2 ln n] (an oracle
+    # input never comes from the GPU)
+    r = synth.uniform(7, 21, np.arange(k * k, dtype=np.uint64)).reshape(k, k)
+    Dsyn = (2.0 + (2.0 * math.log(g.n) - 2.0) * (r + r.T) / 2.0).astype(np.float32)
+    np.fill_diagonal(Dsyn, 0.0)
+    del r
     X = synth.uniform_x0(k, seed=0) * 8.0
-    e, gx, _ = ctx.energy(Delta, X, grad_scale=1.0, grad_x=True)
-    Dd, Xd = Delta.astype(np.float64), X.astype(np.float64)
+    e, gx, _ = ctx.energy(Dsyn, X, grad_scale=1.0, grad_x=True)
+    Dd, Xd = Dsyn.astype(np.float64), X.astype(np.float64)
     e_ref = O.stress(Xd, Dd)
     assert abs(e - e_ref) <= 2e-5 * e_ref
     g_ref = O.stress_grad(Xd, Dd)[pos]

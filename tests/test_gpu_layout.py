@@ -20,6 +20,12 @@ Tolerances:
                finite and centred. The batched propagation advances many views'
                sources in shared launches; each view's PDist is gated
                against the oracle with its own certificates.
+  Batched FP32 layout vs the oracle: with a tight eps (1e-9) one batched
+               update of each checked view matches the oracle's update on the
+               oracle's PDist within 1e-4 * max(1, |X|_max), and (small views)
+               the final stress after 40 updates within 1e-3 of the oracle's.
+Every oracle input (PDist, coordinates) comes from the oracle or the seeded
+generators, never from the GPU.
 """
 import math
 
@@ -28,7 +34,7 @@ import pytest
 
 import oracle as O
 import synth
-from _parity import check_pdist
+from _parity import check_pdist, oracle_dppr, oracle_pdist
 
 pytestmark = pytest.mark.gpu
 ALPHA = 0.15
@@ -42,13 +48,9 @@ def ctx():
     c.close()
 
 
-def _pdist_for(ctx, n, mean_deg, seed, out64):
-    import paper_2112_14944_gb300 as P
-    g = synth.chung_lu(n, mean_deg, 2.5, seed=seed)
-    G = ctx.upload_graph(g)
-    _, Delta, _, _ = ctx.dppr(G, np.arange(n, dtype=np.int32), ALPHA, 1e-6, P.FP64 if out64 else P.FP32,
-                              out64=out64)
-    return Delta
+def _pdist_for(n, mean_deg, seed):
+    """The oracle's FP64 PDist of a seeded Chung-Lu graph (exponent 2.5)."""
+    return oracle_pdist(synth.chung_lu(n, mean_deg, 2.5, seed=seed), ALPHA)
 
 
 def _rel(a, b):
@@ -80,7 +82,7 @@ def _same_trajectory(X1, Xb, s1, sb):
 def test_layout_fp64_config_small_full_trajectory(ctx):
     """n = 1,000 Chung-Lu (mean degree 10), 300 updates from U[-1,1]^2, FP64."""
     import paper_2112_14944_gb300 as P
-    Delta = _pdist_for(ctx, 1000, 10, 0, out64=True)
+    Delta = _pdist_for(1000, 10, 0)
     x0 = synth.uniform_x0(1000, seed=0).astype(np.float64)
     X, stress = ctx.layout(Delta, x0, 300, P.FP64)
     Xr, hist = O.smacof(x0, Delta, 300)
@@ -90,7 +92,7 @@ def test_layout_fp64_config_small_full_trajectory(ctx):
 
 def test_layout_fp32_one_step_matches_oracle(ctx):
     import paper_2112_14944_gb300 as P
-    Delta32 = _pdist_for(ctx, 1500, 10, 3, out64=False)
+    Delta32 = _pdist_for(1500, 10, 3).astype(np.float32)
     D64 = Delta32.astype(np.float64)
     Xt, _ = O.smacof(synth.uniform_x0(1500, seed=1), D64, 15)
     X1, _ = ctx.layout(Delta32, Xt.astype(np.float32), 1, P.FP32)
@@ -99,10 +101,34 @@ def test_layout_fp32_one_step_matches_oracle(ctx):
     assert err <= 1e-4, err
 
 
+@pytest.mark.parametrize("n", [5000, 10000])
+def test_layout_fp32_one_update_bench_scale(ctx, n):
+    """One FP32 update at the benchmark's sizes against the oracle's update
+    (Eq. (10), pinned Cholesky solve) on the oracle's PDist of the benchmark
+    graph family (Chung-Lu, mean degree 20, exponent 2.5, seed 0). At
+    n = 10,000 (kp = 10,112) the L^w inverse runs its 79 pivot steps with the
+    lookahead, and each persistent layout-pass CTA streams ~21 of the 3,160
+    upper tiles (column runs across chunk boundaries, L2-resident and streamed
+    tiles, many run slots per reduce); at n = 5,000, 40 pivots. Two updates
+    are checked: from the seeded U[-1,1]^2 start (the benchmark's first
+    update) and from the oracle's first update."""
+    import paper_2112_14944_gb300 as P
+    D32 = _pdist_for(n, 20, 0).astype(np.float32)
+    D64 = D32.astype(np.float64)
+    X = synth.uniform_x0(n, seed=0).astype(np.float64)
+    for _ in range(2):
+        Xin = X.astype(np.float32)
+        Xg, _ = ctx.layout(D32, Xin, 1, P.FP32)
+        ref = O.smacof_step(Xin.astype(np.float64), D64)
+        err = np.abs(Xg - ref).max() / max(1.0, np.abs(ref).max())
+        assert err <= 1e-4, err
+        X = ref
+
+
 def test_layout_fp32_trajectory_properties(ctx):
     import paper_2112_14944_gb300 as P
     n = 800
-    Delta32 = _pdist_for(ctx, n, 10, 4, out64=False)
+    Delta32 = _pdist_for(n, 10, 4).astype(np.float32)
     x0 = synth.uniform_x0(n, seed=4)
     prev = math.inf
     for it in (0, 1, 5, 20, 60, 150):
@@ -149,7 +175,7 @@ def test_layout_rejects_bad_pdist(ctx):
 @pytest.mark.parametrize("dt,tol", [(np.float64, 1e-11), (np.float32, 2e-5)])
 def test_energy_and_gradients_match_oracle(ctx, dt, tol):
     k = 300
-    Delta = _pdist_for(ctx, k, 8, 7, out64=True)
+    Delta = _pdist_for(k, 8, 7)
     X = (synth.uniform_x0(k, seed=3).astype(np.float64) * 4.0)
     X[7] = X[8]  # a coincident pair: its gradient term is 0
     e, gx, gd = ctx.energy(Delta.astype(dt), X.astype(dt), grad_scale=0.5, grad_x=True, grad_pdist=True)
@@ -167,7 +193,7 @@ def test_autograd_function_gradcheck():
     import paper_2112_14944_gb300 as P
     c = P.Context(0, torch_stream=True)
     k = 10
-    D = torch.tensor(_pdist_for(c, 30, 4, 8, out64=True)[:k, :k], device="cuda")
+    D = torch.tensor(_pdist_for(30, 4, 8)[:k, :k], device="cuda")
     X = torch.tensor(synth.uniform_x0(k, seed=5).astype(np.float64) * 3, device="cuda")
     Xr = X.clone().requires_grad_(True)
     Dr = D.clone().requires_grad_(True)
@@ -180,7 +206,7 @@ def test_gradient_finite_differences_subview_512(ctx):
     """Energy backward against central finite differences of the energy on an
     n=512 sub-view (the differentiable-layout gradient check), FP64."""
     k = 512
-    D = _pdist_for(ctx, 2048, 10, 5, out64=True)[:k, :k].copy()
+    D = _pdist_for(2048, 10, 5)[:k, :k].copy()
     X = synth.uniform_x0(k, seed=6).astype(np.float64) * 5
     _, gx, _ = ctx.energy(D, X, grad_x=True)
     g_ref = O.stress_grad(X, D)
@@ -196,9 +222,26 @@ def test_gradient_finite_differences_subview_512(ctx):
 
 
 def _views_oracle(g):
-    n = g.n
-    return O.dppr_rows(O.ppr_direct(O.transition_matrix(n, g.row_ptr, g.col), ALPHA),
-                       O.degrees(n, g.row_ptr, g.col), np.arange(n))
+    return oracle_dppr(g, ALPHA)
+
+
+def _batched_update_vs_oracle(ctx, graphs, G, x0, pick, eps=1e-9):
+    """One batched FP32 update of each picked view against the oracle's update
+    (Eq. (10)) from the same start on the oracle's PDist of the view. The
+    batch computes its own PDist; with a tight eps its certified error is
+    ~1e-5 or less on all but the entries near the upper clamp, far inside the
+    layout gate, so the batched update must match the oracle's within
+    1e-4 * max(1, |X|_max)."""
+    torch_in = not isinstance(x0, np.ndarray)
+    xb1, _, _, off, cert = ctx.views_batch(G, x0, ALPHA, eps, 1, want_pdist=False, want_cert=True)
+    assert np.all(cert <= eps)
+    xb1 = xb1.cpu().numpy() if torch_in else xb1
+    x0h = x0.cpu().numpy() if torch_in else x0
+    for v in pick:
+        D64 = oracle_pdist(graphs[v], ALPHA).astype(np.float32).astype(np.float64)
+        ref = O.smacof_step(x0h[off[v]:off[v + 1]].astype(np.float64), D64)
+        err = np.abs(xb1[off[v]:off[v + 1]] - ref).max() / max(1.0, np.abs(ref).max())
+        assert err <= 1e-4, (v, graphs[v].n, err)
 
 
 def test_views_batch_matches_single_views(ctx):
@@ -232,6 +275,14 @@ def test_views_batch_matches_single_views(ctx):
         X1, s1 = ctx.layout(pdb[sq:sq + n * n].reshape(n, n).copy(), x0[off[v]:off[v + 1]].copy(), 1, P.FP32)
         _same_layout(X1, xb1[off[v]:off[v + 1]], s1, stress1[v], 1e-5)
         sq += n * n
+    # against the oracle: one update of every view, and after 40 updates the
+    # final stress (the trajectory gate of the FP32 layout)
+    _batched_update_vs_oracle(ctx, graphs, G, x0, range(len(graphs)))
+    xt, _, st_t, _ = ctx.views_batch(G, x0, ALPHA, 1e-9, 40, want_pdist=False)
+    for v, g in enumerate(graphs):
+        D64 = oracle_pdist(g, ALPHA).astype(np.float32).astype(np.float64)
+        _, hist = O.smacof(x0[off[v]:off[v + 1]].astype(np.float64), D64, 40)
+        assert abs(st_t[v] - hist[-1]) <= 1e-3 * hist[-1], (v, st_t[v], hist[-1])
 
 
 def test_views_batch_waves_edge_cases(ctx):
@@ -307,6 +358,7 @@ def test_views_batch_sbm_sample_of_the_batched_workload(ctx):
     for v, g in enumerate(graphs):
         X1, s1 = ctx.layout(pdb[sq[v]:sq[v + 1]].reshape(g.n, g.n).copy(), x0[off[v]:off[v + 1]].copy(), 1, P.FP32)
         _same_layout(X1, xb1[off[v]:off[v + 1]], s1, stress1[v], 1e-5)
+    _batched_update_vs_oracle(ctx, graphs, G, x0, sorted({0, big, len(graphs) - 1}))
 
 
 def test_views_batch_full_size_sbm_workload_sampled(ctx):
@@ -343,3 +395,5 @@ def test_views_batch_full_size_sbm_workload_sampled(ctx):
         _same_trajectory(X1, xb[off[v]:off[v + 1]], s1, stress[v])
         X1, s1 = ctx.layout(Pd, x0[off[v]:off[v + 1]].copy(), 1, P.FP32)
         _same_layout(X1, xb1[off[v]:off[v + 1]], s1, stress1[v], 1e-5)
+    # one batched update of the sampled views against the oracle's update
+    _batched_update_vs_oracle(ctx, graphs, G, torch.from_numpy(x0).cuda(), pick)
