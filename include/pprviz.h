@@ -119,6 +119,14 @@ typedef struct pprviz_stats {
  * Errors: E_INVALID_ARG (out == NULL, bad device), E_CUDA. */
 int pprviz_create(pprviz_ctx **out, int device, void *cuda_stream);
 void pprviz_destroy(pprviz_ctx *ctx);
+/* Cap the device workspace of a context (a library convenience; the paper
+ * has no counterpart): the buffers the context allocates for its calls
+ * (staging, propagation state, matrices of the layout) may hold at most
+ * `bytes` in all; 0 removes the cap. A call whose workspace would exceed it
+ * fails with PPRVIZ_E_OOM before allocating, and the context stays usable
+ * (buffers already held are kept). Graph objects and caller buffers are not
+ * counted. Errors: E_INVALID_ARG (ctx NULL, bytes < 0). */
+int pprviz_set_workspace_limit(pprviz_ctx *ctx, int64_t bytes);
 const char *pprviz_last_error(const pprviz_ctx *ctx);
 /* Wait for all work enqueued on the context stream. */
 int pprviz_sync(pprviz_ctx *ctx);

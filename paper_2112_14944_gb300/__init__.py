@@ -101,6 +101,11 @@ class Context:
         except Exception:
             pass
 
+    def set_workspace_limit(self, nbytes: int):
+        """Cap the context's device workspace (0 = no cap); calls that would
+        exceed it fail with E_OOM."""
+        B.pprviz_set_workspace_limit(self.h, nbytes)
+
     def stats(self) -> dict:
         return B.pprviz_get_stats(self.h)
 

@@ -41,6 +41,7 @@ _VP = C.c_void_p
 _SIGS = {
     "pprviz_create": (C.c_int, [C.POINTER(_VP), C.c_int, _VP]),
     "pprviz_destroy": (None, [_VP]),
+    "pprviz_set_workspace_limit": (C.c_int, [_VP, C.c_int64]),
     "pprviz_last_error": (C.c_char_p, [_VP]),
     "pprviz_sync": (C.c_int, [_VP]),
     "pprviz_get_stats": (C.c_int, [_VP, _VP]),
@@ -147,6 +148,10 @@ def pprviz_destroy(ctx: int) -> None:
     load().pprviz_destroy(ctx)
 
 
+def pprviz_set_workspace_limit(ctx: int, nbytes: int) -> None:
+    _check(ctx, load().pprviz_set_workspace_limit(ctx, int(nbytes)))
+
+
 def pprviz_last_error(ctx: int) -> str:
     m = load().pprviz_last_error(ctx)
     return m.decode() if m else ""
@@ -246,7 +251,7 @@ def _check_noalloc_buffers(k, pdist, x, grad_x, grad_pdist):
         if not b.is_contiguous():
             raise ValueError(f"pprviz_energy_noalloc: {name} must be contiguous")
     for name, b, n in given:
-        if k >= 1 and b.numel() < n:
+        if 1 <= k <= 65536 and b.numel() < n:
             raise ValueError(f"pprviz_energy_noalloc: {name} holds {b.numel()} elements, needs {n}")
     for name, b, _ in given:
         if not b.is_cuda:

@@ -23,6 +23,16 @@ int cuda_err(pprviz_ctx *ctx, cudaError_t e, const char *what) {
 }
 
 int ws_ensure(pprviz_ctx *ctx, int slot, size_t bytes) {
+  if (ctx->ws_limit && !(bytes <= ctx->ws[slot].cap && ctx->ws[slot].p)) {
+    // the slot grows: its old capacity is released and `bytes` taken
+    size_t used = 0;
+    for (int q = 0; q < WS_COUNT; ++q)
+      if (q != slot) used += ctx->ws[q].cap;
+    if (used + bytes > ctx->ws_limit)
+      return set_err(ctx, PPRVIZ_E_OOM,
+                     "device workspace limit: " + std::to_string(used + bytes) + " bytes needed, limit " +
+                         std::to_string(ctx->ws_limit));
+  }
   cudaError_t e = ctx->ws[slot].ensure(bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free allocation error
@@ -132,6 +142,12 @@ int pprviz_create(pprviz_ctx **out, int device, void *cuda_stream) {
     ctx->own_stream = true;
   }
   *out = ctx;
+  return PPRVIZ_OK;
+}
+
+int pprviz_set_workspace_limit(pprviz_ctx *ctx, int64_t bytes) {
+  if (!ctx || bytes < 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "bad context or negative limit");
+  ctx->ws_limit = (size_t)bytes;
   return PPRVIZ_OK;
 }
 

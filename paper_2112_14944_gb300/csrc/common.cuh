@@ -72,6 +72,7 @@ struct pprviz_ctx {
   cudaEvent_t ev_t1 = nullptr, ev_dp = nullptr;
   std::string err;
   pprviz::DevBuf ws[pprviz::WS_COUNT];
+  size_t ws_limit = 0;  // cap on the summed workspace capacity (0 = none); pprviz_set_workspace_limit
   pprviz_stats stats{};
   int launches = 0;  // kernels launched in the current call
   // source-group widths chosen by the sweep autotuner, by graph size class
