@@ -22,9 +22,10 @@ per step (DPPR + PDist + 200 layout updates of every view).
 `--workload dense` measures the dense-view propagation instead (not the
 default line): a dense clustered weighted view, n = 20,000, 20 blocks, 15 %
 density, lognormal(0, 1) weights, all nodes as the view; one step = all-pairs
-DPPR + PDist with the FP64 certificate, every sweep a 3xTF32 tensor-core
-contraction; the roofline is the tensor pipe's (TF32 peak = measured BF16
-peak x the nominal TF32/BF16 ratio 1.1/2.25).
+DPPR + PDist with the FP64 certificate, every sweep a BF16 x BF16 -> FP32
+tensor-core contraction with FP32 refinement (`--dense-precision tf32x3`: the
+3xTF32 sweeps; the other mode is timed beside it); the roofline is the tensor
+pipe's against the measured BF16 peak (TF32: x the nominal ratio 1.1/2.25).
 """
 from __future__ import annotations
 
@@ -107,6 +108,8 @@ def parse():
                     help="timed steps of the plain FP64 GPU path on the same workload (0 = skip)")
     ap.add_argument("--case", action="store_true",
                     help="one untimed pass of the hot path (for profiler command lines)")
+    ap.add_argument("--dense-precision", default="bf16", choices=["bf16", "tf32x3"],
+                    help="tensor-core sweep operands of --workload dense (the other mode is timed beside it)")
     ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views"],
                     help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000); "
                          "views: the 256 batched SBM views")
@@ -438,6 +441,10 @@ def run_dense_case(args):
 
 
 def run_dense(args, rank, world, local_rank):
+    """The dense weighted view: all-pairs DPPR + PDist with the FP64
+    certificate, every sweep a tensor-core contraction. The line's mode is
+    BF16 x BF16 -> FP32 (kind::f16) with FP32 refinement; the 3xTF32 mode is
+    timed beside it on the same view."""
     import torch
 
     import paper_2112_14944_gb300 as P
@@ -455,39 +462,51 @@ def run_dense(args, rank, world, local_rank):
     Dl = torch.empty_like(D)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     G = ctx.upload(n, rp, col, w)
+    modes = {"bf16": P.FP32_BF16TC, "tf32x3": P.FP32_TC}
+    main = args.dense_precision
+    other = "tf32x3" if main == "bf16" else "bf16"
 
-    def step():
-        _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
-        assert status == 0 and cert.max() <= EPS, (status, cert.max())
-        return ctx.stats()
+    def step(prec):
+        _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, prec, dppr_out=D, pdist_out=Dl, cert=True)
+        return ctx.stats(), status, float(cert.max())
+
+    def timed(prec, steps, prof):
+        if prof:
+            ctx.profile(PROF_EVERY)
+        ms, flops, launches, sweeps, stats, sts, certs = [], 0.0, 0, 0, None, [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, st, cm = step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            sts.append(st)
+            certs.append(cm)
+            flops += stats["flops_dense"]
+            launches += stats["kernel_launches"]
+            sweeps += stats["sweeps_main"] + stats["sweeps_refine"]
+        kt = ctx.kernel_times() if prof else None
+        if prof:
+            ctx.profile(False)
+        assert all(x == 0 for x in sts) and max(certs) <= EPS, (sts, max(certs))
+        return ms, flops, launches, sweeps, stats, kt, max(certs)
 
     for _ in range(args.warmup):
-        step()
+        step(modes[main])
+    step(modes[other])
     torch.cuda.synchronize()
     barrier_if_group()
     torch.cuda.synchronize()
-    ctx.profile(PROF_EVERY)
     sampler = ClockSampler(local_rank)
     sampler.start()
-    ms, flops, launches, sweeps, stats = [], 0.0, 0, 0, None
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        stats = step()
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        flops += stats["flops_dense"]
-        launches += stats["kernel_launches"]
-        sweeps += stats["sweeps_main"] + stats["sweeps_refine"]
+    ms, flops, launches, sweeps, stats, ktimes, cmax = timed(modes[main], args.steps, True)
     torch.cuda.synchronize()
     sampler.stop()
-    ktimes = ctx.kernel_times()
-    ctx.profile(False)
-    total = sum(ms)
-    total = max_over_ranks(total, dev)
+    total = max_over_ranks(sum(ms), dev)
+    ms_o, fl_o, _, sw_o, st_o, _, cm_o = timed(modes[other], 1, False)
     if rank != 0:
         return
     entries = float(n) * n
@@ -497,27 +516,39 @@ def run_dense(args, rank, world, local_rank):
         with open(pk) as f:
             bf16, kind = json.load(f)["bf16_tflops"], "measured"
     tf32 = bf16 * 1.1 / 2.25
+    peak = bf16 if main == "bf16" else tf32
     sw_ms, sw_all, sw_n = ktimes["sweep"]
     ach = flops / sw_all * sw_n / (sw_ms / 1e3) / 1e12  # flops of the timed launches / their time
-    roof = {"kernel": "tensor-core sweep (k_dsweep_tc, 3xTF32 tcgen05.mma)", "bound": "tensor",
-            "achieved": ach, "peak": tf32, "unit": "TFLOP/s", "frac": ach / tf32,
-            "executed_tflops": 3 * ach, "executed_frac": 3 * ach / tf32,
+    issued = 1 if main == "bf16" else 3
+    roof = {"kernel": ("tensor-core sweep (k_dsweep_tc, BF16 x BF16 -> FP32 tcgen05.mma kind::f16)" if main == "bf16"
+                       else "tensor-core sweep (k_dsweep_tc, 3xTF32 tcgen05.mma kind::tf32)"),
+            "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "executed_tflops": issued * ach, "executed_frac": issued * ach / peak,
             "launches": sw_all, "timed_launches": sw_n, "avg_launch_us": 1e3 * sw_ms / max(1, sw_n),
             "alg_flops_per_launch": flops / max(1, sw_all), "traffic": measured_traffic("dsweep"),
-            "peak_kind": f"{kind} bf16_tflops x 1.1/2.25 (nominal TF32/BF16), frac of {kind}"}
+            "peak_kind": (f"{kind} bf16_tflops, frac of {kind}" if main == "bf16" else
+                          f"{kind} bf16_tflops x 1.1/2.25 (nominal TF32/BF16), frac of {kind}")}
     share = class_share(ktimes, args.steps)
     line = {
         "metric": "DPPR entries/s, dense weighted view n=20k, err<=1e-6 vs FP64 (tensor-core sweeps)",
         "value": whole_job_rate(entries, args.steps, world, total), "unit": "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3/f32/f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32/f64" if main == "bf16" else "tf32x3/f32/f64",
+        "data": "synthetic",
         "config": {"workload": DENSE_WORKLOAD, "graph": "dense clustered SBM, lognormal(0,1) weights", "n": n,
                    "nnz": int(g.nnz), "blocks": 20, "density": 0.15, "seed": 0, "view": "all nodes (k = n)",
                    "alpha": ALPHA, "eps": EPS,
-                   "propagation": "fp32 chebyshev on 3xTF32 tensor-core sweeps + fp64 residual + refinement",
+                   "propagation": (f"fp32 chebyshev on {main} tensor-core sweeps + fp64 residual certificate "
+                                   "+ fp32 refinement"),
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
-        "sweeps_per_step": sweeps / args.steps, "max_cert": stats["max_cert"] if stats else None,
-        "roofline": roof, "kernel_share": share, "gpu_launches": int(launches), "clocks": sampler.summary(),
+        "sweeps_per_step": sweeps / args.steps,
+        "refine_passes_per_step": stats["refine_passes"] if stats else None,
+        "residual_passes_per_step": stats["residual_passes"] if stats else None,
+        "max_cert": cmax, "roofline": roof, "kernel_share": share, "gpu_launches": int(launches),
+        "other_mode": {"mode": other, "ms_per_step": statistics.mean(ms_o), "sweeps_per_step": sw_o,
+                       "refine_passes": st_o["refine_passes"], "residual_passes": st_o["residual_passes"],
+                       "max_cert": cm_o},
+        "clocks": sampler.summary(),
     }
     print(json.dumps(line), flush=True)
 

@@ -69,6 +69,10 @@ extern "C" {
 #define PPRVIZ_FP32_TC 3         /* pprviz_dppr only: PPRVIZ_FP32 with every sweep a dense
                                   * tensor-core contraction (3xTF32 tcgen05.mma); E_OOM if the
                                   * n x n weight matrix does not fit */
+#define PPRVIZ_FP32_BF16TC 4     /* pprviz_dppr only: as PPRVIZ_FP32_TC, but every sweep is one
+                                  * BF16 x BF16 tcgen05.mma (kind::f16) with FP32 accumulation;
+                                  * the FP64 residual and up to 16 FP32 refinement passes
+                                  * restore eps (E_NOT_CONVERGED if they do not) */
 
 typedef struct pprviz_ctx pprviz_ctx;
 typedef struct pprviz_graph pprviz_graph;
@@ -185,7 +189,8 @@ int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out
  *            Through Eq. (1) the certificates bound the PDist error too:
  *            |dDelta_ij| <= (c_i + c_j) / max(z_ij - c_i - c_j, e / n_clamp^2).
  * precision: PPRVIZ_FP64, PPRVIZ_FP32 (sweep kernel chosen by density),
- *            PPRVIZ_FP32_CSR or PPRVIZ_FP32_TC (sweep kernel forced). The
+ *            PPRVIZ_FP32_CSR, PPRVIZ_FP32_TC or PPRVIZ_FP32_BF16TC (sweep
+ *            kernel and operand precision forced). The
  *            tensor-core sweeps (P1d, Sec. 3.1 in matrix form: one sweep is the
  *            dense product W Y of the n x n weights and the n x G state) change
  *            only how a sweep is computed: the certificate and the refinement

@@ -15,15 +15,16 @@ from __future__ import annotations
 import numpy as np
 
 from . import _binding as B
-from ._binding import (PPRVIZ_DEGREE_COUNT, PPRVIZ_DEVICE_PTRS, PPRVIZ_FP32, PPRVIZ_FP32_CSR, PPRVIZ_FP32_TC,
-                       PPRVIZ_FP64, PPRVIZ_OUT_FP64, PPRVIZ_UNDIRECTED, PPRVIZ_VALIDATE, PPRVizError)
+from ._binding import (PPRVIZ_DEGREE_COUNT, PPRVIZ_DEVICE_PTRS, PPRVIZ_FP32, PPRVIZ_FP32_BF16TC, PPRVIZ_FP32_CSR,
+                       PPRVIZ_FP32_TC, PPRVIZ_FP64, PPRVIZ_OUT_FP64, PPRVIZ_UNDIRECTED, PPRVIZ_VALIDATE, PPRVizError)
 
-__all__ = ["Context", "Graph", "StressEnergy", "PPRVizError", "FP32", "FP32_CSR", "FP32_TC", "FP64",
+__all__ = ["Context", "Graph", "StressEnergy", "PPRVizError", "FP32", "FP32_CSR", "FP32_TC", "FP32_BF16TC", "FP64",
            "library_path"]
 
 FP32 = PPRVIZ_FP32
 FP32_CSR = PPRVIZ_FP32_CSR
 FP32_TC = PPRVIZ_FP32_TC
+FP32_BF16TC = PPRVIZ_FP32_BF16TC
 FP64 = PPRVIZ_FP64
 
 

@@ -31,6 +31,7 @@ PPRVIZ_FP64 = 0
 PPRVIZ_FP32 = 1
 PPRVIZ_FP32_CSR = 2
 PPRVIZ_FP32_TC = 3
+PPRVIZ_FP32_BF16TC = 4
 KERNEL_CLASSES = ["graph", "sweep", "residual", "extract", "pdist", "factor", "ly", "apply", "energy", "other"]
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID_ARG", 2: "E_BAD_GRAPH", 3: "E_OOM", 4: "E_CUDA",

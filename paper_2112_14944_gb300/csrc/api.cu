@@ -317,9 +317,10 @@ int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int
   if (k < 1 || (int64_t)k > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be in [1, n]");
   if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
   if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
-  if (precision < PPRVIZ_FP64 || precision > PPRVIZ_FP32_TC)
+  if (precision < PPRVIZ_FP64 || precision > PPRVIZ_FP32_BF16TC)
     return set_err(ctx, PPRVIZ_E_INVALID_ARG,
-                   "precision must be PPRVIZ_FP64, PPRVIZ_FP32, PPRVIZ_FP32_CSR or PPRVIZ_FP32_TC");
+                   "precision must be PPRVIZ_FP64, PPRVIZ_FP32, PPRVIZ_FP32_CSR, PPRVIZ_FP32_TC or "
+                   "PPRVIZ_FP32_BF16TC");
   if (n_clamp == 0) n_clamp = g->n;
   if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
   const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;

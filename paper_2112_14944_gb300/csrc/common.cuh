@@ -172,8 +172,9 @@ int64_t dense_group(int32_t k);
 int dense_prepare(pprviz_ctx *ctx, const pprviz_graph *g);
 // One Chebyshev sweep of a group with the semantics of the CSR sweep; yold is
 // overwritten with the new iterate; err gets bit 0 if an MMA wait expired.
+// bf16: BF16 operands (kind::f16) instead of the 3xTF32 split.
 int dense_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src, const float *rhs,
-                const float *ycur, float *yold, double alpha, double om, int *err);
+                const float *ycur, float *yold, double alpha, double om, int *err, bool bf16);
 
 // ---- pdist (pdist.cu) ------------------------------------------------------
 int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp,

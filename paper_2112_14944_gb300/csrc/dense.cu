@@ -19,6 +19,14 @@
 // products, which is what the sweeps need (the certificate comes from the
 // FP64 residual over the CSR, not from these products).
 //
+// BF16 mode (PPRVIZ_FP32_BF16TC): the same sweep with the operands rounded to
+// BF16 while they are staged (W and Y each to 8 significant bits) and one
+// tcgen05.mma kind::f16 (BF16 x BF16, FP32 accumulation in tensor memory)
+// per 16-wide inner step instead of the three TF32 products. A sweep is then
+// accurate to ~2^-9 of its products only; the refinement passes, driven by
+// the same FP64 residual over the CSR, restore the eps bound (each pass
+// gains what one BF16 solve resolves).
+//
 // Tiling: one CTA per 128 (target rows j) x NT (sources q) output tile, the
 // inner dimension i streamed in 32-wide chunks through two shared-memory
 // stages. Both operands are staged K-major in the canonical no-swizzle layout
@@ -32,6 +40,8 @@
 
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace pprviz {
@@ -40,26 +50,43 @@ namespace dtc {
 constexpr int TM = 128;                  // target rows per tile (MMA M)
 constexpr int KC = 32;                   // inner-dimension chunk per stage
 constexpr uint32_t LBO = 128;            // bytes to the next core matrix along K
-constexpr uint32_t SBO = (KC / 4) * 128; // bytes to the next 8-row group
 constexpr int THREADS = 256;
 constexpr long WAIT_LIMIT = 1L << 22;
 
-template <int NT>
+// BF: BF16 operands (2 bytes, one product per step), else split TF32 (4 bytes,
+// high and low parts: three products per step).
+template <int NT, bool BF>
 struct Cfg {
-  static constexpr int A_BYTES = TM * KC * 4;  // one split part of the W chunk
-  static constexpr int B_BYTES = NT * KC * 4;  // one split part of the Y chunk
-  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int SMEM = 2 * STAGE;
+  static constexpr int EB = BF ? 2 : 4;                  // operand element bytes
+  static constexpr uint32_t SBO = (KC * EB / 16) * 128;  // bytes to the next 8-row group
+  static constexpr int A_BYTES = TM * KC * EB;  // one (split part of the) W chunk
+  static constexpr int B_BYTES = NT * KC * EB;  // one (split part of the) Y chunk
+  static constexpr int STAGE = BF ? A_BYTES + B_BYTES : 2 * A_BYTES + 2 * B_BYTES;
+  // a CTA holds NT tensor-memory columns, so at most 512 / NT CTAs fit on an
+  // SM; the BF16 stages are small, so their request is padded to keep the
+  // scheduler from placing more CTAs than that (232,448 bytes per SM)
+  static constexpr int MAXC = 512 / NT;
+  static constexpr int SMEM = BF ? (2 * STAGE > 232448 / (MAXC + 1) + 1024 ? 2 * STAGE : 232448 / (MAXC + 1) + 1024)
+                                 : 2 * STAGE;
   static constexpr int B_ITEMS = NT * (KC / 4) / THREADS;  // float4 groups of Y per thread
-  static constexpr uint32_t IDESC =
-      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  // kind::tf32: A, B format 2 (TF32); kind::f16: A, B format 1 (BF16); F32 accumulator
+  static constexpr uint32_t IDESC = (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) |
+                                    ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  static constexpr int K_STEP = BF ? 16 : 8;  // inner extent of one MMA
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// byte offset of element (row r, inner index k) in the canonical no-swizzle
+// K-major layout: 8-row x 16-byte core matrices, LBO along K, SBO along rows
+template <bool BF>
 __device__ __forceinline__ uint32_t canon(int r, int k) {
-  return (uint32_t)((r >> 3) * SBO + (k >> 2) * LBO + (r & 7) * 16 + (k & 3) * 4);
+  constexpr uint32_t SBO = (KC * (BF ? 2 : 4) / 16) * 128;
+  return BF ? (uint32_t)((r >> 3) * SBO + (k >> 3) * LBO + (r & 7) * 16 + (k & 7) * 2)
+            : (uint32_t)((r >> 3) * SBO + (k >> 2) * LBO + (r & 7) * 16 + (k & 3) * 4);
 }
+template <bool BF>
 __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+  constexpr uint32_t SBO = (KC * (BF ? 2 : 4) / 16) * 128;
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
@@ -77,6 +104,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
+// four consecutive inner elements rounded to BF16 (round to nearest even), 8 bytes
+__device__ __forceinline__ void put_bf16(unsigned char *dst, uint32_t off, float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<const uint32_t *>(&a);
+  u.y = *reinterpret_cast<const uint32_t *>(&b);
+  *reinterpret_cast<uint2 *>(dst + off) = u;
+}
+
 __device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
   float4 h, l;
   h.x = hi_part(v.x); h.y = hi_part(v.y); h.z = hi_part(v.z); h.w = hi_part(v.w);
@@ -89,8 +125,8 @@ __device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, 
 // global loads and the split stores into a stage.
 template <int NT>
 struct Chunk {
-  float4 a[4];                      // W: 128 rows x 32 -> 1024 float4, 4 per thread
-  float4 b[Cfg<NT>::B_ITEMS];       // Y: NT sources x 8 quads of i
+  float4 a[4];                          // W: 128 rows x 32 -> 1024 float4, 4 per thread
+  float4 b[Cfg<NT, false>::B_ITEMS];    // Y: NT sources x 8 quads of i
 };
 
 // W chunk mapping: 8 lanes of a warp cover 8 rows at one 16-byte column quad,
@@ -114,7 +150,7 @@ __device__ __forceinline__ void load_chunk(Chunk<NT> &ch, const float *__restric
     ch.a[it] = __ldg(reinterpret_cast<const float4 *>(W + (j0 + r) * nw + k0 + 4 * kq));
   }
 #pragma unroll
-  for (int it = 0; it < Cfg<NT>::B_ITEMS; ++it) {
+  for (int it = 0; it < Cfg<NT, false>::B_ITEMS; ++it) {
     const int item = tid + THREADS * it;
     const int q = item % NT, kq = item / NT;
     const int64_t i = k0 + 4 * kq;
@@ -128,20 +164,36 @@ __device__ __forceinline__ void load_chunk(Chunk<NT> &ch, const float *__restric
   }
 }
 
-template <int NT>
+template <int NT, bool BF>
 __device__ __forceinline__ void store_chunk(const Chunk<NT> &ch, unsigned char *st, int tid) {
-  unsigned char *a_hi = st, *a_lo = st + Cfg<NT>::A_BYTES;
-  unsigned char *b_hi = st + 2 * Cfg<NT>::A_BYTES, *b_lo = b_hi + Cfg<NT>::B_BYTES;
+  using C = Cfg<NT, BF>;
+  if (BF) {
+    unsigned char *a = st, *b = st + C::A_BYTES;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      int r, kq;
+      a_coords(tid, it, r, kq);
+      put_bf16(a, canon<true>(r, 4 * kq), ch.a[it]);
+    }
+#pragma unroll
+    for (int it = 0; it < C::B_ITEMS; ++it) {
+      const int item = tid + THREADS * it;
+      put_bf16(b, canon<true>(item % NT, 4 * (item / NT)), ch.b[it]);
+    }
+    return;
+  }
+  unsigned char *a_hi = st, *a_lo = st + C::A_BYTES;
+  unsigned char *b_hi = st + 2 * C::A_BYTES, *b_lo = b_hi + C::B_BYTES;
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     int r, kq;
     a_coords(tid, it, r, kq);
-    put_split(a_hi, a_lo, canon(r, 4 * kq), ch.a[it]);
+    put_split(a_hi, a_lo, canon<false>(r, 4 * kq), ch.a[it]);
   }
 #pragma unroll
-  for (int it = 0; it < Cfg<NT>::B_ITEMS; ++it) {
+  for (int it = 0; it < C::B_ITEMS; ++it) {
     const int item = tid + THREADS * it;
-    put_split(b_hi, b_lo, canon(item % NT, 4 * (item / NT)), ch.b[it]);
+    put_split(b_hi, b_lo, canon<false>(item % NT, 4 * (item / NT)), ch.b[it]);
   }
 }
 }  // namespace dtc
@@ -153,13 +205,13 @@ __device__ __forceinline__ void store_chunk(const Chunk<NT> &ch, unsigned char *
 // yold (each element is read and written by the same thread).
 // W: mw x nw FP32 (mw = n rounded up to 128, nw = n rounded up to 32, zero
 // padded); the state has n rows of ld floats; grid (ld / NT, mw / 128).
-template <int NT, bool RHS>
-__global__ void __launch_bounds__(dtc::THREADS, 1)
+template <int NT, bool RHS, bool BF>
+__global__ void __launch_bounds__(dtc::THREADS, BF ? 2 : 1)
 k_dsweep_tc(int64_t n, int64_t nw, int64_t ld, const float *__restrict__ W, const float *__restrict__ invdw,
             const int32_t *__restrict__ src, const float *__restrict__ rhs, const float *__restrict__ ycur,
             const float *yold, float *yout, float alpha, float c, float om, float om1, int *__restrict__ err) {
   using namespace dtc;
-  using C = Cfg<NT>;
+  using C = Cfg<NT, BF>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_sh;
@@ -193,7 +245,7 @@ k_dsweep_tc(int64_t n, int64_t nw, int64_t ld, const float *__restrict__ W, cons
       ok = false;
       break;
     }
-    store_chunk<NT>(ch, st, tid);
+    store_chunk<NT, BF>(ch, st, tid);
     if (cidx + 1 < nchunks) load_chunk<NT>(ch, W, nw, j0, ycur, ld, q0, n, (cidx + 1) * KC, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -201,21 +253,35 @@ k_dsweep_tc(int64_t n, int64_t nw, int64_t ld, const float *__restrict__ W, cons
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (tid == 0) {
       const uint32_t base = smem_u32(st);
+      if (BF) {
+        // one BF16 product per 16-wide inner step (32 bytes = two core matrices)
+#pragma unroll
+        for (int ks = 0; ks < KC / C::K_STEP; ++ks) {
+          const uint64_t da = desc<true>(base + ks * 2 * LBO);
+          const uint64_t db = desc<true>(base + C::A_BYTES + ks * 2 * LBO);
+          const uint32_t acc = (cidx == 0 && ks == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
+        }
+      } else {
 #pragma unroll 1
       for (int pass = 0; pass < 3; ++pass) {
         // hi*hi, hi*lo (W_hi Y_lo), lo*hi (W_lo Y_hi)
         const uint32_t pa = base + (pass == 2 ? C::A_BYTES : 0);
         const uint32_t pb = base + 2 * C::A_BYTES + (pass == 1 ? C::B_BYTES : 0);
 #pragma unroll
-        for (int ks = 0; ks < KC / 8; ++ks) {
-          const uint64_t da = desc(pa + ks * 2 * LBO);
-          const uint64_t db = desc(pb + ks * 2 * LBO);
+        for (int ks = 0; ks < KC / C::K_STEP; ++ks) {
+          const uint64_t da = desc<false>(pa + ks * 2 * LBO);
+          const uint64_t db = desc<false>(pb + ks * 2 * LBO);
           const uint32_t acc = (cidx == 0 && pass == 0 && ks == 0) ? 0u : 1u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
               "l"(da), "l"(db), "r"(C::IDESC), "r"(acc));
         }
+      }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mbar[buf])));
@@ -343,30 +409,37 @@ int dense_prepare(pprviz_ctx *ctx, const pprviz_graph *g) {
   return PPRVIZ_OK;
 }
 
-template <int NT, bool RHS>
+template <int NT, bool RHS, bool BF>
 static int dsweep_launch(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                          const float *rhs, const float *ycur, float *yold, double alpha, double om, int *err) {
-  using C = dtc::Cfg<NT>;
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_dsweep_tc<NT, RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using C = dtc::Cfg<NT, BF>;
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_dsweep_tc<NT, RHS, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         C::SMEM));
   const int64_t mw = (g->n + 127) / 128 * 128;
   const dim3 grid((unsigned)(ld / NT), (unsigned)(mw / dtc::TM));
   const double c = 1.0 - alpha;
   PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
-  k_dsweep_tc<NT, RHS><<<grid, dtc::THREADS, C::SMEM, ctx->stream>>>(
+  k_dsweep_tc<NT, RHS, BF><<<grid, dtc::THREADS, C::SMEM, ctx->stream>>>(
       g->n, g->dense_nw, ld, g->dense.as<float>(), g->invdw_f.as<float>(), src, rhs, ycur, yold, yold,
       (float)alpha, (float)c, (float)om, (float)(1.0 - om), err);
   PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
 }
 
-int dense_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src, const float *rhs,
-                const float *ycur, float *yold, double alpha, double om, int *err) {
+template <bool BF>
+static int dense_sweep_t(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src, const float *rhs,
+                         const float *ycur, float *yold, double alpha, double om, int *err) {
   if (ld % 256 == 0)
-    return rhs ? dsweep_launch<256, true>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err)
-               : dsweep_launch<256, false>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err);
-  return rhs ? dsweep_launch<128, true>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err)
-             : dsweep_launch<128, false>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err);
+    return rhs ? dsweep_launch<256, true, BF>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err)
+               : dsweep_launch<256, false, BF>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err);
+  return rhs ? dsweep_launch<128, true, BF>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err)
+             : dsweep_launch<128, false, BF>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err);
+}
+
+int dense_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src, const float *rhs,
+                const float *ycur, float *yold, double alpha, double om, int *err, bool bf16) {
+  return bf16 ? dense_sweep_t<true>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err)
+              : dense_sweep_t<false>(ctx, g, ld, src, rhs, ycur, yold, alpha, om, err);
 }
 
 }  // namespace pprviz

@@ -49,6 +49,7 @@ constexpr int kSweepWarps = 1;    // warps per block in k_sweep: one-warp blocks
                                   // row, so a hub row does not hold seven finished warps' slots
 constexpr int kChunk = 128;       // group width granule (sources)
 constexpr int kMaxRefine = 6;     // refinement passes before E_NOT_CONVERGED
+constexpr int kMaxRefineBf16 = 16;  // the same with BF16 tensor-core sweeps
 constexpr int kMaxRefineSweeps = 32;  // Chebyshev sweeps per refinement pass
 
 template <typename T>
@@ -880,7 +881,7 @@ double chebyshev_rate(double c) { return (1.0 - sqrt(1.0 - c * c)) / c; }
 int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     int32_t gcount, const float *rhs, float *ya, float *yb, int sweeps,
                     double alpha, int *tcerr, const int32_t *csrc, const double *kappa, double delta,
-                    float **result, const Wave *wv = nullptr) {
+                    float **result, const Wave *wv = nullptr, bool bf16 = false) {
   const size_t bytes = sizeof(float) * (size_t)(g->n * ld);
   const double c = 1.0 - alpha;
   if (wv) {
@@ -915,7 +916,7 @@ int chebyshev_solve(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   for (int s = 1; s < sweeps; ++s) {
     om = (s == 1) ? 1.0 / (1.0 - d2 / 2.0) : 1.0 / (1.0 - d2 * om / 4.0);
     if (tcerr)
-      PPRVIZ_TRY(dense_sweep(ctx, g, ld, src, rhs, cur, old, alpha, om, tcerr));
+      PPRVIZ_TRY(dense_sweep(ctx, g, ld, src, rhs, cur, old, alpha, om, tcerr, bf16));
     else
       PPRVIZ_TRY(launch_sweep<float>(ctx, g, ld, true, rhs != nullptr, src, rhs, cur, old, old, alpha, om, wv));
     std::swap(cur, old);
@@ -934,7 +935,10 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   // sweep kernel: dense tensor-core contraction (forced, or chosen by density
   // when the n x n matrix fits) or CSR gathers
   bool dense = false;
-  if (precision == PPRVIZ_FP32_TC) {
+  // BF16 operands on the tensor cores; a BF16 solve resolves ~2^-8 of its
+  // correction, so its sweeps stop there and more refinement passes follow
+  const bool bf16 = precision == PPRVIZ_FP32_BF16TC;
+  if (precision == PPRVIZ_FP32_TC || bf16) {
     PPRVIZ_TRY(dense_prepare(ctx, g));
     dense = true;
   } else if (precision == PPRVIZ_FP32 && dense_eligible(g)) {
@@ -1053,10 +1057,11 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       // main solve to a Chebyshev error bound 2 rho^K <= 1e-5: every further
       // sweep here would only save one refinement sweep, and the refinement
       // (driven by the exact FP64 residual) finishes the job
-      const int K1 = std::max(2, sweeps_for(1e-5, rate(delta_c)));
+      // (BF16: to 2 rho^K <= 1e-3, about what BF16 products resolve)
+      const int K1 = std::max(2, sweeps_for(bf16 ? 1e-3 : 1e-5, rate(delta_c)));
       float *hi = nullptr;
       PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, nullptr, bufs[0], bufs[1], K1, alpha, tcerr,
-                                 defl ? csrc : nullptr, kappa, delta_c, &hi));
+                                 defl ? csrc : nullptr, kappa, delta_c, &hi, nullptr, bf16));
       st.sweeps_main += K1;
       if (dense) st.flops_dense += 2.0 * (double)g->n * (double)g->n * gvalid * (K1 - 1);
       else st.bytes_sweep += 12.0 * (double)g->n * gvalid * (K1 - 1);
@@ -1068,13 +1073,13 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       st.residual_passes++;
       PPRVIZ_TRY(read_certs(ctx, g, view_h, g0, gvalid, ld, l1, alpha, cert, sigma));
       double cprev = 0.0;
-      for (int pass = 0; pass < kMaxRefine; ++pass) {
+      for (int pass = 0; pass < (bf16 ? kMaxRefineBf16 : kMaxRefine); ++pass) {
         double cmax = 0.0;
         for (double v : cert) cmax = std::max(cmax, v);
         if (cmax <= eps) break;
-        // a pass that gained less than 10x means modes outside the estimated
-        // interval: iterate the full interval [1 - c, 1 + c] from here on
-        if (pass > 0 && cmax > 0.1 * cprev) delta_c = c;
+        // a pass that gained less than 10x (BF16: 2x) means modes outside the
+        // estimated interval: iterate the full interval [1 - c, 1 + c] from here on
+        if (pass > 0 && cmax > (bf16 ? 0.5 : 0.1) * cprev) delta_c = c;
         cprev = cmax;
         // correction's stationary coefficient: sum_j res_jq / alpha over m_C
         if (defl) {
@@ -1087,9 +1092,10 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         // sweeps past 2 rho^K ~ 3e-8 are left to the next pass
         int K2 = sweeps_for(0.5 * eps / cmax, rate(delta_c)) + 2;
         K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
+        if (bf16) K2 = std::min(K2, sweeps_for(1e-3, rate(delta_c)) + 1);
         float *delta = nullptr;
         PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, tcerr,
-                                   defl ? csrc : nullptr, kappa, delta_c, &delta));
+                                   defl ? csrc : nullptr, kappa, delta_c, &delta, nullptr, bf16));
         st.sweeps_refine += K2;
         if (dense) st.flops_dense += 2.0 * (double)g->n * (double)g->n * gvalid * (K2 - 1);
         else st.bytes_sweep += 16.0 * (double)g->n * gvalid * (K2 - 1);

@@ -8,6 +8,10 @@ sparse path's: every certificate <= eps, DPPR within 1e-6 * max(1, |ref|) of
 the oracle (reading of the paper's "max-abs 1e-6" for FP32 outputs), PDist
 under the certified per-entry tolerance of Lemma 1's mechanism.
 
+The BF16 mode (PPRVIZ_FP32_BF16TC: BF16 x BF16 -> FP32 kind::f16 sweeps) is
+held to the same gates: its sweeps are only BF16-accurate, and the FP64
+residual with FP32 refinement restores eps.
+
 Shapes: n = 600 (ragged against the 128-row tile and the 32-wide inner chunk,
 128-source tiles), n = 1000 with k = 1000 (256-source tiles), a 300-node view
 of a 900-node graph (84 padded source columns), isolated nodes (a zero row of
@@ -90,6 +94,47 @@ def test_tc_view_subset_with_padded_sources(ctx):
     check_pdist(Pd, Dref, cert, 900)
 
 
+@pytest.mark.parametrize("n,seed", [(600, 1), (1000, 2)])
+def test_bf16_weighted_dense_view_matches_oracle(ctx, n, seed):
+    """BF16 x BF16 -> FP32 tensor-core sweeps (kind::f16): every sweep is only
+    BF16-accurate, and the FP64 residual with FP32 refinement passes restores
+    eps, so the gates are the FP32 path's: certificate <= eps, DPPR within
+    1e-6 * max(1, |ref|), PDist under the certified tolerance. The BF16 solve
+    needs more refinement passes than the 3xTF32 one."""
+    import paper_2112_14944_gb300 as P
+    g = synth.dense_clustered(n, blocks=10, density=0.15, seed=seed)
+    view = np.arange(n, dtype=np.int32)
+    D, Pd, cert, st = _run(ctx, g, view, P.FP32_BF16TC)
+    assert st["flops_dense"] > 0 and st["bytes_sweep"] == 0
+    assert cert.max() <= EPS
+    assert st["refine_passes"] >= 1
+    Dref = _oracle_dppr(g, view)
+    check_dppr(D, Dref)
+    check_pdist(Pd, Dref, cert, n)
+    _, _, _, st32 = _run(ctx, g, view, P.FP32_TC)
+    assert st["refine_passes"] >= st32["refine_passes"]
+
+
+def test_bf16_isolated_nodes_and_padded_sources(ctx):
+    import paper_2112_14944_gb300 as P
+    g = synth.sbm([400, 199, 1, 1], 0.2, 0.0, seed=3)
+    deg = np.diff(g.row_ptr)
+    view = np.arange(g.n, dtype=np.int32)
+    D, Pd, cert, _ = _run(ctx, g, view, P.FP32_BF16TC)
+    assert cert.max() <= EPS
+    Dref = _oracle_dppr(g, view)
+    check_dppr(D, Dref)
+    assert np.all(D[np.nonzero(deg == 0)[0]] == 0.0)
+    check_pdist(Pd, Dref, cert, g.n)
+    g = synth.dense_clustered(900, blocks=12, density=0.12, seed=4)
+    view = synth.sample_view(900, 300, seed=4)
+    D, Pd, cert, st = _run(ctx, g, view, P.FP32_BF16TC)
+    assert st["source_group"] == 384 and cert.max() <= EPS
+    Dref = _oracle_dppr(g, view)
+    check_dppr(D, Dref)
+    check_pdist(Pd, Dref, cert, 900)
+
+
 def test_sweep_kernel_selection_and_agreement(ctx):
     """PPRVIZ_FP32 takes the tensor-core sweeps on a dense view and the CSR
     sweeps on a sparse one; forced CSR and forced tensor-core runs of the same
@@ -138,3 +183,9 @@ def test_tc_full_size_dense_weighted_view_sampled(ctx):
     pi = O.ppr_rows(P_, sample, ALPHA)
     Dref = O.dppr_rows(pi, d, sample)
     check_dppr(D[sample], Dref)
+    # the same view on BF16 tensor-core sweeps with refinement
+    Db, _, certb, stb = _run(ctx, g, view, P.FP32_BF16TC)
+    assert stb["flops_dense"] > 0 and certb.max() <= EPS
+    check_dppr(Db[sample], Dref)
+    rows = Db.sum(axis=1, dtype=np.float64) / d
+    assert np.all(np.abs(rows - 1.0) <= certb / d + 1e-6)
