@@ -73,6 +73,7 @@ struct pprviz_ctx {
   std::string err;
   pprviz::DevBuf ws[pprviz::WS_COUNT];
   size_t ws_limit = 0;  // cap on the summed workspace capacity (0 = none); pprviz_set_workspace_limit
+  bool test_expire_wait = false;  // pprviz_test_expire_wait: the next FP32 inverse withholds one copy
   pprviz_stats stats{};
   int launches = 0;  // kernels launched in the current call
   // source-group widths chosen by the sweep autotuner, by graph size class

@@ -147,6 +147,107 @@ __global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, fl
   fac_diag128(kp, K0, A, P);
 }
 
+// The same 128 x 128 inverse as a symmetric block sweep over four 32-wide
+// pivot blocks (the sweep of the whole inverse, one level down), with the
+// full symmetric block in shared memory and 1,024 threads:
+//   Q = S^-1 of the 32 x 32 pivot block S (one warp, rows in registers,
+//   pivots broadcast by shuffles), S -> -Q; U_I = T_IK Q for the other rows;
+//   T_IJ -= U_I T_KJ; then T_IK = U_I and T_KI = U_I^T.
+// After the four pivots the block holds -A_KK^-1: P = A_KK^-1 and A_KK = -P
+// (as fac_diag128). Dynamic shared memory: FAC_DIAGB_SMEM bytes.
+constexpr int kDgLd = 129;  // padded row of the staged block
+constexpr int FAC_DIAGB_SMEM = (128 * kDgLd + 128 * 33 + 32 * 33) * 4;
+
+__device__ __forceinline__ void fac_diag128b(int32_t kp, int32_t K0, float *__restrict__ A, float *__restrict__ P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float *T = reinterpret_cast<float *>(smem_raw);  // [128][129]
+  float *U = T + 128 * kDgLd;                      // [128][33]: new column panel
+  float *Q = U + 128 * 33;                         // [32][33]: pivot block inverse
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < 128 * 32; e += 1024) {  // 128 rows x 32 float4
+    const int r = e >> 5, c4 = e & 31;
+    const float4 v = *reinterpret_cast<const float4 *>(A + (int64_t)(K0 + r) * kp + K0 + 4 * c4);
+    float *t = T + r * kDgLd + 4 * c4;
+    t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int kb = 0; kb < 4; ++kb) {
+    const int K = 32 * kb;
+    if (warp == 0) {
+      // in-place Gauss-Jordan inverse of the SPD 32 x 32 block: lane = row
+      float a[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) a[c] = T[(K + lane) * kDgLd + K + c];
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        const float piv = 1.0f / __shfl_sync(0xffffffffu, a[p], p);
+        const float f = a[p] * piv;  // a_rp / a_pp
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float apc = __shfl_sync(0xffffffffu, a[c], p);
+          if (c == p) a[c] = (lane == p) ? piv : -f;
+          else a[c] = (lane == p) ? apc * piv : fmaf(-f, apc, a[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        Q[lane * 33 + c] = a[c];
+        T[(K + lane) * kDgLd + K + c] = -a[c];
+      }
+    }
+    __syncthreads();
+    // U_I = T_IK Q for the 96 rows outside the pivot block (lane = column)
+    for (int i = warp; i < 128; i += 32) {
+      if (i >= K && i < K + 32) continue;
+      float u = 0.0f;
+#pragma unroll 8
+      for (int s2 = 0; s2 < 32; ++s2) u = fmaf(T[i * kDgLd + K + s2], Q[s2 * 33 + lane], u);
+      U[i * 33 + lane] = u;
+    }
+    __syncthreads();
+    // T_IJ -= U_I T_KJ (T_KJ still the old row panel); rows i = warp + 32 ib,
+    // columns j = lane + 32 jb, outside the pivot block
+#pragma unroll 1
+    for (int ib = 0; ib < 4; ++ib) {
+      if (ib == kb) continue;
+      const int i = warp + 32 * ib;
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+      for (int s2 = 0; s2 < 32; ++s2) {
+        const float ui = U[i * 33 + s2];
+#pragma unroll
+        for (int jb = 0; jb < 4; ++jb) acc[jb] = fmaf(ui, T[(K + s2) * kDgLd + lane + 32 * jb], acc[jb]);
+      }
+#pragma unroll
+      for (int jb = 0; jb < 4; ++jb)
+        if (jb != kb) T[i * kDgLd + lane + 32 * jb] -= acc[jb];
+    }
+    __syncthreads();
+    // T_IK = U_I and T_KI = U_I^T
+    for (int e = tid; e < 128 * 32; e += 1024) {
+      const int i = e >> 5, c = e & 31;
+      if (i >= K && i < K + 32) continue;
+      const float u = U[i * 33 + c];
+      T[i * kDgLd + K + c] = u;
+      T[(K + c) * kDgLd + i] = u;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 128 * 32; e += 1024) {
+    const int r = e >> 5, c4 = e & 31;
+    const float *t = T + r * kDgLd + 4 * c4;
+    const float4 v = make_float4(t[0], t[1], t[2], t[3]);
+    *reinterpret_cast<float4 *>(P + r * 128 + 4 * c4) = make_float4(-v.x, -v.y, -v.z, -v.w);
+    *reinterpret_cast<float4 *>(A + (int64_t)(K0 + r) * kp + K0 + 4 * c4) = v;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_fac_diag128b(int32_t kp, int32_t K0, float *__restrict__ A,
+                                                       float *__restrict__ P) {
+  fac_diag128b(kp, K0, A, P);
+}
+
 template <typename T>
 struct V4;  // 4-vector load/store of T
 template <>
@@ -575,6 +676,354 @@ k_fac_trailing_tc(int32_t kp, int32_t K0, int k1, int only_k1, float *__restrict
   trailing_tc_tile(kp, I0, J0, A, Ct, Ut, err);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialized tensor-core trailing update (single FP32
+// inverse). One CTA per SM walks a static share of the launch's tiles:
+//   warp 0 (one lane): streams each tile's 8 inner chunks (32 KiB: the split
+//     high and low parts of Ct block I and Ut block J, bulk copies) through
+//     NST shared-memory stages (full / empty mbarriers);
+//   warp 1 (one lane): issues the 3 x 2 tcgen05.mma.kind::tf32 of each chunk
+//     into one of two tensor-memory accumulators (128 columns each) and
+//     commits the stage back to the producer and the accumulator to the
+//     epilogue;
+//   warps 4-7 (thread = tile row = TMEM lane): load their C rows by bulk
+//     copies into a padded staging tile, subtract the accumulator (tcgen05.ld),
+//     release it, and store the rows back by bulk copies.
+// With two accumulators the epilogue of one tile overlaps the MMAs of the
+// next, and the operand stream runs ahead by NST chunks. Every wait is bounded
+// by a global-timer deadline: on expiry the CTA records the error, stops, waits
+// (bounded) for its copies and MMAs in flight, and frees its tensor memory.
+// `withhold` >= 0 makes CTA 0 skip that chunk's copies (a test of the expiry
+// path; the wait for it then runs out); -1 in normal use.
+// ---------------------------------------------------------------------------
+namespace tcp {
+constexpr int TM = 128, NB = 128, KC = 16;
+constexpr int OPB = TM * KC * 4;            // 8 KiB: one split part of a 128 x 16 chunk
+constexpr int CHUNK = 4 * OPB;              // A_hi, A_lo, B_hi, B_lo
+constexpr int NST = 4;                      // operand stages
+constexpr int NCH = NB / KC;                // chunks per tile
+constexpr int CROW = TM * 4 + 16;           // staged C row stride: 528 B, conflict-free 16-byte accesses
+constexpr int SMEM = NST * CHUNK + TM * CROW + 1024;
+constexpr int THREADS = 256;
+constexpr int SIDE_SMS = 16;                // SMs left to the next pivot's inverse and panel
+}  // namespace tcp
+
+namespace {
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase `parity` of `bar`: false once the deadline
+// passes or another role of the CTA has given up (abort set).
+__device__ __forceinline__ bool pwait(uint64_t *bar, uint32_t parity, uint64_t limit_ns, volatile int *abort_f) {
+  const uint32_t b = tc::smem_u32(bar);
+  uint32_t done = 0;
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 0) {
+      if (*abort_f) return false;
+      const uint64_t t = gtimer();
+      if (it == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
+  }
+}
+
+// Tiles of one launch in a fixed order. mode 0: the upper tiles (I <= J) of
+// the blocks other than K and k1 (k1 < 0: only K excluded), row-major over the
+// kept blocks; mode 1: the tiles of block row / column k1 other than K's.
+struct TileWalk {
+  int mode, m, i, j, e1, e2, k1, nblk;
+  __device__ void init(int mode_, int nblk_, int K, int k1_, int t) {
+    mode = mode_;
+    nblk = nblk_;
+    k1 = k1_;
+    if (mode == 1) {
+      m = nblk - 1;
+      i = t;
+      j = 0;
+      e1 = K;
+      return;
+    }
+    e1 = k1 < 0 ? K : min(K, k1);
+    e2 = k1 < 0 ? 0x7fffffff : max(K, k1);
+    m = nblk - (k1 < 0 ? 1 : 2);
+    i = 0;
+    while (i < m && t >= m - i) {
+      t -= m - i;
+      ++i;
+    }
+    j = i + t;
+  }
+  __device__ bool valid() const { return i < m; }
+  __device__ void advance(int g) {
+    if (mode == 1) {
+      i += g;
+      return;
+    }
+    j += g;
+    while (i < m && j >= m) {
+      j -= m - (i + 1);
+      ++i;
+    }
+  }
+  __device__ int blk(int x) const {
+    int b = x;
+    if (b >= e1) ++b;
+    if (b >= e2) ++b;
+    return b;
+  }
+  __device__ void tile(int &I0, int &J0) const {
+    if (mode == 1) {
+      const int b = i + (i >= e1 ? 1 : 0);
+      I0 = min(b, k1) * tcp::TM;
+      J0 = max(b, k1) * tcp::TM;
+      return;
+    }
+    I0 = blk(i) * tcp::TM;
+    J0 = blk(j) * tcp::TM;
+  }
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(tcp::THREADS, 1)
+k_fac_trailing_pp(int32_t kp, int nblk, int K, int k1, int mode, float *__restrict__ A, const float *__restrict__ Ct,
+                  const float *__restrict__ Ut, int *__restrict__ err, uint64_t limit_ns, int withhold) {
+  using namespace tcp;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], accf[2], acce[2], cfull[4], fin;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh, prod_issued, mma_done, held;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char *sbuf = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sb = tc::smem_u32(sbuf);
+  unsigned char *cbuf = sbuf + NST * CHUNK;
+  volatile int *abort_f = &abort_sh;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_sh)),
+                 "r"(2 * TM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < NST; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&empty[q])));
+    }
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&accf[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(tc::smem_u32(&acce[q])));
+    }
+    for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&cfull[q])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&fin)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_sh = 0;
+    prod_issued = 0;
+    mma_done = 0;
+    held = -1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const int G = (int)gridDim.x;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    TileWalk w;
+    w.init(mode, nblk, K, k1, (int)blockIdx.x);
+    int g = 0;
+    bool ok = true;
+    for (; ok && w.valid(); w.advance(G)) {
+      int I0, J0;
+      w.tile(I0, J0);
+      for (int c = 0; c < NCH; ++c, ++g) {
+        const int st = g % NST, n = g / NST;
+        if (g >= NST && !pwait(&empty[st], (uint32_t)((n - 1) & 1), limit_ns, abort_f)) {
+          ok = false;
+          break;
+        }
+        if (withhold == g && blockIdx.x == 0) {
+          held = g;  // this chunk's copies are not issued: the MMA warp's wait for it runs out
+          continue;
+        }
+        const uint32_t dst = sb + st * CHUNK;
+        const uint32_t b = tc::smem_u32(&full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(CHUNK) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+            "l"(Ct + (int64_t)((I0 / TM) * NCH + c) * 4096), "r"(2 * OPB), "r"(b)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                dst + 2 * OPB),
+            "l"(Ut + (int64_t)((J0 / TM) * NCH + c) * 4096), "r"(2 * OPB), "r"(b)
+            : "memory");
+      }
+    }
+    if (!ok) {
+      atomicOr(err, 1);
+      abort_sh = 1;
+    }
+    prod_issued = g;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    TileWalk w;
+    w.init(mode, nblk, K, k1, (int)blockIdx.x);
+    int g = 0, li = 0;
+    bool ok = true;
+    for (; ok && w.valid(); w.advance(G), ++li) {
+      const int ab = li & 1;
+      if (li >= 2 && !pwait(&acce[ab], (uint32_t)(((li >> 1) - 1) & 1), limit_ns, abort_f)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dacc = tmem + (uint32_t)(ab * TM);
+      for (int c = 0; c < NCH; ++c, ++g) {
+        const int st = g % NST;
+        if (!pwait(&full[st], (uint32_t)((g / NST) & 1), limit_ns, abort_f)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = sb + st * CHUNK;
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t pa = base + (pass == 2 ? OPB : 0);
+          const uint32_t pb = base + 2 * OPB + (pass == 1 ? OPB : 0);
+#pragma unroll
+          for (int ks = 0; ks < KC / 8; ++ks) {
+            const uint64_t da = tc::desc(pa + ks * 2 * tc::LBO);
+            const uint64_t db = tc::desc(pb + ks * 2 * tc::LBO);
+            const uint32_t accum = (c == 0 && pass == 0 && ks == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                "l"(da), "l"(db), "r"(tc::IDESC), "r"(accum));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            tc::smem_u32(&empty[st])));
+      }
+      if (!ok) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          tc::smem_u32(&accf[ab])));
+    }
+    if (!ok) {
+      atomicOr(err, 1);
+      abort_sh = 1;
+    }
+    mma_done = g;
+    // every MMA this thread issued has completed before the tensor memory is freed
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        tc::smem_u32(&fin)));
+    if (!pwait(&fin, 0u, limit_ns, abort_f)) {
+      volatile int zero = 0;  // a second bounded wait that ignores abort
+      (void)pwait(&fin, 0u, limit_ns, &zero);
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue: thread = tile row r = TMEM lane
+    const int ew = warp & 3, r = 32 * ew + lane;
+    unsigned char *crow = cbuf + r * CROW;
+    const uint32_t crow_s = tc::smem_u32(crow);
+    TileWalk w;
+    w.init(mode, nblk, K, k1, (int)blockIdx.x);
+    int li = 0;
+    bool ok = true, cpending = false;
+    for (; ok && w.valid(); w.advance(G), ++li) {
+      int I0, J0;
+      w.tile(I0, J0);
+      const int ab = li & 1;
+      float *grow = A + (int64_t)(I0 + r) * kp + J0;
+      // the previous tile's store has read this row: load the new C row
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      __syncwarp();
+      const uint32_t cb = tc::smem_u32(&cfull[ew]);
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(32 * TM * 4) : "memory");
+      __syncwarp();
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       crow_s),
+                   "l"(grow), "r"(TM * 4), "r"(cb)
+                   : "memory");
+      cpending = true;
+      // the warp decides together (tcgen05.ld below is warp-collective)
+      if (!__all_sync(0xffffffffu, pwait(&accf[ab], (uint32_t)((li >> 1) & 1), limit_ns, abort_f))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!__all_sync(0xffffffffu, pwait(&cfull[ew], (uint32_t)(li & 1), limit_ns, abort_f))) {
+        ok = false;
+        break;
+      }
+      cpending = false;
+      const uint32_t tb = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(ab * TM);
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(tb + (uint32_t)(32 * q)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t4 = 0; t4 < 8; ++t4) {
+          float4 *cp = reinterpret_cast<float4 *>(crow + 4 * (32 * q + 4 * t4));
+          float4 x = *cp;
+          x.x -= __uint_as_float(v[4 * t4 + 0]);
+          x.y -= __uint_as_float(v[4 * t4 + 1]);
+          x.z -= __uint_as_float(v[4 * t4 + 2]);
+          x.w -= __uint_as_float(v[4 * t4 + 3]);
+          *cp = x;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acce[ab])) : "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(grow), "r"(crow_s),
+                   "r"(TM * 4)
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    if (!ok) {
+      atomicOr(err, 1);
+      abort_sh = 1;
+      if (cpending) {  // a C row load still in flight: let it land before the CTA exits
+        volatile int zero = 0;
+        (void)pwait(&cfull[ew], (uint32_t)(li & 1), limit_ns, &zero);
+      }
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && abort_sh) {
+    // operand copies issued but never consumed: let them land before exit
+    volatile int zero = 0;
+    for (int g = mma_done; g < prod_issued; ++g)
+      if (g != held) (void)pwait(&full[g % NST], (uint32_t)((g / NST) & 1), limit_ns, &zero);
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TM));
+}
+
 // A <- -A on the upper block triangle; with NB = 64 also the lower 64-block of
 // every 128 x 128 diagonal tile filled from its mirror, giving M = A^-1 on the
 // upper tile triangle with full diagonal tiles (what the layout reads).
@@ -639,10 +1088,18 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     }
     if (!ctx->ev_t1) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_t1, cudaEventDisableTiming));
     if (!ctx->ev_dp) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_dp, cudaEventDisableTiming));
+    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag128b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          FAC_DIAGB_SMEM));
+    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_pp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tcp::SMEM));
+    int nsm = 0;
+    PPRVIZ_CUDA(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const uint64_t limit_ns = 2000000000ull;  // bounded waits: 2 s
+    int withhold = ctx->test_expire_wait ? 0 : -1;  // consumed by the first main trailing launch
+    ctx->test_expire_wait = false;
     PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
     float *Af = (float *)A;
-    const unsigned tg = (unsigned)(kp / tc::TM);
-    k_fac_diag128<<<1, 1024, 0, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
+    k_fac_diag128b<<<1, 1024, FAC_DIAGB_SMEM, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
     PPRVIZ_LAUNCHED(ctx);
     if (nblk > 1) {
       k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, 0, A, P[0], Ct[0], Ut[0]);
@@ -651,20 +1108,30 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     for (int kb = 0; nblk > 1 && kb < nblk; ++kb) {
       const int q = kb & 1, K0 = kb * NB, k1 = kb + 1 < nblk ? kb + 1 : -1;
       if (k1 >= 0) {
-        k_fac_trailing_tc<<<dim3((unsigned)nblk, 1), 256, tc::SMEM, ctx->stream>>>(kp, K0, k1, 1, Af, (float *)Ct[q],
-                                                                                 (float *)Ut[q], err);
+        // block row and column k1 first (nblk - 1 tiles), then the next
+        // pivot's inverse and panel on the side stream, on the SMs that the
+        // main update leaves free
+        const int t1 = nblk - 1;
+        k_fac_trailing_pp<<<(unsigned)std::min(t1, nsm), tcp::THREADS, tcp::SMEM, ctx->stream>>>(
+            kp, nblk, kb, k1, 1, Af, (const float *)Ct[q], (const float *)Ut[q], err, limit_ns, -1);
         PPRVIZ_LAUNCHED(ctx);
         PPRVIZ_CUDA(ctx, cudaEventRecord(ctx->ev_t1, ctx->stream));
         PPRVIZ_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_t1, 0));
-        k_fac_diag128<<<1, 1024, 0, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
+        k_fac_diag128b<<<1, 1024, FAC_DIAGB_SMEM, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
         PPRVIZ_LAUNCHED(ctx);
         k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->side>>>(kp, k1 * NB, A, P[q ^ 1], Ct[q ^ 1], Ut[q ^ 1]);
         PPRVIZ_LAUNCHED(ctx);
         PPRVIZ_CUDA(ctx, cudaEventRecord(ctx->ev_dp, ctx->side));
       }
-      k_fac_trailing_tc<<<dim3(tg, tg), 256, tc::SMEM, ctx->stream>>>(kp, K0, k1, 0, Af, (float *)Ct[q],
-                                                                    (float *)Ut[q], err);
-      PPRVIZ_LAUNCHED(ctx);
+      const int m = nblk - (k1 >= 0 ? 2 : 1);
+      const int tiles = m * (m + 1) / 2;
+      if (tiles > 0) {
+        const int cap = k1 >= 0 ? std::max(1, nsm - tcp::SIDE_SMS) : nsm;
+        k_fac_trailing_pp<<<(unsigned)std::min(tiles, cap), tcp::THREADS, tcp::SMEM, ctx->stream>>>(
+            kp, nblk, kb, k1, 0, Af, (const float *)Ct[q], (const float *)Ut[q], err, limit_ns, withhold);
+        PPRVIZ_LAUNCHED(ctx);
+        withhold = -1;
+      }
       if (k1 >= 0) PPRVIZ_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_dp, 0));
       if (k1 < 0) break;
     }
@@ -689,7 +1156,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     int herr = 0;
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (herr) return set_err(ctx, PPRVIZ_E_TIMEOUT, "tensor-core trailing update: MMA completion wait expired");
+    if (herr) return set_err(ctx, PPRVIZ_E_TIMEOUT, "tensor-core trailing update: a bounded wait expired");
   }
   return PPRVIZ_OK;
 }
@@ -729,7 +1196,7 @@ __device__ __forceinline__ int find_slot(const int *__restrict__ off, int n, int
 __global__ void __launch_bounds__(1024) k_fac_diag128_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
                                                             int32_t K0) {
   const FacJob j = jobs[act[blockIdx.x]];
-  fac_diag128(j.kp, K0, j.A, j.P);
+  fac_diag128b(j.kp, K0, j.A, j.P);
 }
 
 __global__ void __launch_bounds__(256) k_fac_panel_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
@@ -823,13 +1290,15 @@ int spd_inverse_batch_f32(pprviz_ctx *ctx, int32_t nviews, const int32_t *kp, fl
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SMEM));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag128_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        FAC_DIAGB_SMEM));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   {
     PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
     for (int kb = 0; kb < maxnb; ++kb) {
       const StepTab &st = steps[kb];
       const int32_t K0 = kb * 128;
-      k_fac_diag128_batch<<<(unsigned)st.nall, 1024, 0, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
+      k_fac_diag128_batch<<<(unsigned)st.nall, 1024, FAC_DIAGB_SMEM, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
       PPRVIZ_LAUNCHED(ctx);
       if (st.nmulti == 0) continue;
       k_fac_panel_batch<<<(unsigned)st.npan, 256, panel_smem, ctx->stream>>>(jobs_d, tab_d + st.act_multi,
