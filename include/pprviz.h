@@ -131,6 +131,15 @@ void pprviz_destroy(pprviz_ctx *ctx);
  * (buffers already held are kept). Graph objects and caller buffers are not
  * counted. Errors: E_INVALID_ARG (ctx NULL, bytes < 0). */
 int pprviz_set_workspace_limit(pprviz_ctx *ctx, int64_t bytes);
+/* Test aid for the bounded-wait error path (the paper has no counterpart).
+ * The tensor-core kernels bound every wait on a copy or an MMA completion by
+ * a deadline (2 s) and report PPRVIZ_E_TIMEOUT instead of hanging. This call
+ * makes the next FP32 L^w inverse on the context (pprviz_layout with
+ * PPRVIZ_FP32) leave out one operand copy of one tile, so that the wait for
+ * it runs out: that call returns PPRVIZ_E_TIMEOUT after about 2 s, its
+ * outputs are undefined, and the context stays usable for the next call.
+ * Nothing faults. Errors: E_INVALID_ARG (ctx NULL). */
+int pprviz_test_expire_wait(pprviz_ctx *ctx);
 const char *pprviz_last_error(const pprviz_ctx *ctx);
 /* Wait for all work enqueued on the context stream. */
 int pprviz_sync(pprviz_ctx *ctx);

@@ -43,6 +43,7 @@ _SIGS = {
     "pprviz_create": (C.c_int, [C.POINTER(_VP), C.c_int, _VP]),
     "pprviz_destroy": (None, [_VP]),
     "pprviz_set_workspace_limit": (C.c_int, [_VP, C.c_int64]),
+    "pprviz_test_expire_wait": (C.c_int, [_VP]),
     "pprviz_last_error": (C.c_char_p, [_VP]),
     "pprviz_sync": (C.c_int, [_VP]),
     "pprviz_get_stats": (C.c_int, [_VP, _VP]),
@@ -151,6 +152,10 @@ def pprviz_destroy(ctx: int) -> None:
 
 def pprviz_set_workspace_limit(ctx: int, nbytes: int) -> None:
     _check(ctx, load().pprviz_set_workspace_limit(ctx, int(nbytes)))
+
+
+def pprviz_test_expire_wait(ctx: int) -> None:
+    _check(ctx, load().pprviz_test_expire_wait(ctx))
 
 
 def pprviz_last_error(ctx: int) -> str:

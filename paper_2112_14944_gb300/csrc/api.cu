@@ -145,6 +145,12 @@ int pprviz_create(pprviz_ctx **out, int device, void *cuda_stream) {
   return PPRVIZ_OK;
 }
 
+int pprviz_test_expire_wait(pprviz_ctx *ctx) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  ctx->test_expire_wait = true;
+  return PPRVIZ_OK;
+}
+
 int pprviz_set_workspace_limit(pprviz_ctx *ctx, int64_t bytes) {
   if (!ctx || bytes < 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "bad context or negative limit");
   ctx->ws_limit = (size_t)bytes;

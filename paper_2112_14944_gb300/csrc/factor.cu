@@ -1106,7 +1106,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
       PPRVIZ_LAUNCHED(ctx);
     }
     for (int kb = 0; nblk > 1 && kb < nblk; ++kb) {
-      const int q = kb & 1, K0 = kb * NB, k1 = kb + 1 < nblk ? kb + 1 : -1;
+      const int q = kb & 1, k1 = kb + 1 < nblk ? kb + 1 : -1;
       if (k1 >= 0) {
         // block row and column k1 first (nblk - 1 tiles), then the next
         // pivot's inverse and panel on the side stream, on the SMs that the

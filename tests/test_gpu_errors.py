@@ -7,7 +7,10 @@
       of the oracle's.
   PPRVIZ_E_OOM: a context whose workspace is capped below what a call needs
       fails before allocating; lifting the cap makes the same call succeed.
-In both cases the context stays usable.
+  PPRVIZ_E_TIMEOUT: a test aid makes one operand copy of the FP32 inverse's
+      tensor-core update go missing, so the bounded wait for it expires; the
+      kernel stops, drains what it issued and reports the status.
+In every case the context stays usable.
 """
 import numpy as np
 import pytest
@@ -76,3 +79,31 @@ def test_workspace_limit_gives_oom_and_the_context_recovers():
         assert np.all(np.isfinite(X)) and np.isfinite(s)
     finally:
         c.close()
+
+
+def test_expired_wait_returns_timeout_and_the_context_recovers(ctx):
+    """PPRVIZ_E_TIMEOUT: every wait of the tensor-core kernels is bounded by a
+    deadline. pprviz_test_expire_wait makes the next FP32 L^w inverse leave
+    out one operand copy of one tile, so the wait for it runs out (nothing
+    faults); the layout call returns E_TIMEOUT after about the deadline, and
+    the next call on the same context is correct."""
+    import time
+
+    import oracle as O
+    import paper_2112_14944_gb300 as P
+    from _parity import oracle_pdist
+    from paper_2112_14944_gb300 import _binding as B
+    g = synth.chung_lu(300, 8, 2.5, seed=21)      # kp = 384: three pivot blocks
+    D32 = oracle_pdist(g, ALPHA).astype(np.float32)
+    x0 = synth.uniform_x0(g.n, seed=2)
+    B.pprviz_test_expire_wait(ctx.h)
+    t0 = time.perf_counter()
+    with pytest.raises(P.PPRVizError) as ei:
+        ctx.layout(D32, x0, 1, P.FP32)
+    dt = time.perf_counter() - t0
+    assert ei.value.status == B.PPRVIZ_E_TIMEOUT
+    assert "wait expired" in B.pprviz_last_error(ctx.h)
+    assert dt < 30.0
+    X, _ = ctx.layout(D32, x0, 1, P.FP32)
+    ref = O.smacof_step(x0.astype(np.float64), D32.astype(np.float64))
+    assert np.abs(X - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
