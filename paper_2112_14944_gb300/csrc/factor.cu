@@ -147,106 +147,6 @@ __global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, fl
   fac_diag128(kp, K0, A, P);
 }
 
-// The same 128 x 128 inverse as a symmetric block sweep over four 32-wide
-// pivot blocks (the sweep of the whole inverse, one level down), with the
-// full symmetric block in shared memory and 1,024 threads:
-//   Q = S^-1 of the 32 x 32 pivot block S (one warp, rows in registers,
-//   pivots broadcast by shuffles), S -> -Q; U_I = T_IK Q for the other rows;
-//   T_IJ -= U_I T_KJ; then T_IK = U_I and T_KI = U_I^T.
-// After the four pivots the block holds -A_KK^-1: P = A_KK^-1 and A_KK = -P
-// (as fac_diag128). Dynamic shared memory: FAC_DIAGB_SMEM bytes.
-constexpr int kDgLd = 129;  // padded row of the staged block
-constexpr int FAC_DIAGB_SMEM = (128 * kDgLd + 128 * 33 + 32 * 33) * 4;
-
-__device__ __forceinline__ void fac_diag128b(int32_t kp, int32_t K0, float *__restrict__ A, float *__restrict__ P) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float *T = reinterpret_cast<float *>(smem_raw);  // [128][129]
-  float *U = T + 128 * kDgLd;                      // [128][33]: new column panel
-  float *Q = U + 128 * 33;                         // [32][33]: pivot block inverse
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < 128 * 32; e += 1024) {  // 128 rows x 32 float4
-    const int r = e >> 5, c4 = e & 31;
-    const float4 v = *reinterpret_cast<const float4 *>(A + (int64_t)(K0 + r) * kp + K0 + 4 * c4);
-    float *t = T + r * kDgLd + 4 * c4;
-    t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int kb = 0; kb < 4; ++kb) {
-    const int K = 32 * kb;
-    if (warp == 0) {
-      // in-place Gauss-Jordan inverse of the SPD 32 x 32 block: lane = row
-      float a[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) a[c] = T[(K + lane) * kDgLd + K + c];
-#pragma unroll
-      for (int p = 0; p < 32; ++p) {
-        const float piv = 1.0f / __shfl_sync(0xffffffffu, a[p], p);
-        const float f = a[p] * piv;  // a_rp / a_pp
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float apc = __shfl_sync(0xffffffffu, a[c], p);
-          if (c == p) a[c] = (lane == p) ? piv : -f;
-          else a[c] = (lane == p) ? apc * piv : fmaf(-f, apc, a[c]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        Q[lane * 33 + c] = a[c];
-        T[(K + lane) * kDgLd + K + c] = -a[c];
-      }
-    }
-    __syncthreads();
-    // U_I = T_IK Q for the 96 rows outside the pivot block (lane = column)
-    for (int i = warp; i < 128; i += 32) {
-      if (i >= K && i < K + 32) continue;
-      float u = 0.0f;
-#pragma unroll 8
-      for (int s2 = 0; s2 < 32; ++s2) u = fmaf(T[i * kDgLd + K + s2], Q[s2 * 33 + lane], u);
-      U[i * 33 + lane] = u;
-    }
-    __syncthreads();
-    // T_IJ -= U_I T_KJ (T_KJ still the old row panel); rows i = warp + 32 ib,
-    // columns j = lane + 32 jb, outside the pivot block
-#pragma unroll 1
-    for (int ib = 0; ib < 4; ++ib) {
-      if (ib == kb) continue;
-      const int i = warp + 32 * ib;
-      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 8
-      for (int s2 = 0; s2 < 32; ++s2) {
-        const float ui = U[i * 33 + s2];
-#pragma unroll
-        for (int jb = 0; jb < 4; ++jb) acc[jb] = fmaf(ui, T[(K + s2) * kDgLd + lane + 32 * jb], acc[jb]);
-      }
-#pragma unroll
-      for (int jb = 0; jb < 4; ++jb)
-        if (jb != kb) T[i * kDgLd + lane + 32 * jb] -= acc[jb];
-    }
-    __syncthreads();
-    // T_IK = U_I and T_KI = U_I^T
-    for (int e = tid; e < 128 * 32; e += 1024) {
-      const int i = e >> 5, c = e & 31;
-      if (i >= K && i < K + 32) continue;
-      const float u = U[i * 33 + c];
-      T[i * kDgLd + K + c] = u;
-      T[(K + c) * kDgLd + i] = u;
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < 128 * 32; e += 1024) {
-    const int r = e >> 5, c4 = e & 31;
-    const float *t = T + r * kDgLd + 4 * c4;
-    const float4 v = make_float4(t[0], t[1], t[2], t[3]);
-    *reinterpret_cast<float4 *>(P + r * 128 + 4 * c4) = make_float4(-v.x, -v.y, -v.z, -v.w);
-    *reinterpret_cast<float4 *>(A + (int64_t)(K0 + r) * kp + K0 + 4 * c4) = v;
-  }
-}
-
-__global__ void __launch_bounds__(1024) k_fac_diag128b(int32_t kp, int32_t K0, float *__restrict__ A,
-                                                       float *__restrict__ P) {
-  fac_diag128b(kp, K0, A, P);
-}
 
 template <typename T>
 struct V4;  // 4-vector load/store of T
@@ -1088,8 +988,6 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     }
     if (!ctx->ev_t1) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_t1, cudaEventDisableTiming));
     if (!ctx->ev_dp) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_dp, cudaEventDisableTiming));
-    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag128b, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          FAC_DIAGB_SMEM));
     PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_pp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           tcp::SMEM));
     int nsm = 0;
@@ -1099,7 +997,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     ctx->test_expire_wait = false;
     PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
     float *Af = (float *)A;
-    k_fac_diag128b<<<1, 1024, FAC_DIAGB_SMEM, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
+    k_fac_diag128<<<1, 1024, 0, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
     PPRVIZ_LAUNCHED(ctx);
     if (nblk > 1) {
       k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, 0, A, P[0], Ct[0], Ut[0]);
@@ -1117,7 +1015,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
         PPRVIZ_LAUNCHED(ctx);
         PPRVIZ_CUDA(ctx, cudaEventRecord(ctx->ev_t1, ctx->stream));
         PPRVIZ_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_t1, 0));
-        k_fac_diag128b<<<1, 1024, FAC_DIAGB_SMEM, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
+        k_fac_diag128<<<1, 1024, 0, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
         PPRVIZ_LAUNCHED(ctx);
         k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->side>>>(kp, k1 * NB, A, P[q ^ 1], Ct[q ^ 1], Ut[q ^ 1]);
         PPRVIZ_LAUNCHED(ctx);
@@ -1196,7 +1094,7 @@ __device__ __forceinline__ int find_slot(const int *__restrict__ off, int n, int
 __global__ void __launch_bounds__(1024) k_fac_diag128_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
                                                             int32_t K0) {
   const FacJob j = jobs[act[blockIdx.x]];
-  fac_diag128b(j.kp, K0, j.A, j.P);
+  fac_diag128(j.kp, K0, j.A, j.P);
 }
 
 __global__ void __launch_bounds__(256) k_fac_panel_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
@@ -1290,15 +1188,13 @@ int spd_inverse_batch_f32(pprviz_ctx *ctx, int32_t nviews, const int32_t *kp, fl
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SMEM));
-  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag128_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        FAC_DIAGB_SMEM));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   {
     PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
     for (int kb = 0; kb < maxnb; ++kb) {
       const StepTab &st = steps[kb];
       const int32_t K0 = kb * 128;
-      k_fac_diag128_batch<<<(unsigned)st.nall, 1024, FAC_DIAGB_SMEM, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
+      k_fac_diag128_batch<<<(unsigned)st.nall, 1024, 0, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
       PPRVIZ_LAUNCHED(ctx);
       if (st.nmulti == 0) continue;
       k_fac_panel_batch<<<(unsigned)st.npan, 256, panel_smem, ctx->stream>>>(jobs_d, tab_d + st.act_multi,
