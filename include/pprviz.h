@@ -217,6 +217,29 @@ int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int
                 double alpha, double eps, int precision, void *dppr_out, void *pdist_out,
                 int64_t n_clamp, double *cert_out, uint32_t mem_flags);
 
+/* Level-l DPPR and PDist between supernodes (Sec. 3.2, Definition 2, Eq. (2)):
+ *   pi_d(V_i, V_j) = sum_{s in F(V_i), t in F(V_j)} pi_d(s, t) / (|F(V_i)| |F(V_j)|)
+ * for the nsup children V_0 .. V_{nsup-1} of a supernode, each given by its
+ * leaf set F(V_i) (CSR: leaf_ptr[nsup + 1] int64 with leaf_ptr[0] = 0 and
+ * every set non-empty, leaf_idx[leaf_ptr[nsup]] int32 node ids; the sets are
+ * disjoint). One FP32 propagation per supernode from the group start
+ * alpha d(s) / |F(V_i)| on its leaves (the initial residues of GFP,
+ * Algorithm 2), certified by the FP64 residual and refined until
+ * cert_i = ||res_i||_1 / alpha <= eps; every entry of row i is then within
+ * cert_i of Eq. (2). With singleton leaf sets this is pprviz_dppr's DPPR.
+ * ldppr_out: nsup*nsup, row i = pi_d(V_i, .); may be NULL.
+ * pdist_out: nsup*nsup, Eq. (1) on the level-l DPPR (upper clamp 2 ln n_clamp,
+ *            n_clamp = 0 means the graph's n; zero diagonal); may be NULL.
+ * cert_out:  nsup doubles (host); may be NULL.
+ * Float outputs unless PPRVIZ_OUT_FP64; host or device buffers (leaf arrays
+ * and outputs) per PPRVIZ_DEVICE_PTRS.
+ * Errors: E_INVALID_ARG (nsup < 1 or > n, empty or overlapping leaf sets, a
+ * leaf id out of range, alpha / eps / n_clamp out of range), E_NOT_CONVERGED,
+ * E_OOM, E_CUDA. */
+int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
+                      const int32_t *leaf_idx, double alpha, double eps, void *ldppr_out, void *pdist_out,
+                      int64_t n_clamp, double *cert_out, uint32_t mem_flags);
+
 /* P3 alone - PDist from a k*k DPPR matrix (Sec. 3.1, Eq. (1)):
  * Delta[i][j] = min(max(1 - ln(D[i][j] + D[j][i]), 2), 2 ln n_clamp), zero
  * diagonal, z = 0 mapped to the upper clamp. Types per PPRVIZ_OUT_FP64.

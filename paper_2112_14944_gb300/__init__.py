@@ -156,6 +156,23 @@ class Context:
         self._leave(dev, view, dppr_out, pdist_out)
         return dppr_out, pdist_out, cert_out, st
 
+    def level_dppr(self, graph: Graph, leaf_sets, alpha=0.15, eps=1e-6, n_clamp=0, out64=False):
+        """Level-l DPPR and PDist between supernodes given by their leaf sets
+        (a list of node-id arrays, disjoint and non-empty; Sec. 3.2, Eq. (2)).
+        Returns (level DPPR, level PDist, certificates, status) as numpy arrays."""
+        sizes = np.array([len(s) for s in leaf_sets], dtype=np.int64)
+        leaf_ptr = np.zeros(len(leaf_sets) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=leaf_ptr[1:])
+        leaf_idx = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32) for s in leaf_sets]))
+        k = len(leaf_sets)
+        dt = np.float64 if out64 else np.float32
+        D = np.empty((k, k), dtype=dt)
+        Pd = np.empty((k, k), dtype=dt)
+        cert = np.empty(k, dtype=np.float64)
+        st = B.pprviz_level_dppr(self.h, graph.h, k, leaf_ptr, leaf_idx, alpha, eps, D, Pd, n_clamp, cert,
+                                 PPRVIZ_OUT_FP64 if out64 else 0)
+        return D, Pd, cert, st
+
     def pdist(self, dppr, n_clamp, out=None):
         k = dppr.shape[0]
         dev = B._mem_flags(dppr, out) == PPRVIZ_DEVICE_PTRS

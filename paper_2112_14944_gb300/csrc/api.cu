@@ -397,6 +397,82 @@ int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int
   return finish(ctx, status);
 }
 
+int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
+                      const int32_t *leaf_idx, double alpha, double eps, void *ldppr_out, void *pdist_out,
+                      int64_t n_clamp, double *cert_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!g || !leaf_ptr || !leaf_idx) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or leaf sets are NULL");
+  if (nsup < 1 || (int64_t)nsup > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup must be in [1, n]");
+  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
+  if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
+  if (n_clamp == 0) n_clamp = g->n;
+  if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool out64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  // the leaf sets on the host (validated there) and on the device
+  std::vector<int64_t> lp((size_t)nsup + 1);
+  if (dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(lp.data(), leaf_ptr, sizeof(int64_t) * lp.size(), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    memcpy(lp.data(), leaf_ptr, sizeof(int64_t) * lp.size());
+  }
+  if (lp[0] != 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "leaf_ptr[0] must be 0");
+  for (int32_t v = 0; v < nsup; ++v)
+    if (lp[v + 1] <= lp[v]) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "every supernode needs at least one leaf");
+  const int64_t nleaf = lp[nsup];
+  if (nleaf > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "more leaves than nodes: leaf sets must be disjoint");
+  std::vector<int32_t> li((size_t)nleaf);
+  if (dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(li.data(), leaf_idx, sizeof(int32_t) * li.size(), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    memcpy(li.data(), leaf_idx, sizeof(int32_t) * li.size());
+  }
+  std::vector<char> seen((size_t)g->n, 0);
+  for (int32_t t : li) {
+    if (t < 0 || (int64_t)t >= g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "leaf id out of range");
+    if (seen[t]) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "leaf sets must be disjoint (a node is listed twice)");
+    seen[t] = 1;
+  }
+  const int64_t *lp_d = leaf_ptr;
+  const int32_t *li_d = leaf_idx;
+  if (!dev) {
+    const void *p = nullptr;
+    PPRVIZ_TRY(stage_in(ctx, lp.data(), sizeof(int64_t) * lp.size(), false, WS_IN0, &p));
+    lp_d = (const int64_t *)p;
+    PPRVIZ_TRY(stage_in(ctx, li.data(), sizeof(int32_t) * li.size(), false, WS_IN1, &p));
+    li_d = (const int32_t *)p;
+  }
+  const size_t kk = (size_t)nsup * (size_t)nsup;
+  const size_t ob = (out64 ? sizeof(double) : sizeof(float)) * kk;
+  void *ld_d = nullptr;
+  if (ldppr_out && dev) ld_d = ldppr_out;
+  else {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, ob));
+    ld_d = ctx->ws[WS_DPPR].p;
+  }
+  int status = level_dppr_solve(ctx, g, nsup, lp_d, li_d, lp, li, alpha, eps, ld_d, out64, cert_out);
+  if (status != PPRVIZ_OK && status != PPRVIZ_E_NOT_CONVERGED) return finish(ctx, status);
+  const std::string keep_err = ctx->err;
+  if (pdist_out) {
+    void *pd_d = dev ? pdist_out : nullptr;
+    if (!pd_d) {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_PDIST, ob));
+      pd_d = ctx->ws[WS_PDIST].p;
+    }
+    PPRVIZ_TRY(pdist_launch(ctx, ld_d, nsup, n_clamp, pd_d, out64));
+    if (!dev) PPRVIZ_CUDA(ctx, cudaMemcpyAsync(pdist_out, pd_d, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (ldppr_out && !dev) PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ldppr_out, ld_d, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dev || cert_out) PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (status != PPRVIZ_OK) ctx->err = keep_err;
+  return finish(ctx, status);
+}
+
 int pprviz_pdist(pprviz_ctx *ctx, const void *dppr, int32_t k, int64_t n_clamp, void *pdist_out, uint32_t mem_flags) {
   if (!ctx) return PPRVIZ_E_INVALID_ARG;
   PPRVIZ_TRY(begin(ctx));

@@ -159,6 +159,15 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
                      const int64_t *sq_off, double alpha, double eps, const int32_t *iota_d, float *pdist_all,
                      double *cert_h);
 
+// Level-l DPPR between nsup supernodes with disjoint, non-empty leaf sets
+// (CSR leaf_ptr / leaf_idx, on the device and the host); out_d: nsup x nsup
+// row-major (source supernode = row), double if out64; cert_h: nsup
+// certificates ||res||_1 / alpha.
+int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr_d,
+                     const int32_t *leaf_idx_d, const std::vector<int64_t> &leaf_ptr_h,
+                     const std::vector<int32_t> &leaf_idx_h, double alpha, double eps, void *out_d, bool out64,
+                     double *cert_h);
+
 // ---- graph analysis for the deflated sweeps (spectral.cu) ------------------
 // Fills g->comp / h_comp / h_mc / spec_b / spec_deflate once per graph.
 int graph_spectral(pprviz_ctx *ctx, const pprviz_graph *g);

@@ -291,13 +291,17 @@ __device__ __forceinline__ void load4(const double *hi, const float *lo, double 
 // Batched views (BATCH, see k_sweep): block b covers the state rows
 // brows[b] = [x, y), all of one view, so its partial sums belong to that view;
 // graph node i is state row i - row0 and the source test is src[i] == g0 + q.
-template <typename T, bool WEIGHTED, bool EXACT, bool BATCH>
+// Level-l DPPR (LEVEL): column q is the group start of supernode g0 + q
+// (Sec. 3.2, Eq. (2)): b_jq = alpha d(j) / |F(V_q)| for the leaves j of V_q,
+// given per node by src[j] = its supernode (-1 for none) and bscale[j] =
+// d(j) / |F(V_src[j])| in FP64, so the residual is exact for that b.
+template <typename T, bool WEIGHTED, bool EXACT, bool BATCH, bool LEVEL>
 __global__ void __launch_bounds__(kWarps * 32)
 k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
            const float *__restrict__ w, const double *__restrict__ invdw, const float2 *__restrict__ dwff,
            const int32_t *__restrict__ src, const T *__restrict__ yhi, const float *__restrict__ ylo,
            float *__restrict__ rhs_out, double *__restrict__ part_out, double alpha, double c,
-           const int2 *__restrict__ brows, int64_t row0, int32_t g0) {
+           const int2 *__restrict__ brows, int64_t row0, int32_t g0, const double *__restrict__ bscale) {
   constexpr int VEC = 4;  // 128 sources per warp chunk for both state types
   __shared__ double red[kWarps][32 * VEC];
   __shared__ double reds[kWarps][32 * VEC];
@@ -307,7 +311,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
   const int64_t off = chunk * (32 * VEC) + lane * VEC;
   int32_t sq[VEC];
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) sq[u] = BATCH ? 0 : src[off + u];
+  for (int u = 0; u < VEC; ++u) sq[u] = (BATCH || LEVEL) ? 0 : src[off + u];
   const int64_t rb = BATCH ? row0 : 0;  // state row of graph node i: i - rb
   // alpha and c as float-float pairs (float-float residual of the FP32 path)
   const float alh = (float)alpha, all = (float)(alpha - (double)alh);
@@ -332,11 +336,12 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
   }
   for (int64_t j = jfirst; j < jend; j += stride) {
     const int64_t jg = j + row0;  // row of the graph
-    if (BATCH) {
+    if (BATCH || LEVEL) {
       const int32_t lj = src[jg] - g0 - (int32_t)off;
 #pragma unroll
       for (int u = 0; u < VEC; ++u) sq[u] = (lj == u) ? (int32_t)jg : -1;
     }
+    const double bval = LEVEL ? alpha * bscale[jg] : alpha;  // b_jq where q is j's column
     double acc[VEC];
 #pragma unroll
     for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
@@ -426,7 +431,12 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
         const float b1 = s1 - p2;
         const float e1 = (p2 - (s1 - b1)) + (-p1 - b1);
         const bool src_here = sq[u] == (int32_t)jg;
-        const float bh = src_here ? alh : 0.0f, bl = src_here ? all : 0.0f;
+        float bh = src_here ? alh : 0.0f, bl = src_here ? all : 0.0f;
+        if (LEVEL) {
+          const float bvh = (float)bval;
+          bh = src_here ? bvh : 0.0f;
+          bl = src_here ? (float)(bval - (double)bvh) : 0.0f;
+        }
         const float s2 = s1 + bh;
         const float b2 = s2 - s1;
         const float e2 = (s1 - (s2 - b2)) + (bh - b2);
@@ -471,7 +481,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
     for (int u = 0; u < VEC; ++u) {
       const double y = yrow[u];
       if (e == b) acc[u] += y;
-      const double bq = (sq[u] == (int32_t)jg) ? alpha : 0.0;
+      const double bq = (sq[u] == (int32_t)jg) ? bval : 0.0;
       const double r = bq - dw * y + c * acc[u];
       if (rhs_out) rhs_out[rowoff + u] = (float)r;
       part[u] += fabs(r);
@@ -687,7 +697,8 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
 template <typename T, bool EXACT>
 int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src,
                     const T *yhi, const float *ylo, float *rhs_out, double *l1, double alpha,
-                    const Wave *wv = nullptr, int total_blocks = 1216) {
+                    const Wave *wv = nullptr, int total_blocks = 1216, const double *bscale = nullptr,
+                    int32_t level_g0 = 0) {
   const int nchunks = (int)(ld / 128);
   int rows_blocks;
   if (wv) {
@@ -708,16 +719,17 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   const int64_t n = wv ? wv->nrows : g->n;
   const int2 *brows = wv ? wv->brows : nullptr;
   const int64_t row0 = wv ? wv->row0 : 0;
-  const int32_t g0 = wv ? wv->g0 : 0;
+  const int32_t g0 = wv ? wv->g0 : level_g0;
   if (wv) src = wv->lidx;
-#define PPRVIZ_RES(W, B)                                                                                  \
-  k_residual<T, W, EXACT, B><<<grid, kWarps * 32, 0, ctx->stream>>>(                                        \
+#define PPRVIZ_RES(W, B, L)                                                                                  \
+  k_residual<T, W, EXACT, B, L><<<grid, kWarps * 32, 0, ctx->stream>>>(                                        \
       n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), w, g->invdw_d.as<double>(), g->dwff.as<float2>(), src, \
-      yhi, ylo, rhs_out, part, alpha, 1.0 - alpha, brows, row0, g0)
+      yhi, ylo, rhs_out, part, alpha, 1.0 - alpha, brows, row0, g0, bscale)
   {
     PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL);
-    if (wv) { if (g->weighted) PPRVIZ_RES(true, true); else PPRVIZ_RES(false, true); }
-    else { if (g->weighted) PPRVIZ_RES(true, false); else PPRVIZ_RES(false, false); }
+    if (wv) { if (g->weighted) PPRVIZ_RES(true, true, false); else PPRVIZ_RES(false, true, false); }
+    else if (bscale) { if (g->weighted) PPRVIZ_RES(true, false, true); else PPRVIZ_RES(false, false, true); }
+    else { if (g->weighted) PPRVIZ_RES(true, false, false); else PPRVIZ_RES(false, false, false); }
   }
 #undef PPRVIZ_RES
   PPRVIZ_LAUNCHED(ctx);
@@ -1159,6 +1171,174 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   return PPRVIZ_OK;
 }
 
+
+// --------------------------------------------------------------------------
+// Level-l DPPR between supernodes (Sec. 3.2, Definition 2, Eq. (2)):
+//   pi_d(V_i, V_j) = sum_{s in F(V_i), t in F(V_j)} pi_d(s, t) / (|F(V_i)| |F(V_j)|).
+// By linearity the inner sum over s is one PPR solve from the group start
+// b_i = alpha sum_{s in F(V_i)} d(s) / |F(V_i)| e_s (the initial residues of
+// GFP, Algorithm 2): rho_i = b_i (I - cP)^-1 = sum_s d(s) / |F(V_i)| pi(s, .),
+// and pi_d(V_i, V_j) is the average of rho_i over F(V_j). One source column per
+// supernode runs the FP32 Chebyshev sweeps with a dense right-hand side; the
+// FP64 residual (LEVEL mode, exact b) and FP32 refinement certify every entry
+// of rho_i to ||res_i||_1 / alpha, which bounds each average as well.
+// --------------------------------------------------------------------------
+namespace {
+
+// rhs[j][q] = alpha * bscale[j] if node j is a leaf of supernode g0 + q, else 0
+__global__ void k_level_rhs(int64_t n, int64_t ld, int32_t g0, const int32_t *__restrict__ owner,
+                            const double *__restrict__ bscale, double alpha, float *__restrict__ rhs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * ld) return;
+  const int64_t j = idx / ld, q = idx - j * ld;
+  rhs[idx] = (owner[j] == g0 + (int32_t)q) ? (float)(alpha * bscale[j]) : 0.0f;
+}
+
+// out[(g0 + q) * nsup + r] = sum_{t in F(V_r)} x_q(t) / |F(V_r)|, x = dw (y_hi + y_lo),
+// in FP64; block (chunk of 128 columns, target supernode r), thread = column.
+template <typename TO>
+__global__ void __launch_bounds__(128)
+k_level_extract(int32_t nsup, int32_t g0, int32_t gvalid, int64_t ld, const int64_t *__restrict__ leaf_ptr,
+                const int32_t *__restrict__ leaf_idx, const double *__restrict__ invdw, const float *__restrict__ yhi,
+                const float *__restrict__ ylo, TO *__restrict__ out) {
+  const int32_t r = blockIdx.y;
+  const int32_t q = blockIdx.x * 128 + threadIdx.x;
+  if (q >= gvalid) return;
+  const int64_t a = leaf_ptr[r], e = leaf_ptr[r + 1];
+  double acc = 0.0;
+  for (int64_t p = a; p < e; ++p) {
+    const int64_t t = leaf_idx[p];
+    const double y = (double)yhi[t * ld + q] + (ylo ? (double)ylo[t * ld + q] : 0.0);
+    acc += y / invdw[t];
+  }
+  out[(int64_t)(g0 + q) * nsup + r] = (TO)(acc / (double)(e - a));
+}
+
+}  // namespace
+
+int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr_d,
+                     const int32_t *leaf_idx_d, const std::vector<int64_t> &leaf_ptr_h,
+                     const std::vector<int32_t> &leaf_idx_h, double alpha, double eps, void *out_d, bool out64,
+                     double *cert_h) {
+  const int64_t n = g->n;
+  // owner of each node and the FP64 right-hand-side scale d(j) / |F(V_owner)|
+  std::vector<int32_t> owner((size_t)n, -1);
+  std::vector<double> bscale((size_t)n, 0.0);
+  for (int32_t v = 0; v < nsup; ++v) {
+    const double sz = (double)(leaf_ptr_h[v + 1] - leaf_ptr_h[v]);
+    for (int64_t p = leaf_ptr_h[v]; p < leaf_ptr_h[v + 1]; ++p) {
+      const int32_t t = leaf_idx_h[p];
+      owner[t] = v;
+      bscale[t] = g->h_deg[t] / sz;
+    }
+  }
+  const int64_t ld = choose_group(n, nsup, sizeof(float));
+  const size_t sbytes = sizeof(float) * (size_t)(n * ld);
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y0, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y1, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y2, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y3, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_RHS, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_SRC, sizeof(int32_t) * (size_t)std::max<int64_t>(n, ld)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, 2 * sizeof(double) * (size_t)ld));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_KAPPA, sizeof(double) * (size_t)n));
+  int32_t *owner_d = ctx->ws[WS_SRC].as<int32_t>();
+  double *bscale_d = ctx->ws[WS_KAPPA].as<double>();
+  double *l1 = ctx->ws[WS_CERT].as<double>();
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(owner_d, owner.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(bscale_d, bscale.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  pprviz_stats &st = ctx->stats;
+  st.source_group = (int32_t)ld;
+  const double c = 1.0 - alpha;
+  auto rate = [](double delta) { return delta > 1e-12 ? chebyshev_rate(delta) : 0.0; };
+  auto sweeps_for = [](double factor, double r) { return r > 0.0 ? (int)ceil(log(0.5 * factor) / log(r)) : 1; };
+  const bool exact_res = eps < 1e-9;
+  bool not_converged = false;
+  std::vector<double> l1h((size_t)2 * ld);
+  for (int32_t g0 = 0; g0 < nsup; g0 += (int32_t)ld) {
+    const int32_t gvalid = (int32_t)std::min<int64_t>(ld, (int64_t)nsup - g0);
+    st.groups++;
+    float *bufs[4] = {ctx->ws[WS_Y0].as<float>(), ctx->ws[WS_Y1].as<float>(), ctx->ws[WS_Y2].as<float>(),
+                      ctx->ws[WS_Y3].as<float>()};
+    float *rhs = ctx->ws[WS_RHS].as<float>();
+    {
+      PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER);
+      k_level_rhs<<<(unsigned)((n * ld + 255) / 256), 256, 0, ctx->stream>>>(n, ld, g0, owner_d, bscale_d, alpha, rhs);
+    }
+    PPRVIZ_LAUNCHED(ctx);
+    // undeflated Chebyshev on the whole interval [1 - c, 1 + c]: a leaf set
+    // may span several components
+    const double delta_c = c;
+    const int K1 = std::max(2, sweeps_for(1e-5, rate(delta_c)));
+    float *hi = nullptr;
+    PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, owner_d, (int32_t)ld, rhs, bufs[0], bufs[1], K1, alpha, nullptr, nullptr,
+                               nullptr, delta_c, &hi));
+    st.sweeps_main += K1;
+    st.bytes_sweep += 16.0 * (double)n * gvalid * (K1 - 1);
+    float *fa = hi == bufs[0] ? bufs[1] : bufs[0], *fb = bufs[2], *fc = bufs[3];
+    float *lo = nullptr;
+    std::vector<double> cert((size_t)gvalid);
+    auto certs = [&](const float *yh, const float *yl) -> int {
+      PPRVIZ_TRY((exact_res ? launch_residual<float, true>(ctx, g, ld, owner_d, yh, yl, rhs, l1, alpha, nullptr, 1216,
+                                                            bscale_d, g0)
+                            : launch_residual<float, false>(ctx, g, ld, owner_d, yh, yl, rhs, l1, alpha, nullptr, 1216,
+                                                             bscale_d, g0)));
+      st.residual_passes++;
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(l1h.data(), l1, sizeof(double) * 2 * (size_t)ld, cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+      PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      for (int32_t q = 0; q < gvalid; ++q) cert[q] = l1h[q] / alpha;
+      return PPRVIZ_OK;
+    };
+    PPRVIZ_TRY(certs(hi, nullptr));
+    for (int pass = 0; pass < kMaxRefine; ++pass) {
+      double cmax = 0.0;
+      for (double v : cert) cmax = std::max(cmax, v);
+      if (cmax <= eps) break;
+      int K2 = sweeps_for(0.5 * eps / cmax, rate(delta_c)) + 2;
+      K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
+      float *delta = nullptr;
+      PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, owner_d, (int32_t)ld, rhs, fa, fb, K2, alpha, nullptr, nullptr, nullptr,
+                                 delta_c, &delta));
+      st.sweeps_refine += K2;
+      st.bytes_sweep += 16.0 * (double)n * gvalid * (K2 - 1);
+      st.refine_passes++;
+      const int64_t cnt = n * ld;
+      if (!lo) {
+        lo = delta;
+        fa = (delta == fa) ? fb : fa;
+        fb = fc;
+      } else {
+        { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_axpy<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, delta, lo); }
+        PPRVIZ_LAUNCHED(ctx);
+      }
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_renorm<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(cnt, hi, lo); }
+      PPRVIZ_LAUNCHED(ctx);
+      PPRVIZ_TRY(certs(hi, lo));
+    }
+    for (int32_t q = 0; q < gvalid; ++q) {
+      st.max_cert = std::max(st.max_cert, cert[q]);
+      if (cert[q] > eps) not_converged = true;
+      if (cert_h) cert_h[g0 + q] = cert[q];
+    }
+    {
+      PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT);
+      const dim3 grid((unsigned)((gvalid + 127) / 128), (unsigned)nsup);
+      if (out64)
+        k_level_extract<double><<<grid, 128, 0, ctx->stream>>>(nsup, g0, gvalid, ld, leaf_ptr_d, leaf_idx_d,
+                                                                g->invdw_d.as<double>(), hi, lo, (double *)out_d);
+      else
+        k_level_extract<float><<<grid, 128, 0, ctx->stream>>>(nsup, g0, gvalid, ld, leaf_ptr_d, leaf_idx_d,
+                                                               g->invdw_d.as<double>(), hi, lo, (float *)out_d);
+    }
+    PPRVIZ_LAUNCHED(ctx);
+  }
+  if (not_converged)
+    return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "certificate above eps after the refinement cap");
+  return PPRVIZ_OK;
+}
 
 // --------------------------------------------------------------------------
 // Batched views (P7): many views of uneven size in shared launches.

@@ -346,3 +346,22 @@ def test_level_dppr_reduces_to_node_dppr_for_singletons():
     sets = [list(range(0, 20)), list(range(20, 60))]
     lv = O.level_dppr(D, sets)
     assert abs(lv[0, 1] - D[:20, 20:].mean()) < 1e-14
+
+
+def test_level_dppr_star_closed_form():
+    # Definition 2 on the star (centre 0, L leaves) with supernodes A = {0} and
+    # B = {1..L}: every pi_d(centre, leaf) = pi_d(leaf, centre) = c / (1 + c),
+    # so both cross averages are c / (1 + c); within B, pi_d(s, s) =
+    # alpha + c^2 / (L (1 + c)) and pi_d(s, t) = c^2 / (L (1 + c)) (s != t), so
+    # pi_d(B, B) = alpha / L + c^2 / (L (1 + c)); pi_d(A, A) = 1 / (1 + c) * L.
+    L = 7
+    n = L + 1
+    rp, col = _csr_from_edges(n, [(0, i) for i in range(1, n)], True)
+    P = O.transition_matrix(n, rp, col)
+    d = O.degrees(n, rp, col)
+    D = O.dppr_rows(O.ppr_direct(P, ALPHA), d, np.arange(n))
+    lv = O.level_dppr(D, [[0], list(range(1, n))])
+    assert abs(lv[0, 1] - C / (1 + C)) < 1e-14
+    assert abs(lv[1, 0] - C / (1 + C)) < 1e-14
+    assert abs(lv[1, 1] - (ALPHA / L + C * C / (L * (1 + C)))) < 1e-14
+    assert abs(lv[0, 0] - L / (1 + C)) < 1e-13
