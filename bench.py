@@ -19,6 +19,11 @@ workload (the reference arm of this benchmark).
 default line): 256 SBM views of 50..5,000 nodes, one pprviz_views_batch call
 per step (DPPR + PDist + 200 layout updates of every view).
 
+`--workload view2m`: the 8,192-node view of a 2M-node Chung-Lu graph (DPPR /
+PDist among the view, then the stress energy and its backward through the
+autograd function). `--workload small`: the n = 1,000 FP64 plain-method
+workload (DPPR + PDist + 300 FP64 layout updates). Neither is the default line.
+
 `--workload dense` measures the dense-view propagation instead (not the
 default line): a dense clustered weighted view, n = 20,000, 20 blocks, 15 %
 density, lognormal(0, 1) weights, all nodes as the view; one step = all-pairs
@@ -110,7 +115,7 @@ def parse():
                     help="one untimed pass of the hot path (for profiler command lines)")
     ap.add_argument("--dense-precision", default="bf16", choices=["bf16", "tf32x3"],
                     help="tensor-core sweep operands of --workload dense (the other mode is timed beside it)")
-    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views"],
+    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small"],
                     help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000); "
                          "views: the 256 batched SBM views")
     return ap.parse_args()
@@ -627,6 +632,193 @@ def run_views(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- view of a 2M-node graph
+VIEW2M_WORKLOAD = "chung_lu_n2000000_deg10_view8192"
+
+
+def run_view2m(args, rank, world, local_rank):
+    """The differentiable-layout workload: Chung-Lu n = 2,000,000, mean degree
+    10, exponent 2.5, seed 0; a view of 8,192 nodes drawn uniformly (seed 0).
+    One step = graph ingest + validation, FP32 DPPR / PDist among the view
+    (n_clamp = n) with the FP64 certificate, then the stress energy of a layout
+    of the view and its gradient through the autograd function (forward + the
+    hand-written backward, pair recomputation)."""
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = synth.chung_lu(2_000_000, 10, 2.5, seed=0)
+    k = 8192
+    view_h = synth.sample_view(g.n, k, seed=0)
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    view = torch.from_numpy(view_h).to(dev)
+    D = torch.empty((k, k), dtype=torch.float32, device=dev)
+    Dl = torch.empty_like(D)
+    X0 = torch.from_numpy(synth.uniform_x0(k, seed=0) * 8.0).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    SE = P.StressEnergy
+
+    def step():
+        G = ctx.upload(g.n, rp, col)
+        launches = ctx.stats()["kernel_launches"]
+        _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
+        sd = ctx.stats()
+        launches += sd["kernel_launches"]
+        X = X0.clone().requires_grad_(True)
+        with torch.cuda.stream(stream):
+            e = SE.apply(X, Dl, ctx)
+            launches += ctx.stats()["kernel_launches"]
+            e.backward()
+            launches += ctx.stats()["kernel_launches"]
+        G.free()
+        return sd, status, float(cert.max()), launches, X.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier_if_group()
+    torch.cuda.synchronize()
+    ctx.profile(PROF_EVERY)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, sts, certs, launches, bytes_sweep, sweeps = [], [], [], 0, 0.0, 0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sd, st, cm, nl, gx = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        sts.append(st)
+        certs.append(cm)
+        launches += nl
+        bytes_sweep += sd["bytes_sweep"]
+        sweeps += sd["sweeps_main"] + sd["sweeps_refine"]
+    torch.cuda.synchronize()
+    sampler.stop()
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    assert all(x == 0 for x in sts) and max(certs) <= EPS, (sts, max(certs))
+    assert bool(torch.isfinite(gx).all())
+    total = max_over_ranks(sum(ms), dev)
+    # Algorithm 2's frontier on this workload: per power-iteration sweep, the
+    # share of (node, source) entries whose push residue is above GFP's
+    # threshold for eps (512 of the view's sources; outside the timed steps)
+    nf, T = 512, 140
+    G = ctx.upload(g.n, rp, col)
+    act = ctx.frontier_profile(G, view_h[:nf].copy(), T, ALPHA, EPS)
+    G.free()
+    frac = act / float(g.n * nf)
+    frontier = {"sources": nf, "sweeps": T, "active_fraction_every_10_sweeps": [float(x) for x in frac[::10]],
+                "max_active_fraction": float(frac.max()), "argmax_sweep": int(frac.argmax()),
+                "mean_active_fraction_first_third": float(frac[:T // 3].mean()),
+                "sweeps_with_any_active": int((act > 0).sum())}
+    if rank != 0:
+        return
+    hbm, _, peak_kind = peaks()
+    sw_ms, sw_all, sw_n = ktimes["sweep"]
+    per = bytes_sweep / max(1, sw_all)
+    ach = per / (sw_ms / max(1, sw_n) / 1e3) / 1e9 if sw_n else None
+    roof = {"kernel": "propagation sweep (k_sweep): the [2M][G] state streams from HBM", "bound": "hbm",
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+            "launches": sw_all, "timed_launches": sw_n, "avg_launch_us": 1e3 * sw_ms / max(1, sw_n),
+            "alg_bytes_per_launch": per, "traffic": None,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
+    entries = float(k) * k
+    line = {
+        "metric": "DPPR entries/s, 8,192-node view of a 2M-node Chung-Lu graph (+ energy and backward)",
+        "value": whole_job_rate(entries, args.steps, world, total), "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": VIEW2M_WORKLOAD, "graph": "chung-lu", "n": g.n, "nnz": int(g.nnz), "mean_degree": 10,
+                   "exponent": 2.5, "seed": 0, "view": "8,192 nodes uniform without replacement (seed 0)",
+                   "n_clamp": g.n, "alpha": ALPHA, "eps": EPS,
+                   "propagation": "fp32 chebyshev + fp64 residual certificate + fp32 refinement",
+                   "energy": "stress energy of U[-8,8]^2 coordinates + backward (autograd.Function)",
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "sweeps_per_step": sweeps / args.steps, "max_cert": max(certs), "roofline": roof,
+        "frontier": frontier,
+        "kernel_share": class_share(ktimes, args.steps), "gpu_launches": int(launches), "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- small FP64 workload
+SMALL_WORKLOAD = "chung_lu_n1000_deg10_fp64"
+
+
+def run_small(args, rank, world, local_rank):
+    """The small FP64 workload: Chung-Lu n = 1,000, mean degree 10, exponent
+    2.5, seed 0; all-pairs FP64 DPPR -> PDist -> 300 FP64 layout updates from
+    U[-1,1]^2 (seed 0); device buffers. Reported as latency (it fits in L2)."""
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = 1000
+    g = synth.chung_lu(n, 10, 2.5, seed=0)
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    view = torch.arange(n, dtype=torch.int32, device=dev)
+    D = torch.empty((n, n), dtype=torch.float64, device=dev)
+    Dl = torch.empty_like(D)
+    x0 = torch.from_numpy(synth.uniform_x0(n, seed=0).astype(np.float64)).to(dev)
+    xo = torch.empty_like(x0)
+
+    def step():
+        G = ctx.upload(n, rp, col)
+        launches = ctx.stats()["kernel_launches"]
+        _, _, cert, status = ctx.dppr(G, view, ALPHA, EPS, P.FP64, dppr_out=D, pdist_out=Dl, cert=True, out64=True)
+        launches += ctx.stats()["kernel_launches"]
+        _, s = ctx.layout(Dl, x0, 300, P.FP64, x_out=xo, stress=True)
+        launches += ctx.stats()["kernel_launches"]
+        G.free()
+        return status, float(cert.max()), launches, s
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms, sts, certs, launches = [], [], [], 0
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, cm, nl, s = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        sts.append(st)
+        certs.append(cm)
+        launches += nl
+    assert all(x == 0 for x in sts) and max(certs) <= EPS
+    total = max_over_ranks(sum(ms), dev)
+    if rank != 0:
+        return
+    line = {
+        "metric": "DPPR entries/s, Chung-Lu n=1k, FP64 plain method (DPPR + PDist + 300 layout updates)",
+        "value": whole_job_rate(float(n) * n, args.steps, world, total), "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": SMALL_WORKLOAD, "graph": "chung-lu", "n": n, "mean_degree": 10, "exponent": 2.5,
+                   "seed": 0, "alpha": ALPHA, "eps": EPS, "layout_iters": 300,
+                   "l2": "not flushed: the whole workload fits in L2 (reported as latency)",
+                   "parallelism": f"replicas x{world}"},
+        "final_stress": s, "max_cert": max(certs), "gpu_launches": int(launches),
+        "layout_iters_per_s": 300 / (total / args.steps / 1e3),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -879,6 +1071,10 @@ def main():
         run_dense(args, rank, world, local_rank)
     elif args.workload == "views":
         run_views(args, rank, world, local_rank)
+    elif args.workload == "view2m":
+        run_view2m(args, rank, world, local_rank)
+    elif args.workload == "small":
+        run_small(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

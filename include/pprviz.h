@@ -240,6 +240,20 @@ int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, cons
                       const int32_t *leaf_idx, double alpha, double eps, void *ldppr_out, void *pdist_out,
                       int64_t n_clamp, double *cert_out, uint32_t mem_flags);
 
+/* Frontier profile of the view's propagation (a diagnostic for the threshold
+ * of Algorithm 2, GFP). Runs `sweeps` FP64 power-iteration sweeps
+ * x_{t+1} = alpha e_s + (1 - alpha) x_t P from every view source (Forward-Push
+ * with every node pushed once per sweep) and writes to active_out[t] (host,
+ * `sweeps` int64) the number of (node v, source s) entries whose push residue
+ * after sweep t, r = d(s) (x_{t+1} - x_t)_v / alpha (Eq. (3)), exceeds
+ * d(v) r_max with r_max = eps / max_{t in view} d(t): the entries that GFP
+ * would still push. The fraction active_out[t] / (n k) is the share of a sweep
+ * that a frontier-thresholded sweep could skip no more than. view: as in
+ * pprviz_dppr (host or device per mem_flags).
+ * Errors: E_INVALID_ARG (k, sweeps outside [1, 100000], alpha, eps), E_OOM, E_CUDA. */
+int pprviz_frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k, double alpha,
+                            double eps, int32_t sweeps, int64_t *active_out, uint32_t mem_flags);
+
 /* P3 alone - PDist from a k*k DPPR matrix (Sec. 3.1, Eq. (1)):
  * Delta[i][j] = min(max(1 - ln(D[i][j] + D[j][i]), 2), 2 ln n_clamp), zero
  * diagonal, z = 0 mapped to the upper clamp. Types per PPRVIZ_OUT_FP64.

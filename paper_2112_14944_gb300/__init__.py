@@ -173,6 +173,14 @@ class Context:
                                  PPRVIZ_OUT_FP64 if out64 else 0)
         return D, Pd, cert, st
 
+    def frontier_profile(self, graph: Graph, view, sweeps, alpha=0.15, eps=1e-6):
+        """Per power-iteration sweep, the (node, source) entries whose push
+        residue is above GFP's threshold d(v) eps / max d (Algorithm 2)."""
+        out = np.zeros(int(sweeps), dtype=np.int64)
+        mf = B._mem_flags(view)
+        B.pprviz_frontier_profile(self.h, graph.h, view, len(view), alpha, eps, sweeps, out, mf)
+        return out
+
     def pdist(self, dppr, n_clamp, out=None):
         k = dppr.shape[0]
         dev = B._mem_flags(dppr, out) == PPRVIZ_DEVICE_PTRS

@@ -56,6 +56,8 @@ _SIGS = {
     "pprviz_dppr": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_double, C.c_double, C.c_int, _VP, _VP, C.c_int64,
                               _VP, C.c_uint32]),
     "pprviz_pdist": (C.c_int, [_VP, _VP, C.c_int32, C.c_int64, _VP, C.c_uint32]),
+    "pprviz_frontier_profile": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_double, C.c_double, C.c_int32, _VP,
+                                          C.c_uint32]),
     "pprviz_level_dppr": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, C.c_double, C.c_double, _VP, _VP, C.c_int64, _VP,
                                     C.c_uint32]),
     "pprviz_layout": (C.c_int, [_VP, _VP, C.c_int32, _VP, C.c_int32, C.c_int, _VP, _VP, C.c_uint32]),
@@ -221,6 +223,11 @@ def pprviz_level_dppr(ctx, g, nsup, leaf_ptr, leaf_idx, alpha, eps, ldppr_out, p
     return _check(ctx, load().pprviz_level_dppr(ctx, g, int(nsup), _ptr(leaf_ptr)[0], _ptr(leaf_idx)[0], float(alpha),
                                                 float(eps), _ptr(ldppr_out)[0], _ptr(pdist_out)[0], int(n_clamp),
                                                 _ptr(cert_out)[0], mem_flags), allow=(PPRVIZ_E_NOT_CONVERGED,))
+
+
+def pprviz_frontier_profile(ctx, g, view, k, alpha, eps, sweeps, active_out, mem_flags):
+    return _check(ctx, load().pprviz_frontier_profile(ctx, g, _ptr(view)[0], int(k), float(alpha), float(eps),
+                                                      int(sweeps), _ptr(active_out)[0], mem_flags))
 
 
 def pprviz_pdist(ctx, dppr, k, n_clamp, pdist_out, mem_flags):

@@ -473,6 +473,32 @@ int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, cons
   return finish(ctx, status);
 }
 
+int pprviz_frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k, double alpha,
+                            double eps, int32_t sweeps, int64_t *active_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!g || !view || !active_out) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph, view or output is NULL");
+  if (k < 1 || (int64_t)k > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be in [1, n]");
+  if (sweeps < 1 || sweeps > 100000) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "sweeps must be in [1, 100000]");
+  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
+  if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  std::vector<int32_t> view_h((size_t)k);
+  const int32_t *view_d = nullptr;
+  if (dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(view_h.data(), view, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    view_d = view;
+  } else {
+    memcpy(view_h.data(), view, sizeof(int32_t) * k);
+    const void *p = nullptr;
+    PPRVIZ_TRY(stage_in(ctx, view, sizeof(int32_t) * k, false, WS_VIEW, &p));
+    view_d = (const int32_t *)p;
+  }
+  PPRVIZ_TRY(view_check(ctx, g, view_d, k));
+  return finish(ctx, frontier_profile(ctx, g, view_d, view_h, k, alpha, eps, sweeps, active_out));
+}
+
 int pprviz_pdist(pprviz_ctx *ctx, const void *dppr, int32_t k, int64_t n_clamp, void *pdist_out, uint32_t mem_flags) {
   if (!ctx) return PPRVIZ_E_INVALID_ARG;
   PPRVIZ_TRY(begin(ctx));

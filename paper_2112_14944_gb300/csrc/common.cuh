@@ -168,6 +168,13 @@ int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const
                      const std::vector<int32_t> &leaf_idx_h, double alpha, double eps, void *out_d, bool out64,
                      double *cert_h);
 
+// Per power-iteration sweep t < sweeps, the number of (node, source) entries
+// of the k view sources whose push residue exceeds d(v) eps / max_view d
+// (active_h: host, sweeps entries).
+int frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
+                     const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps, int32_t sweeps,
+                     int64_t *active_h);
+
 // ---- graph analysis for the deflated sweeps (spectral.cu) ------------------
 // Fills g->comp / h_comp / h_mc / spec_b / spec_deflate once per graph.
 int graph_spectral(pprviz_ctx *ctx, const pprviz_graph *g);

@@ -1341,6 +1341,93 @@ int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const
 }
 
 // --------------------------------------------------------------------------
+// Frontier profile (diagnostic for Algorithm 2's threshold). Power iteration
+// x_{t+1} = alpha e_s + c x_t P is Forward-Push with every node pushed once
+// per sweep: after sweep t the push residue of node v is, in DPPR units,
+// r_v = d(s) (x_{t+1} - x_t)_v / alpha (Eq. (3)). GFP pushes only nodes with
+// r_v > d(v) r_max; r_max = eps / max_{t in view} d(t) bounds every DPPR
+// entry of the view by eps (sum_v r_v pi(v, t) <= r_max d(t) on an undirected
+// graph). This counts, per sweep, the (node, source) entries above it.
+// --------------------------------------------------------------------------
+namespace {
+
+__global__ void k_frontier_count(int64_t n, int64_t ld, int32_t gvalid, const double *__restrict__ ycur,
+                                 const double *__restrict__ ynext, const double *__restrict__ invdw,
+                                 const double *__restrict__ deg, const double *__restrict__ dsrc, double alpha,
+                                 double rmax, unsigned long long *__restrict__ count) {
+  __shared__ unsigned int blk;
+  if (threadIdx.x == 0) blk = 0;
+  __syncthreads();
+  unsigned int mine = 0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * ld;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = idx / ld, q = idx - v * ld;
+    if (q >= gvalid) continue;
+    const double r = dsrc[q] * fabs(ynext[idx] - ycur[idx]) / invdw[v] / alpha;
+    if (r > deg[v] * rmax) ++mine;
+  }
+  atomicAdd(&blk, mine);
+  __syncthreads();
+  if (threadIdx.x == 0 && blk) atomicAdd(count, (unsigned long long)blk);
+}
+
+}  // namespace
+
+int frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
+                     const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps, int32_t sweeps,
+                     int64_t *active_h) {
+  const int64_t n = g->n;
+  const int64_t ld = choose_group(n, k, sizeof(double));
+  const size_t sbytes = sizeof(double) * (size_t)(n * ld);
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y0, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_Y1, sbytes));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_SRC, sizeof(int32_t) * (size_t)ld));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_KAPPA, sizeof(double) * (size_t)ld));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_MISC, sizeof(unsigned long long) * (size_t)sweeps));
+  int32_t *src = ctx->ws[WS_SRC].as<int32_t>();
+  double *dsrc = ctx->ws[WS_KAPPA].as<double>();
+  unsigned long long *cnt = ctx->ws[WS_MISC].as<unsigned long long>();
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (size_t)sweeps, ctx->stream));
+  double dmax = 0.0;
+  for (int32_t q = 0; q < k; ++q) dmax = std::max(dmax, g->h_deg[view_h[q]]);
+  const double rmax = dmax > 0.0 ? eps / dmax : eps;
+  std::vector<int32_t> srch((size_t)ld);
+  std::vector<double> dsh((size_t)ld);
+  const double c = 1.0 - alpha;
+  (void)c;
+  for (int32_t g0 = 0; g0 < k; g0 += (int32_t)ld) {
+    const int32_t gvalid = (int32_t)std::min<int64_t>(ld, (int64_t)k - g0);
+    for (int64_t q = 0; q < ld; ++q) {
+      srch[q] = q < gvalid ? view_h[g0 + q] : -1;
+      dsh[q] = q < gvalid ? g->h_deg[view_h[g0 + q]] : 0.0;
+    }
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(src, srch.data(), sizeof(int32_t) * (size_t)ld, cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(dsrc, dsh.data(), sizeof(double) * (size_t)ld, cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    double *ya = ctx->ws[WS_Y0].as<double>(), *yb = ctx->ws[WS_Y1].as<double>();
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(ya, 0, sbytes, ctx->stream));
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_init_delta<double><<<(unsigned)((ld + 255) / 256), 256, 0, ctx->stream>>>(
+        (int32_t)ld, src, ld, g->invdw_d.as<double>(), alpha, ya); }
+    PPRVIZ_LAUNCHED(ctx);
+    double *cur = ya, *nxt = yb;
+    for (int32_t t = 0; t < sweeps; ++t) {
+      PPRVIZ_TRY(launch_sweep<double>(ctx, g, ld, false, false, src, nullptr, cur, nullptr, nxt, alpha, 1.0));
+      { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); k_frontier_count<<<1216, 256, 0, ctx->stream>>>(
+          n, ld, gvalid, cur, nxt, g->invdw_d.as<double>(), g->deg.as<double>(), dsrc, alpha, rmax, cnt + t); }
+      PPRVIZ_LAUNCHED(ctx);
+      std::swap(cur, nxt);
+    }
+  }
+  std::vector<unsigned long long> h((size_t)sweeps);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * (size_t)sweeps,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int32_t t = 0; t < sweeps; ++t) active_h[t] = (int64_t)h[t];
+  return PPRVIZ_OK;
+}
+
+// --------------------------------------------------------------------------
 // Batched views (P7): many views of uneven size in shared launches.
 //
 // The views are laid out, largest first, as the disjoint union of their

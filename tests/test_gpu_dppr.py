@@ -321,3 +321,33 @@ def test_full_size_view_of_2m_graph_sampled(ctx):
     assert abs(e - e_ref) <= 2e-5 * e_ref
     g_ref = O.stress_grad(Xd, Dd)[pos]
     assert np.abs(gx[pos] - g_ref).max() <= 2e-4 * max(1.0, np.abs(g_ref).max())
+
+
+def test_frontier_profile_matches_oracle_power_iteration(ctx):
+    """The frontier diagnostic (Algorithm 2's threshold) against the oracle's
+    power iteration: after sweep t the push residue of node v for source s is
+    r = d(s) (x_{t+1} - x_t)_v / alpha, active when r > d(v) eps / max_view d.
+    The counts are integers decided by FP64 comparisons on both sides, which
+    sum in different orders, so entries within rounding of the threshold may
+    differ: a 0.5 % + 3 slack."""
+    g = synth.chung_lu(600, 8, 2.5, seed=4)
+    view = synth.sample_view(g.n, 40, seed=3)
+    G = ctx.upload_graph(g)
+    T = 60
+    act = ctx.frontier_profile(G, view, T, ALPHA, EPS)
+    Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    rmax = EPS / d[view].max()
+    B = np.zeros((len(view), g.n))
+    B[np.arange(len(view)), view] = ALPHA
+    PT = Pm.T.tocsr()
+    X = B.copy()
+    ref = []
+    for _ in range(T):
+        Xn = B + (1 - ALPHA) * (PT @ X.T).T
+        r = d[view][:, None] * np.abs(Xn - X) / ALPHA
+        ref.append(int((r > d[None, :] * rmax).sum()))
+        X = Xn
+    ref = np.array(ref)
+    assert np.all(np.abs(act - ref) <= 0.005 * ref + 3), (act[:10], ref[:10])
+    assert act[0] < act[5] and act[-1] < act.max()
