@@ -93,6 +93,7 @@ static int stage_in(pprviz_ctx *ctx, const void *p, size_t bytes, bool device, i
 
 static int begin(pprviz_ctx *ctx) {
   ctx->err.clear();
+  ctx->scnt_clear = false;
   ctx->launches = 0;
   memset(&ctx->stats, 0, sizeof(ctx->stats));
   PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -294,6 +295,8 @@ void pprviz_graph_free(pprviz_graph *g) {
   g->dwff.release();
   g->dense.release();
   g->comp.release();
+  g->sp_items.release();
+  g->sp_srow.release();
   delete g;
 }
 

@@ -50,6 +50,8 @@ enum Slot {
   WS_UDESC, WS_UBROWS, WS_UBPTR,
   // batched inverses: panels and pivot inverses of every view, job and step tables
   WS_FACB, WS_FACT,
+  // split heavy rows of the FP32 sweeps: per-segment partial sums and arrival counters
+  WS_SPART, WS_SCNT,
   WS_COUNT
 };
 
@@ -74,6 +76,7 @@ struct pprviz_ctx {
   pprviz::DevBuf ws[pprviz::WS_COUNT];
   size_t ws_limit = 0;  // cap on the summed workspace capacity (0 = none); pprviz_set_workspace_limit
   bool test_expire_wait = false;  // pprviz_test_expire_wait: the next FP32 inverse withholds one copy
+  bool scnt_clear = false;        // the split sweep's arrival counters are zero (set per call)
   pprviz_stats stats{};
   int launches = 0;  // kernels launched in the current call
   // source-group widths chosen by the sweep autotuner, by graph size class
@@ -99,6 +102,11 @@ struct pprviz_graph {
   mutable double spec_b = 1.0;             // |lambda| <= spec_b off the stationary modes (estimate + margin)
   mutable bool spec_deflate = false;       // components resolved
   mutable bool spec_ready = false;
+  // sweep work items with heavy rows split into segments of at most 64 edges,
+  // built on first use (sweep_plan in propagate.cu)
+  mutable pprviz::DevBuf sp_items, sp_srow;
+  mutable int64_t sp_nitems = 0, sp_nsplit = 0, sp_nslots = 0;
+  mutable bool sp_ready = false;
 };
 
 namespace pprviz {

@@ -256,6 +256,113 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
   Vec<T>::store(yout + rowoff, out);
 }
 
+// The FP32 Chebyshev sweep with heavy rows split (same result up to the
+// order of the additions). One warp per (work item, 128-source chunk); a
+// work item is a whole row, or a segment of at most kSegEdges edges of a row
+// with more. A row's work then ends within a few round trips to L2 however
+// high its degree (in one piece, a degree-477 hub of the power-law graphs
+// is a chain of ~60 dependent gather rounds, as long as the whole sweep).
+// A segment writes its partial neighbour sum to its slot; the warp that
+// arrives last at the row (per-row, per-chunk counter) adds the row's slots
+// in slot order, so the result does not depend on the arrival order, applies
+// the update and resets the counter for the next sweep.
+// items[t] = {row, first edge within the row, edge count, split row or -1};
+// srow[s] = {first slot, segments} of split row s.
+constexpr int kSegEdges = 64;
+
+template <bool WEIGHTED, bool RHS>
+__global__ void __launch_bounds__(32)
+k_sweep_sp(int64_t nitems, int64_t ld, int nchunks, const int4 *__restrict__ items, const int2 *__restrict__ srow,
+           const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
+           const float *__restrict__ invdw, const int32_t *__restrict__ src, const float *__restrict__ rhs,
+           const float *__restrict__ ycur, const float *yold, float *yout, float alpha, float c, float om, float om1,
+           float *__restrict__ part, int *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gid = blockIdx.x;
+  if (gid >= nitems * nchunks) return;
+  const int64_t chunk = gid / nitems;
+  const int4 it = items[gid - chunk * nitems];
+  const int64_t j = it.x;
+  const int64_t off = chunk * 128 + lane * 4;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const int64_t b = rp[j] + it.y, e = b + it.z;
+  for (int64_t base = b; base < e; base += 32) {
+    const int cnt_e = (int)min((int64_t)32, e - base);
+    const int32_t myc = lane < cnt_e ? col[base + lane] : 0;
+    float myw = 1.0f;
+    if (WEIGHTED) myw = lane < cnt_e ? w[base + lane] : 0.0f;
+    int t = 0;
+    for (; t + 8 <= cnt_e; t += 8) {
+      float v[8][4], wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int32_t iq = __shfl_sync(0xffffffffu, myc, t + q);
+        if (WEIGHTED) wv[q] = __shfl_sync(0xffffffffu, myw, t + q);
+        Vec<float>::load(ycur + (int64_t)iq * ld + off, v[q]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (WEIGHTED) {
+          float s2 = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) s2 += wv[q] * v[q][u];
+          acc[u] += s2;
+        } else {
+          acc[u] += ((v[0][u] + v[1][u]) + (v[2][u] + v[3][u])) + ((v[4][u] + v[5][u]) + (v[6][u] + v[7][u]));
+        }
+      }
+    }
+    for (; t < cnt_e; ++t) {
+      float v0[4];
+      const int32_t i0 = __shfl_sync(0xffffffffu, myc, t);
+      Vec<float>::load(ycur + (int64_t)i0 * ld + off, v0);
+      const float w0 = WEIGHTED ? __shfl_sync(0xffffffffu, myw, t) : 1.0f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += w0 * v0[u];
+    }
+  }
+  if (it.w >= 0) {
+    const int2 s = srow[it.w];
+    float *mine = part + (int64_t)(s.x + it.y / kSegEdges) * ld + off;
+    Vec<float>::store(mine, acc);
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&cnt[(int64_t)it.w * nchunks + chunk], 1) == s.y - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = 0.0f;
+    for (int k2 = 0; k2 < s.y; ++k2) {
+      const float4 p4 = __ldcg(reinterpret_cast<const float4 *>(part + (int64_t)(s.x + k2) * ld + off));
+      acc[0] += p4.x; acc[1] += p4.y; acc[2] += p4.z; acc[3] += p4.w;
+    }
+    if (lane == 0) cnt[(int64_t)it.w * nchunks + chunk] = 0;
+  }
+  const int64_t rowoff = j * ld + off;
+  if (it.z == 0) {  // no edges: the walk stays on j (self-loop of weight 1)
+    float v0[4];
+    Vec<float>::load(ycur + rowoff, v0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += v0[u];
+  }
+  const float invd = invdw[j];
+  float bq[4];
+  if (RHS) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bq[u] = rhs[rowoff + u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bq[u] = (src[off + u] == (int32_t)j) ? alpha : 0.0f;
+  }
+  float old[4], out[4];
+  Vec<float>::load(yold + rowoff, old);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = om1 * old[u] + om * ((bq[u] + c * acc[u]) * invd);
+  Vec<float>::store(yout + rowoff, out);
+}
+
 // v[u] = (double)(y_hi[u] + y_lo[u]), u < 4, with 16-byte loads (p is 4-aligned).
 __device__ __forceinline__ void load4(const float *hi, const float *lo, double (&v)[4]) {
   float a[4];
@@ -648,11 +755,90 @@ struct Wave {
   int nblocks = 0, nviews = 0;
 };
 
+// Work items of the split sweep (k_sweep_sp) for a graph, built once: rows
+// of at most kSegEdges edges whole, longer rows in kSegEdges-edge segments.
+int sweep_plan(pprviz_ctx *ctx, const pprviz_graph *g) {
+  if (g->sp_ready) return PPRVIZ_OK;
+  const int64_t n = g->n;
+  std::vector<int64_t> rp((size_t)n + 1);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rp.data(), g->rp.p, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int4> items;
+  std::vector<int2> srow;
+  items.reserve((size_t)n);
+  int64_t slots = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t len = rp[j + 1] - rp[j];
+    if (len <= kSegEdges) {
+      items.push_back(make_int4((int)j, 0, (int)len, -1));
+      continue;
+    }
+    const int nseg = (int)((len + kSegEdges - 1) / kSegEdges);
+    const int sr = (int)srow.size();
+    srow.push_back(make_int2((int)slots, nseg));
+    for (int q = 0; q < nseg; ++q) {
+      const int64_t a = (int64_t)q * kSegEdges;
+      items.push_back(make_int4((int)j, (int)a, (int)std::min<int64_t>(kSegEdges, len - a), sr));
+    }
+    slots += nseg;
+  }
+  cudaError_t e = g->sp_items.ensure(sizeof(int4) * items.size());
+  if (e == cudaSuccess) e = g->sp_srow.ensure(sizeof(int2) * std::max<size_t>(1, srow.size()));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, PPRVIZ_E_OOM, "sweep work items: allocation failed");
+  }
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(g->sp_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  if (!srow.empty())
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(g->sp_srow.p, srow.data(), sizeof(int2) * srow.size(), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  g->sp_nitems = (int64_t)items.size();
+  g->sp_nsplit = (int64_t)srow.size();
+  g->sp_nslots = slots;
+  g->sp_ready = true;
+  return PPRVIZ_OK;
+}
+
 template <typename T>
 int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, bool rhs,
                  const int32_t *src, const float *rhsbuf, const T *ycur, const T *yold, T *yout,
                  double alpha, double om, const Wave *wv = nullptr) {
   constexpr int VEC = Vec<T>::N;
+  if constexpr (std::is_same<T, float>::value) {
+    if (!wv && cheb) {
+      // FP32 Chebyshev sweep of a single graph: heavy rows split into segments
+      PPRVIZ_TRY(sweep_plan(ctx, g));
+      if (g->sp_nsplit > 0) {
+        const int nchunks = (int)(ld / 128);
+        PPRVIZ_TRY(ws_ensure(ctx, WS_SPART, sizeof(float) * (size_t)std::max<int64_t>(1, g->sp_nslots) * (size_t)ld));
+        const size_t cbytes = sizeof(int) * (size_t)g->sp_nsplit * (size_t)nchunks;
+        const bool fresh = ctx->ws[WS_SCNT].cap < cbytes || !ctx->ws[WS_SCNT].p;
+        PPRVIZ_TRY(ws_ensure(ctx, WS_SCNT, cbytes));
+        // the counters return to zero after every sweep; clear them once per call
+        if (fresh || !ctx->scnt_clear) {
+          PPRVIZ_CUDA(ctx, cudaMemsetAsync(ctx->ws[WS_SCNT].p, 0, ctx->ws[WS_SCNT].cap, ctx->stream));
+          ctx->scnt_clear = true;
+        }
+        const int64_t blocks = g->sp_nitems * nchunks;
+        const float *w = g->weighted ? g->w.as<float>() : nullptr;
+        const float a = (float)alpha, c = (float)(1.0 - alpha), o = (float)om, o1 = (float)(1.0 - om);
+        PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
+#define PPRVIZ_SWEEP_SP(W, R)                                                                                  \
+  k_sweep_sp<W, R><<<(unsigned)blocks, 32, 0, ctx->stream>>>(                                                   \
+      g->sp_nitems, ld, nchunks, g->sp_items.as<int4>(), g->sp_srow.as<int2>(), g->rp.as<int64_t>(),            \
+      g->col.as<int32_t>(), w, g->invdw_f.as<float>(), src, rhsbuf, (const float *)ycur, (const float *)yold,   \
+      (float *)yout, a, c, o, o1, ctx->ws[WS_SPART].as<float>(), ctx->ws[WS_SCNT].as<int>())
+        if (g->weighted) { if (rhs) PPRVIZ_SWEEP_SP(true, true); else PPRVIZ_SWEEP_SP(true, false); }
+        else { if (rhs) PPRVIZ_SWEEP_SP(false, true); else PPRVIZ_SWEEP_SP(false, false); }
+#undef PPRVIZ_SWEEP_SP
+        PPRVIZ_LAUNCHED(ctx);
+        return PPRVIZ_OK;
+      }
+    }
+  }
   const int nchunks = (int)(ld / (32 * VEC));
   const int64_t nrows = wv ? wv->nrows : g->n;
   const int64_t items = nrows * nchunks;
