@@ -52,6 +52,8 @@ enum Slot {
   WS_FACB, WS_FACT,
   // split heavy rows of the FP32 sweeps: per-segment partial sums and arrival counters
   WS_SPART, WS_SCNT,
+  // batched views: the waves' split work items and split rows
+  WS_UITEMS, WS_USROW,
   WS_COUNT
 };
 

@@ -270,22 +270,27 @@ k_sweep(int64_t n, int64_t ld, int nchunks, const int64_t *__restrict__ rp,
 // srow[s] = {first slot, segments} of split row s.
 constexpr int kSegEdges = 64;
 
-template <bool WEIGHTED, bool RHS>
+// BATCH: a wave of views (see k_sweep): item rows are union-graph rows, the
+// state covers rows [row0, row0 + nrows) and column q is source g0 + q of
+// every row's view (src = each node's index within its view).
+template <bool WEIGHTED, bool RHS, bool BATCH>
 __global__ void __launch_bounds__(32)
 k_sweep_sp(int64_t nitems, int64_t ld, int nchunks, const int4 *__restrict__ items, const int2 *__restrict__ srow,
            const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const float *__restrict__ w,
            const float *__restrict__ invdw, const int32_t *__restrict__ src, const float *__restrict__ rhs,
            const float *__restrict__ ycur, const float *yold, float *yout, float alpha, float c, float om, float om1,
-           float *__restrict__ part, int *__restrict__ cnt) {
+           float *__restrict__ part, int *__restrict__ cnt, int64_t row0, int32_t g0) {
   const int lane = threadIdx.x & 31;
   const int64_t gid = blockIdx.x;
   if (gid >= nitems * nchunks) return;
   const int64_t chunk = gid / nitems;
   const int4 it = items[gid - chunk * nitems];
-  const int64_t j = it.x;
+  const int64_t jg = it.x;                  // row of the graph
+  const int64_t rb = BATCH ? row0 : 0;      // state row of graph node i: i - rb
+  const int64_t j = jg - rb;                // row of the state
   const int64_t off = chunk * 128 + lane * 4;
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  const int64_t b = rp[j] + it.y, e = b + it.z;
+  const int64_t b = rp[jg] + it.y, e = b + it.z;
   for (int64_t base = b; base < e; base += 32) {
     const int cnt_e = (int)min((int64_t)32, e - base);
     const int32_t myc = lane < cnt_e ? col[base + lane] : 0;
@@ -298,7 +303,7 @@ k_sweep_sp(int64_t nitems, int64_t ld, int nchunks, const int4 *__restrict__ ite
       for (int q = 0; q < 8; ++q) {
         const int32_t iq = __shfl_sync(0xffffffffu, myc, t + q);
         if (WEIGHTED) wv[q] = __shfl_sync(0xffffffffu, myw, t + q);
-        Vec<float>::load(ycur + (int64_t)iq * ld + off, v[q]);
+        Vec<float>::load(ycur + ((int64_t)iq - rb) * ld + off, v[q]);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -315,7 +320,7 @@ k_sweep_sp(int64_t nitems, int64_t ld, int nchunks, const int4 *__restrict__ ite
     for (; t < cnt_e; ++t) {
       float v0[4];
       const int32_t i0 = __shfl_sync(0xffffffffu, myc, t);
-      Vec<float>::load(ycur + (int64_t)i0 * ld + off, v0);
+      Vec<float>::load(ycur + ((int64_t)i0 - rb) * ld + off, v0);
       const float w0 = WEIGHTED ? __shfl_sync(0xffffffffu, myw, t) : 1.0f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[u] += w0 * v0[u];
@@ -347,14 +352,18 @@ k_sweep_sp(int64_t nitems, int64_t ld, int nchunks, const int4 *__restrict__ ite
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[u] += v0[u];
   }
-  const float invd = invdw[j];
+  const float invd = invdw[jg];
   float bq[4];
   if (RHS) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) bq[u] = rhs[rowoff + u];
+  } else if (BATCH) {
+    const int32_t lj = src[jg] - g0 - (int32_t)off;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bq[u] = (lj == u) ? alpha : 0.0f;
   } else {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) bq[u] = (src[off + u] == (int32_t)j) ? alpha : 0.0f;
+    for (int u = 0; u < 4; ++u) bq[u] = (src[off + u] == (int32_t)jg) ? alpha : 0.0f;
   }
   float old[4], out[4];
   Vec<float>::load(yold + rowoff, old);
@@ -753,22 +762,20 @@ struct Wave {
   const int *bptr = nullptr;
   const int32_t *nv = nullptr;  // size of each node's view
   int nblocks = 0, nviews = 0;
+  // split work items of the wave's rows (k_sweep_sp), or none
+  const int4 *items = nullptr;
+  const int2 *srow = nullptr;
+  int64_t nitems = 0, nsplit = 0, nslots = 0;
 };
 
-// Work items of the split sweep (k_sweep_sp) for a graph, built once: rows
-// of at most kSegEdges edges whole, longer rows in kSegEdges-edge segments.
-int sweep_plan(pprviz_ctx *ctx, const pprviz_graph *g) {
-  if (g->sp_ready) return PPRVIZ_OK;
-  const int64_t n = g->n;
-  std::vector<int64_t> rp((size_t)n + 1);
-  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rp.data(), g->rp.p, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
-                                   ctx->stream));
-  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  std::vector<int4> items;
-  std::vector<int2> srow;
-  items.reserve((size_t)n);
+// Work items of the split sweep (k_sweep_sp) for the rows [r0, r1) of a CSR
+// (host row_ptr): rows of at most kSegEdges edges whole, longer rows in
+// kSegEdges-edge segments; split rows and slots numbered from 0. Returns the
+// number of slots.
+int64_t split_items(const std::vector<int64_t> &rp, int64_t r0, int64_t r1, std::vector<int4> &items,
+                    std::vector<int2> &srow) {
   int64_t slots = 0;
-  for (int64_t j = 0; j < n; ++j) {
+  for (int64_t j = r0; j < r1; ++j) {
     const int64_t len = rp[j + 1] - rp[j];
     if (len <= kSegEdges) {
       items.push_back(make_int4((int)j, 0, (int)len, -1));
@@ -783,6 +790,21 @@ int sweep_plan(pprviz_ctx *ctx, const pprviz_graph *g) {
     }
     slots += nseg;
   }
+  return slots;
+}
+
+// The split plan of a whole graph, built once and kept with it.
+int sweep_plan(pprviz_ctx *ctx, const pprviz_graph *g) {
+  if (g->sp_ready) return PPRVIZ_OK;
+  const int64_t n = g->n;
+  std::vector<int64_t> rp((size_t)n + 1);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rp.data(), g->rp.p, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int4> items;
+  std::vector<int2> srow;
+  items.reserve((size_t)n);
+  const int64_t slots = split_items(rp, 0, n, items, srow);
   cudaError_t e = g->sp_items.ensure(sizeof(int4) * items.size());
   if (e == cudaSuccess) e = g->sp_srow.ensure(sizeof(int2) * std::max<size_t>(1, srow.size()));
   if (e != cudaSuccess) {
@@ -808,13 +830,18 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
                  double alpha, double om, const Wave *wv = nullptr) {
   constexpr int VEC = Vec<T>::N;
   if constexpr (std::is_same<T, float>::value) {
-    if (!wv && cheb) {
-      // FP32 Chebyshev sweep of a single graph: heavy rows split into segments
-      PPRVIZ_TRY(sweep_plan(ctx, g));
-      if (g->sp_nsplit > 0) {
+    if (cheb && (wv ? wv->nsplit > 0 : true)) {
+      // FP32 Chebyshev sweep: heavy rows split into segments
+      if (!wv) PPRVIZ_TRY(sweep_plan(ctx, g));
+      const int64_t nitems = wv ? wv->nitems : g->sp_nitems;
+      const int64_t nsplit = wv ? wv->nsplit : g->sp_nsplit;
+      const int64_t nslots = wv ? wv->nslots : g->sp_nslots;
+      const int4 *items = wv ? wv->items : g->sp_items.as<int4>();
+      const int2 *srowp = wv ? wv->srow : g->sp_srow.as<int2>();
+      if (nsplit > 0) {
         const int nchunks = (int)(ld / 128);
-        PPRVIZ_TRY(ws_ensure(ctx, WS_SPART, sizeof(float) * (size_t)std::max<int64_t>(1, g->sp_nslots) * (size_t)ld));
-        const size_t cbytes = sizeof(int) * (size_t)g->sp_nsplit * (size_t)nchunks;
+        PPRVIZ_TRY(ws_ensure(ctx, WS_SPART, sizeof(float) * (size_t)std::max<int64_t>(1, nslots) * (size_t)ld));
+        const size_t cbytes = sizeof(int) * (size_t)nsplit * (size_t)nchunks;
         const bool fresh = ctx->ws[WS_SCNT].cap < cbytes || !ctx->ws[WS_SCNT].p;
         PPRVIZ_TRY(ws_ensure(ctx, WS_SCNT, cbytes));
         // the counters return to zero after every sweep; clear them once per call
@@ -822,17 +849,25 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
           PPRVIZ_CUDA(ctx, cudaMemsetAsync(ctx->ws[WS_SCNT].p, 0, ctx->ws[WS_SCNT].cap, ctx->stream));
           ctx->scnt_clear = true;
         }
-        const int64_t blocks = g->sp_nitems * nchunks;
+        const int64_t blocks = nitems * nchunks;
         const float *w = g->weighted ? g->w.as<float>() : nullptr;
         const float a = (float)alpha, c = (float)(1.0 - alpha), o = (float)om, o1 = (float)(1.0 - om);
+        const int32_t *srcp = wv ? wv->lidx : src;
+        const int64_t row0 = wv ? wv->row0 : 0;
+        const int32_t g0 = wv ? wv->g0 : 0;
         PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
-#define PPRVIZ_SWEEP_SP(W, R)                                                                                  \
-  k_sweep_sp<W, R><<<(unsigned)blocks, 32, 0, ctx->stream>>>(                                                   \
-      g->sp_nitems, ld, nchunks, g->sp_items.as<int4>(), g->sp_srow.as<int2>(), g->rp.as<int64_t>(),            \
-      g->col.as<int32_t>(), w, g->invdw_f.as<float>(), src, rhsbuf, (const float *)ycur, (const float *)yold,   \
-      (float *)yout, a, c, o, o1, ctx->ws[WS_SPART].as<float>(), ctx->ws[WS_SCNT].as<int>())
-        if (g->weighted) { if (rhs) PPRVIZ_SWEEP_SP(true, true); else PPRVIZ_SWEEP_SP(true, false); }
-        else { if (rhs) PPRVIZ_SWEEP_SP(false, true); else PPRVIZ_SWEEP_SP(false, false); }
+#define PPRVIZ_SWEEP_SP(W, R, B)                                                                               \
+  k_sweep_sp<W, R, B><<<(unsigned)blocks, 32, 0, ctx->stream>>>(                                                \
+      nitems, ld, nchunks, items, srowp, g->rp.as<int64_t>(), g->col.as<int32_t>(), w, g->invdw_f.as<float>(),  \
+      srcp, rhsbuf, (const float *)ycur, (const float *)yold, (float *)yout, a, c, o, o1,                       \
+      ctx->ws[WS_SPART].as<float>(), ctx->ws[WS_SCNT].as<int>(), row0, g0)
+        if (wv) {
+          if (g->weighted) { if (rhs) PPRVIZ_SWEEP_SP(true, true, true); else PPRVIZ_SWEEP_SP(true, false, true); }
+          else { if (rhs) PPRVIZ_SWEEP_SP(false, true, true); else PPRVIZ_SWEEP_SP(false, false, true); }
+        } else {
+          if (g->weighted) { if (rhs) PPRVIZ_SWEEP_SP(true, true, false); else PPRVIZ_SWEEP_SP(true, false, false); }
+          else { if (rhs) PPRVIZ_SWEEP_SP(false, true, false); else PPRVIZ_SWEEP_SP(false, false, false); }
+        }
 #undef PPRVIZ_SWEEP_SP
         PPRVIZ_LAUNCHED(ctx);
         return PPRVIZ_OK;
@@ -1803,6 +1838,32 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
   PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, sizeof(float) * std::max<size_t>(dmax, 1)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_UBROWS, sizeof(int2) * (size_t)nbmax));
   PPRVIZ_TRY(ws_ensure(ctx, WS_UBPTR, sizeof(int) * (size_t)(nviews + 1)));
+  // split work items of every wave (rows of more than kSegEdges edges in
+  // segments), from the union CSR, concatenated wave after wave
+  std::vector<int64_t> urp((size_t)N + 1);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(urp.data(), U.rp.p, sizeof(int64_t) * urp.size(), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int4> witems;
+  std::vector<int2> wsrow;
+  struct WaveSplit { size_t item0, srow0; int64_t nitems, nsplit, nslots; };
+  std::vector<WaveSplit> wsplit;
+  for (const WaveDef &wd : waves) {
+    WaveSplit ws{witems.size(), wsrow.size(), 0, 0, 0};
+    std::vector<int2> sr;
+    ws.nslots = split_items(urp, wd.row0, wd.row0 + wd.nrows, witems, sr);
+    ws.nitems = (int64_t)(witems.size() - ws.item0);
+    ws.nsplit = (int64_t)sr.size();
+    wsrow.insert(wsrow.end(), sr.begin(), sr.end());
+    wsplit.push_back(ws);
+  }
+  PPRVIZ_TRY(ws_ensure(ctx, WS_UITEMS, sizeof(int4) * std::max<size_t>(1, witems.size())));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_USROW, sizeof(int2) * std::max<size_t>(1, wsrow.size())));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ctx->ws[WS_UITEMS].p, witems.data(), sizeof(int4) * witems.size(),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  if (!wsrow.empty())
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ctx->ws[WS_USROW].p, wsrow.data(), sizeof(int2) * wsrow.size(),
+                                     cudaMemcpyHostToDevice, ctx->stream));
   int64_t ldmax = 0;
   for (const WaveDef &wd : waves) ldmax = std::max(ldmax, wd.ld);
   PPRVIZ_TRY(ws_ensure(ctx, WS_CERT, 2 * sizeof(double) * (size_t)ldmax * (size_t)nviews));
@@ -1816,7 +1877,8 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
   auto sweeps_for = [](double factor, double r) { return r > 0.0 ? (int)ceil(log(0.5 * factor) / log(r)) : 1; };
   bool not_converged = false;
 
-  for (const WaveDef &wd : waves) {
+  for (size_t wi = 0; wi < waves.size(); ++wi) {
+    const WaveDef &wd = waves[wi];
     const int nvw = (int)(wd.last - wd.first);
     // residual row blocks: ~1,216 blocks of the wave shared in proportion to
     // the views' sizes (at least one each), never straddling two views
@@ -1848,6 +1910,11 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
     wv.bptr = bptr_d;
     wv.nblocks = (int)brows.size();
     wv.nviews = nvw;
+    wv.items = ctx->ws[WS_UITEMS].as<int4>() + wsplit[wi].item0;
+    wv.srow = ctx->ws[WS_USROW].as<int2>() + wsplit[wi].srow0;
+    wv.nitems = wsplit[wi].nitems;
+    wv.nsplit = wsplit[wi].nsplit;
+    wv.nslots = wsplit[wi].nslots;
     const int64_t ld = wd.ld;
     const int64_t cnt = wd.nrows * ld;
     // the wave's iterated modes: |lambda| <= the largest bound of its views
