@@ -769,15 +769,19 @@ struct Wave {
 };
 
 // Work items of the split sweep (k_sweep_sp) for the rows [r0, r1) of a CSR
-// (host row_ptr): rows of at most kSegEdges edges whole, longer rows in
-// kSegEdges-edge segments; split rows and slots numbered from 0. Returns the
-// number of slots.
+// (host row_ptr): the hub rows, with more than max(kSegEdges, 4 x the mean
+// degree of the range) edges, in kSegEdges-edge segments, the others whole
+// (rows of uniformly high degree gain less from splitting than the partial
+// sums cost); split rows and slots numbered from 0. Returns the number of
+// slots.
 int64_t split_items(const std::vector<int64_t> &rp, int64_t r0, int64_t r1, std::vector<int4> &items,
                     std::vector<int2> &srow) {
   int64_t slots = 0;
+  const double mean = r1 > r0 ? (double)(rp[r1] - rp[r0]) / (double)(r1 - r0) : 0.0;
+  const int64_t thr = std::max<int64_t>(kSegEdges, (int64_t)(4.0 * mean));
   for (int64_t j = r0; j < r1; ++j) {
     const int64_t len = rp[j + 1] - rp[j];
-    if (len <= kSegEdges) {
+    if (len <= thr) {
       items.push_back(make_int4((int)j, 0, (int)len, -1));
       continue;
     }
