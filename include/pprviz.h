@@ -316,6 +316,24 @@ int pprviz_views_batch(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *cons
                        const float *x0_packed, float *pdist_packed, float *x_packed,
                        double *stress_out, double *cert_out, uint32_t mem_flags);
 
+/* Layout quality metrics (Sec. 2, visualization quality assessment):
+ *   ND(X)   = sum_{i<j} 1 / |X_i - X_j|^2 (node distribution; +inf when two
+ *             points coincide);
+ *   ULCV(X) = l_sigma / l_mu of the edge lengths (uniform length coefficient
+ *             variance; population standard deviation; each undirected edge
+ *             once; NaN when the view holds no edge).
+ * x:        k*2 coordinates (float, or double with PPRVIZ_OUT_FP64), host or
+ *           device per PPRVIZ_DEVICE_PTRS; sums are accumulated in FP64 in a
+ *           fixed order.
+ * g, view:  the graph whose edges ULCV measures and the k node ids of the rows
+ *           of x (NULL view: k = n and row i is node i); the edges are those
+ *           of g between view nodes. g may be NULL when ulcv_out is NULL.
+ * nd_out, ulcv_out: host doubles; either may be NULL.
+ * Errors: E_INVALID_ARG (k < 1, no graph for ULCV, k != n without a view, a
+ * bad view id), E_OOM, E_CUDA. */
+int pprviz_layout_metrics(pprviz_ctx *ctx, const void *x, int32_t k, const pprviz_graph *g, const int32_t *view,
+                          double *nd_out, double *ulcv_out, uint32_t mem_flags);
+
 /* Stress energy and gradients without allocating anything (no counterpart in
  * the paper; a library convenience). Same results as pprviz_energy with FP32
  * device buffers, for callers that may not allocate device memory when they

@@ -38,7 +38,7 @@ __all__ = [
     "degrees", "transition_matrix", "ppr_direct", "ppr_rows", "ppr_cols", "dppr_rows",
     "pdist_from_z", "pdist_from_dppr", "stress", "stress_grad", "stress_grad_pdist",
     "lw_matrix", "ly_matrix", "smacof_step", "smacof", "forward_push",
-    "residual_certificate", "power_sweeps_needed", "level_dppr",
+    "residual_certificate", "power_sweeps_needed", "level_dppr", "node_distribution", "ulcv",
 ]
 
 
@@ -302,3 +302,30 @@ def level_dppr(dppr_full, leaf_sets):
         for j, Fj in enumerate(leaf_sets):
             out[i, j] = dppr_full[np.ix_(Fi, Fj)].sum() / (len(Fi) * len(Fj))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Sec. 2 (visualization quality): node distribution and uniform length
+# coefficient variance of a layout.
+# ----------------------------------------------------------------------------
+def node_distribution(X):
+    """ND(X) = sum_{i<j} 1 / |X_i - X_j|^2 (the node-distribution definition of
+    Sec. 2); a coincident pair makes it infinite."""
+    _, dist = _pair_dist(X)
+    iu = np.triu_indices(len(dist), 1)
+    d2 = dist[iu] ** 2
+    if np.any(d2 == 0):
+        return float("inf")
+    return float((1.0 / d2).sum())
+
+
+def ulcv(X, edges):
+    """ULCV(X) = l_sigma / l_mu over the edge lengths (Sec. 2), with the
+    population standard deviation; `edges` lists each undirected edge (u, v)
+    once, u, v indexing the rows of X."""
+    X = np.asarray(X, dtype=np.float64)
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    lengths = np.sqrt(((X[e[:, 0]] - X[e[:, 1]]) ** 2).sum(axis=1))
+    mu = lengths.mean()
+    sigma = np.sqrt(((lengths - mu) ** 2).mean())
+    return float(sigma / mu)

@@ -232,6 +232,21 @@ class Context:
         self._leave(dev, pdist, x, gx_out, gd_out)
         return float(e[0]), (gx_out if grad_x else None), (gd_out if grad_pdist else None)
 
+    def layout_metrics(self, x, graph: Graph = None, view=None):
+        """(ND, ULCV) of a layout (Sec. 2): ND over all pairs of rows of x;
+        ULCV over the graph's edges among the view's nodes (None without a
+        graph). x: numpy (host) or torch CUDA tensor, float32 or float64."""
+        k = x.shape[0]
+        dev = B._mem_flags(x, view) == PPRVIZ_DEVICE_PTRS
+        f64 = str(x.dtype).endswith("float64")
+        nd = np.zeros(1, dtype=np.float64)
+        ul = np.zeros(1, dtype=np.float64) if graph is not None else None
+        mf = (PPRVIZ_DEVICE_PTRS if dev else 0) | (PPRVIZ_OUT_FP64 if f64 else 0)
+        self._enter(dev)
+        B.pprviz_layout_metrics(self.h, x, k, graph.h if graph is not None else None, view, nd, ul, mf)
+        self._leave(dev, x, view)
+        return float(nd[0]), (float(ul[0]) if ul is not None else None)
+
     def views_batch(self, graphs, x0_packed, alpha=0.15, eps=1e-6, iters=200, want_pdist=False, want_cert=False):
         """Batched views. x0_packed is a numpy array (host buffers) or a torch
         CUDA tensor (device buffers: the packed layouts and PDists come back as

@@ -65,6 +65,7 @@ _SIGS = {
     "pprviz_views_batch": (C.c_int, [_VP, C.c_int32, _VP, _VP, C.c_double, C.c_double, C.c_int32, _VP, _VP, _VP,
                                      _VP, _VP, C.c_uint32]),
     "pprviz_energy_noalloc": (C.c_int, [_VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, _VP]),
+    "pprviz_layout_metrics": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, _VP, _VP, C.c_uint32]),
 }
 
 
@@ -242,6 +243,11 @@ def pprviz_layout(ctx, pdist, k, x0, iters, precision, x_out, stress_out, mem_fl
 def pprviz_energy(ctx, pdist, k, x, grad_scale, e_out, grad_x, grad_pdist, mem_flags):
     return _check(ctx, load().pprviz_energy(ctx, _ptr(pdist)[0], int(k), _ptr(x)[0], float(grad_scale),
                                             _ptr(e_out)[0], _ptr(grad_x)[0], _ptr(grad_pdist)[0], mem_flags))
+
+
+def pprviz_layout_metrics(ctx, x, k, g, view, nd_out, ulcv_out, mem_flags):
+    return _check(ctx, load().pprviz_layout_metrics(ctx, _ptr(x)[0], int(k), g, _ptr(view)[0], _ptr(nd_out)[0],
+                                                    _ptr(ulcv_out)[0], mem_flags))
 
 
 def pprviz_views_batch(ctx, graphs, offsets, alpha, eps, iters, x0_packed, pdist_packed, x_packed, stress_out,

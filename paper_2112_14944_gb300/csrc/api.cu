@@ -502,6 +502,28 @@ int pprviz_frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_
   return finish(ctx, frontier_profile(ctx, g, view_d, view_h, k, alpha, eps, sweeps, active_out));
 }
 
+int pprviz_layout_metrics(pprviz_ctx *ctx, const void *x, int32_t k, const pprviz_graph *g, const int32_t *view,
+                          double *nd_out, double *ulcv_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!x || k < 1) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "x is NULL or k < 1");
+  if (ulcv_out && !g) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "ULCV needs the graph");
+  if (g && !view && (int64_t)k != g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "without a view, k must be n");
+  if (g && view && (int64_t)k > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "k must be <= n");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool f64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  const void *xd = nullptr;
+  PPRVIZ_TRY(stage_in(ctx, x, (f64 ? sizeof(double) : sizeof(float)) * 2 * (size_t)k, dev, WS_IN0, &xd));
+  const int32_t *view_d = nullptr;
+  if (g && view) {
+    const void *p = nullptr;
+    PPRVIZ_TRY(stage_in(ctx, view, sizeof(int32_t) * (size_t)k, dev, WS_VIEW, &p));
+    view_d = (const int32_t *)p;
+    PPRVIZ_TRY(view_check(ctx, g, view_d, k));
+  }
+  return finish(ctx, layout_metrics(ctx, xd, f64, k, g, view_d, nd_out, ulcv_out));
+}
+
 int pprviz_pdist(pprviz_ctx *ctx, const void *dppr, int32_t k, int64_t n_clamp, void *pdist_out, uint32_t mem_flags) {
   if (!ctx) return PPRVIZ_E_INVALID_ARG;
   PPRVIZ_TRY(begin(ctx));

@@ -203,6 +203,13 @@ int dense_prepare(pprviz_ctx *ctx, const pprviz_graph *g);
 int dense_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const int32_t *src, const float *rhs,
                 const float *ycur, float *yold, double alpha, double om, int *err, bool bf16);
 
+// ---- layout quality metrics (metrics.cu) ----------------------------------
+// ND and ULCV (Sec. 2) of k coordinates x_d (device, k x 2, double if f64);
+// ULCV over the edges of g among the view's nodes (view_d: k node ids of g, or
+// NULL when row i is node i). nd_h / ulcv_h: host outputs, either may be NULL.
+int layout_metrics(pprviz_ctx *ctx, const void *x_d, bool f64, int32_t k, const pprviz_graph *g,
+                   const int32_t *view_d, double *nd_h, double *ulcv_h);
+
 // ---- pdist (pdist.cu) ------------------------------------------------------
 int pdist_launch(pprviz_ctx *ctx, const void *dppr_d, int32_t k, int64_t n_clamp,
                  void *pdist_d, bool f64);

@@ -365,3 +365,25 @@ def test_level_dppr_star_closed_form():
     assert abs(lv[1, 0] - C / (1 + C)) < 1e-14
     assert abs(lv[1, 1] - (ALPHA / L + C * C / (L * (1 + C)))) < 1e-14
     assert abs(lv[0, 0] - L / (1 + C)) < 1e-13
+
+
+def test_node_distribution_and_ulcv_hand_values():
+    # unit square: four sides of length 1 and two diagonals of length sqrt(2):
+    # ND = 4 * 1 + 2 * 1/2 = 5; a coincident pair makes ND infinite
+    sq = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    assert abs(O.node_distribution(sq) - 5.0) < 1e-14
+    assert O.node_distribution(np.array([[0.0, 0.0], [1.0, 2.0], [0.0, 0.0]])) == float("inf")
+    # equal edge lengths: ULCV = 0; lengths 1 and 3: mean 2, population std 1
+    assert O.ulcv(sq, [(0, 1), (1, 2), (2, 3), (3, 0)]) < 1e-15
+    pts = np.array([[0.0, 0.0], [1.0, 0.0], [4.0, 0.0]])
+    assert abs(O.ulcv(pts, [(0, 1), (1, 2)]) - 0.5) < 1e-15
+    # invariances: ND and ULCV do not change under rotation and translation;
+    # scaling X by s multiplies ND by 1/s^2 and leaves ULCV unchanged
+    X = synth.uniform_x0(20, seed=4).astype(np.float64) * 3
+    th = 0.4
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    E = [(i, (i * 7 + 3) % 20) for i in range(20) if i != (i * 7 + 3) % 20]
+    assert abs(O.node_distribution(X @ R.T + 2.0) - O.node_distribution(X)) < 1e-9 * O.node_distribution(X)
+    assert abs(O.node_distribution(2.0 * X) - O.node_distribution(X) / 4.0) < 1e-12 * O.node_distribution(X)
+    assert abs(O.ulcv(X @ R.T - 1.0, E) - O.ulcv(X, E)) < 1e-12
+    assert abs(O.ulcv(5.0 * X, E) - O.ulcv(X, E)) < 1e-12
