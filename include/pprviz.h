@@ -51,7 +51,7 @@ extern "C" {
 #define PPRVIZ_E_TIMEOUT 6       /* a bounded device wait expired */
 
 /* graph flags */
-#define PPRVIZ_UNDIRECTED 1u     /* CSR stores both directions; checked when validating */
+#define PPRVIZ_UNDIRECTED 1u     /* CSR stores both directions (checked); without it: directed */
 #define PPRVIZ_VALIDATE 2u       /* accepted for clarity; validation always runs */
 #define PPRVIZ_DEGREE_COUNT 4u   /* weighted graph, but d(v) = edge count instead of strength */
 
@@ -165,10 +165,19 @@ int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, 
  * weights: nnz float edge weights (> 0, finite) or NULL for unit weights;
  *          weighted walks step to v_j with probability w_ij / sum_j w_ij and
  *          d(v) is that sum (the strength) unless PPRVIZ_DEGREE_COUNT.
- * flags:   PPRVIZ_UNDIRECTED is required (the propagation uses the pull form
- *          over the symmetric CSR). Every rule above and the symmetry
- *          (including equal weights both ways) are always checked on the
- *          device before the graph is accepted.
+ * flags:   PPRVIZ_UNDIRECTED: the CSR stores both directions of every edge;
+ *          the symmetry (including equal weights both ways) is checked.
+ *          Without it the graph is directed (Sec. 2.1's general setting):
+ *          row v lists v's out-neighbours, the walk steps along out-edges,
+ *          d(v) is the out-degree (or out-strength), and a node without
+ *          out-edges (dangling) keeps its walk; the library builds the
+ *          in-neighbour CSR the pull-form sweeps need. Directed graphs take
+ *          the CSR sweeps only (no tensor-core sweeps, no batched views);
+ *          their FP32 propagation runs power sweeps with the same FP64
+ *          certificate and refinement (a directed walk has a complex
+ *          spectrum, outside the Chebyshev recurrence's interval). Every rule
+ *          above is always checked on the device before the graph is
+ *          accepted.
  * Host pointers unless mem_flags has PPRVIZ_DEVICE_PTRS. The library copies
  * the arrays; the caller may free them on return. A node with no edges is
  * kept: its walk stays on it and its d(v) = 0.
@@ -212,7 +221,8 @@ int pprviz_graph_degrees(pprviz_ctx *ctx, const pprviz_graph *g, double *deg_out
  * Float outputs unless PPRVIZ_OUT_FP64 (then double). The certificate bounds
  * the computed row before the output is rounded to the output type.
  * Errors: E_INVALID_ARG (k < 1, k > n, bad id, duplicate id, alpha or eps out
- * of range, graph not undirected), E_NOT_CONVERGED, E_OOM, E_CUDA. */
+ * of range, a tensor-core precision on a directed graph), E_NOT_CONVERGED,
+ * E_OOM, E_CUDA. */
 int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k,
                 double alpha, double eps, int precision, void *dppr_out, void *pdist_out,
                 int64_t n_clamp, double *cert_out, uint32_t mem_flags);

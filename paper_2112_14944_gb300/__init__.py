@@ -122,8 +122,11 @@ class Context:
         """{class: (device ms of the timed launches, launches, timed launches)} since the last profile() call."""
         return B.pprviz_kernel_times(self.h)
 
-    def upload(self, n, row_ptr, col, weights=None, validate=True, degree_count=False) -> Graph:
-        flags = PPRVIZ_UNDIRECTED | (PPRVIZ_VALIDATE if validate else 0) | (PPRVIZ_DEGREE_COUNT if degree_count else 0)
+    def upload(self, n, row_ptr, col, weights=None, validate=True, degree_count=False, directed=False) -> Graph:
+        """Upload a CSR graph: undirected (both directions stored) unless
+        `directed` (each row lists the node's out-neighbours)."""
+        flags = ((0 if directed else PPRVIZ_UNDIRECTED) | (PPRVIZ_VALIDATE if validate else 0)
+                 | (PPRVIZ_DEGREE_COUNT if degree_count else 0))
         dev = B._mem_flags(row_ptr, col, weights) == PPRVIZ_DEVICE_PTRS
         self._enter(dev)
         h = B.pprviz_graph_upload(self.h, n, row_ptr, col, weights, flags)
@@ -131,8 +134,9 @@ class Context:
         return Graph(self, h, int(n))
 
     def upload_graph(self, g, validate=True) -> Graph:
-        """Upload a synth.Graph-like object (n, row_ptr, col, weight)."""
-        return self.upload(g.n, g.row_ptr, g.col, g.weight, validate=validate)
+        """Upload a synth.Graph-like object (n, row_ptr, col, weight[, directed])."""
+        return self.upload(g.n, g.row_ptr, g.col, g.weight, validate=validate,
+                           directed=bool(getattr(g, "directed", False)))
 
     def dppr(self, graph: Graph, view, alpha=0.15, eps=1e-6, precision=FP32, n_clamp=0, dppr_out=None,
              pdist_out=None, cert=True, out64=False):

@@ -240,9 +240,6 @@ int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr, cons
   PPRVIZ_TRY(begin(ctx));
   if (n < 1 || n > INT32_MAX) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n must be in [1, 2^31 - 1]");
   if (!row_ptr) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "row_ptr is NULL");
-  if (!(flags & PPRVIZ_UNDIRECTED))
-    return set_err(ctx, PPRVIZ_E_INVALID_ARG,
-                   "directed graphs are not supported: pass the symmetric CSR with PPRVIZ_UNDIRECTED");
   const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
   int64_t nnz = 0;
   if (dev) {
@@ -279,6 +276,23 @@ int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr, cons
     return fail(cuda_err(ctx, e, "copy weights"));
   int s = graph_build(ctx, g, flags);
   if (s != PPRVIZ_OK) return fail(s);
+  if (!(flags & PPRVIZ_UNDIRECTED)) {
+    // directed: the pull CSR from host copies of the (validated) arrays
+    std::vector<int64_t> rp_h((size_t)n + 1);
+    std::vector<int32_t> col_h((size_t)nnz);
+    std::vector<float> w_h(g->weighted ? (size_t)nnz : 0);
+    if ((e = cudaMemcpyAsync(rp_h.data(), g->rp.p, sizeof(int64_t) * rp_h.size(), cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess ||
+        (nnz && (e = cudaMemcpyAsync(col_h.data(), g->col.p, sizeof(int32_t) * col_h.size(), cudaMemcpyDeviceToHost,
+                                     ctx->stream)) != cudaSuccess) ||
+        (g->weighted && nnz &&
+         (e = cudaMemcpyAsync(w_h.data(), g->w.p, sizeof(float) * w_h.size(), cudaMemcpyDeviceToHost, ctx->stream)) !=
+             cudaSuccess) ||
+        (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+      return fail(cuda_err(ctx, e, "copy the CSR back for the pull CSR"));
+    s = pull_csr_build(ctx, g, rp_h.data(), col_h.data(), g->weighted ? w_h.data() : nullptr);
+    if (s != PPRVIZ_OK) return fail(s);
+  }
   *out = g;
   return finish(ctx, PPRVIZ_OK);
 }
@@ -297,6 +311,9 @@ void pprviz_graph_free(pprviz_graph *g) {
   g->comp.release();
   g->sp_items.release();
   g->sp_srow.release();
+  g->prp.release();
+  g->pcol.release();
+  g->pw.release();
   delete g;
 }
 

@@ -109,7 +109,25 @@ struct pprviz_graph {
   mutable pprviz::DevBuf sp_items, sp_srow;
   mutable int64_t sp_nitems = 0, sp_nsplit = 0, sp_nslots = 0;
   mutable bool sp_ready = false;
+  // directed graphs: the pull CSR (row j lists the in-neighbours i of j with
+  // the weights w_ij, or 1; a dangling j has the entry (j, 1), a j without
+  // in-edges the entry (j, 0)), so that no gather row is empty
+  bool directed = false;
+  pprviz::DevBuf prp, pcol, pw;
 };
+
+namespace pprviz {
+// The CSR the pull-form kernels gather over: the graph itself when it is
+// undirected, its pull CSR when it is directed (always weighted).
+inline const int64_t *pull_rp(const pprviz_graph *g) { return g->directed ? g->prp.as<int64_t>() : g->rp.as<int64_t>(); }
+inline const int32_t *pull_col(const pprviz_graph *g) {
+  return g->directed ? g->pcol.as<int32_t>() : g->col.as<int32_t>();
+}
+inline const float *pull_w(const pprviz_graph *g) {
+  return g->directed ? g->pw.as<float>() : (g->weighted ? g->w.as<float>() : nullptr);
+}
+inline bool pull_weighted(const pprviz_graph *g) { return g->directed || g->weighted; }
+}  // namespace pprviz
 
 namespace pprviz {
 
@@ -151,6 +169,9 @@ struct ProfScope {
 
 // ---- graph (graph.cu) ---------------------------------------------------
 int graph_build(pprviz_ctx *ctx, pprviz_graph *g, uint32_t flags);
+// The pull CSR of a directed graph from host copies of its out-edge CSR;
+// marks the graph directed.
+int pull_csr_build(pprviz_ctx *ctx, pprviz_graph *g, const int64_t *rp, const int32_t *col, const float *w);
 // Map view ids -> check range and duplicates on the device. `view_d` device.
 int view_check(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d, int32_t k);
 

@@ -377,7 +377,7 @@ bool dense_eligible(const pprviz_graph *g) {
   // tensor-core sweep costs ~6 n^2 G flop at ~1 PFLOP/s, a CSR sweep gathers
   // nnz G 4-byte values at L2 speed (~10 TB/s); above 5 % the former wins
   // by more than 1.5x
-  return g->n >= 512 && (double)g->nnz >= 0.05 * (double)g->n * (double)g->n;
+  return !g->directed && g->n >= 512 && (double)g->nnz >= 0.05 * (double)g->n * (double)g->n;
 }
 
 int64_t dense_group(int32_t k) {

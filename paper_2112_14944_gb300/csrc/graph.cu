@@ -7,6 +7,8 @@
 // matrix) and has d(v) = 0.
 #include <math.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pprviz {
@@ -133,6 +135,63 @@ int graph_build(pprviz_ctx *ctx, pprviz_graph *g, uint32_t flags) {
   double m = 0.0;
   for (double d : g->h_deg) m += d;
   g->m = m;
+  return PPRVIZ_OK;
+}
+
+// The pull CSR of a directed graph (host arrays of the validated out-edge CSR):
+// row j lists the in-neighbours i of j in increasing order with the pull
+// weight w_ij (1 when unweighted), so that (x P)_j = sum_i w_ij y_i with
+// y = x / dw. A dangling j (no out-edge) keeps its walk: the entry (j, 1)
+// (dw = 1); a j without in-edges gets (j, 0), so that no row is empty and the
+// kernels' rule for empty rows (the undirected graphs' isolated nodes) never
+// applies to a directed graph.
+int pull_csr_build(pprviz_ctx *ctx, pprviz_graph *g, const int64_t *rp, const int32_t *col, const float *w) {
+  const int64_t n = g->n;
+  std::vector<int64_t> cnt((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) cnt[(size_t)col[p] + 1]++;
+  std::vector<char> extra((size_t)n, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    const bool dangling = rp[j + 1] == rp[j];
+    if (dangling || cnt[(size_t)j + 1] == 0) {
+      extra[(size_t)j] = 1;
+      cnt[(size_t)j + 1]++;
+    }
+  }
+  for (int64_t j = 0; j < n; ++j) cnt[(size_t)j + 1] += cnt[(size_t)j];
+  const int64_t pnnz = cnt[(size_t)n];
+  std::vector<int32_t> pcol((size_t)std::max<int64_t>(pnnz, 1));
+  std::vector<float> pw((size_t)std::max<int64_t>(pnnz, 1));
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  // sources in increasing order, so every row comes out sorted; a node's own
+  // entry is placed when the scan reaches it
+  for (int64_t i = 0; i < n; ++i) {
+    if (extra[(size_t)i]) {
+      const int64_t q = fill[(size_t)i]++;
+      pcol[(size_t)q] = (int32_t)i;
+      pw[(size_t)q] = (rp[i + 1] == rp[i]) ? 1.0f : 0.0f;
+    }
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int64_t q = fill[(size_t)col[p]]++;
+      pcol[(size_t)q] = (int32_t)i;
+      pw[(size_t)q] = w ? w[p] : 1.0f;
+    }
+  }
+  cudaError_t e = g->prp.ensure(sizeof(int64_t) * (size_t)(n + 1));
+  if (e == cudaSuccess) e = g->pcol.ensure(sizeof(int32_t) * pcol.size());
+  if (e == cudaSuccess) e = g->pw.ensure(sizeof(float) * pw.size());
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, PPRVIZ_E_OOM, "pull CSR of the directed graph: allocation failed");
+  }
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(g->prp.p, cnt.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(g->pcol.p, pcol.data(), sizeof(int32_t) * pcol.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(g->pw.p, pw.data(), sizeof(float) * pw.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  g->directed = true;
   return PPRVIZ_OK;
 }
 

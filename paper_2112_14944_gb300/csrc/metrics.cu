@@ -59,13 +59,14 @@ __global__ void k_view_map(int32_t k, const int32_t *__restrict__ view, int32_t 
   if (q < k) map[view[q]] = q;
 }
 
-// Edge lengths |X_map(u) - X_map(v)| over the CSR edges u -> v with u < v and
-// both ends in the view (each undirected edge once). pass 0: part[b] =
-// (sum of lengths, count); pass 1: part[b].x = sum of (length - mu)^2.
+// Edge lengths |X_map(u) - X_map(v)| over the CSR edges u -> v with both ends
+// in the view: each undirected edge once (u < v), every edge of a directed
+// graph. pass 0: part[b] = (sum of lengths, count); pass 1: part[b].x = sum
+// of (length - mu)^2.
 template <typename T>
 __global__ void __launch_bounds__(kMetWarps * 32)
 k_ulcv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const int32_t *__restrict__ map,
-       const T *__restrict__ x, int pass, double mu, double2 *__restrict__ part) {
+       const T *__restrict__ x, int pass, double mu, int directed, double2 *__restrict__ part) {
   __shared__ double2 rs[kMetWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t u = (int64_t)blockIdx.x * kMetWarps + warp;
@@ -76,7 +77,7 @@ k_ulcv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ co
       const double2 xu = xload(x, iu);
       for (int64_t p = rp[u] + lane; p < rp[u + 1]; p += 32) {
         const int32_t v = col[p];
-        if (v <= u) continue;
+        if (!directed && v <= u) continue;
         const int32_t iv = map ? map[v] : v;
         if (iv < 0) continue;
         const double2 xv = xload(x, iv);
@@ -173,7 +174,7 @@ static int metrics_run(pprviz_ctx *ctx, const T *x_d, int32_t k, const pprviz_gr
       {
         PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY);
         k_ulcv<T><<<nb, kMetWarps * 32, 0, ctx->stream>>>(n, g->rp.as<int64_t>(), g->col.as<int32_t>(), map, x_d,
-                                                          pass, mu, part);
+                                                          pass, mu, g->directed ? 1 : 0, part);
       }
       PPRVIZ_LAUNCHED(ctx);
       { PPRVIZ_PROF(ctx, PPRVIZ_K_ENERGY); k_sum_parts<<<1, 32, 0, ctx->stream>>>(nb, part, sum2); }

@@ -802,7 +802,7 @@ int sweep_plan(pprviz_ctx *ctx, const pprviz_graph *g) {
   if (g->sp_ready) return PPRVIZ_OK;
   const int64_t n = g->n;
   std::vector<int64_t> rp((size_t)n + 1);
-  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rp.data(), g->rp.p, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rp.data(), pull_rp(g), sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost,
                                    ctx->stream));
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   std::vector<int4> items;
@@ -854,7 +854,7 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
           ctx->scnt_clear = true;
         }
         const int64_t blocks = nitems * nchunks;
-        const float *w = g->weighted ? g->w.as<float>() : nullptr;
+        const float *w = pull_w(g);
         const float a = (float)alpha, c = (float)(1.0 - alpha), o = (float)om, o1 = (float)(1.0 - om);
         const int32_t *srcp = wv ? wv->lidx : src;
         const int64_t row0 = wv ? wv->row0 : 0;
@@ -862,14 +862,14 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
         PPRVIZ_PROF(ctx, PPRVIZ_K_SWEEP);
 #define PPRVIZ_SWEEP_SP(W, R, B)                                                                               \
   k_sweep_sp<W, R, B><<<(unsigned)blocks, 32, 0, ctx->stream>>>(                                                \
-      nitems, ld, nchunks, items, srowp, g->rp.as<int64_t>(), g->col.as<int32_t>(), w, g->invdw_f.as<float>(),  \
+      nitems, ld, nchunks, items, srowp, pull_rp(g), pull_col(g), w, g->invdw_f.as<float>(),                    \
       srcp, rhsbuf, (const float *)ycur, (const float *)yold, (float *)yout, a, c, o, o1,                       \
       ctx->ws[WS_SPART].as<float>(), ctx->ws[WS_SCNT].as<int>(), row0, g0)
         if (wv) {
-          if (g->weighted) { if (rhs) PPRVIZ_SWEEP_SP(true, true, true); else PPRVIZ_SWEEP_SP(true, false, true); }
+          if (pull_weighted(g)) { if (rhs) PPRVIZ_SWEEP_SP(true, true, true); else PPRVIZ_SWEEP_SP(true, false, true); }
           else { if (rhs) PPRVIZ_SWEEP_SP(false, true, true); else PPRVIZ_SWEEP_SP(false, false, true); }
         } else {
-          if (g->weighted) { if (rhs) PPRVIZ_SWEEP_SP(true, true, false); else PPRVIZ_SWEEP_SP(true, false, false); }
+          if (pull_weighted(g)) { if (rhs) PPRVIZ_SWEEP_SP(true, true, false); else PPRVIZ_SWEEP_SP(true, false, false); }
           else { if (rhs) PPRVIZ_SWEEP_SP(false, true, false); else PPRVIZ_SWEEP_SP(false, false, false); }
         }
 #undef PPRVIZ_SWEEP_SP
@@ -884,9 +884,9 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
   const unsigned blocks = (unsigned)((items + kSweepWarps - 1) / kSweepWarps);
   const T *invdw = std::is_same<T, float>::value ? (const T *)g->invdw_f.p : (const T *)g->invdw_d.p;
   const T a = (T)alpha, c = (T)(1.0 - alpha), o = (T)om, o1 = (T)(1.0 - om);
-  const float *w = g->weighted ? g->w.as<float>() : nullptr;
-  const int64_t *rp = g->rp.as<int64_t>();
-  const int32_t *col = g->col.as<int32_t>();
+  const float *w = pull_w(g);
+  const int64_t *rp = pull_rp(g);
+  const int32_t *col = pull_col(g);
   const int64_t row0 = wv ? wv->row0 : 0;
   const int32_t g0 = wv ? wv->g0 : 0;
   if (wv) src = wv->lidx;
@@ -897,12 +897,12 @@ int launch_sweep(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, bool cheb, 
   if (wv) {
     if constexpr (std::is_same<T, float>::value) {
       if (!cheb) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "batched sweeps are Chebyshev sweeps");
-      if (g->weighted) { if (rhs) PPRVIZ_SWEEP(true, true, true, true); else PPRVIZ_SWEEP(true, true, false, true); }
+      if (pull_weighted(g)) { if (rhs) PPRVIZ_SWEEP(true, true, true, true); else PPRVIZ_SWEEP(true, true, false, true); }
       else { if (rhs) PPRVIZ_SWEEP(false, true, true, true); else PPRVIZ_SWEEP(false, true, false, true); }
     } else {
       return set_err(ctx, PPRVIZ_E_INVALID_ARG, "batched sweeps are FP32");
     }
-  } else if (g->weighted) {
+  } else if (pull_weighted(g)) {
     if (cheb) { if (rhs) PPRVIZ_SWEEP(true, true, true, false); else PPRVIZ_SWEEP(true, true, false, false); }
     else { if (rhs) PPRVIZ_SWEEP(true, false, true, false); else PPRVIZ_SWEEP(true, false, false, false); }
   } else {
@@ -940,7 +940,7 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   dim3 grid(rows_blocks, nchunks);
   PPRVIZ_TRY(ws_ensure(ctx, WS_RPART, sizeof(double) * 2 * (size_t)rows_blocks * (size_t)ld));
   double *part = ctx->ws[WS_RPART].as<double>();
-  const float *w = g->weighted ? g->w.as<float>() : nullptr;
+  const float *w = pull_w(g);
   const int64_t n = wv ? wv->nrows : g->n;
   const int2 *brows = wv ? wv->brows : nullptr;
   const int64_t row0 = wv ? wv->row0 : 0;
@@ -948,13 +948,13 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   if (wv) src = wv->lidx;
 #define PPRVIZ_RES(W, B, L)                                                                                  \
   k_residual<T, W, EXACT, B, L><<<grid, kWarps * 32, 0, ctx->stream>>>(                                        \
-      n, ld, g->rp.as<int64_t>(), g->col.as<int32_t>(), w, g->invdw_d.as<double>(), g->dwff.as<float2>(), src, \
+      n, ld, pull_rp(g), pull_col(g), w, g->invdw_d.as<double>(), g->dwff.as<float2>(), src,                   \
       yhi, ylo, rhs_out, part, alpha, 1.0 - alpha, brows, row0, g0, bscale)
   {
     PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL);
-    if (wv) { if (g->weighted) PPRVIZ_RES(true, true, false); else PPRVIZ_RES(false, true, false); }
-    else if (bscale) { if (g->weighted) PPRVIZ_RES(true, false, true); else PPRVIZ_RES(false, false, true); }
-    else { if (g->weighted) PPRVIZ_RES(true, false, false); else PPRVIZ_RES(false, false, false); }
+    if (wv) { if (pull_weighted(g)) PPRVIZ_RES(true, true, false); else PPRVIZ_RES(false, true, false); }
+    else if (bscale) { if (pull_weighted(g)) PPRVIZ_RES(true, false, true); else PPRVIZ_RES(false, false, true); }
+    else { if (pull_weighted(g)) PPRVIZ_RES(true, false, false); else PPRVIZ_RES(false, false, false); }
   }
 #undef PPRVIZ_RES
   PPRVIZ_LAUNCHED(ctx);
@@ -989,7 +989,7 @@ TunedShape tuned_shape(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int *s
   *status = PPRVIZ_OK;
   auto bits = [](uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return (uint64_t)b; };
   const uint64_t key = (bits((uint64_t)g->n) << 40) | (bits((uint64_t)g->nnz) << 32) | (bits((uint64_t)k) << 8) |
-                       (g->weighted ? 1u : 0u);
+                       (g->weighted ? 1u : 0u) | (g->directed ? 2u : 0u);
   for (const auto &e : ctx->tuned_groups)
     if (e.first == key) return TunedShape{e.second >> 16, (int)(e.second & 0xFFFF)};
   const int64_t gmax = choose_group(g->n, k, sizeof(float));
@@ -1175,10 +1175,12 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   // BF16 operands on the tensor cores; a BF16 solve resolves ~2^-8 of its
   // correction, so its sweeps stop there and more refinement passes follow
   const bool bf16 = precision == PPRVIZ_FP32_BF16TC;
+  if ((precision == PPRVIZ_FP32_TC || bf16) && g->directed)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "the tensor-core sweeps take undirected graphs");
   if (precision == PPRVIZ_FP32_TC || bf16) {
     PPRVIZ_TRY(dense_prepare(ctx, g));
     dense = true;
-  } else if (precision == PPRVIZ_FP32 && dense_eligible(g)) {
+  } else if (precision == PPRVIZ_FP32 && !g->directed && dense_eligible(g)) {
     dense = dense_prepare(ctx, g) == PPRVIZ_OK;
     if (!dense) ctx->err.clear();
   }
@@ -1213,10 +1215,16 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   double bsp = 1.0;
   int32_t *csrc = nullptr;
   double *kappa = nullptr;
-  if (!fp64) {
+  // a directed walk is not reversible: its spectrum is complex, so the FP32
+  // path runs power sweeps (the Chebyshev weights with an interval of width 0)
+  // from the plain start instead of deflated Chebyshev sweeps
+  const bool power = g->directed;
+  if (!fp64 && !power) {
     PPRVIZ_TRY(graph_spectral(ctx, g));
     defl = g->spec_deflate;
     bsp = defl ? g->spec_b : 1.0;
+  }
+  if (!fp64) {
     PPRVIZ_TRY(ws_ensure(ctx, WS_CSRC, sizeof(int32_t) * (size_t)ld));
     PPRVIZ_TRY(ws_ensure(ctx, WS_KAPPA, sizeof(double) * (size_t)ld));
     csrc = ctx->ws[WS_CSRC].as<int32_t>();
@@ -1235,8 +1243,8 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
   std::vector<int32_t> srch((size_t)ld);
   std::vector<double> cert;
   bool not_converged = false;
-  // rate of the iterated modes on [1 - delta, 1 + delta]
-  auto rate = [](double delta) { return delta > 1e-12 ? chebyshev_rate(delta) : 0.0; };
+  // rate of the iterated modes on [1 - delta, 1 + delta] (power sweeps: c)
+  auto rate = [power, c](double delta) { return power ? c : (delta > 1e-12 ? chebyshev_rate(delta) : 0.0); };
   auto sweeps_for = [](double factor, double r) {  // K with 2 r^K <= factor
     return r > 0.0 ? (int)ceil(log(0.5 * factor) / log(r)) : 1;
   };
@@ -1290,7 +1298,7 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         PPRVIZ_CUDA(ctx, cudaMemcpyAsync(kappa, kappa_h.data(), sizeof(double) * (size_t)ld,
                                          cudaMemcpyHostToDevice, ctx->stream));
       }
-      double delta_c = c * bsp;
+      double delta_c = power ? 0.0 : c * bsp;
       // main solve to a Chebyshev error bound 2 rho^K <= 1e-5: every further
       // sweep here would only save one refinement sweep, and the refinement
       // (driven by the exact FP64 residual) finishes the job
@@ -1316,7 +1324,7 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         if (cmax <= eps) break;
         // a pass that gained less than 10x (BF16: 2x) means modes outside the
         // estimated interval: iterate the full interval [1 - c, 1 + c] from here on
-        if (pass > 0 && cmax > (bf16 ? 0.5 : 0.1) * cprev) delta_c = c;
+        if (!power && pass > 0 && cmax > (bf16 ? 0.5 : 0.1) * cprev) delta_c = c;
         cprev = cmax;
         // correction's stationary coefficient: sum_j res_jq / alpha over m_C
         if (defl) {
@@ -1328,7 +1336,7 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
         // but an FP32 correction resolves only ~1e-7 of itself per pass, so
         // sweeps past 2 rho^K ~ 3e-8 are left to the next pass
         int K2 = sweeps_for(0.5 * eps / cmax, rate(delta_c)) + 2;
-        K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
+        K2 = std::min(std::max(K2, 4), power ? 4 * kMaxRefineSweeps : kMaxRefineSweeps);
         if (bf16) K2 = std::min(K2, sweeps_for(1e-3, rate(delta_c)) + 1);
         float *delta = nullptr;
         PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, src, (int32_t)ld, rhs, fa, fb, K2, alpha, tcerr,
@@ -1477,7 +1485,8 @@ int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const
   pprviz_stats &st = ctx->stats;
   st.source_group = (int32_t)ld;
   const double c = 1.0 - alpha;
-  auto rate = [](double delta) { return delta > 1e-12 ? chebyshev_rate(delta) : 0.0; };
+  const bool power = g->directed;
+  auto rate = [power, c](double delta) { return power ? c : (delta > 1e-12 ? chebyshev_rate(delta) : 0.0); };
   auto sweeps_for = [](double factor, double r) { return r > 0.0 ? (int)ceil(log(0.5 * factor) / log(r)) : 1; };
   const bool exact_res = eps < 1e-9;
   bool not_converged = false;
@@ -1493,9 +1502,9 @@ int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const
       k_level_rhs<<<(unsigned)((n * ld + 255) / 256), 256, 0, ctx->stream>>>(n, ld, g0, owner_d, bscale_d, alpha, rhs);
     }
     PPRVIZ_LAUNCHED(ctx);
-    // undeflated Chebyshev on the whole interval [1 - c, 1 + c]: a leaf set
-    // may span several components
-    const double delta_c = c;
+    // undeflated Chebyshev on the whole interval [1 - c, 1 + c] (a leaf set
+    // may span several components); power sweeps on a directed graph
+    const double delta_c = g->directed ? 0.0 : c;
     const int K1 = std::max(2, sweeps_for(1e-5, rate(delta_c)));
     float *hi = nullptr;
     PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, owner_d, (int32_t)ld, rhs, bufs[0], bufs[1], K1, alpha, nullptr, nullptr,
@@ -1523,7 +1532,7 @@ int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const
       for (double v : cert) cmax = std::max(cmax, v);
       if (cmax <= eps) break;
       int K2 = sweeps_for(0.5 * eps / cmax, rate(delta_c)) + 2;
-      K2 = std::min(std::max(K2, 4), kMaxRefineSweeps);
+      K2 = std::min(std::max(K2, 4), power ? 4 * kMaxRefineSweeps : kMaxRefineSweeps);
       float *delta = nullptr;
       PPRVIZ_TRY(chebyshev_solve(ctx, g, ld, owner_d, (int32_t)ld, rhs, fa, fb, K2, alpha, nullptr, nullptr, nullptr,
                                  delta_c, &delta));
@@ -1715,6 +1724,8 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
   std::vector<int64_t> uoff((size_t)nviews), unnz((size_t)nviews);
   int64_t N = 0, NNZ = 0, maxn = 0;
   bool weighted = false;
+  for (int32_t v = 0; v < nviews; ++v)
+    if (views[v]->directed) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "batched views take undirected graphs");
   for (int32_t i = 0; i < nviews; ++i) {
     const pprviz_graph *g = views[order[i]];
     uoff[order[i]] = N;

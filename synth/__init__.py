@@ -26,7 +26,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 __all__ = [
     "mix64", "uniform", "chung_lu_weights", "chung_lu", "sbm", "dense_clustered",
-    "uniform_x0", "sample_view", "sbm_views", "Graph",
+    "uniform_x0", "sample_view", "sbm_views", "Graph", "directed_from",
 ]
 
 
@@ -55,16 +55,18 @@ def uniform(seed: int, tag: int, counters: np.ndarray) -> np.ndarray:
 
 
 class Graph:
-    """Undirected graph in CSR form, both directions stored, columns sorted.
+    """Graph in CSR form, columns sorted: undirected (both directions stored)
+    unless `directed`, then each row lists the node's out-neighbours.
 
     row_ptr: int64[n + 1]; col: int32[nnz]; weight: float32[nnz] or None.
     """
 
-    def __init__(self, n, row_ptr, col, weight=None):
+    def __init__(self, n, row_ptr, col, weight=None, directed=False):
         self.n = int(n)
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
         self.weight = None if weight is None else np.ascontiguousarray(weight, dtype=np.float32)
+        self.directed = bool(directed)
 
     @property
     def nnz(self) -> int:
@@ -249,3 +251,34 @@ def sbm_views(count: int, seed: int = 0, n_min: int = 50, n_max: int = 5000,
         sizes[: nv - sizes.sum()] += 1
         out.append(sbm(sizes, p_in, p_out, seed=seed * 1000003 + v, tag=11))
     return out
+
+
+def directed_from(g: Graph, p_both: float = 0.3, dangling: float = 0.02, seed: int = 0, tag: int = 11) -> Graph:
+    """A directed graph drawn from an undirected one: each edge {u, v} keeps
+    both directions with probability p_both, else one direction chosen
+    uniformly; then a `dangling` fraction of the nodes lose all out-edges
+    (dangling nodes). Weights, if any, follow their edges."""
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    dst = g.col.astype(np.int64)
+    up = src < dst
+    u, v = src[up], dst[up]
+    w = None if g.weight is None else g.weight[up]
+    idx = np.arange(len(u), dtype=np.uint64)
+    r1 = uniform(seed, tag, idx)
+    r2 = uniform(seed, tag + 1, idx)
+    both = r1 < p_both
+    fwd = both | (r2 < 0.5)
+    bwd = both | (r2 >= 0.5)
+    s2 = np.concatenate([u[fwd], v[bwd]])
+    d2 = np.concatenate([v[fwd], u[bwd]])
+    w2 = None if w is None else np.concatenate([w[fwd], w[bwd]])
+    drop = uniform(seed, tag + 2, np.arange(g.n, dtype=np.uint64)) < dangling
+    keep = ~drop[s2]
+    s2, d2 = s2[keep], d2[keep]
+    if w2 is not None:
+        w2 = w2[keep]
+    order = np.lexsort((d2, s2))
+    s2, d2 = s2[order], d2[order]
+    row_ptr = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(s2, minlength=g.n), out=row_ptr[1:])
+    return Graph(g.n, row_ptr, d2.astype(np.int32), None if w2 is None else w2[order], directed=True)

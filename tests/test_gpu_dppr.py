@@ -90,7 +90,6 @@ def _bad(ctx, n, rp, col, w=None, flags=None):
 
 def test_graph_validation_rejects_bad_csr(ctx):
     from paper_2112_14944_gb300 import _binding as B
-    ok_rp, ok_col = [0, 1, 2], [1, 0]
     assert _bad(ctx, 2, [0, 1, 2], [1, 1]) == B.PPRVIZ_E_BAD_GRAPH          # asymmetric (1->1 self-loop too)
     assert _bad(ctx, 3, [0, 2, 3, 4], [2, 1, 0, 0]) == B.PPRVIZ_E_BAD_GRAPH  # unsorted row 0
     assert _bad(ctx, 2, [0, 1, 2], [5, 0]) == B.PPRVIZ_E_BAD_GRAPH          # column out of range
@@ -99,7 +98,7 @@ def test_graph_validation_rejects_bad_csr(ctx):
     assert _bad(ctx, 2, [0, 1, 2], [1, 0], w=[1.0, 2.0]) == B.PPRVIZ_E_BAD_GRAPH   # asymmetric weight
     assert _bad(ctx, 2, [0, 2, 1], [1, 0]) == B.PPRVIZ_E_BAD_GRAPH          # decreasing row_ptr
     assert _bad(ctx, 3, [0, 1, 1, 2], [2, 1]) == B.PPRVIZ_E_BAD_GRAPH       # 0->2 without 2->0
-    assert _bad(ctx, 2, ok_rp, ok_col, flags=B.PPRVIZ_VALIDATE) == B.PPRVIZ_E_INVALID_ARG  # directed not supported
+    assert _bad(ctx, 3, [0, 1, 1, 2], [2, 1], flags=B.PPRVIZ_VALIDATE) == B.PPRVIZ_E_BAD_GRAPH  # self-loop (directed)
     assert _bad(ctx, 0, [0], []) == B.PPRVIZ_E_INVALID_ARG
 
 

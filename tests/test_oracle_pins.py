@@ -387,3 +387,28 @@ def test_node_distribution_and_ulcv_hand_values():
     assert abs(O.node_distribution(2.0 * X) - O.node_distribution(X) / 4.0) < 1e-12 * O.node_distribution(X)
     assert abs(O.ulcv(X @ R.T - 1.0, E) - O.ulcv(X, E)) < 1e-12
     assert abs(O.ulcv(5.0 * X, E) - O.ulcv(X, E)) < 1e-12
+
+
+def test_directed_walk_closed_forms():
+    # Sec. 2.1's directed setting. Cycle a -> b -> c -> a: the walk from a is at
+    # step t on node t mod 3, so pi(a, .) = alpha (1, c, c^2) / (1 - c^3).
+    rp, col = _csr_from_edges(3, [(0, 1), (1, 2), (2, 0)], False)
+    Pi = O.ppr_rows(O.transition_matrix(3, rp, col), [0], ALPHA)
+    z = 1 - C ** 3
+    assert np.allclose(Pi[0], [ALPHA / z, ALPHA * C / z, ALPHA * C * C / z], atol=1e-15, rtol=0)
+    # a -> b with b dangling (reading 2: the walk stays on b): pi(a, a) = alpha,
+    # pi(a, b) = c, pi(b, b) = 1; d(b) = 0 so b's DPPR row is 0
+    rp, col = _csr_from_edges(2, [(0, 1)], False)
+    P = O.transition_matrix(2, rp, col)
+    Pi = O.ppr_rows(P, [0, 1], ALPHA)
+    assert np.allclose(Pi, [[ALPHA, C], [0.0, 1.0]], atol=1e-15, rtol=0)
+    d = O.degrees(2, rp, col)
+    D = O.dppr_rows(Pi, d, [0, 1])
+    assert np.all(D[1] == 0.0) and abs(D[0, 1] - C) < 1e-15
+    # the direct solve agrees on a random directed graph with dangling nodes,
+    # and every PPR row is a distribution
+    g = synth.directed_from(synth.chung_lu(150, 8, 2.5, seed=3), seed=4)
+    P = O.transition_matrix(g.n, g.row_ptr, g.col)
+    rows = O.ppr_rows(P, np.arange(g.n), ALPHA)
+    assert np.abs(rows - O.ppr_direct(P, ALPHA)).max() < 1e-13
+    assert np.abs(rows.sum(axis=1) - 1).max() < 1e-13
