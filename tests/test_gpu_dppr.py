@@ -98,7 +98,8 @@ def test_graph_validation_rejects_bad_csr(ctx):
     assert _bad(ctx, 2, [0, 1, 2], [1, 0], w=[1.0, 2.0]) == B.PPRVIZ_E_BAD_GRAPH   # asymmetric weight
     assert _bad(ctx, 2, [0, 2, 1], [1, 0]) == B.PPRVIZ_E_BAD_GRAPH          # decreasing row_ptr
     assert _bad(ctx, 3, [0, 1, 1, 2], [2, 1]) == B.PPRVIZ_E_BAD_GRAPH       # 0->2 without 2->0
-    assert _bad(ctx, 3, [0, 1, 1, 2], [2, 1], flags=B.PPRVIZ_VALIDATE) == B.PPRVIZ_E_BAD_GRAPH  # self-loop (directed)
+    assert _bad(ctx, 2, [0, 1, 1], [0], flags=B.PPRVIZ_VALIDATE) == B.PPRVIZ_E_BAD_GRAPH  # self-loop (directed)
+    assert _bad(ctx, 2, [0, 2, 2], [1, 1], flags=B.PPRVIZ_VALIDATE) == B.PPRVIZ_E_BAD_GRAPH  # duplicate (directed)
     assert _bad(ctx, 0, [0], []) == B.PPRVIZ_E_INVALID_ARG
 
 
