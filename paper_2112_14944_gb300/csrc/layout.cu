@@ -579,64 +579,59 @@ k_sympass_pipe(int ntile, int npin /* per CTA */, const TileRec *__restrict__ ti
   }
 }
 
-// Row block R of view v, (v, R) = blocks[blockIdx.x / 4], rows 32 q .. 32 q + 31
-// of it for q = blockIdx.x % 4:
+// Row block R of view v, (v, R) = blocks[blockIdx.x]:
 //   Vout[R 128 + row] = sum_{J = R}^{nbt - 1} Part[J][R 128 + row]        (row sums of tiles (R, J))
 //                     + sum over the runs of column block R and their warps
 //                       of RunPart[(r CWARPS + w) 128 + row]                (column sums of tiles (I < R, R))
-// The items are numbered in that order; thread (g, row) adds items g, g + 32,
-// ... in order (a few per thread, so the pass that waits on this one waits
-// for a few round trips only), then the 32 group sums of a row are added in
-// order: a fixed order, the same result on every run.
-constexpr int kRedRows = 32, kRedGroups = 32;
-__global__ void __launch_bounds__(kRedRows * kRedGroups)
+// The items are numbered in that order; thread (g, row) adds items g, g + 8,
+// ... in order, then the eight group sums are added in order (a fixed order:
+// the same result on every run).
+__global__ void __launch_bounds__(1024)
 k_reduce_rows(const int2 *__restrict__ blocks, const BatchView *__restrict__ views, const int *__restrict__ run_ptr,
               const int *__restrict__ run_idx, const float2 *__restrict__ Part, const float2 *__restrict__ RunPart,
               float2 *__restrict__ Vout) {
-  constexpr int UN = 4;
-  __shared__ float2 red[kRedGroups][kRedRows + 1];
+  constexpr int NG = 8, UN = 10;
+  __shared__ float2 red[NG][ST];
   // launched as a programmatic dependent of the pass: wait for it to complete
   // (its partial sums visible); the next pass may be scheduled meanwhile
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int bi = blockIdx.x >> 2, q = blockIdx.x & 3;
-  const int2 b = blocks[bi];
+  const int2 b = blocks[blockIdx.x];
   const BatchView bv = views[b.x];
-  const int lrow = threadIdx.x & (kRedRows - 1), g = threadIdx.x / kRedRows;
-  const int row = q * kRedRows + lrow;
+  const int row = threadIdx.x & (ST - 1), g = threadIdx.x >> 7;
   const int64_t r = (int64_t)b.y * ST + row;
   const int nrow = bv.nbt - b.y;
-  const int r0 = run_ptr[bi], nitem = nrow + (run_ptr[bi + 1] - r0) * spipe::CWARPS;
+  const int r0 = run_ptr[blockIdx.x], nitem = nrow + (run_ptr[blockIdx.x + 1] - r0) * spipe::CWARPS;
   float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll 1
-  for (int i0 = g; i0 < nitem; i0 += kRedGroups * UN) {
+  for (int i0 = g; i0 < nitem; i0 += NG * UN) {
     float2 u[UN];
 #pragma unroll
     for (int e = 0; e < UN; ++e) {
-      const int i = i0 + kRedGroups * e;
+      const int i = i0 + NG * e;
       if (i < nrow) {
         u[e] = __ldcg(Part + bv.part_off + (int64_t)(b.y + i) * bv.kp + r);
       } else if (i < nitem) {
-        const int qq = i - nrow;
-        const int run = run_idx[r0 + qq / spipe::CWARPS];
-        u[e] = __ldcg(RunPart + ((int64_t)run * spipe::CWARPS + qq % spipe::CWARPS) * ST + row);
+        const int q = i - nrow;
+        const int run = run_idx[r0 + q / spipe::CWARPS];
+        u[e] = __ldcg(RunPart + ((int64_t)run * spipe::CWARPS + q % spipe::CWARPS) * ST + row);
       }
     }
 #pragma unroll
     for (int e = 0; e < UN; ++e)
-      if (i0 + kRedGroups * e < nitem) {
+      if (i0 + NG * e < nitem) {
         acc.x += u[e].x;
         acc.y += u[e].y;
       }
   }
-  red[g][lrow] = acc;
+  red[g][row] = acc;
   __syncthreads();
-  if (threadIdx.x < kRedRows) {
-    float2 v = red[0][lrow];
-#pragma unroll 8
-    for (int e = 1; e < kRedGroups; ++e) {
-      v.x += red[e][lrow].x;
-      v.y += red[e][lrow].y;
+  if (threadIdx.x < ST) {
+    float2 v = red[0][row];
+#pragma unroll
+    for (int e = 1; e < NG; ++e) {
+      v.x += red[e][row].x;
+      v.y += red[e][row].y;
     }
     Vout[bv.vec_off + r] = v;
   }
@@ -955,11 +950,11 @@ int pass_pair(pprviz_ctx *ctx, unsigned grid, const PassTables &pt, const CUtens
   const int npin = (int)(kPinBytes / spipe::TILE_BYTES / grid);  // tiles per CTA
   { PPRVIZ_PROF(ctx, PPRVIZ_K_LY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<0>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, npin, pt.recs, maps, (const float2 *)X, Part, RunPart, perr)); }
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, 4 * nb, kRedRows * kRedGroups, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, Bv)); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, nb, 1024, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, Bv)); }
   PPRVIZ_LAUNCHED(ctx);
   { PPRVIZ_PROF(ctx, PPRVIZ_K_APPLY); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_sympass_pipe<1>, grid, spipe::THREADS, spipe::SMEM, pt.ntile, npin, pt.recs, maps, (const float2 *)Bv, Part, RunPart, perr)); }
   PPRVIZ_LAUNCHED(ctx);
-  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, 4 * nb, kRedRows * kRedGroups, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, X)); }
+  { PPRVIZ_PROF(ctx, PPRVIZ_K_OTHER); PPRVIZ_CUDA(ctx, launch_dependent(ctx, k_reduce_rows, nb, 1024, 0, pt.blocks, views_d, pt.run_ptr, pt.run_idx, (const float2 *)Part, (const float2 *)RunPart, X)); }
   PPRVIZ_LAUNCHED(ctx);
   return PPRVIZ_OK;
 }
