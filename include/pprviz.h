@@ -103,6 +103,9 @@ typedef struct pprviz_stats {
     /* Algorithmic flops of the dense tensor-core sweeps: 2 n^2 per (sweep,
      * valid source); the 3xTF32 split executes three times as many. */
     double flops_dense;
+    /* 1 when the layout updates of the call ran as one CUDA graph (batched
+     * views: the updates are recorded once and launched as a graph), else 0. */
+    int32_t graph_launched;
 } pprviz_stats;
 
 /* Kernel classes for per-class device timing (pprviz_profile). */

@@ -74,7 +74,7 @@ class pprviz_stats(C.Structure):
                 ("refine_passes", C.c_int32), ("residual_passes", C.c_int32), ("kernel_launches", C.c_int32),
                 ("max_cert", C.c_double), ("layout_iters", C.c_int32), ("source_group", C.c_int32),
                 ("bytes_sweep", C.c_double), ("bytes_ly", C.c_double), ("bytes_apply", C.c_double),
-                ("flops_factor", C.c_double), ("flops_dense", C.c_double)]
+                ("flops_factor", C.c_double), ("flops_dense", C.c_double), ("graph_launched", C.c_int32)]
 
 
 _lib = None

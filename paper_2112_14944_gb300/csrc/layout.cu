@@ -1188,7 +1188,42 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   V2 *RunPart = ctx->ws[WS_RUNP].as<V2>();
   int *perr = flag + 1;
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
-  for (int it = 0; it < iters; ++it) PPRVIZ_TRY(pass_pair(ctx, pgrid, pt, maps, views_d, X, Bv, Part, RunPart, perr));
+  // The updates of a batch are launches only (no host decision between them):
+  // they are recorded once into a CUDA graph and the graph is launched (the
+  // profiling events, when on, are recorded into it too). If recording or
+  // instantiating fails, the same launches go to the stream directly.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graphed = false;
+  if (iters > 1 && cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    int st = PPRVIZ_OK;
+    for (int it = 0; it < iters && st == PPRVIZ_OK; ++it)
+      st = pass_pair(ctx, pgrid, pt, maps, views_d, X, Bv, Part, RunPart, perr);
+    const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st == PPRVIZ_OK && ec == cudaSuccess && graph && cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess &&
+        cudaGraphLaunch(gexec, ctx->stream) == cudaSuccess)
+      graphed = true;
+    if (!graphed) {
+      cudaGetLastError();
+      ctx->err.clear();
+      if (gexec) cudaGraphExecDestroy(gexec);
+      if (graph) cudaGraphDestroy(graph);
+      gexec = nullptr;
+      graph = nullptr;
+    }
+  } else {
+    cudaGetLastError();
+  }
+  ctx->stats.graph_launched = graphed ? 1 : 0;
+  if (!graphed)
+    for (int it = 0; it < iters; ++it) PPRVIZ_TRY(pass_pair(ctx, pgrid, pt, maps, views_d, X, Bv, Part, RunPart, perr));
+  if (graphed) {
+    // the graph has run before the objects go (the wait below is the call's own)
+    const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+    cudaGraphExecDestroy(gexec);
+    cudaGraphDestroy(graph);
+    if (es != cudaSuccess) return cuda_err(ctx, es, "layout updates (CUDA graph)");
+  }
   if (iters > 0) {
     int herr = 0;
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -1713,6 +1713,71 @@ pprviz::DevBuf slot_view(pprviz_ctx *ctx, int slot) { return ctx->ws[slot]; }
 
 }  // namespace
 
+// Source-group width of a wave of the batched propagation, tuned on first
+// use per size class (bit lengths of the wave's rows, edges and width): the
+// candidates 128, 256, ... up to the budget's width each run three timed
+// Chebyshev sweeps of the wave (after one untimed) on zeroed buffers, and
+// the width with the least time per source and sweep wins.
+int64_t tuned_wave_group(pprviz_ctx *ctx, const pprviz_graph *U, const Wave &wv0, int64_t width, int64_t ldmax,
+                         int64_t nnz, int *status) {
+  *status = PPRVIZ_OK;
+  if (ldmax <= kChunk) return ldmax;
+  auto bits = [](uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return (uint64_t)b; };
+  const uint64_t key = (1ull << 63) | (bits((uint64_t)wv0.nrows) << 40) | (bits((uint64_t)nnz) << 32) |
+                       (bits((uint64_t)width) << 8) | (U->weighted ? 1u : 0u);
+  for (const auto &e : ctx->tuned_groups)
+    if (e.first == key) return std::min<int64_t>(e.second, ldmax);
+  std::vector<int64_t> cands;
+  for (int64_t c = kChunk; c < ldmax; c *= 2) cands.push_back(c);
+  cands.push_back(ldmax);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    *status = set_err(ctx, PPRVIZ_E_CUDA, "wave autotuner: event creation failed");
+    return ldmax;
+  }
+  int64_t best = ldmax;
+  double best_score = 0.0;
+  float *ya = ctx->ws[WS_Y0].as<float>(), *yb = ctx->ws[WS_Y1].as<float>();
+  for (int64_t G : cands) {
+    const size_t bytes = sizeof(float) * (size_t)(wv0.nrows * G);
+    cudaError_t ce = cudaMemsetAsync(ya, 0, bytes, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(yb, 0, bytes, ctx->stream);
+    if (ce != cudaSuccess) {
+      *status = cuda_err(ctx, ce, "wave autotuner");
+      break;
+    }
+    Wave wv = wv0;
+    wv.g0 = 0;
+    float ms = 0.0f;
+    int st = PPRVIZ_OK;
+    for (int rep = 0; rep < 4 && st == PPRVIZ_OK; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, ctx->stream);
+      st = launch_sweep<float>(ctx, U, G, true, false, nullptr, nullptr, (rep & 1) ? yb : ya, (rep & 1) ? ya : yb,
+                               (rep & 1) ? ya : yb, 0.15, 1.0, &wv);
+    }
+    if (st != PPRVIZ_OK) {
+      *status = st;
+      break;
+    }
+    cudaEventRecord(e1, ctx->stream);
+    if ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+      *status = cuda_err(ctx, ce, "wave autotuner timing");
+      break;
+    }
+    const double score = (double)ms / (double)G;
+    if (best_score == 0.0 || score < best_score) {
+      best_score = score;
+      best = G;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (*status == PPRVIZ_OK) ctx->tuned_groups.push_back({key, best});
+  return best;
+}
+
 int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const *views, const int64_t *node_off,
                      const int64_t *sq_off, double alpha, double eps, const int32_t *iota_d, float *pdist_all,
                      double *cert_h) {
@@ -1893,8 +1958,26 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
   bool not_converged = false;
 
   for (size_t wi = 0; wi < waves.size(); ++wi) {
-    const WaveDef &wd = waves[wi];
+    WaveDef wd = waves[wi];
     const int nvw = (int)(wd.last - wd.first);
+    {
+      // autotuned source-group width of the wave (cached per size class)
+      Wave tw;
+      tw.lidx = lidx;
+      tw.nv = nvr;
+      tw.row0 = wd.row0;
+      tw.nrows = wd.nrows;
+      tw.nviews = nvw;
+      tw.items = ctx->ws[WS_UITEMS].as<int4>() + wsplit[wi].item0;
+      tw.srow = ctx->ws[WS_USROW].as<int2>() + wsplit[wi].srow0;
+      tw.nitems = wsplit[wi].nitems;
+      tw.nsplit = wsplit[wi].nsplit;
+      tw.nslots = wsplit[wi].nslots;
+      int64_t nnzw = urp[(size_t)(wd.row0 + wd.nrows)] - urp[(size_t)wd.row0];
+      int ts = PPRVIZ_OK;
+      wd.ld = tuned_wave_group(ctx, &U, tw, wd.width, wd.ld, nnzw, &ts);
+      PPRVIZ_TRY(ts);
+    }
     // residual row blocks: ~1,216 blocks of the wave shared in proportion to
     // the views' sizes (at least one each), never straddling two views
     std::vector<int2> brows;

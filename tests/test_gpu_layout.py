@@ -256,6 +256,7 @@ def test_views_batch_matches_single_views(ctx):
     x0 = np.concatenate([synth.uniform_x0(g.n, seed=10 + i) for i, g in enumerate(graphs)])
     xb, pdb, stress, off, cert = ctx.views_batch(G, x0, ALPHA, 1e-6, 40, want_pdist=True, want_cert=True)
     assert np.all(cert <= 1e-6)
+    assert ctx.stats()["graph_launched"] == 1  # the 40 updates ran as one CUDA graph
     sq = 0
     for v, g in enumerate(graphs):
         n = g.n
