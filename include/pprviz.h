@@ -104,7 +104,8 @@ typedef struct pprviz_stats {
      * valid source); the 3xTF32 split executes three times as many. */
     double flops_dense;
     /* 1 when the layout updates of the call ran as one CUDA graph (batched
-     * views: the updates are recorded once and launched as a graph), else 0. */
+     * views: the updates are recorded once and launched as a graph), else 0.
+     * With kernel timing on (pprviz_profile) they are launched one by one. */
     int32_t graph_launched;
 } pprviz_stats;
 
@@ -158,7 +159,9 @@ int pprviz_profile(pprviz_ctx *ctx, int enable);
  * entries; NULL arrays are skipped) since the last reset: the total device
  * milliseconds of the timed launches, the number of launches, and the number
  * of timed launches (the ones in ms_out). Launch counts are kept even when
- * timing is off. */
+ * timing is off. A pair of events that cannot be timed is left out of both
+ * ms_out and timed_out, every event goes back to the context's pool, the
+ * arrays are still written, and the call returns E_CUDA. */
 int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, int64_t *timed_out);
 
 /* P0 - graph ingest (Sec. 2.1; Table 1: n nodes, out-degree d(v)).

@@ -60,7 +60,9 @@ ProfScope::ProfScope(pprviz_ctx *ctx, int k) : c(ctx), cls(k) {
   const int64_t nth = c->class_launches[cls]++;
   // the classes launched hundreds of times per call are sampled: one launch in prof_every
   const bool hot = cls == PPRVIZ_K_SWEEP || cls == PPRVIZ_K_LY || cls == PPRVIZ_K_APPLY || cls == PPRVIZ_K_OTHER;
-  if (c->profiling && (!hot || nth % c->prof_every == 0)) {
+  // launches recorded into a CUDA graph are counted, never timed: an event
+  // recorded during stream capture marks no point on the device timeline
+  if (c->profiling && !c->capturing && (!hot || nth % c->prof_every == 0)) {
     c->class_timed[cls]++;
     a = ev_get(c);
     b = ev_get(c);
@@ -216,10 +218,19 @@ int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, 
   if (!ctx) return PPRVIZ_E_INVALID_ARG;
   PPRVIZ_CUDA(ctx, cudaSetDevice(ctx->device));
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // every pending pair goes back to the pool, timed or not, so that no event
+  // is both pending and pooled; a pair that cannot be timed is dropped from
+  // the class's timed count and reported once after the pass
+  cudaError_t bad = cudaSuccess;
   for (auto &p : ctx->ev_pending) {
     float ms = 0.0f;
-    PPRVIZ_CUDA(ctx, cudaEventElapsedTime(&ms, p.second.first, p.second.second));
-    ctx->class_ms[p.first] += ms;
+    const cudaError_t e = cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    if (e == cudaSuccess) {
+      ctx->class_ms[p.first] += ms;
+    } else {
+      if (bad == cudaSuccess) bad = e;
+      if (ctx->class_timed[p.first] > 0) ctx->class_timed[p.first]--;
+    }
     ctx->ev_pool.push_back(p.second.first);
     ctx->ev_pool.push_back(p.second.second);
   }
@@ -228,6 +239,10 @@ int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, 
     if (ms_out) ms_out[i] = ctx->class_ms[i];
     if (launches_out) launches_out[i] = ctx->class_launches[i];
     if (timed_out) timed_out[i] = ctx->class_timed[i];
+  }
+  if (bad != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_err(ctx, bad, "cudaEventElapsedTime (kernel_times)");
   }
   return PPRVIZ_OK;
 }

@@ -62,6 +62,7 @@ enum Slot {
 struct pprviz_ctx {
   // per-class device timing (pprviz_profile / pprviz_kernel_times)
   bool profiling = false;
+  bool capturing = false;  // launches are being recorded into a CUDA graph
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double class_ms[PPRVIZ_NKCLASS] = {0};

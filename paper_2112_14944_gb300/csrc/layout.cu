@@ -1189,16 +1189,19 @@ int layout_batch_run(pprviz_ctx *ctx, int32_t nviews, const int64_t *k_h, const 
   int *perr = flag + 1;
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(perr, 0, sizeof(int), ctx->stream));
   // The updates of a batch are launches only (no host decision between them):
-  // they are recorded once into a CUDA graph and the graph is launched (the
-  // profiling events, when on, are recorded into it too). If recording or
-  // instantiating fails, the same launches go to the stream directly.
+  // they are recorded once into a CUDA graph and the graph is launched. With
+  // kernel timing on, or if recording or instantiating fails, the same
+  // launches go to the stream directly (timing events mark points of the
+  // stream, which a recorded graph does not have).
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool graphed = false;
-  if (iters > 1 && cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+  if (iters > 1 && !ctx->profiling && cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
     int st = PPRVIZ_OK;
+    ctx->capturing = true;
     for (int it = 0; it < iters && st == PPRVIZ_OK; ++it)
       st = pass_pair(ctx, pgrid, pt, maps, views_d, X, Bv, Part, RunPart, perr);
+    ctx->capturing = false;
     const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
     if (st == PPRVIZ_OK && ec == cudaSuccess && graph && cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess &&
         cudaGraphLaunch(gexec, ctx->stream) == cudaSuccess)

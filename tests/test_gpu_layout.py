@@ -286,6 +286,30 @@ def test_views_batch_matches_single_views(ctx):
         assert abs(st_t[v] - hist[-1]) <= 1e-3 * hist[-1], (v, st_t[v], hist[-1])
 
 
+def test_views_batch_profiled_runs_launches_directly(ctx):
+    """With kernel timing on, the batched updates go to the stream one by one
+    (no CUDA graph: a recorded graph has no stream points to time), give the
+    layout of the graph launch (up to the rounding of the propagation's
+    reductions), and every timing event pair is readable."""
+    graphs = synth.sbm_views(4, seed=5, n_min=60, n_max=200)
+    G = [ctx.upload_graph(g) for g in graphs]
+    x0 = np.concatenate([synth.uniform_x0(g.n, seed=20 + i) for i, g in enumerate(graphs)])
+    ctx.views_batch(G, x0, ALPHA, 1e-6, 12, want_pdist=False)  # settles the tuned wave widths
+    xg, _, sg, _, _ = ctx.views_batch(G, x0, ALPHA, 1e-6, 12, want_pdist=False, want_cert=True)
+    assert ctx.stats()["graph_launched"] == 1
+    ctx.profile(1)
+    try:
+        xp, _, sp, _, _ = ctx.views_batch(G, x0, ALPHA, 1e-6, 12, want_pdist=False, want_cert=True)
+        assert ctx.stats()["graph_launched"] == 0
+        kt = ctx.kernel_times()
+    finally:
+        ctx.profile(0)
+    np.testing.assert_allclose(xp, xg, rtol=0, atol=1e-4 * max(1.0, np.abs(xg).max()))
+    np.testing.assert_allclose(sp, sg, rtol=1e-4)
+    assert sum(t for _, _, t in kt.values()) > 0
+    assert all(t <= c for _, c, t in kt.values())
+
+
 def test_views_batch_waves_edge_cases(ctx):
     """Batched propagation over views that exercise the wave plan: single
     nodes, a single edge, a star, many small SBM views sharing one wave, and
