@@ -20,11 +20,13 @@ Readings where the paper is silent (each also listed in the design notes):
   * m = sum_v d(v) (both directions of an undirected edge are counted);
   * PDist with z = 0 is 2 ln n_clamp, the diagonal of PDist is 0 and unused;
   * "(L^w)^-1" in Eq. (10) is the Moore-Penrose solution: the pinned solve
-    followed by centring.
+    followed by centring;
+  * Tau-Push (Sec. 4): the readings are listed above gfp() below.
 
 Parity status: every function here is pinned by a test in
 tests/test_oracle_pins.py (closed forms, a direct linear solve, invariants,
-the paper's forward-push running example, finite differences).
+the paper's forward- and backward-push examples, the error bounds of
+Lemmas 2 and 3 and Theorem 3 against a direct solve, finite differences).
 """
 from __future__ import annotations
 
@@ -39,6 +41,7 @@ __all__ = [
     "pdist_from_z", "pdist_from_dppr", "stress", "stress_grad", "stress_grad_pdist",
     "lw_matrix", "ly_matrix", "smacof_step", "smacof", "forward_push",
     "residual_certificate", "power_sweeps_needed", "level_dppr", "node_distribution", "ulcv",
+    "backward_push", "dpr", "dpr_power", "gfp", "gbp", "tau_push",
 ]
 
 
@@ -329,3 +332,195 @@ def ulcv(X, edges):
     mu = lengths.mean()
     sigma = np.sqrt(((lengths - mu) ** 2).mean())
     return float(sigma / mu)
+
+
+# ----------------------------------------------------------------------------
+# Sec. 4.1: backward push (the conventional single-target form, PPR units), in
+# a caller-given order (used to check the paper's backward-push example).
+# ----------------------------------------------------------------------------
+def backward_push(P, target, alpha, order):
+    """Initial residue r(t) = 1 at the target t. A push at v_k moves
+    alpha * r(v_k) to the estimate of v_k and gives every in-neighbour v_i of
+    v_k the amount (1 - alpha) * r(v_k) * P[i, k] (= (1 - alpha) r(v_k) / d(v_i)
+    unweighted), then zeroes r(v_k). The residue is read and zeroed before it
+    is spread. Returns (estimate, residue) with pi(s, t) = estimate_s +
+    sum_k pi(s, k) r_k (the backward invariant)."""
+    n = P.shape[0]
+    PT = sp.csr_matrix(P.T)  # row k lists the in-neighbours i of k with P[i, k]
+    est = np.zeros(n)
+    r = np.zeros(n)
+    r[target] = 1.0
+    for v in order:
+        rv = r[v]
+        est[v] += alpha * rv
+        r[v] = 0.0
+        for q in range(PT.indptr[v], PT.indptr[v + 1]):
+            r[PT.indices[q]] += (1 - alpha) * rv * PT.data[q]
+    return est, r
+
+
+# ----------------------------------------------------------------------------
+# Sec. 4, Eq. (dnpr-dnppr): degree-normalised PageRank (DPR) of single nodes,
+#   tau_t = (1 / m) sum_k pi_d(v_k, v_t);
+# a supernode's tau_j is the mean of tau_t over its leaves.
+# ----------------------------------------------------------------------------
+def dpr(P, d, alpha):
+    """tau_t from the dense PPR matrix (the definition; tiny graphs)."""
+    d = np.asarray(d, dtype=np.float64)
+    Pi = ppr_direct(P, alpha)
+    return (d[:, None] * Pi).sum(axis=0) / d.sum()
+
+
+def dpr_power(P, d, alpha, tol=1e-15):
+    """The index precompute of Sec. 4.3: a global PageRank whose start vector
+    has entry d(v_k) / m at v_k, by power iteration,
+        x_0 = alpha s,   x_{t+1} = alpha s + (1 - alpha) x_t P,   s = d / m,
+    stopped once the unended walk mass (1 - alpha)^(t+1) is at most `tol`.
+    Summing sum_k d(v_k) pi(v_k, .) / m this is the same vector as dpr()."""
+    d = np.asarray(d, dtype=np.float64)
+    s = d / d.sum()
+    PT = sp.csr_matrix(P.T)
+    x = alpha * s
+    for _ in range(power_sweeps_needed(alpha, tol)):
+        x = alpha * s + (1 - alpha) * (PT @ x)
+    return x
+
+
+# ----------------------------------------------------------------------------
+# Sec. 4.2: Group Forward-Push (Algorithm 2) and Group Backward-Push
+# (Algorithm 3); Sec. 4.1: Tau-Push (Algorithm 1).
+#
+# Readings (the paper is silent on these):
+#   * "while some residue is above its threshold" takes the nodes first in,
+#     first out: a node joins the queue when its residue rises above the
+#     threshold and is pushed when it reaches the front;
+#   * a push reads and zeroes the residue before spreading it;
+#   * a node without out-edges keeps the walk (P[v, v] = 1, the dangling
+#     reading above); a push there takes the sum of its endless repeats:
+#     forward, the whole residue goes to the estimate; backward, the estimate
+#     gains d(v) r = 0 and each other in-neighbour x of v receives
+#     (1 - alpha) r P[x, v] / alpha;
+#   * Eq. (brmax)'s maximum over the other supernodes: with no other supernode
+#     (a single child) the target's own mean degree is used, and a maximum of 0
+#     (no source can reach anything) means no backward push at all.
+# ----------------------------------------------------------------------------
+def _owners(n, leaf_sets):
+    owner = np.full(n, -1, dtype=np.int64)
+    for j, F in enumerate(leaf_sets):
+        owner[np.asarray(F, dtype=np.int64)] = j
+    return owner
+
+
+def gfp(P, d, leaf_sets, i, alpha, r_max):
+    """Algorithm 2 from source supernode V_i: initial residue d(v) / |F(V_i)|
+    on each leaf of V_i; while some v_k has r(v_k) > d(v_k) r_max, add
+    alpha r(v_k) / |F(V_j)| to the estimate of the supernode V_j holding v_k
+    (if any) and give each out-neighbour v_j the share (1 - alpha) r(v_k) P[k, j].
+    Returns the estimates of every supernode (length len(leaf_sets))."""
+    n = P.shape[0]
+    d = np.asarray(d, dtype=np.float64)
+    owner = _owners(n, leaf_sets)
+    size = np.array([len(F) for F in leaf_sets], dtype=np.float64)
+    Pc = sp.csr_matrix(P)
+    est = np.zeros(len(leaf_sets))
+    r = np.zeros(n)
+    Fi = np.asarray(leaf_sets[i], dtype=np.int64)
+    r[Fi] = d[Fi] / len(Fi)
+    queue = [int(v) for v in Fi if r[v] > d[v] * r_max]
+    head = 0
+    while head < len(queue):
+        v = queue[head]
+        head += 1
+        rv = r[v]
+        r[v] = 0.0
+        dangling = Pc.indptr[v + 1] - Pc.indptr[v] == 1 and Pc.indices[Pc.indptr[v]] == v and d[v] == 0
+        j = owner[v]
+        if dangling:
+            if j >= 0:
+                est[j] += rv / size[j]
+            continue
+        if j >= 0:
+            est[j] += alpha * rv / size[j]
+        for q in range(Pc.indptr[v], Pc.indptr[v + 1]):
+            u = Pc.indices[q]
+            thr = d[u] * r_max
+            before = r[u]
+            r[u] += (1 - alpha) * rv * Pc.data[q]
+            if before <= thr < r[u]:
+                queue.append(int(u))
+    return est
+
+
+def gbp(P, d, leaf_sets, j, alpha, rb_max):
+    """Algorithm 3 towards target supernode V_j: initial residue 1 / |F(V_j)| on
+    each leaf of V_j; while some v_k has r(v_k) > rb_max, add
+    alpha d(v_k) r(v_k) / |F(V_i)| to the estimate of the supernode V_i holding
+    v_k (if any) and give each in-neighbour v_i the share
+    (1 - alpha) r(v_k) P[i, k] (= (1 - alpha) r(v_k) / d(v_i) unweighted).
+    Returns the estimates pi_d(V_i, V_j) of every source supernode."""
+    n = P.shape[0]
+    d = np.asarray(d, dtype=np.float64)
+    owner = _owners(n, leaf_sets)
+    size = np.array([len(F) for F in leaf_sets], dtype=np.float64)
+    Pc = sp.csr_matrix(P)
+    PT = sp.csr_matrix(P.T)
+    est = np.zeros(len(leaf_sets))
+    r = np.zeros(n)
+    Fj = np.asarray(leaf_sets[j], dtype=np.int64)
+    r[Fj] = 1.0 / len(Fj)
+    queue = [int(v) for v in Fj if r[v] > rb_max]
+    head = 0
+    while head < len(queue):
+        v = queue[head]
+        head += 1
+        rv = r[v]
+        r[v] = 0.0
+        dangling = Pc.indptr[v + 1] - Pc.indptr[v] == 1 and Pc.indices[Pc.indptr[v]] == v and d[v] == 0
+        i = owner[v]
+        if i >= 0:
+            est[i] += (d[v] * rv if dangling else alpha * d[v] * rv) / size[i]
+        share = (1 - alpha) * rv / alpha if dangling else (1 - alpha) * rv
+        for q in range(PT.indptr[v], PT.indptr[v + 1]):
+            x = PT.indices[q]
+            if dangling and x == v:
+                continue
+            before = r[x]
+            r[x] += share * PT.data[q]
+            if before <= rb_max < r[x]:
+                queue.append(int(x))
+    return est
+
+
+def tau_push(P, d, leaf_sets, alpha, eps, delta, dpr_nodes, tau=None):
+    """Algorithm 1: (eps, delta)-approximate level-l DPPR between the children
+    V_0 .. V_{k-1} of a supernode (k = len(leaf_sets)).
+      1. tau = 1 / sqrt(k n) unless given;
+      2. r_max = eps delta / (m tau)  (Eq. (rmax));
+      3. row i = gfp from V_i with r_max, for every i;
+      4. for every V_j whose DPR tau_j (mean of dpr_nodes over F(V_j)) exceeds
+         tau: column j = gbp towards V_j with
+         rb_max = eps delta / max_{i != j} mean_{v in F(V_i)} d(v)  (Eq. (brmax)).
+    Returns (estimates k x k with row = source, tau, r_max, {refined target j:
+    its rb_max})."""
+    n = P.shape[0]
+    d = np.asarray(d, dtype=np.float64)
+    k = len(leaf_sets)
+    m = d.sum()
+    if tau is None:
+        tau = 1.0 / math.sqrt(k * n)
+    r_max = eps * delta / (m * tau)
+    est = np.zeros((k, k))
+    for i in range(k):
+        est[i, :] = gfp(P, d, leaf_sets, i, alpha, r_max)
+    dpr_nodes = np.asarray(dpr_nodes, dtype=np.float64)
+    davg = np.array([d[np.asarray(F)].mean() for F in leaf_sets])
+    tau_j = np.array([dpr_nodes[np.asarray(F)].mean() for F in leaf_sets])
+    refined = {}
+    for j in range(k):
+        if tau_j[j] > tau:
+            others = [davg[i] for i in range(k) if i != j]
+            dmax = max(others) if others else davg[j]
+            rb_max = eps * delta / dmax if dmax > 0 else math.inf
+            est[:, j] = gbp(P, d, leaf_sets, j, alpha, rb_max)
+            refined[j] = rb_max
+    return est, tau, r_max, refined

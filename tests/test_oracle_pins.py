@@ -412,3 +412,156 @@ def test_directed_walk_closed_forms():
     rows = O.ppr_rows(P, np.arange(g.n), ALPHA)
     assert np.abs(rows - O.ppr_direct(P, ALPHA)).max() < 1e-13
     assert np.abs(rows.sum(axis=1) - 1).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Sec. 4: backward push, DPR (Eq. (dnpr-dnppr)), GFP / GBP / Tau-Push
+# (Algorithms 1-3) against the exact level-l DPPR of a direct solve
+# --------------------------------------------------------------------------
+def test_backward_push_example():
+    with open(os.path.join(GOLDEN, "backward_push_example.json")) as f:
+        ex = json.load(f)
+    n, a, t = ex["n"], ex["alpha"], ex["target"]
+    rp, col = _csr_from_edges(n, [tuple(e) for e in ex["edges"]], False)
+    P = O.transition_matrix(n, rp, col)
+    est, r = O.backward_push(P, t, a, ex["after_first_push"]["order"])
+    for v, val in ex["after_first_push"]["estimate"].items():
+        assert abs(est[int(v)] - val) < 1e-15
+    for v, val in ex["after_first_push"]["residue"].items():
+        assert abs(r[int(v)] - val) < 1e-15
+    assert np.count_nonzero(r) == 2 and np.count_nonzero(est) == 1
+    # the backward invariant pi(s, t) = est_s + sum_k pi(s, k) r_k holds for
+    # every s after any sequence of pushes
+    Pi = O.ppr_direct(P, a)
+    for order in ([10], [10, 5, 6], [10, 6, 5, 9, 10]):
+        est, r = O.backward_push(P, t, a, order)
+        assert np.abs(Pi[:, t] - (est + Pi @ r)).max() < 1e-15
+
+
+def _tp_graphs():
+    """Small graphs covering the unweighted, weighted and directed (with
+    dangling nodes) walks."""
+    g_u = synth.sbm([14, 12, 10, 9], 0.35, 0.04, seed=21)
+    rng = np.random.default_rng(5)
+    wedges = []
+    for u in range(g_u.n):
+        for q in range(g_u.row_ptr[u], g_u.row_ptr[u + 1]):
+            v = int(g_u.col[q])
+            if u < v:
+                wedges.append((u, v, float(np.exp(rng.normal()))))
+    rp_w, col_w, w_w = _weighted_csr_from_edges(g_u.n, wedges)
+    g_d = synth.directed_from(g_u, p_both=0.3, dangling=0.08, seed=6)
+    out = [("unweighted", g_u.n, g_u.row_ptr, g_u.col, None),
+           ("weighted", g_u.n, rp_w, col_w, w_w),
+           ("directed", g_d.n, g_d.row_ptr, g_d.col, None)]
+    return out
+
+
+def _tp_exact(n, rp, col, w, leaf_sets, alpha):
+    P = O.transition_matrix(n, rp, col, w)
+    d = O.degrees(n, rp, col, w)
+    full = d[:, None] * O.ppr_direct(P, alpha)
+    return P, d, O.level_dppr(full, leaf_sets)
+
+
+def _tp_leaf_sets(n, sizes, seed):
+    perm = np.argsort(synth.uniform(seed, 31, np.arange(n)))
+    out, at = [], 0
+    for s in sizes:
+        out.append([int(v) for v in perm[at:at + s]])
+        at += s
+    return out
+
+
+def test_dpr_closed_form_and_definition():
+    """Undirected: pi_d is symmetric, so sum_k pi_d(v_k, t) = d(t) and
+    tau_t = d(t) / m. Directed: the index precompute (PageRank from d / m)
+    equals the definition; either way sum_t tau_t = 1."""
+    for name, n, rp, col, w in _tp_graphs():
+        P = O.transition_matrix(n, rp, col, w)
+        d = O.degrees(n, rp, col, w)
+        t_def = O.dpr(P, d, ALPHA)
+        t_pow = O.dpr_power(P, d, ALPHA)
+        assert np.abs(t_def - t_pow).max() < 1e-15, name
+        assert abs(t_def.sum() - 1.0) < 1e-13, name
+        if name != "directed":
+            assert np.abs(t_def - d / d.sum()).max() < 1e-15, name
+        else:
+            assert np.abs(t_def - d / d.sum()).max() > 1e-3  # the closed form is undirected-only
+
+
+def test_gfp_meets_its_error_bound():
+    """Lemma 2 (with Lemma 4's invariant): GFP underestimates, by at most
+    r_max m tau_j for target V_j; with a tiny r_max it reaches Eq. (2)."""
+    for name, n, rp, col, w in _tp_graphs():
+        leaf_sets = _tp_leaf_sets(n, [1, 3, 5, 2, 7], seed=3)
+        P, d, exact = _tp_exact(n, rp, col, w, leaf_sets, ALPHA)
+        tau_nodes = O.dpr(P, d, ALPHA)
+        tau_j = np.array([tau_nodes[F].mean() for F in leaf_sets])
+        m = d.sum()
+        for r_max in (3e-3, 2e-4):
+            for i in range(len(leaf_sets)):
+                est = O.gfp(P, d, leaf_sets, i, ALPHA, r_max)
+                err = exact[i] - est
+                assert np.all(err >= -1e-15), (name, i, err)
+                assert np.all(err <= r_max * m * tau_j + 1e-15), (name, i, err, r_max * m * tau_j)
+        for i in range(len(leaf_sets)):
+            est = O.gfp(P, d, leaf_sets, i, ALPHA, 1e-15)
+            assert np.abs(exact[i] - est).max() < 1e-12, name
+
+
+def test_gbp_meets_its_error_bound():
+    """Lemma 3 (with its invariant): GBP towards V_j underestimates
+    pi_d(V_i, V_j) by at most rb_max times the mean leaf degree of V_i; with a
+    tiny rb_max it reaches Eq. (2)."""
+    for name, n, rp, col, w in _tp_graphs():
+        leaf_sets = _tp_leaf_sets(n, [2, 1, 4, 6, 3], seed=4)
+        P, d, exact = _tp_exact(n, rp, col, w, leaf_sets, ALPHA)
+        davg = np.array([d[F].mean() for F in leaf_sets])
+        for rb_max in (2e-2, 1e-3):
+            for j in range(len(leaf_sets)):
+                est = O.gbp(P, d, leaf_sets, j, ALPHA, rb_max)
+                err = exact[:, j] - est
+                assert np.all(err >= -1e-15), (name, j, err)
+                assert np.all(err <= rb_max * davg + 1e-15), (name, j, err, rb_max * davg)
+        for j in range(len(leaf_sets)):
+            est = O.gbp(P, d, leaf_sets, j, ALPHA, 1e-16)
+            assert np.abs(exact[:, j] - est).max() < 1e-12, name
+
+
+def test_tau_push_is_eps_delta_approximate():
+    """Theorem 3: every off-diagonal estimate meets Definition 3 (absolute
+    eps delta below delta, relative eps above), whichever targets the DPR
+    threshold sends to GBP: the paper's tau = 1 / sqrt(k n), none, all."""
+    eps, delta = 1 - 1 / math.e, 0.01
+    for name, n, rp, col, w in _tp_graphs():
+        leaf_sets = _tp_leaf_sets(n, [3, 1, 4, 2, 5, 2], seed=5)
+        k = len(leaf_sets)
+        P, d, exact = _tp_exact(n, rp, col, w, leaf_sets, ALPHA)
+        tau_nodes = O.dpr(P, d, ALPHA)
+        tau_j = np.array([tau_nodes[F].mean() for F in leaf_sets])
+        for tau, want in ((None, None), (10.0, []), (1e-12, list(range(k)))):
+            est, t, r_max, refined = O.tau_push(P, d, leaf_sets, ALPHA, eps, delta, tau_nodes, tau)
+            assert t == (1 / math.sqrt(k * n) if tau is None else tau)
+            assert abs(r_max - eps * delta / (d.sum() * t)) <= 1e-18
+            assert list(refined) == [j for j in range(k) if tau_j[j] > t]
+            if want is not None:
+                assert list(refined) == want
+            # Lemma 3's condition: rb_max is the largest threshold whose bound
+            # rb_max * (mean leaf degree of V_i) stays within eps delta for
+            # every source V_i other than the target
+            davg = np.array([d[F].mean() for F in leaf_sets])
+            for j, rb in refined.items():
+                worst = max(rb * davg[i] for i in range(k) if i != j)
+                assert abs(worst - eps * delta) <= 1e-15, (j, worst)
+            off = ~np.eye(k, dtype=bool)
+            err = np.abs(est - exact)[off]
+            ex = exact[off]
+            bound = np.where(ex < delta, eps * delta, eps * ex)
+            assert np.all(err <= bound + 1e-15), (name, tau, err.max())
+            assert np.all(est <= exact + 1e-15)
+        # tight eps delta: both phases reach Eq. (2)
+        est, *_ = O.tau_push(P, d, leaf_sets, ALPHA, 1e-7, 1e-7, tau_nodes, 1e-12)
+        assert np.abs(est - exact)[~np.eye(k, dtype=bool)].max() < 1e-13
+        est, *_ = O.tau_push(P, d, leaf_sets, ALPHA, 1e-7, 1e-7, tau_nodes, 10.0)
+        assert np.abs(est - exact).max() < 1e-10
