@@ -120,7 +120,8 @@ typedef struct pprviz_stats {
 #define PPRVIZ_K_APPLY 7         /* X = (L^w)^+ b pass */
 #define PPRVIZ_K_ENERGY 8        /* energy / gradient passes and reductions */
 #define PPRVIZ_K_OTHER 9         /* initialisation, casts, small helpers */
-#define PPRVIZ_NKCLASS 10
+#define PPRVIZ_K_PUSH 10         /* Tau-Push rounds and the DPR power iterations */
+#define PPRVIZ_NKCLASS 11
 
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
  * to run on (borrowed, not destroyed), or NULL for a stream the context owns.
@@ -269,6 +270,74 @@ int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, cons
  * Errors: E_INVALID_ARG (k, sweeps outside [1, 100000], alpha, eps), E_OOM, E_CUDA. */
 int pprviz_frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k, double alpha,
                             double eps, int32_t sweeps, int64_t *active_out, uint32_t mem_flags);
+
+/* The DPR index of Tau-Push (Sec. 4, Eq. (dnpr-dnppr) with single-node
+ * leaf sets; Sec. 4.3, indexing scheme): per node t
+ *   tau_t = (1 / m) sum_k pi_d(v_k, v_t),
+ * computed as the paper's global PageRank whose start vector has entry
+ * d(v_k) / m at v_k: FP64 power iterations
+ *   x_0 = alpha s,  x_{t+1} = alpha s + (1 - alpha) x_t P,  s = d / m,
+ * until the walk mass not yet ended, (1 - alpha)^(T + 1), is at most eps.
+ * (An undirected graph has tau_t = d(t) / m exactly.)
+ * dpr_out:  n doubles (host or device per PPRVIZ_DEVICE_PTRS).
+ * cert_out: host double, (1 - alpha)^(T + 1), the L1 bound on the error of
+ *           dpr_out before rounding; may be NULL.
+ * Errors: E_INVALID_ARG (dpr_out NULL, alpha outside (0, 1), eps outside
+ * (0, 1), a graph without edges), E_OOM, E_CUDA. */
+int pprviz_dpr(pprviz_ctx *ctx, const pprviz_graph *g, double alpha, double eps, double *dpr_out, double *cert_out,
+               uint32_t mem_flags);
+
+/* What one pprviz_tau_push call did (host struct). */
+typedef struct pprviz_tau_info {
+    double tau;               /* DPR threshold used */
+    double r_max;             /* forward residue threshold, Eq. (rmax) */
+    int32_t backward_targets; /* supernodes V_j with tau_j > tau (refined by GBP) */
+    int32_t fwd_rounds;       /* synchronous push rounds of the forward phase */
+    int32_t bwd_rounds;       /* and of the backward phase */
+    int32_t pad0;
+    int64_t fwd_pushes;       /* (node, source supernode) pushes, forward */
+    int64_t bwd_pushes;       /* (node, target supernode) pushes, backward */
+    int64_t fwd_edges;        /* residue shares sent along edges, forward */
+    int64_t bwd_edges;        /* and backward */
+} pprviz_tau_info;
+
+/* Tau-Push (Sec. 4, Algorithm 1 with GFP, Algorithm 2, and GBP, Algorithm 3):
+ * (eps, delta)-approximate level-l DPPR (Definition 3) between the nsup
+ * children V_0 .. V_{nsup-1} of a supernode, leaf sets as in
+ * pprviz_level_dppr (leaf_ptr / leaf_idx, disjoint, non-empty).
+ *   tau    = the DPR threshold; tau <= 0 selects the paper's 1 / sqrt(nsup n);
+ *   r_max  = eps delta / (m tau)  (Eq. (rmax));
+ *   row i  = GFP from V_i: initial residue d(v) / |F(V_i)| on its leaves,
+ *            pushes while some residue exceeds d(v) r_max, the reserve kept at
+ *            the leaves of the children only;
+ *   col j  = for every V_j with tau_j = mean over F(V_j) of dpr > tau: GBP
+ *            towards V_j (initial residue 1 / |F(V_j)| on its leaves, pushes
+ *            along in-edges while a residue exceeds
+ *            rb_max = eps delta / max_{i != j} mean_{F(V_i)} d  (Eq. (brmax))),
+ *            replacing the GFP estimates of that column.
+ * The pushes run as synchronous rounds: every residue above its threshold is
+ * pushed at once and shares arrive by FP64 atomic adds, so the order of the
+ * pushes (which the paper leaves open) differs from a sequential push; the
+ * stopping rule, and with it the error bounds of Lemmas 2 and 3 and
+ * Theorem 3, are those of Algorithms 2 and 3. Every estimate is at most the
+ * exact value; forward columns miss by at most r_max m tau_j, refined columns
+ * by at most rb_max times the source's mean leaf degree. A node without
+ * out-edges keeps the walk: its push takes the sum of its endless repeats.
+ * dpr:       n doubles, the DPR index (pprviz_dpr), host or device.
+ * ldppr_out: nsup*nsup estimates, row i = source V_i; may be NULL.
+ * pdist_out: nsup*nsup, Eq. (1) on the estimates (Algorithm 1, conversion
+ *            step; upper clamp 2 ln n_clamp, n_clamp = 0 means n); may be NULL.
+ * info:      host struct; may be NULL.
+ * Float outputs unless PPRVIZ_OUT_FP64; leaf arrays, dpr and outputs host or
+ * device per PPRVIZ_DEVICE_PTRS.
+ * Errors: E_INVALID_ARG (leaf sets as in pprviz_level_dppr, nsup * n at or
+ * above 2^31, dpr NULL or with a negative or non-finite entry, alpha outside
+ * (0, 1), eps or delta not finite and > 0, tau not finite, n_clamp < 2),
+ * E_NOT_CONVERGED (a phase still had residues above its threshold after
+ * 65,535 rounds), E_OOM, E_CUDA. */
+int pprviz_tau_push(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
+                    const int32_t *leaf_idx, const double *dpr, double alpha, double eps, double delta, double tau,
+                    void *ldppr_out, void *pdist_out, int64_t n_clamp, pprviz_tau_info *info, uint32_t mem_flags);
 
 /* P3 alone - PDist from a k*k DPPR matrix (Sec. 3.1, Eq. (1)):
  * Delta[i][j] = min(max(1 - ln(D[i][j] + D[j][i]), 2), 2 ln n_clamp), zero

@@ -41,7 +41,7 @@ __all__ = [
     "pdist_from_z", "pdist_from_dppr", "stress", "stress_grad", "stress_grad_pdist",
     "lw_matrix", "ly_matrix", "smacof_step", "smacof", "forward_push",
     "residual_certificate", "power_sweeps_needed", "level_dppr", "node_distribution", "ulcv",
-    "backward_push", "dpr", "dpr_power", "gfp", "gbp", "tau_push",
+    "backward_push", "dpr", "dpr_power", "gfp", "gbp", "tau_push", "level_dppr_rows_power",
 ]
 
 
@@ -304,6 +304,29 @@ def level_dppr(dppr_full, leaf_sets):
     for i, Fi in enumerate(leaf_sets):
         for j, Fj in enumerate(leaf_sets):
             out[i, j] = dppr_full[np.ix_(Fi, Fj)].sum() / (len(Fi) * len(Fj))
+    return out
+
+
+def level_dppr_rows_power(P, d, leaf_sets, sources, alpha, tol=1e-15):
+    """Rows `sources` of Eq. (2) without the dense matrix. By linearity
+    sum_{s in F(V_i)} d(s) pi(s, .) / |F(V_i)| is the power iteration from the
+    group start b = d(s) / |F(V_i)| on F(V_i) (the initial residues of
+    Algorithm 2): y_0 = alpha b, y_{t+1} = alpha b + (1 - alpha) y_t P, stopped
+    once the unended walk mass is at most `tol` times the start's; entry j of
+    row i is the mean of y over F(V_j). Returns (len(sources), k)."""
+    n = P.shape[0]
+    d = np.asarray(d, dtype=np.float64)
+    PT = sp.csr_matrix(P.T)
+    Bm = np.zeros((n, len(sources)))
+    for c, i in enumerate(sources):
+        Fi = np.asarray(leaf_sets[i], dtype=np.int64)
+        Bm[Fi, c] = d[Fi] / len(Fi)
+    Y = alpha * Bm
+    for _ in range(power_sweeps_needed(alpha, tol)):
+        Y = alpha * Bm + (1 - alpha) * (PT @ Y)
+    out = np.zeros((len(sources), len(leaf_sets)))
+    for j, Fj in enumerate(leaf_sets):
+        out[:, j] = Y[np.asarray(Fj, dtype=np.int64), :].mean(axis=0)
     return out
 
 

@@ -177,6 +177,50 @@ class Context:
                                  PPRVIZ_OUT_FP64 if out64 else 0)
         return D, Pd, cert, st
 
+    def dpr(self, graph: Graph, alpha=0.15, eps=1e-12, out=None):
+        """DPR index of every node (Sec. 4, Eq. (dnpr-dnppr); Sec. 4.3): the
+        PageRank from d / m. `out`: a float64 device tensor to fill, else a
+        numpy array is returned. Returns (dpr, L1 error bound)."""
+        dev = out is not None and B._mem_flags(out) == PPRVIZ_DEVICE_PTRS
+        if out is None:
+            out = np.empty(graph.n, dtype=np.float64)
+        self._enter(dev)
+        cert = B.pprviz_dpr(self.h, graph.h, alpha, eps, out, PPRVIZ_DEVICE_PTRS if dev else 0)
+        self._leave(dev, out)
+        return out, cert
+
+    @staticmethod
+    def leaf_csr(leaf_sets):
+        """(leaf_ptr int64, leaf_idx int32) of a list of leaf-id arrays."""
+        sizes = np.array([len(s) for s in leaf_sets], dtype=np.int64)
+        leaf_ptr = np.zeros(len(leaf_sets) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=leaf_ptr[1:])
+        leaf_idx = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32) for s in leaf_sets]))
+        return leaf_ptr, leaf_idx
+
+    def tau_push(self, graph: Graph, leaf_ptr, leaf_idx, dpr, alpha=0.15, eps=1 - 1 / np.e, delta=None, tau=0.0,
+                 n_clamp=0, out64=True, ldppr_out=None, pdist_out=None, want_pdist=True):
+        """Tau-Push (Sec. 4, Algorithms 1-3): (eps, delta)-approximate level-l
+        DPPR between the children given by a leaf CSR, and its PDist.
+        delta defaults to the paper's 1 / (10 k); tau <= 0 to 1 / sqrt(k n).
+        Host (numpy) or device (torch) arrays, all of one kind; device calls
+        write into ldppr_out / pdist_out. Returns (DPPR, PDist or None, info)."""
+        k = len(leaf_ptr) - 1
+        if delta is None:
+            delta = 1.0 / (10 * k)
+        dev = B._mem_flags(leaf_ptr, leaf_idx, dpr, ldppr_out, pdist_out) == PPRVIZ_DEVICE_PTRS
+        dt = np.float64 if out64 else np.float32
+        if not dev:
+            ldppr_out = np.empty((k, k), dtype=dt) if ldppr_out is None else ldppr_out
+            if want_pdist and pdist_out is None:
+                pdist_out = np.empty((k, k), dtype=dt)
+        mf = (PPRVIZ_DEVICE_PTRS if dev else 0) | (PPRVIZ_OUT_FP64 if out64 else 0)
+        self._enter(dev)
+        info = B.pprviz_tau_push(self.h, graph.h, k, leaf_ptr, leaf_idx, dpr, alpha, eps, delta, tau, ldppr_out,
+                                 pdist_out if want_pdist else None, n_clamp, mf)
+        self._leave(dev, ldppr_out, pdist_out)
+        return ldppr_out, (pdist_out if want_pdist else None), info
+
     def frontier_profile(self, graph: Graph, view, sweeps, alpha=0.15, eps=1e-6):
         """Per power-iteration sweep, the (node, source) entries whose push
         residue is above GFP's threshold d(v) eps / max d (Algorithm 2)."""

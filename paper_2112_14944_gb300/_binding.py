@@ -32,7 +32,8 @@ PPRVIZ_FP32 = 1
 PPRVIZ_FP32_CSR = 2
 PPRVIZ_FP32_TC = 3
 PPRVIZ_FP32_BF16TC = 4
-KERNEL_CLASSES = ["graph", "sweep", "residual", "extract", "pdist", "factor", "ly", "apply", "energy", "other"]
+KERNEL_CLASSES = ["graph", "sweep", "residual", "extract", "pdist", "factor", "ly", "apply", "energy", "other",
+                  "push"]
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID_ARG", 2: "E_BAD_GRAPH", 3: "E_OOM", 4: "E_CUDA",
                 5: "E_NOT_CONVERGED", 6: "E_TIMEOUT"}
@@ -66,6 +67,9 @@ _SIGS = {
                                      _VP, _VP, C.c_uint32]),
     "pprviz_energy_noalloc": (C.c_int, [_VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, _VP]),
     "pprviz_layout_metrics": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, _VP, _VP, C.c_uint32]),
+    "pprviz_dpr": (C.c_int, [_VP, _VP, C.c_double, C.c_double, _VP, _VP, C.c_uint32]),
+    "pprviz_tau_push": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  _VP, _VP, C.c_int64, _VP, C.c_uint32]),
 }
 
 
@@ -75,6 +79,13 @@ class pprviz_stats(C.Structure):
                 ("max_cert", C.c_double), ("layout_iters", C.c_int32), ("source_group", C.c_int32),
                 ("bytes_sweep", C.c_double), ("bytes_ly", C.c_double), ("bytes_apply", C.c_double),
                 ("flops_factor", C.c_double), ("flops_dense", C.c_double), ("graph_launched", C.c_int32)]
+
+
+class pprviz_tau_info(C.Structure):
+    _fields_ = [("tau", C.c_double), ("r_max", C.c_double), ("backward_targets", C.c_int32),
+                ("fwd_rounds", C.c_int32), ("bwd_rounds", C.c_int32), ("pad0", C.c_int32),
+                ("fwd_pushes", C.c_int64), ("bwd_pushes", C.c_int64), ("fwd_edges", C.c_int64),
+                ("bwd_edges", C.c_int64)]
 
 
 _lib = None
@@ -224,6 +235,23 @@ def pprviz_level_dppr(ctx, g, nsup, leaf_ptr, leaf_idx, alpha, eps, ldppr_out, p
     return _check(ctx, load().pprviz_level_dppr(ctx, g, int(nsup), _ptr(leaf_ptr)[0], _ptr(leaf_idx)[0], float(alpha),
                                                 float(eps), _ptr(ldppr_out)[0], _ptr(pdist_out)[0], int(n_clamp),
                                                 _ptr(cert_out)[0], mem_flags), allow=(PPRVIZ_E_NOT_CONVERGED,))
+
+
+def pprviz_dpr(ctx, g, alpha, eps, dpr_out, mem_flags):
+    """Returns the certificate (1 - alpha)^(T + 1)."""
+    cert = C.c_double()
+    _check(ctx, load().pprviz_dpr(ctx, g, float(alpha), float(eps), _ptr(dpr_out)[0], C.byref(cert), mem_flags))
+    return cert.value
+
+
+def pprviz_tau_push(ctx, g, nsup, leaf_ptr, leaf_idx, dpr, alpha, eps, delta, tau, ldppr_out, pdist_out, n_clamp,
+                    mem_flags):
+    """Returns the call's pprviz_tau_info as a dict."""
+    info = pprviz_tau_info()
+    _check(ctx, load().pprviz_tau_push(ctx, g, int(nsup), _ptr(leaf_ptr)[0], _ptr(leaf_idx)[0], _ptr(dpr)[0],
+                                       float(alpha), float(eps), float(delta), float(tau), _ptr(ldppr_out)[0],
+                                       _ptr(pdist_out)[0], int(n_clamp), C.byref(info), mem_flags))
+    return {name: getattr(info, name) for name, _ in info._fields_ if name != "pad0"}
 
 
 def pprviz_frontier_profile(ctx, g, view, k, alpha, eps, sweeps, active_out, mem_flags):

@@ -59,7 +59,8 @@ static cudaEvent_t ev_get(pprviz_ctx *ctx) {
 ProfScope::ProfScope(pprviz_ctx *ctx, int k) : c(ctx), cls(k) {
   const int64_t nth = c->class_launches[cls]++;
   // the classes launched hundreds of times per call are sampled: one launch in prof_every
-  const bool hot = cls == PPRVIZ_K_SWEEP || cls == PPRVIZ_K_LY || cls == PPRVIZ_K_APPLY || cls == PPRVIZ_K_OTHER;
+  const bool hot = cls == PPRVIZ_K_SWEEP || cls == PPRVIZ_K_LY || cls == PPRVIZ_K_APPLY || cls == PPRVIZ_K_OTHER ||
+                   cls == PPRVIZ_K_PUSH;
   // launches recorded into a CUDA graph are counted, never timed: an event
   // recorded during stream capture marks no point on the device timeline
   if (c->profiling && !c->capturing && (!hot || nth % c->prof_every == 0)) {
@@ -432,21 +433,12 @@ int pprviz_dppr(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int
   return finish(ctx, status);
 }
 
-int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
-                      const int32_t *leaf_idx, double alpha, double eps, void *ldppr_out, void *pdist_out,
-                      int64_t n_clamp, double *cert_out, uint32_t mem_flags) {
-  if (!ctx) return PPRVIZ_E_INVALID_ARG;
-  PPRVIZ_TRY(begin(ctx));
-  if (!g || !leaf_ptr || !leaf_idx) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or leaf sets are NULL");
-  if (nsup < 1 || (int64_t)nsup > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup must be in [1, n]");
-  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
-  if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
-  if (n_clamp == 0) n_clamp = g->n;
-  if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
-  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
-  const bool out64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
-  // the leaf sets on the host (validated there) and on the device
-  std::vector<int64_t> lp((size_t)nsup + 1);
+// Reads and checks a leaf-set CSR (host or device): lp / li get host copies,
+// lp_d / li_d device pointers (the caller's, or staged copies).
+static int leaf_sets_in(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
+                        const int32_t *leaf_idx, bool dev, std::vector<int64_t> &lp, std::vector<int32_t> &li,
+                        const int64_t **lp_d, const int32_t **li_d) {
+  lp.assign((size_t)nsup + 1, 0);
   if (dev) {
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(lp.data(), leaf_ptr, sizeof(int64_t) * lp.size(), cudaMemcpyDeviceToHost,
                                      ctx->stream));
@@ -459,7 +451,7 @@ int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, cons
     if (lp[v + 1] <= lp[v]) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "every supernode needs at least one leaf");
   const int64_t nleaf = lp[nsup];
   if (nleaf > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "more leaves than nodes: leaf sets must be disjoint");
-  std::vector<int32_t> li((size_t)nleaf);
+  li.assign((size_t)nleaf, 0);
   if (dev) {
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(li.data(), leaf_idx, sizeof(int32_t) * li.size(), cudaMemcpyDeviceToHost,
                                      ctx->stream));
@@ -473,15 +465,36 @@ int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, cons
     if (seen[t]) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "leaf sets must be disjoint (a node is listed twice)");
     seen[t] = 1;
   }
-  const int64_t *lp_d = leaf_ptr;
-  const int32_t *li_d = leaf_idx;
+  *lp_d = leaf_ptr;
+  *li_d = leaf_idx;
   if (!dev) {
     const void *p = nullptr;
     PPRVIZ_TRY(stage_in(ctx, lp.data(), sizeof(int64_t) * lp.size(), false, WS_IN0, &p));
-    lp_d = (const int64_t *)p;
+    *lp_d = (const int64_t *)p;
     PPRVIZ_TRY(stage_in(ctx, li.data(), sizeof(int32_t) * li.size(), false, WS_IN1, &p));
-    li_d = (const int32_t *)p;
+    *li_d = (const int32_t *)p;
   }
+  return PPRVIZ_OK;
+}
+
+int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
+                      const int32_t *leaf_idx, double alpha, double eps, void *ldppr_out, void *pdist_out,
+                      int64_t n_clamp, double *cert_out, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!g || !leaf_ptr || !leaf_idx) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or leaf sets are NULL");
+  if (nsup < 1 || (int64_t)nsup > g->n) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup must be in [1, n]");
+  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
+  if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
+  if (n_clamp == 0) n_clamp = g->n;
+  if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool out64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  std::vector<int64_t> lp;
+  std::vector<int32_t> li;
+  const int64_t *lp_d = nullptr;
+  const int32_t *li_d = nullptr;
+  PPRVIZ_TRY(leaf_sets_in(ctx, g, nsup, leaf_ptr, leaf_idx, dev, lp, li, &lp_d, &li_d));
   const size_t kk = (size_t)nsup * (size_t)nsup;
   const size_t ob = (out64 ? sizeof(double) : sizeof(float)) * kk;
   void *ld_d = nullptr;
@@ -506,6 +519,94 @@ int pprviz_level_dppr(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, cons
   if (!dev || cert_out) PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (status != PPRVIZ_OK) ctx->err = keep_err;
   return finish(ctx, status);
+}
+
+int pprviz_dpr(pprviz_ctx *ctx, const pprviz_graph *g, double alpha, double eps, double *dpr_out, double *cert_out,
+               uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (!g || !dpr_out) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or output is NULL");
+  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
+  if (!(eps > 0.0 && eps < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be in (0, 1)");
+  if (!(g->m > 0.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "the DPR needs a graph with edges (m > 0)");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  double *out_d = dpr_out;
+  if (!dev) {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_OUT0, sizeof(double) * (size_t)g->n));
+    out_d = ctx->ws[WS_OUT0].as<double>();
+  }
+  PPRVIZ_TRY(dpr_solve(ctx, g, alpha, eps, out_d, cert_out));
+  if (!dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(dpr_out, out_d, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return finish(ctx, PPRVIZ_OK);
+}
+
+int pprviz_tau_push(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
+                    const int32_t *leaf_idx, const double *dpr, double alpha, double eps, double delta, double tau,
+                    void *ldppr_out, void *pdist_out, int64_t n_clamp, pprviz_tau_info *info, uint32_t mem_flags) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (info) memset(info, 0, sizeof(*info));
+  if (!g || !leaf_ptr || !leaf_idx) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or leaf sets are NULL");
+  if (!dpr) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "the DPR index is NULL");
+  if (nsup < 1 || (int64_t)nsup > g->n || nsup > 65535)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup must be in [1, min(n, 65535)]");
+  if ((int64_t)nsup * g->n >= ((int64_t)1 << 31))
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup * n must stay below 2^31 (the residue entries are int32-indexed)");
+  if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
+  if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
+  if (!(delta > 0.0) || !isfinite(delta)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "delta must be finite and > 0");
+  if (!isfinite(tau)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "tau must be finite (<= 0 selects 1 / sqrt(k n))");
+  if (n_clamp == 0) n_clamp = g->n;
+  if (n_clamp < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "n_clamp must be >= 2");
+  const bool dev = (mem_flags & PPRVIZ_DEVICE_PTRS) != 0;
+  const bool out64 = (mem_flags & PPRVIZ_OUT_FP64) != 0;
+  std::vector<int64_t> lp;
+  std::vector<int32_t> li;
+  const int64_t *lp_d = nullptr;
+  const int32_t *li_d = nullptr;
+  PPRVIZ_TRY(leaf_sets_in(ctx, g, nsup, leaf_ptr, leaf_idx, dev, lp, li, &lp_d, &li_d));
+  // the DPR index: checked on the host (a negative or non-finite entry is an error)
+  std::vector<double> dh((size_t)g->n);
+  if (dev) {
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(dh.data(), dpr, sizeof(double) * dh.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    memcpy(dh.data(), dpr, sizeof(double) * dh.size());
+  }
+  for (double x : dh)
+    if (!(x >= 0.0) || !isfinite(x)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "DPR entries must be finite and >= 0");
+  const double *dpr_d = dpr;
+  if (!dev) {
+    const void *p = nullptr;
+    PPRVIZ_TRY(stage_in(ctx, dh.data(), sizeof(double) * dh.size(), false, WS_OUT1, &p));
+    dpr_d = (const double *)p;
+  }
+  const size_t kk = (size_t)nsup * (size_t)nsup;
+  const size_t ob = (out64 ? sizeof(double) : sizeof(float)) * kk;
+  void *ld_d = nullptr;
+  if (ldppr_out && dev) ld_d = ldppr_out;
+  else {
+    PPRVIZ_TRY(ws_ensure(ctx, WS_DPPR, ob));
+    ld_d = ctx->ws[WS_DPPR].p;
+  }
+  const int status = tau_push_solve(ctx, g, nsup, lp_d, li_d, lp, dpr_d, alpha, eps, delta, tau, ld_d, out64, info);
+  if (status != PPRVIZ_OK) return finish(ctx, status);
+  if (pdist_out) {
+    void *pd_d = dev ? pdist_out : nullptr;
+    if (!pd_d) {
+      PPRVIZ_TRY(ws_ensure(ctx, WS_PDIST, ob));
+      pd_d = ctx->ws[WS_PDIST].p;
+    }
+    PPRVIZ_TRY(pdist_launch(ctx, ld_d, nsup, n_clamp, pd_d, out64));
+    if (!dev) PPRVIZ_CUDA(ctx, cudaMemcpyAsync(pdist_out, pd_d, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (ldppr_out && !dev) PPRVIZ_CUDA(ctx, cudaMemcpyAsync(ldppr_out, ld_d, ob, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dev) PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return finish(ctx, PPRVIZ_OK);
 }
 
 int pprviz_frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view, int32_t k, double alpha,

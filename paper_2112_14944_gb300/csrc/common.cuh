@@ -54,6 +54,9 @@ enum Slot {
   WS_SPART, WS_SCNT,
   // batched views: the waves' split work items and split rows
   WS_UITEMS, WS_USROW,
+  // Tau-Push: residues, reserves, frontier queues, push items, per-round
+  // counters, leaf maps and small per-supernode tables
+  WS_TPR, WS_TPQ, WS_TPFA, WS_TPFB, WS_TPVAL, WS_TPITEM, WS_TPCNT, WS_TPMAP, WS_TPTAB,
   WS_COUNT
 };
 
@@ -206,6 +209,16 @@ int level_dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const
 int frontier_profile(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
                      const std::vector<int32_t> &view_h, int32_t k, double alpha, double eps, int32_t sweeps,
                      int64_t *active_h);
+
+// ---- Tau-Push and its DPR index (taupush.cu) -------------------------------
+// DPR of every node into dpr_d (device, n doubles); cert_h: (1 - alpha)^(T+1).
+int dpr_solve(pprviz_ctx *ctx, const pprviz_graph *g, double alpha, double eps, double *dpr_d, double *cert_h);
+// Tau-Push estimates (nsup x nsup, row = source) into out_d (double if out64);
+// leaf sets on the device and the host (validated); dpr_d: device, n doubles.
+int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr_d,
+                   const int32_t *leaf_idx_d, const std::vector<int64_t> &leaf_ptr_h, const double *dpr_d,
+                   double alpha, double eps, double delta, double tau, void *out_d, bool out64,
+                   pprviz_tau_info *info);
 
 // ---- graph analysis for the deflated sweeps (spectral.cu) ------------------
 // Fills g->comp / h_comp / h_mc / spec_b / spec_deflate once per graph.

@@ -26,7 +26,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 __all__ = [
     "mix64", "uniform", "chung_lu_weights", "chung_lu", "sbm", "dense_clustered",
-    "uniform_x0", "sample_view", "sbm_views", "Graph", "directed_from",
+    "uniform_x0", "sample_view", "sbm_views", "Graph", "directed_from", "random_leaf_sets",
 ]
 
 
@@ -282,3 +282,15 @@ def directed_from(g: Graph, p_both: float = 0.3, dangling: float = 0.02, seed: i
     row_ptr = np.zeros(g.n + 1, dtype=np.int64)
     np.cumsum(np.bincount(s2, minlength=g.n), out=row_ptr[1:])
     return Graph(g.n, row_ptr, d2.astype(np.int32), None if w2 is None else w2[order], directed=True)
+
+
+def random_leaf_sets(n: int, sizes, seed: int = 0, tag: int = 12):
+    """Disjoint leaf sets of the given sizes drawn uniformly from 0..n-1 (the
+    children of a randomly chosen supernode, the case the paper's expected
+    Tau-Push cost is stated for). Returns (leaf_ptr int64, leaf_idx int32)."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    total = int(sizes.sum())
+    ids = sample_view(n, total, seed=seed, tag=tag)
+    leaf_ptr = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=leaf_ptr[1:])
+    return leaf_ptr, np.ascontiguousarray(ids.astype(np.int32))

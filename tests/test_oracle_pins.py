@@ -565,3 +565,13 @@ def test_tau_push_is_eps_delta_approximate():
         assert np.abs(est - exact)[~np.eye(k, dtype=bool)].max() < 1e-13
         est, *_ = O.tau_push(P, d, leaf_sets, ALPHA, 1e-7, 1e-7, tau_nodes, 10.0)
         assert np.abs(est - exact).max() < 1e-10
+
+
+def test_level_dppr_rows_power_matches_the_definition():
+    """The group-start power iteration gives the rows of Eq. (2) as the
+    leaf-set average of the dense DPPR matrix does."""
+    for name, n, rp, col, w in _tp_graphs():
+        leaf_sets = _tp_leaf_sets(n, [4, 1, 6, 3], seed=7)
+        P, d, exact = _tp_exact(n, rp, col, w, leaf_sets, ALPHA)
+        rows = O.level_dppr_rows_power(P, d, leaf_sets, [0, 2, 3], ALPHA)
+        assert np.abs(rows - exact[[0, 2, 3]]).max() < 1e-13, name
