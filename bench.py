@@ -22,7 +22,9 @@ per step (DPPR + PDist + 200 layout updates of every view).
 `--workload view2m`: the 8,192-node view of a 2M-node Chung-Lu graph (DPPR /
 PDist among the view, then the stress energy and its backward through the
 autograd function). `--workload small`: the n = 1,000 FP64 plain-method
-workload (DPPR + PDist + 300 FP64 layout updates). Neither is the default line.
+workload (DPPR + PDist + 300 FP64 layout updates). `--workload taupush`: Tau-Push
+queries (Sec. 4) on the 2M-node Chung-Lu graph, 8 level-1 supernodes of 25
+children x 25 leaves per step. None of these is the default line.
 
 `--workload dense` measures the dense-view propagation instead (not the
 default line): a dense clustered weighted view, n = 20,000, 20 blocks, 15 %
@@ -115,9 +117,9 @@ def parse():
                     help="one untimed pass of the hot path (for profiler command lines)")
     ap.add_argument("--dense-precision", default="bf16", choices=["bf16", "tf32x3"],
                     help="tensor-core sweep operands of --workload dense (the other mode is timed beside it)")
-    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small"],
+    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small", "taupush"],
                     help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000); "
-                         "views: the 256 batched SBM views")
+                         "views: the 256 batched SBM views; taupush: Tau-Push queries on the 2M-node graph")
     return ap.parse_args()
 
 
@@ -642,6 +644,170 @@ def run_views(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- Tau-Push queries
+TAUPUSH_WORKLOAD = "chung_lu_n2000000_deg10_taupush_level1_k25x25"
+TP_QUERIES = 8
+
+
+def run_taupush(args, rank, world, local_rank):
+    """Tau-Push queries (Sec. 4, Algorithm 1) on the Chung-Lu graph of
+    n = 2,000,000 nodes (mean degree 10, exponent 2.5, seed 0). A query is a
+    level-1 supernode of k = 25 children of 25 leaves each, drawn uniformly
+    (the randomly chosen supernode of the paper's expected-cost analysis),
+    with the paper's eps = 1 - 1/e, delta = 1 / (10 k) and tau = 1 / sqrt(k n).
+    One step = 8 queries (seeds 1000..1007); leaf sets, the DPR index and the
+    outputs are resident on the device. The DPR index is built once, before
+    the timed region, and timed on its own."""
+    import math
+
+    import torch
+
+    import oracle as O
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = synth.chung_lu(2_000_000, 10, 2.5, seed=0)
+    k, per = 25, 25
+    eps_p, delta = 1 - 1 / math.e, 1.0 / (10 * k)
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    G = ctx.upload_graph(g)
+    dpr = torch.empty(g.n, dtype=torch.float64, device=dev)
+    ctx.dpr(G, ALPHA, 1e-12, out=dpr)  # warm-up of the index build
+    torch.cuda.synchronize()
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    _, dpr_cert = ctx.dpr(G, ALPHA, 1e-12, out=dpr)
+    i1.record(stream)
+    i1.synchronize()
+    index_ms = i0.elapsed_time(i1)
+    qs = [synth.random_leaf_sets(g.n, [per] * k, seed=1000 + q) for q in range(TP_QUERIES)]
+    qd = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in qs]
+    outs = [(torch.empty((k, k), dtype=torch.float64, device=dev),
+             torch.empty((k, k), dtype=torch.float64, device=dev)) for _ in qs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        infos, launches = [], 0
+        for (pd, idd), (o, po) in zip(qd, outs):
+            _, _, info = ctx.tau_push(G, pd, idd, dpr, ALPHA, eps_p, delta, 0.0, ldppr_out=o, pdist_out=po)
+            infos.append(info)
+            launches += ctx.stats()["kernel_launches"]
+        return infos, launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier_if_group()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, launches, infos = [], 0, None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos, nl = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        launches += nl
+    torch.cuda.synchronize()
+    sampler.stop()
+    total = max_over_ranks(sum(ms), dev)
+    # kernel shares: one more step with kernel timing on (every launch timed)
+    ctx.profile(1)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    step()
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    # end to end through the public API with host buffers: each query copies
+    # its leaf arrays and the DPR index in and its DPPR and PDist out
+    dpr_h = dpr.cpu().numpy()
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in qs:
+            ctx.tau_push(G, a, b, dpr_h, ALPHA, eps_p, delta, 0.0)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d = sum(a.nbytes + b.nbytes for a, b in qs) + TP_QUERIES * dpr_h.nbytes
+    d2h = TP_QUERIES * 2 * k * k * 8
+    if rank != 0:
+        return
+    hbm, _, peak_kind = peaks()
+    units = sum(i["fwd_edges"] + i["bwd_edges"] for i in infos)
+    takes = sum(i["fwd_pushes"] + i["bwd_pushes"] for i in infos)
+    push_ms, push_n, _ = ktimes["push"]
+    # algorithmic bytes: per unit (an edge times a taken residue) the column
+    # index (4 B) and the residue's read-modify-write (8 + 8 B); per taken
+    # residue its read and zeroing (8 + 8 B) and its (slot, share) pair (16 B)
+    alg = 20.0 * units + 32.0 * takes
+    ach = alg / (push_ms / 1e3) / 1e9 if push_ms else None
+    roof = {"kernel": "Tau-Push rounds (k_tp_push + k_tp_collect_front), FP64 atomic reductions at random nodes",
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+            "launches": push_n, "alg_bytes_per_step": alg, "alg_bytes_note": "20 B per unit + 32 B per taken residue",
+            "device_ms_per_step": push_ms, "traffic": None,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle's GFP (Algorithm 2, sequential pushes) from the first child
+        # of the first query, scaled to a whole query (k children)
+        Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
+        d = O.degrees(g.n, g.row_ptr, g.col)
+        a, b = qs[0]
+        leaf_sets = [b[a[i]:a[i + 1]].astype(np.int64) for i in range(k)]
+        r_max = eps_p * delta / (d.sum() * (1 / math.sqrt(k * g.n)))
+        t0 = time.perf_counter()
+        O.gfp(Pm, d, leaf_sets, 0, ALPHA, r_max)
+        t_src = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (t_src * k), "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"GFP (sequential pushes, pure Python) from 1 of the 25 children of query 0 "
+                         f"({t_src:.1f} s), times 25 for a query; the backward phase refines no target here"}
+    # error of query 0's first row against the oracle's group-start power
+    # iteration (exact to 1e-9 of the walk mass), with Lemma 2's bound
+    a, b = qs[0]
+    leaf_sets = [b[a[i]:a[i + 1]].astype(np.int64) for i in range(k)]
+    Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    exact = O.level_dppr_rows_power(Pm, d, leaf_sets, [0], ALPHA, tol=1e-9)[0]
+    est = outs[0][0][0].cpu().numpy()
+    tau_j = np.array([d[F].mean() for F in leaf_sets]) / d.sum()
+    bound = infos[0]["r_max"] * d.sum() * tau_j
+    err = exact - est
+    errors = {"row": 0, "max_underestimate": float(err.max()), "min_underestimate": float(err.min()),
+              "lemma2_bound_max": float(bound.max()), "within_bound": bool(np.all(err <= bound + 1e-9)),
+              "oracle_tol": 1e-9}
+    q_per_step = float(TP_QUERIES)
+    e2e_rate = TP_QUERIES / (statistics.mean(e2e_ms) / 1e3)
+    line = {
+        "metric": "Tau-Push queries/s, level-1 supernode (25 children x 25 leaves), 2M-node power-law graph",
+        "value": whole_job_rate(q_per_step, args.steps, world, total), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "ms_per_query": total / args.steps / TP_QUERIES, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": TAUPUSH_WORKLOAD, "graph": "chung-lu", "n": g.n, "nnz": int(g.nnz),
+                   "mean_degree": 10, "exponent": 2.5, "seed": 0, "queries_per_step": TP_QUERIES,
+                   "query": "k = 25 children x 25 leaves, uniform without replacement (seeds 1000..1007)",
+                   "alpha": ALPHA, "eps": eps_p, "delta": delta, "tau": 1 / math.sqrt(k * g.n),
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "index": {"dpr_ms": index_ms, "dpr_l1_bound": dpr_cert},
+        "per_query": {"rounds": statistics.mean(i["fwd_rounds"] + i["bwd_rounds"] for i in infos),
+                      "taken_residues": takes / TP_QUERIES, "units": units / TP_QUERIES,
+                      "backward_targets": statistics.mean(i["backward_targets"] for i in infos)},
+        "roofline": roof, "errors": errors,
+        "kernel_share": class_share(ktimes, 1),
+        "kernel_share_from": "one extra step after the timed region, every launch timed",
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_rate, "unit": "queries/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+        "cpu_baseline": cpu, "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- view of a 2M-node graph
 VIEW2M_WORKLOAD = "chung_lu_n2000000_deg10_view8192"
 
@@ -1081,6 +1247,8 @@ def main():
         run_dense(args, rank, world, local_rank)
     elif args.workload == "views":
         run_views(args, rank, world, local_rank)
+    elif args.workload == "taupush":
+        run_taupush(args, rank, world, local_rank)
     elif args.workload == "view2m":
         run_view2m(args, rank, world, local_rank)
     elif args.workload == "small":

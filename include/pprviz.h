@@ -331,7 +331,7 @@ typedef struct pprviz_tau_info {
  * Float outputs unless PPRVIZ_OUT_FP64; leaf arrays, dpr and outputs host or
  * device per PPRVIZ_DEVICE_PTRS.
  * Errors: E_INVALID_ARG (leaf sets as in pprviz_level_dppr, nsup * n at or
- * above 2^31, dpr NULL or with a negative or non-finite entry, alpha outside
+ * above 2^31, a graph of 2^31 or more stored edges, dpr NULL or with a negative or non-finite entry, alpha outside
  * (0, 1), eps or delta not finite and > 0, tau not finite, n_clamp < 2),
  * E_NOT_CONVERGED (a phase still had residues above its threshold after
  * 65,535 rounds), E_OOM, E_CUDA. */

@@ -556,6 +556,8 @@ int pprviz_tau_push(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const 
     return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup must be in [1, min(n, 65535)]");
   if ((int64_t)nsup * g->n >= ((int64_t)1 << 31))
     return set_err(ctx, PPRVIZ_E_INVALID_ARG, "nsup * n must stay below 2^31 (the residue entries are int32-indexed)");
+  if (g->nnz >= ((int64_t)1 << 31))
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "Tau-Push takes graphs below 2^31 stored edges");
   if (!(alpha > 0.0 && alpha < 1.0)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "alpha must be in (0, 1)");
   if (!(eps > 0.0) || !isfinite(eps)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "eps must be finite and > 0");
   if (!(delta > 0.0) || !isfinite(delta)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "delta must be finite and > 0");

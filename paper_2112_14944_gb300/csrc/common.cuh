@@ -54,9 +54,9 @@ enum Slot {
   WS_SPART, WS_SCNT,
   // batched views: the waves' split work items and split rows
   WS_UITEMS, WS_USROW,
-  // Tau-Push: residues, reserves, frontier queues, push items, per-round
-  // counters, leaf maps and small per-supernode tables
-  WS_TPR, WS_TPQ, WS_TPFA, WS_TPFB, WS_TPVAL, WS_TPITEM, WS_TPCNT, WS_TPMAP, WS_TPTAB,
+  // Tau-Push: residues, reserves, push records, (slot, share) pairs, dirty
+  // marks, per-round counters, leaf maps and small per-supernode tables
+  WS_TPR, WS_TPQ, WS_TPFA, WS_TPFB, WS_TPVAL, WS_TPCNT, WS_TPMAP, WS_TPTAB,
   WS_COUNT
 };
 

@@ -4,24 +4,31 @@
 // The paper's pushes are sequential: one node at a time, in no stated order.
 // Here every (node, supernode) residue above its threshold is pushed in the
 // same round. A round is two launches:
-//   prepass  one thread per frontier entry: take the residue (atomic
-//            exchange with 0), add the reserve share if the node is a leaf of
-//            a child, and cut the node's edge list into push items of 32
-//            edges;
-//   push     one warp per item, one edge per lane: FP64 atomic add of the
-//            share into the neighbour's residue; the lane whose add lifts the
-//            residue over its threshold appends the neighbour to the next
-//            frontier (so a residue is listed at most once per round).
-// A residue taken in a round can grow again in the same round; the growth
-// stays in the residue and, if it crosses the threshold, lists the node for
-// the next round. No residue is lost and none above its threshold is left
-// unlisted, so the rounds end exactly when Algorithm 2's (or 3's) loop
-// condition fails, and the error bounds of Lemmas 2 and 3 hold as stated.
+//   collect  one thread per node, dirty nodes only: it takes (sets to 0)
+//            every residue of the node above its threshold, books its
+//            reserve share and lists the node for the push: its taken
+//            residues' (supernode slot, share) pairs, and either one small
+//            record (at most TP_SMALL units of work; unit = one edge times
+//            one taken residue) or pieces of at most TP_PIECE units; the
+//            lists of a warp are placed with one atomic each;
+//   push     one warp per task of at most TP_PIECE units: 32 small records
+//            (a lane finds its record by a 5-step search over the warp's
+//            prefix sums) or one piece; a lane's unit o of a record is its
+//            edge o / c and taken residue o % c; TP_CPW units in flight per
+//            lane; the share is added with a fire-and-forget FP64 atomic
+//            reduction and the neighbour marked dirty.
+// One record serves all of a node's taken residues, so an edge's column
+// index is read once for all of them and their adds land in the same few
+// cache lines of the neighbour. No push reads a residue back, so the adds of
+// a round overlap freely; the residues are read only when no push is in
+// flight. Every residue above its threshold belongs to a node touched since
+// it was last taken, so the rounds end exactly when Algorithm 2's (or 3's)
+// loop condition fails, and the error bounds of Lemmas 2 and 3 hold as stated.
 //
 // Data layout: residues node-major (n x K doubles, K = sources or targets of
-// the phase), so a hub reached by many supernodes keeps its K residues in a
-// few cache lines; reserves only for the leaves of the children
-// (leaves x K doubles, indexed by the leaf's position in leaf_idx).
+// the phase), so the K residues of a node sit in a few cache lines and the
+// collect pass reads them together; reserves only for the leaves of the
+// children (leaves x K doubles, indexed by the leaf's position in leaf_idx).
 #include <cmath>
 #include <cstring>
 
@@ -30,30 +37,33 @@
 namespace pprviz {
 namespace {
 
-constexpr int TP_CH = 32;                  // edges per push item
 constexpr int TP_TPB = 256;
 constexpr int64_t TP_MAX_ROUNDS = 65535;   // a phase still active after this many rounds fails
 constexpr int64_t DPR_HEAVY = 512;         // pull rows longer than this get a block of their own
 
-struct TpEntry {
-  int32_t v, s;  // node, source (forward) or target slot (backward)
+// A listed node: its first edge (out-edges forward, in-edges backward), edge
+// count, number of taken residues and where their (slot, share) pairs start.
+struct TpRec {
+  int64_t q0;
+  int64_t pb;
+  int32_t v, ne, c, pad;
 };
-struct TpItem {
-  int32_t e, c;  // frontier entry, chunk of 32 edges
+struct TpPair {
+  int32_t s, pad;
+  double share;  // per unit walk weight
 };
 
-// Per-phase device counters: frontier size and item count of every round,
-// the edges cut into items, and an overflow flag.
+// Per-phase device counters, per round: small records, pieces and
+// (slot, share) pairs;
+// and the residues taken, the edge relaxations listed and an overflow flag.
 struct TpCounters {
-  unsigned long long front[TP_MAX_ROUNDS + 2];
-  unsigned long long items[TP_MAX_ROUNDS + 2];
+  unsigned long long small[TP_MAX_ROUNDS + 2];
+  unsigned long long big[TP_MAX_ROUNDS + 2];
+  unsigned long long pairs[TP_MAX_ROUNDS + 2];
+  unsigned long long takes;
   unsigned long long edges;
   int overflow;
 };
-
-__device__ __forceinline__ double take_residue(double *p) {
-  return __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long *>(p), 0ull));
-}
 
 // pos_of[v] = position of v in leaf_idx (pos_of prefilled with -1)
 __global__ void k_tp_pos(int64_t nleaf, const int32_t *__restrict__ leaf_idx, int32_t *__restrict__ pos_of) {
@@ -100,152 +110,239 @@ __global__ void k_tp_means(const int64_t *__restrict__ leaf_ptr, const int32_t *
 }
 
 // Forward start (Algorithm 2, initial residues): r(V_i, v) = d(v) / |F(V_i)|
-// on the leaves of every source V_i; the ones above d(v) r_max form round 0.
+// on the leaves of every source V_i; the leaves are marked for the collect pass.
 __global__ void k_tp_fwd_init(int64_t nleaf, const int64_t *__restrict__ leaf_ptr,
                               const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ psup, int32_t K,
-                              const double *__restrict__ deg, double r_max, double *__restrict__ R,
-                              TpEntry *__restrict__ front, TpCounters *__restrict__ cnt) {
+                              const double *__restrict__ deg, double *__restrict__ R, uint8_t *__restrict__ dirty) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nleaf) return;
   const int32_t i = psup[p], v = leaf_idx[p];
-  const double r = deg[v] / (double)(leaf_ptr[i + 1] - leaf_ptr[i]);
-  R[(size_t)v * K + i] = r;
-  if (r > deg[v] * r_max) {
-    const unsigned long long q = atomicAdd(&cnt->front[0], 1ull);
-    front[q] = TpEntry{v, i};
-  }
+  R[(size_t)v * K + i] = deg[v] / (double)(leaf_ptr[i + 1] - leaf_ptr[i]);
+  dirty[v] = 1;
 }
 
 // Backward start (Algorithm 3, initial residues): r(v, V_j) = 1 / |F(V_j)| on
-// the leaves of every refined target V_j (slot[j] >= 0); above thr_b form round 0.
+// the leaves of every refined target V_j (slot[j] >= 0).
 __global__ void k_tp_bwd_init(int64_t nleaf, const int64_t *__restrict__ leaf_ptr,
                               const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ psup,
-                              const int32_t *__restrict__ slot, int32_t K, const double *__restrict__ thr_b,
-                              double *__restrict__ R, TpEntry *__restrict__ front, TpCounters *__restrict__ cnt) {
+                              const int32_t *__restrict__ slot, int32_t K, double *__restrict__ R,
+                              uint8_t *__restrict__ dirty) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nleaf) return;
   const int32_t j = psup[p], jb = slot[j];
   if (jb < 0) return;
   const int32_t v = leaf_idx[p];
-  const double r = 1.0 / (double)(leaf_ptr[j + 1] - leaf_ptr[j]);
-  R[(size_t)v * K + jb] = r;
-  if (r > thr_b[jb]) {
-    const unsigned long long q = atomicAdd(&cnt->front[0], 1ull);
-    front[q] = TpEntry{v, jb};
-  }
+  R[(size_t)v * K + jb] = 1.0 / (double)(leaf_ptr[j + 1] - leaf_ptr[j]);
+  dirty[v] = 1;
 }
 
-// Round prepass. Forward (Algorithm 2): the reserve of a leaf gains
-// alpha r (the estimate's alpha r / |F(V_j)| is applied when the reserves are
-// summed), and the share (1 - alpha) r / dw(v) waits for the push. Backward
-// (Algorithm 3): the reserve gains alpha d(v) r and the share is (1 - alpha) r.
-// A node without out-edges keeps the walk (a self-loop): the sum of its
-// endless pushes is taken at once - forward, the whole residue is reserve and
-// nothing moves; backward, the reserve gains d(v) r (= 0) and the other
-// in-neighbours receive (1 - alpha) r / alpha times their walk probability.
+// One unit of a push: the share sent along edge q lands in the residue
+// (slot sl) of neighbour x = ncol[q], which is marked dirty. Forward: weight
+// w(v, x) (1 unweighted). Backward: walk probability w(x, v) / dw(x); the
+// walk's own self-loop at a node without out-edges was summed when its
+// residue was taken. The add is a reduction (no value read back).
 template <bool BWD>
-__global__ void __launch_bounds__(TP_TPB)
-    k_tp_prepass(int64_t round, const TpEntry *__restrict__ front, int32_t K, double *__restrict__ R,
-                 double *__restrict__ Q, const int32_t *__restrict__ pos_of, const int64_t *__restrict__ rp,
-                 const int64_t *__restrict__ nrp, const double *__restrict__ deg,
-                 const double *__restrict__ invdw, double alpha, double *__restrict__ val,
-                 TpItem *__restrict__ items, int64_t item_cap, int64_t front_cap, TpCounters *__restrict__ cnt) {
-  const int64_t F = min((int64_t)cnt->front[round], front_cap);  // beyond the cap only after an overflow
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < F; base += stride) {
-    const int64_t e = base + lane;
-    int32_t nch = 0;
-    long long ne = 0;
-    if (e < F) {
-      const TpEntry en = front[e];
-      const double r = take_residue(&R[(size_t)en.v * K + en.s]);
-      const bool stays = rp[en.v + 1] == rp[en.v];
-      const int32_t p = pos_of[en.v];
-      if (!BWD) {
-        if (p >= 0) Q[(size_t)p * K + en.s] += stays ? r : alpha * r;
-        val[e] = stays ? 0.0 : (1.0 - alpha) * r * invdw[en.v];
-        ne = stays ? 0 : (long long)(nrp[en.v + 1] - nrp[en.v]);
-      } else {
-        if (p >= 0) Q[(size_t)p * K + en.s] += (stays ? 1.0 : alpha) * deg[en.v] * r;
-        val[e] = stays ? (1.0 - alpha) * r / alpha : (1.0 - alpha) * r;
-        ne = (long long)(nrp[en.v + 1] - nrp[en.v]);
-      }
-      nch = (int32_t)((ne + TP_CH - 1) / TP_CH);
-    }
-    // warp prefix of the item counts; one atomic per warp
-    int32_t incl = nch;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    long long ns = ne;
-    for (int o = 16; o > 0; o >>= 1) ns += __shfl_down_sync(0xffffffffu, ns, o);
-    const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long b0 = 0;
-    if (lane == 31 && tot > 0) b0 = atomicAdd(&cnt->items[round], (unsigned long long)tot);
-    b0 = __shfl_sync(0xffffffffu, b0, 31);
-    if (lane == 0 && ns > 0) atomicAdd(&cnt->edges, (unsigned long long)ns);
-    const int64_t first = (int64_t)b0 + incl - nch;
-    if (first + nch > item_cap) {
-      if (nch > 0) atomicOr(&cnt->overflow, 1);
-    } else {
-      for (int32_t c = 0; c < nch; ++c) items[first + c] = TpItem{(int32_t)e, c};
-    }
+__device__ __forceinline__ void push_unit(int64_t q, int32_t v, const TpPair &pr, int32_t K,
+                                          double *__restrict__ R, const int64_t *__restrict__ rp,
+                                          const int32_t *__restrict__ ncol, const float *__restrict__ nw,
+                                          const double *__restrict__ invdw, uint8_t *__restrict__ dirty) {
+  const int32_t x = ncol[q];
+  double add = pr.share * (nw ? (double)nw[q] : 1.0);
+  if (BWD) {
+    if (x == v && rp[v + 1] == rp[v]) return;
+    add *= invdw[x];
   }
+  if (!(add > 0.0)) return;
+  atomicAdd(&R[(size_t)x * K + pr.s], add);
+  dirty[x] = 1;
 }
 
-// Round push: one warp per item, one edge per lane. Forward shares go to the
-// out-neighbours x with weight w(v, x) (1 unweighted) and threshold
-// d(x) r_max; backward shares go to the in-neighbours x with the walk
-// probability w(x, v) / dw(x) and the target's threshold thr_b.
+// Number of the 32 inclusive prefix sums (one per lane) that are <= t
+// (32 when t is past the last one).
+__device__ __forceinline__ int32_t prefix_count(int32_t incl, int64_t t) {
+  int32_t j = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int32_t v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+    if ((int64_t)v <= t) j += step;
+  }
+  if (t >= (int64_t)__shfl_sync(0xffffffffu, incl, 31)) j = 32;
+  return j;
+}
+
+constexpr int TP_CPW = 4;          // units in flight per lane
+constexpr int32_t TP_SMALL = 32;    // records of at most this much work are packed 32 to a warp
+constexpr int32_t TP_PIECE = 1024;  // larger work is cut into pieces of at most this much, one warp each
+
+// Push of a round. Tasks [0, ceil(S / 32)) take 32 consecutive small records
+// each (one unit per lane: a 5-step search over the warp's prefix sums finds
+// the record); the next B tasks take one piece each (unit o of the piece:
+// edge o / c, residue o % c). Every task is at most TP_PIECE units.
 template <bool BWD>
-__global__ void __launch_bounds__(TP_TPB)
-    k_tp_push(int64_t round, const TpItem *__restrict__ items, const TpEntry *__restrict__ front,
-              const double *__restrict__ val, int32_t K, double *__restrict__ R, const int64_t *__restrict__ rp,
-              const int64_t *__restrict__ nrp, const int32_t *__restrict__ ncol, const float *__restrict__ nw,
-              const double *__restrict__ deg, const double *__restrict__ invdw, double r_max,
-              const double *__restrict__ thr_b, TpEntry *__restrict__ next, int64_t next_cap, int64_t item_cap,
-              TpCounters *__restrict__ cnt) {
-  const int64_t I = min((int64_t)cnt->items[round], item_cap);  // beyond the cap only after an overflow
+__global__ void __launch_bounds__(TP_TPB, 4)
+    k_tp_push(int64_t round, const TpRec *__restrict__ small, const TpRec *__restrict__ big,
+              const TpPair *__restrict__ pairs, int32_t K, double *__restrict__ R, const int64_t *__restrict__ rp,
+              const int32_t *__restrict__ ncol, const float *__restrict__ nw, const double *__restrict__ invdw,
+              uint8_t *__restrict__ dirty, int64_t small_cap, int64_t big_cap, const TpCounters *__restrict__ cnt) {
+  const int64_t S = min((int64_t)cnt->small[round], small_cap);  // beyond the caps only after an overflow
+  const int64_t Bn = min((int64_t)cnt->big[round], big_cap);
+  const int64_t ntask = (S + 31) / 32 + Bn;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < I; it += nwarps) {
-    const TpItem im = items[it];
-    const TpEntry en = front[im.e];
-    const double share = val[im.e];
-    const int64_t q = nrp[en.v] + (int64_t)im.c * TP_CH + lane;
-    bool up = false;
-    int32_t x = 0;
-    if (q < nrp[en.v + 1]) {
-      x = ncol[q];
-      const double w = nw ? (double)nw[q] : 1.0;
-      double add, thr;
-      bool skip = false;
-      if (!BWD) {
-        add = share * w;
-        thr = deg[x] * r_max;
-      } else {
-        skip = x == en.v && rp[en.v + 1] == rp[en.v];  // the walk's own self-loop, summed in the prepass
-        add = share * w * invdw[x];
-        thr = thr_b[en.s];
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
+    if (task < (S + 31) / 32) {
+      const int64_t e = task * 32 + lane;
+      TpRec me{0, 0, 0, 0, 1, 0};
+      int32_t work = 0;
+      if (e < S) {
+        me = small[e];
+        work = me.ne * me.c;
       }
-      if (!skip && add > 0.0) {
-        const double old = atomicAdd(&R[(size_t)x * K + en.s], add);
-        up = old <= thr && old + add > thr;
+      int32_t incl = work;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t a = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += a;
+      }
+      const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      for (int64_t t0 = 0; t0 < tot; t0 += 32 * TP_CPW) {
+#pragma unroll
+        for (int u = 0; u < TP_CPW; ++u) {
+          const int64_t t = t0 + 32 * u + lane;
+          const int32_t j = prefix_count(incl, t);
+          const int32_t jj = j < 32 ? j : 31;
+          const int32_t prev = __shfl_sync(0xffffffffu, incl, jj > 0 ? jj - 1 : 0);
+          const int64_t q0 = __shfl_sync(0xffffffffu, me.q0, jj);
+          const int64_t pb = __shfl_sync(0xffffffffu, me.pb, jj);
+          const int32_t v = __shfl_sync(0xffffffffu, me.v, jj);
+          const int32_t c = __shfl_sync(0xffffffffu, me.c, jj);
+          if (j < 32) {
+            const int32_t o = (int32_t)(t - (j > 0 ? prev : 0));
+            const int32_t ed = o / c;
+            push_unit<BWD>(q0 + ed, v, pairs[pb + (o - ed * c)], K, R, rp, ncol, nw, invdw, dirty);
+          }
+        }
+      }
+    } else {
+      const TpRec r = big[task - (S + 31) / 32];
+      const int32_t work = r.ne * r.c;
+      for (int32_t o0 = 0; o0 < work; o0 += 32 * TP_CPW) {
+#pragma unroll
+        for (int u = 0; u < TP_CPW; ++u) {
+          const int32_t o = o0 + 32 * u + lane;
+          if (o < work) {
+            const int32_t ed = o / r.c;
+            push_unit<BWD>(r.q0 + ed, r.v, pairs[r.pb + (o - ed * r.c)], K, R, rp, ncol, nw, invdw, dirty);
+          }
+        }
       }
     }
-    const unsigned b = __ballot_sync(0xffffffffu, up);
-    if (b) {
-      unsigned long long b0 = 0;
-      const int leader = __ffs(b) - 1;
-      if (lane == leader) b0 = atomicAdd(&cnt->front[round + 1], (unsigned long long)__popc(b));
-      b0 = __shfl_sync(0xffffffffu, b0, leader);
-      if (up) {
-        const int64_t slot = (int64_t)b0 + __popc(b & ((1u << lane) - 1u));
-        if (slot < next_cap) next[slot] = TpEntry{x, en.s};
-        else atomicOr(&cnt->overflow, 2);
+  }
+}
+
+// Inclusive warp prefix sum.
+template <typename T>
+__device__ __forceinline__ T warp_incl(T v, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    const T a = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += a;
+  }
+  return v;
+}
+
+// Collect pass (builds round `round`): one thread per node x; a dirty x has
+// its mark cleared and each residue above its threshold (forward
+// d(x) r_max, backward the target's thr_b) taken. Forward (Algorithm 2): the
+// reserve of a leaf gains alpha r (the estimate's alpha r / |F(V_j)| is
+// applied when the reserves are summed) and the share is (1 - alpha) r / dw(x).
+// Backward (Algorithm 3): the reserve gains alpha d(x) r and the share is
+// (1 - alpha) r. A node without out-edges keeps the walk (a self-loop): the
+// sum of its endless pushes is taken at once - forward, the whole residue is
+// reserve and nothing is listed; backward, the reserve gains d(x) r (= 0) and
+// the other in-neighbours receive (1 - alpha) r / alpha times their walk
+// probability.
+template <bool BWD>
+__global__ void __launch_bounds__(TP_TPB)
+    k_tp_collect_front(int64_t round, int64_t n, int32_t K, double *__restrict__ R, double *__restrict__ Q,
+                       uint8_t *__restrict__ dirty, const int32_t *__restrict__ pos_of,
+                       const int64_t *__restrict__ rp, const int64_t *__restrict__ nrp,
+                       const double *__restrict__ deg, const double *__restrict__ invdw, double alpha, double r_max,
+                       const double *__restrict__ thr_b, TpRec *__restrict__ small, TpRec *__restrict__ big,
+                       TpPair *__restrict__ pairs, int64_t small_cap, int64_t big_cap, int64_t pair_cap,
+                       TpCounters *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); x0 < n; x0 += stride) {
+    const int64_t x = x0 + lane;
+    const bool mine = x < n && dirty[x];
+    if (!__any_sync(0xffffffffu, mine)) continue;
+    int32_t c = 0, ne = 0, p = -1;
+    int64_t q0 = 0;
+    bool stays = false;
+    double thr = 0.0, dx = 0.0;
+    double *Rx = R + (size_t)x * K;
+    if (mine) {
+      dirty[x] = 0;
+      stays = rp[x + 1] == rp[x];
+      q0 = nrp[x];
+      ne = (!BWD && stays) ? 0 : (int32_t)(nrp[x + 1] - q0);
+      p = pos_of[x];
+      dx = deg[x];
+      thr = dx * r_max;
+      // how many residues of x are above their thresholds
+#pragma unroll 8
+      for (int32_t sl = 0; sl < K; ++sl) c += Rx[sl] > (BWD ? thr_b[sl] : thr);
+    }
+    const bool listed = ne > 0 && c > 0;
+    const int64_t work = (int64_t)ne * c;
+    const bool is_small = listed && work <= TP_SMALL;
+    const int32_t epr = c > 0 ? max(1, TP_PIECE / c) : 1;  // edges per piece
+    const int32_t nsm = is_small ? 1 : 0;
+    const int32_t npc = (listed && !is_small) ? (ne + epr - 1) / epr : 0;
+    // warp placement of the pairs, small records and pieces, one atomic each
+    const int32_t pc = listed ? c : 0;
+    const int32_t pin = warp_incl(pc, lane), sin_ = warp_incl(nsm, lane), bin = warp_incl(npc, lane);
+    const int32_t ptot = __shfl_sync(0xffffffffu, pin, 31), stot = __shfl_sync(0xffffffffu, sin_, 31);
+    const int32_t btot = __shfl_sync(0xffffffffu, bin, 31);
+    unsigned long long pb0 = 0, sb0 = 0, bb0 = 0;
+    if (lane == 31) {
+      if (ptot) pb0 = atomicAdd(&cnt->pairs[round], (unsigned long long)ptot);
+      if (stot) sb0 = atomicAdd(&cnt->small[round], (unsigned long long)stot);
+      if (btot) bb0 = atomicAdd(&cnt->big[round], (unsigned long long)btot);
+    }
+    pb0 = __shfl_sync(0xffffffffu, pb0, 31);
+    sb0 = __shfl_sync(0xffffffffu, sb0, 31);
+    bb0 = __shfl_sync(0xffffffffu, bb0, 31);
+    const long long tk = warp_incl((long long)c, lane);
+    const long long ed = warp_incl(listed ? (long long)ne * c : 0ll, lane);
+    if (lane == 31) {
+      if (tk) atomicAdd(&cnt->takes, (unsigned long long)tk);
+      if (ed) atomicAdd(&cnt->edges, (unsigned long long)ed);
+    }
+    if (c == 0) continue;
+    const int64_t pb = (int64_t)pb0 + pin - pc, sb = (int64_t)sb0 + sin_ - nsm, bb = (int64_t)bb0 + bin - npc;
+    const bool fits = pb + pc <= pair_cap && sb + nsm <= small_cap && bb + npc <= big_cap;
+    if (!fits) atomicOr(&cnt->overflow, 1);
+    int32_t k = 0;
+    const double inv = invdw[x];
+    for (int32_t sl = 0; sl < K; ++sl) {
+      const double r = Rx[sl];
+      if (!(r > (BWD ? thr_b[sl] : thr))) continue;
+      Rx[sl] = 0.0;
+      double share;
+      if (!BWD) {
+        if (p >= 0) Q[(size_t)p * K + sl] += stays ? r : alpha * r;
+        share = (1.0 - alpha) * r * inv;
+      } else {
+        if (p >= 0) Q[(size_t)p * K + sl] += (stays ? 1.0 : alpha) * dx * r;
+        share = stays ? (1.0 - alpha) * r / alpha : (1.0 - alpha) * r;
       }
+      if (listed && fits) pairs[pb + k] = TpPair{sl, 0, share};
+      ++k;
+    }
+    if (listed && fits) {
+      if (is_small) small[sb] = TpRec{q0, pb, (int32_t)x, ne, c, 0};
+      for (int32_t i = 0; i < npc; ++i)
+        big[bb + i] = TpRec{q0 + (int64_t)i * epr, pb, (int32_t)x, min(epr, ne - i * epr), c, 0};
     }
   }
 }
@@ -385,67 +482,77 @@ int dpr_solve(pprviz_ctx *ctx, const pprviz_graph *g, double alpha, double eps, 
 namespace {
 
 struct TpBufs {
-  double *R, *Q, *val;
-  TpEntry *fa, *fb;
-  TpItem *items;
+  double *R, *Q;
+  uint8_t *dirty;
+  TpRec *small, *big;
+  TpPair *pairs;
   TpCounters *cnt;
   int32_t *pos_of, *psup;
-  int64_t front_cap, item_cap;
+  int64_t small_cap, big_cap, pair_cap;
 };
 
-// Runs the rounds of one phase until a round starts with an empty frontier.
-// Returns the number of rounds, the pushes (summed frontier sizes) and the
-// edges cut into items.
+// Runs the rounds of one phase (the start residues set and their nodes
+// marked) until a collect pass lists nothing. Returns the number of rounds,
+// the residues taken and the edges of the listed records.
 template <bool BWD>
 int tp_phase(pprviz_ctx *ctx, const pprviz_graph *g, const TpBufs &B, int32_t K, double alpha, double r_max,
-             const double *thr_b, int64_t *rounds_out, int64_t *pushes_out, int64_t *edges_out) {
+             const double *thr_b, int64_t *rounds_out, int64_t *takes_out, int64_t *edges_out) {
+  const int64_t n = g->n;
   const int64_t *rp = g->rp.as<int64_t>();
   const int64_t *nrp = BWD ? pull_rp(g) : g->rp.as<int64_t>();
   const int32_t *ncol = BWD ? pull_col(g) : g->col.as<int32_t>();
   const float *nw = BWD ? pull_w(g) : (g->weighted ? g->w.as<float>() : nullptr);
   const double *deg = g->deg.as<double>();
   const double *invdw = g->invdw_d.as<double>();
-  const unsigned pre_grid = 152 * 4, push_grid = 152 * 8;
-  int64_t r = 0;
+  const unsigned grid = 152 * 8;
+  auto collect = [&](int64_t r) -> int {
+    {
+      PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH);
+      k_tp_collect_front<BWD><<<grid, TP_TPB, 0, ctx->stream>>>(r, n, K, B.R, B.Q, B.dirty, B.pos_of, rp, nrp, deg,
+                                                                invdw, alpha, r_max, thr_b, B.small, B.big, B.pairs,
+                                                                B.small_cap, B.big_cap, B.pair_cap, B.cnt);
+    }
+    PPRVIZ_LAUNCHED(ctx);
+    return PPRVIZ_OK;
+  };
+  PPRVIZ_TRY(collect(0));
+  int64_t r = 0;  // rounds pushed so far; round r's lists are built
   int batch = 4;
   unsigned long long head = 0;
   while (true) {
     for (int b = 0; b < batch && r < TP_MAX_ROUNDS; ++b, ++r) {
-      TpEntry *cur = (r % 2 == 0) ? B.fa : B.fb;
-      TpEntry *nxt = (r % 2 == 0) ? B.fb : B.fa;
       {
         PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH);
-        k_tp_prepass<BWD><<<pre_grid, TP_TPB, 0, ctx->stream>>>(r, cur, K, B.R, B.Q, B.pos_of, rp, nrp, deg, invdw,
-                                                                 alpha, B.val, B.items, B.item_cap, B.front_cap,
-                                                                 B.cnt);
+        k_tp_push<BWD><<<grid, TP_TPB, 0, ctx->stream>>>(r, B.small, B.big, B.pairs, K, B.R, rp, ncol, nw, invdw,
+                                                         B.dirty, B.small_cap, B.big_cap, B.cnt);
       }
       PPRVIZ_LAUNCHED(ctx);
-      {
-        PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH);
-        k_tp_push<BWD><<<push_grid, TP_TPB, 0, ctx->stream>>>(r, B.items, cur, B.val, K, B.R, rp, nrp, ncol, nw, deg,
-                                                              invdw, r_max, thr_b, nxt, B.front_cap, B.item_cap,
-                                                              B.cnt);
-      }
-      PPRVIZ_LAUNCHED(ctx);
+      PPRVIZ_TRY(collect(r + 1));
     }
-    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&head, &B.cnt->front[r], sizeof(head), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long hb = 0;
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&head, &B.cnt->small[r], sizeof(head), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&hb, &B.cnt->big[r], sizeof(hb), cudaMemcpyDeviceToHost, ctx->stream));
     PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    head += hb;
     if (head == 0 || r >= TP_MAX_ROUNDS) break;
     batch = std::min(batch * 2, 64);
   }
-  std::vector<unsigned long long> fr((size_t)r + 1);
-  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(fr.data(), B.cnt->front, sizeof(unsigned long long) * fr.size(),
+  std::vector<unsigned long long> rc((size_t)r + 1), rb((size_t)r + 1);
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rc.data(), B.cnt->small, sizeof(unsigned long long) * rc.size(),
                                    cudaMemcpyDeviceToHost, ctx->stream));
-  unsigned long long edges = 0;
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(rb.data(), B.cnt->big, sizeof(unsigned long long) * rb.size(),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned long long takes = 0, edges = 0;
   int overflow = 0;
+  PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&takes, &B.cnt->takes, sizeof(takes), cudaMemcpyDeviceToHost, ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&edges, &B.cnt->edges, sizeof(edges), cudaMemcpyDeviceToHost, ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&overflow, &B.cnt->overflow, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (overflow) return set_err(ctx, PPRVIZ_E_CUDA, "Tau-Push: a frontier or item queue overflowed its bound");
-  int64_t rounds = 0, pushes = 0;
-  while (rounds <= r && fr[(size_t)rounds] > 0) pushes += (int64_t)fr[(size_t)rounds++];
+  if (overflow) return set_err(ctx, PPRVIZ_E_CUDA, "Tau-Push: a record list overflowed its bound");
+  int64_t rounds = 0;
+  while (rounds <= r && rc[(size_t)rounds] + rb[(size_t)rounds] > 0) ++rounds;
   *rounds_out = rounds;
-  *pushes_out = pushes;
+  *takes_out = (int64_t)takes;
   *edges_out = (int64_t)edges;
   if (head != 0)
     return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "Tau-Push: residues above the threshold after the round limit");
@@ -461,8 +568,8 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
   const int64_t n = g->n;
   const int64_t nleaf = leaf_ptr_h[(size_t)nsup];
   const size_t kk = (size_t)nsup * (size_t)nsup;
-  // queue and item bounds: a (node, supernode) pair is listed at most once per
-  // round, and the items of a round number at most entries + K nnz / 32
+  // list bounds: a node is listed at most once per round and a residue at
+  // most once (one pair)
   int64_t pull_nnz = g->nnz;
   if (g->directed) {
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&pull_nnz, g->prp.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
@@ -470,14 +577,17 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
     PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
   const int64_t K = nsup;
-  const int64_t front_cap = n * K;
-  const int64_t item_cap = front_cap + (K * std::max(g->nnz, pull_nnz) + TP_CH - 1) / TP_CH + 1;
+  const int64_t nnz_max = std::max(g->nnz, pull_nnz);
+  // records: one small record per node, or pieces of at least
+  // max(1, TP_PIECE / K) edges each (the last piece of a node may be shorter)
+  const int64_t small_cap = n;
+  const int64_t big_cap = n + nnz_max / std::max<int64_t>(1, TP_PIECE / K) + 1;
+  const int64_t pair_cap = n * K;
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPR, sizeof(double) * (size_t)(n * K)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPQ, sizeof(double) * (size_t)(nleaf * K)));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_TPFA, sizeof(TpEntry) * (size_t)front_cap));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_TPFB, sizeof(TpEntry) * (size_t)front_cap));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_TPVAL, sizeof(double) * (size_t)front_cap));
-  PPRVIZ_TRY(ws_ensure(ctx, WS_TPITEM, sizeof(TpItem) * (size_t)item_cap));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TPFA, sizeof(TpRec) * (size_t)(small_cap + big_cap)));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TPFB, sizeof(TpPair) * (size_t)pair_cap));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TPVAL, (size_t)n));
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPCNT, sizeof(TpCounters)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPMAP, sizeof(int32_t) * (size_t)(n + nleaf)));
   // table: E (kk doubles), means (2 nsup), thr_b (nsup), slot (nsup int32), tsel (nsup int32)
@@ -485,15 +595,16 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
   TpBufs B;
   B.R = ctx->ws[WS_TPR].as<double>();
   B.Q = ctx->ws[WS_TPQ].as<double>();
-  B.fa = ctx->ws[WS_TPFA].as<TpEntry>();
-  B.fb = ctx->ws[WS_TPFB].as<TpEntry>();
-  B.val = ctx->ws[WS_TPVAL].as<double>();
-  B.items = ctx->ws[WS_TPITEM].as<TpItem>();
+  B.small = ctx->ws[WS_TPFA].as<TpRec>();
+  B.big = B.small + small_cap;
+  B.pairs = ctx->ws[WS_TPFB].as<TpPair>();
+  B.dirty = ctx->ws[WS_TPVAL].as<uint8_t>();
   B.cnt = ctx->ws[WS_TPCNT].as<TpCounters>();
   B.pos_of = ctx->ws[WS_TPMAP].as<int32_t>();
   B.psup = B.pos_of + n;
-  B.front_cap = front_cap;
-  B.item_cap = item_cap;
+  B.small_cap = small_cap;
+  B.big_cap = big_cap;
+  B.pair_cap = pair_cap;
   double *E = ctx->ws[WS_TPTAB].as<double>();
   double *means = E + kk;
   double *thr_b = means + 2 * (size_t)nsup;
@@ -539,8 +650,9 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.R, 0, sizeof(double) * (size_t)(n * K), ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.Q, 0, sizeof(double) * (size_t)(nleaf * K), ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(TpCounters), ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.dirty, 0, (size_t)n, ctx->stream));
   if (std::isfinite(r_max)) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_fwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, (int32_t)K, deg, r_max, B.R, B.fa, B.cnt); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_fwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, (int32_t)K, deg, B.R, B.dirty); }
     PPRVIZ_LAUNCHED(ctx);
     int64_t rounds = 0, pushes = 0, edges = 0;
     const int st = tp_phase<false>(ctx, g, B, (int32_t)K, alpha, r_max, nullptr, &rounds, &pushes, &edges);
@@ -570,7 +682,8 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.R, 0, sizeof(double) * (size_t)(n * Kb), ctx->stream));
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.Q, 0, sizeof(double) * (size_t)(nleaf * Kb), ctx->stream));
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(TpCounters), ctx->stream));
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_bwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, slot, Kb, thr_b, B.R, B.fa, B.cnt); }
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.dirty, 0, (size_t)n, ctx->stream));
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_bwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, slot, Kb, B.R, B.dirty); }
     PPRVIZ_LAUNCHED(ctx);
     int64_t rounds = 0, pushes = 0, edges = 0;
     const int st = tp_phase<true>(ctx, g, B, Kb, alpha, 0.0, thr_b, &rounds, &pushes, &edges);
