@@ -64,85 +64,168 @@ __global__ void __launch_bounds__(512) k_fac_diag(int32_t kp, int32_t K0, T *__r
   }
 }
 
-// The same sweep for a 128 x 128 FP32 block with the block in registers:
-// thread t owns row t / 8 and, with g = t % 8, the 16 columns 32 m + 4 g + w
-// (m, w < 4), so that the 8 threads of a row read a 128-byte run of the
-// published pivot row with each 16-byte load. Per pivot p the owners publish
-// row p, column p and 1 / a_pp through shared memory (double buffered by the
-// parity of p, so one barrier per pivot suffices).
-__device__ __forceinline__ void fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A, float *__restrict__ P) {
-  __shared__ __align__(16) float sRow[2][128];
-  __shared__ float sCol[2][128];
-  __shared__ float sPiv[2];
-  const int r = threadIdx.x >> 3, g = threadIdx.x & 7;
-  float a[16];  // a[4 m + w] = column 32 m + 4 g + w
+// D = A_JJ^-1 for the 32 x 32 block J of a 128 x 128 block whose column
+// block J is stored transposed in colT (colT[c][r] = A[r][32 J + c]), by one
+// warp: the element sweep above in registers, lane = row. Per pivot p lane p
+// publishes its row in a shared buffer (two, alternating, so one warp
+// barrier per pivot suffices) and every lane reads it back with 16-byte
+// broadcast loads. Writes D and its transpose.
+__device__ __noinline__ void warp_inv32(const float *colT, int J, float *D, float *DT, float *rowbuf) {
+  const int l = threadIdx.x & 31;
+  float d[32];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const float4 v = *reinterpret_cast<const float4 *>(A + (int64_t)(K0 + r) * kp + K0 + 32 * m + 4 * g);
-    a[4 * m] = v.x; a[4 * m + 1] = v.y; a[4 * m + 2] = v.z; a[4 * m + 3] = v.w;
-  }
-  // pivot p = 4 q + w (w unrolled): column p is owned by g == q % 8 at
-  // register 4 (q / 8) + w, a 4-way choice instead of a 16-way search
-  for (int q = 0; q < 32; ++q) {
+  for (int c = 0; c < 32; ++c) d[c] = colT[c * 128 + 32 * J + l];
 #pragma unroll
-  for (int w = 0; w < 4; ++w) {
-    const int p = 4 * q + w;
-    const int b = w & 1;
-    const bool col_owner = (q & 7) == g;
-    const int mq = q >> 3;
-    if (col_owner) {
-      const float colv = mq == 0 ? a[w] : mq == 1 ? a[4 + w] : mq == 2 ? a[8 + w] : a[12 + w];
-      sCol[b][r] = colv;
-      if (r == p) sPiv[b] = 1.0f / colv;
-    }
-    if (r == p) {
+  for (int p = 0; p < 32; ++p) {
+    float *rb = rowbuf + (p & 1) * 32;
+    if (l == p) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
-        *reinterpret_cast<float4 *>(&sRow[b][32 * m + 4 * g]) =
-            make_float4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
+      for (int c = 0; c < 32; c += 4)
+        *reinterpret_cast<float4 *>(rb + c) = make_float4(d[c], d[c + 1], d[c + 2], d[c + 3]);
     }
-    __syncthreads();
-    const float piv = sPiv[b];
-    const float f = sCol[b][r] * piv;  // a_rp / a_pp
-    // every element: a_rc - (a_rp / a_pp) a_pc (one FMA); then row p and
-    // column p are overwritten with their own formulas
-    float4 rowv[4];
+    __syncwarp();
+    const float piv = 1.0f / rb[p];
+    const float f = d[p] * piv;  // a_lp / a_pp
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      rowv[m] = *reinterpret_cast<const float4 *>(&sRow[b][32 * m + 4 * g]);
-      a[4 * m + 0] = fmaf(-f, rowv[m].x, a[4 * m + 0]);
-      a[4 * m + 1] = fmaf(-f, rowv[m].y, a[4 * m + 1]);
-      a[4 * m + 2] = fmaf(-f, rowv[m].z, a[4 * m + 2]);
-      a[4 * m + 3] = fmaf(-f, rowv[m].w, a[4 * m + 3]);
-    }
-    if (r == p) {
+    for (int c = 0; c < 32; c += 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(rb + c);
+      const float vs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        a[4 * m + 0] = rowv[m].x * piv;
-        a[4 * m + 1] = rowv[m].y * piv;
-        a[4 * m + 2] = rowv[m].z * piv;
-        a[4 * m + 3] = rowv[m].w * piv;
-      }
+      for (int e = 0; e < 4; ++e) d[c + e] = (l == p) ? vs[e] * piv : fmaf(-f, vs[e], d[c + e]);
     }
-    if (col_owner) {
-      const float vcol = (r == p) ? piv : -f;
-      if (mq == 0) a[w] = vcol;
-      else if (mq == 1) a[4 + w] = vcol;
-      else if (mq == 2) a[8 + w] = vcol;
-      else a[12 + w] = vcol;
-    }
-  }
+    d[p] = (l == p) ? piv : -f;
   }
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int c = 32 * m + 4 * g;
-    *reinterpret_cast<float4 *>(P + r * 128 + c) = make_float4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
-    *reinterpret_cast<float4 *>(A + (int64_t)(K0 + r) * kp + K0 + c) =
-        make_float4(-a[4 * m], -a[4 * m + 1], -a[4 * m + 2], -a[4 * m + 3]);
+  for (int c = 0; c < 32; ++c) {
+    D[l * 32 + c] = d[c];
+    DT[c * 32 + l] = d[c];
   }
 }
 
-__global__ void __launch_bounds__(1024) k_fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A,
+// The same sweep for a 128 x 128 FP32 block, in four 32-wide block steps
+// (the block form of the sweep: sweeping the 32 pivots of block J at once is
+// D = A_JJ^-1, A_JL <- D A_JL, A_IJ <- -A_IJ D, A_IL <- A_IL - A_IJ D A_JL,
+// A_JJ <- D, the same result as 32 single-pivot sweeps). The block lives in
+// registers, a 4 x 8 tile per thread (512 threads): thread t owns rows
+// 4 (t / 16) + i and columns 8 (t % 16) + j. Per block step the old row block
+// J and the old column block J (transposed) go to shared memory, one warp
+// inverts A_JJ, and every thread updates its tile with 32-term products
+// (three 16-byte shared loads per 32 FMAs): four barriers per block step
+// instead of one per pivot. Dynamic shared memory: DIAG128_SMEM bytes.
+constexpr int DIAG128_THREADS = 512;
+constexpr int DIAG128_SMEM = (3 * 32 * 128 + 2 * 32 * 32 + 64) * 4;
+__device__ __forceinline__ void fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A, float *__restrict__ P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float *sRowJ = reinterpret_cast<float *>(smem_raw);  // [32][128] old rows of block J
+  float *sColT = sRowJ + 32 * 128;                     // [32][128] old column block J, transposed
+  float *sNewT = sColT + 32 * 128;                     // [32][128] new column block J, transposed
+  float *sD = sNewT + 32 * 128;                        // [32][32] A_JJ^-1
+  float *sDT = sD + 32 * 32;                           // [32][32] its transpose
+  float *sPiv = sDT + 32 * 32;                         // [2][32] pivot rows of the warp inverse
+  const int rb = threadIdx.x >> 4, cb = threadIdx.x & 15;
+  float a[4][8];  // a[i][j] = row 4 rb + i, column 8 cb + j
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float *src = A + (int64_t)(K0 + 4 * rb + i) * kp + K0 + 8 * cb;
+    const float4 v0 = *reinterpret_cast<const float4 *>(src), v1 = *reinterpret_cast<const float4 *>(src + 4);
+    a[i][0] = v0.x; a[i][1] = v0.y; a[i][2] = v0.z; a[i][3] = v0.w;
+    a[i][4] = v1.x; a[i][5] = v1.y; a[i][6] = v1.z; a[i][7] = v1.w;
+  }
+#pragma unroll 1
+  for (int J = 0; J < 4; ++J) {
+    const bool rowJ = (rb >> 3) == J, colJ = (cb >> 2) == J;
+    const int ri = 4 * (rb & 7), ci = 8 * (cb & 3);  // offsets inside block J
+    if (rowJ) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float *dst = sRowJ + (ri + i) * 128 + 8 * cb;
+        *reinterpret_cast<float4 *>(dst) = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
+        *reinterpret_cast<float4 *>(dst + 4) = make_float4(a[i][4], a[i][5], a[i][6], a[i][7]);
+      }
+    }
+    if (colJ) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4 *>(sColT + (ci + j) * 128 + 4 * rb) = make_float4(a[0][j], a[1][j], a[2][j], a[3][j]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) warp_inv32(sColT, J, sD, sDT, sPiv);
+    __syncthreads();
+    if (rowJ) {  // A_JL <- D A_JL (the pivot block itself becomes D)
+      if (colJ) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) a[i][j] = sD[(ri + i) * 32 + ci + j];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) a[i][j] = 0.0f;
+#pragma unroll 4
+        for (int t = 0; t < 32; ++t) {
+          const float4 x = *reinterpret_cast<const float4 *>(sDT + t * 32 + ri);
+          const float4 y0 = *reinterpret_cast<const float4 *>(sRowJ + t * 128 + 8 * cb);
+          const float4 y1 = *reinterpret_cast<const float4 *>(sRowJ + t * 128 + 8 * cb + 4);
+          const float xs[4] = {x.x, x.y, x.z, x.w};
+          const float ys[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[i][j] = fmaf(xs[i], ys[j], a[i][j]);
+        }
+      }
+    } else if (colJ) {  // A_IJ <- -A_IJ D, also published for the other tiles of the rows
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[i][j] = 0.0f;
+#pragma unroll 4
+      for (int t = 0; t < 32; ++t) {
+        const float4 x = *reinterpret_cast<const float4 *>(sColT + t * 128 + 4 * rb);
+        const float4 y0 = *reinterpret_cast<const float4 *>(sD + t * 32 + ci);
+        const float4 y1 = *reinterpret_cast<const float4 *>(sD + t * 32 + ci + 4);
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+        const float ys[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) a[i][j] = fmaf(-xs[i], ys[j], a[i][j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4 *>(sNewT + (ci + j) * 128 + 4 * rb) = make_float4(a[0][j], a[1][j], a[2][j], a[3][j]);
+    }
+    __syncthreads();
+    if (!rowJ && !colJ) {  // A_IL <- A_IL + (-A_IJ D) A_JL
+#pragma unroll 4
+      for (int t = 0; t < 32; ++t) {
+        const float4 x = *reinterpret_cast<const float4 *>(sNewT + t * 128 + 4 * rb);
+        const float4 y0 = *reinterpret_cast<const float4 *>(sRowJ + t * 128 + 8 * cb);
+        const float4 y1 = *reinterpret_cast<const float4 *>(sRowJ + t * 128 + 8 * cb + 4);
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+        const float ys[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) a[i][j] = fmaf(xs[i], ys[j], a[i][j]);
+      }
+    }
+    __syncthreads();  // before the next block step restages
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = 4 * rb + i;
+    float *p = P + r * 128 + 8 * cb;
+    float *q = A + (int64_t)(K0 + r) * kp + K0 + 8 * cb;
+    *reinterpret_cast<float4 *>(p) = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
+    *reinterpret_cast<float4 *>(p + 4) = make_float4(a[i][4], a[i][5], a[i][6], a[i][7]);
+    *reinterpret_cast<float4 *>(q) = make_float4(-a[i][0], -a[i][1], -a[i][2], -a[i][3]);
+    *reinterpret_cast<float4 *>(q + 4) = make_float4(-a[i][4], -a[i][5], -a[i][6], -a[i][7]);
+  }
+}
+
+__global__ void __launch_bounds__(DIAG128_THREADS) k_fac_diag128(int32_t kp, int32_t K0, float *__restrict__ A,
                                                       float *__restrict__ P) {
   fac_diag128(kp, K0, A, P);
 }
@@ -214,11 +297,21 @@ __device__ __forceinline__ void fac_panel(int32_t kp, int32_t K0, int I0, T *__r
   T *sP = reinterpret_cast<T *>(smem_raw);  // [NB][NB]   sP[s][t]
   T *sC = sP + NB * NB;                     // [NB][LD]   sC[s][i] = C[i][s]
   const bool above = I0 < K0;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    sP[e] = P[e];
+  // 4-vectors, several in flight per thread
+#pragma unroll 4
+  for (int e = 4 * threadIdx.x; e < NB * NB; e += 4 * blockDim.x) {
+    T pv[4], cv[4];
+    V4<T>::ld(P + e, pv);
+    V4<T>::st(sP + e, pv);
     const int r = e / NB, c = e % NB;
-    if (above) sC[c * LD + r] = A[(int64_t)(I0 + r) * kp + K0 + c];  // i = r, s = c
-    else sC[r * LD + c] = A[(int64_t)(K0 + r) * kp + I0 + c];         // s = r, i = c
+    if (above) {  // i = r, s = c .. c + 3
+      V4<T>::ld(A + (int64_t)(I0 + r) * kp + K0 + c, cv);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) sC[(c + w) * LD + r] = cv[w];
+    } else {      // s = r, i = c .. c + 3
+      V4<T>::ld(A + (int64_t)(K0 + r) * kp + I0 + c, cv);
+      V4<T>::st(sC + r * LD + c, cv);
+    }
   }
   __syncthreads();
   if (KM) {  // C[i][t .. t + 3], split
@@ -988,6 +1081,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     }
     if (!ctx->ev_t1) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_t1, cudaEventDisableTiming));
     if (!ctx->ev_dp) PPRVIZ_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_dp, cudaEventDisableTiming));
+    PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag128, cudaFuncAttributeMaxDynamicSharedMemorySize, DIAG128_SMEM));
     PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_pp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           tcp::SMEM));
     int nsm = 0;
@@ -997,7 +1091,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
     ctx->test_expire_wait = false;
     PPRVIZ_PROF(ctx, PPRVIZ_K_FACTOR);
     float *Af = (float *)A;
-    k_fac_diag128<<<1, 1024, 0, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
+    k_fac_diag128<<<1, DIAG128_THREADS, DIAG128_SMEM, ctx->stream>>>(kp, 0, Af, (float *)P[0]);
     PPRVIZ_LAUNCHED(ctx);
     if (nblk > 1) {
       k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->stream>>>(kp, 0, A, P[0], Ct[0], Ut[0]);
@@ -1015,7 +1109,7 @@ static int spd_inverse(pprviz_ctx *ctx, int32_t kp, T *A, T *work) {
         PPRVIZ_LAUNCHED(ctx);
         PPRVIZ_CUDA(ctx, cudaEventRecord(ctx->ev_t1, ctx->stream));
         PPRVIZ_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_t1, 0));
-        k_fac_diag128<<<1, 1024, 0, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
+        k_fac_diag128<<<1, DIAG128_THREADS, DIAG128_SMEM, ctx->side>>>(kp, k1 * NB, Af, (float *)P[q ^ 1]);
         PPRVIZ_LAUNCHED(ctx);
         k_fac_panel<T, NB, TC><<<nblk, 256, panel_smem, ctx->side>>>(kp, k1 * NB, A, P[q ^ 1], Ct[q ^ 1], Ut[q ^ 1]);
         PPRVIZ_LAUNCHED(ctx);
@@ -1091,7 +1185,7 @@ __device__ __forceinline__ int find_slot(const int *__restrict__ off, int n, int
   return lo;
 }
 
-__global__ void __launch_bounds__(1024) k_fac_diag128_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
+__global__ void __launch_bounds__(DIAG128_THREADS) k_fac_diag128_batch(const FacJob *__restrict__ jobs, const int *__restrict__ act,
                                                             int32_t K0) {
   const FacJob j = jobs[act[blockIdx.x]];
   fac_diag128(j.kp, K0, j.A, j.P);
@@ -1186,6 +1280,8 @@ int spd_inverse_batch_f32(pprviz_ctx *ctx, int32_t nviews, const int32_t *kp, fl
   PPRVIZ_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
   const size_t panel_smem = sizeof(float) * (128 * 128 + 128 * (128 + 4));
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_panel_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+  PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_diag128_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        DIAG128_SMEM));
   PPRVIZ_CUDA(ctx, cudaFuncSetAttribute(k_fac_trailing_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SMEM));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
@@ -1194,7 +1290,7 @@ int spd_inverse_batch_f32(pprviz_ctx *ctx, int32_t nviews, const int32_t *kp, fl
     for (int kb = 0; kb < maxnb; ++kb) {
       const StepTab &st = steps[kb];
       const int32_t K0 = kb * 128;
-      k_fac_diag128_batch<<<(unsigned)st.nall, 1024, 0, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
+      k_fac_diag128_batch<<<(unsigned)st.nall, DIAG128_THREADS, DIAG128_SMEM, ctx->stream>>>(jobs_d, tab_d + st.act_all, K0);
       PPRVIZ_LAUNCHED(ctx);
       if (st.nmulti == 0) continue;
       k_fac_panel_batch<<<(unsigned)st.npan, 256, panel_smem, ctx->stream>>>(jobs_d, tab_d + st.act_multi,
