@@ -66,12 +66,25 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
 //   A[i][j]  = 1/k - 1/Delta_s^2 off the diagonal, identity on padded rows,
 //   rowpart[J][i] = sum over the tile's 32 columns of 1/Delta_s^2 (FP64);
 // k_build_diag then sets A[i][i] = sum_J rowpart[J][i] + 1/k in a fixed order.
+// Every consumer reads the upper triangle of 128-row blocks (diagonal 128
+// blocks in full), so tiles below the diagonal 128 blocks are not written: the
+// mirrored tile above supplies their row sums as its column sums (W1 and A are
+// symmetric entry by entry), and checks the mirrored inputs.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T recip(T d) { return T(1) / d; }
+template <>
+__device__ __forceinline__ float recip<float>(float d) { return __frcp_rn(d); }
+
 template <typename TI, typename T>
 __global__ void k_build_sym(int32_t k, int32_t kp, const TI *__restrict__ D, T *__restrict__ W1,
                             T *__restrict__ A, double *__restrict__ rowpart, int *__restrict__ flag) {
+  const int by = blockIdx.y, bx = blockIdx.x;
+  if ((by >> 2) > (bx >> 2)) return;  // below the diagonal 128 blocks
+  const bool mirror = (by >> 2) < (bx >> 2);
   __shared__ TI tr[32][33];
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  __shared__ double csum[8][33];
+  const int i0 = by * 32, j0 = bx * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int jj = ty; jj < 32; jj += 8) {
     const int j = j0 + jj, i = i0 + tx;
@@ -80,16 +93,18 @@ __global__ void k_build_sym(int32_t k, int32_t kp, const TI *__restrict__ D, T *
   __syncthreads();
   const T invk = (T)(1.0 / (double)k);
   int bad = 0;
+  double colacc = 0.0;  // column j0 + tx over this thread's rows
   for (int ii = ty; ii < 32; ii += 8) {
     const int i = i0 + ii, j = j0 + tx;
     double wsq_d = 0.0;
     if (i < k && j < k && i != j) {
       const TI a = D[(int64_t)i * k + j], b = tr[tx][ii];
-      // every input entry must itself be a valid distance (this element checks a;
-      // b is checked by the element (j, i))
+      // every input entry must itself be a valid distance (this element checks
+      // a; b is checked by the element (j, i), or here when that tile is not built)
       if (!(a > TI(0)) || !isfinite((double)a)) bad = 1;
+      if (mirror && (!(b > TI(0)) || !isfinite((double)b))) bad = 1;
       const T d = (T)((a + b) * TI(0.5));
-      const T w1 = T(1) / d;
+      const T w1 = recip(d);
       const T wsq = w1 * w1;
       W1[(int64_t)i * kp + j] = w1;
       A[(int64_t)i * kp + j] = invk - wsq;
@@ -98,8 +113,19 @@ __global__ void k_build_sym(int32_t k, int32_t kp, const TI *__restrict__ D, T *
       W1[(int64_t)i * kp + j] = T(0);
       if (i != j || i >= k) A[(int64_t)i * kp + j] = (i == j) ? T(1) : T(0);
     }
+    colacc += wsq_d;
     for (int o = 16; o > 0; o >>= 1) wsq_d += __shfl_xor_sync(0xffffffffu, wsq_d, o);
-    if (tx == 0) rowpart[(int64_t)blockIdx.x * kp + i] = wsq_d;
+    if (tx == 0) rowpart[(int64_t)bx * kp + i] = wsq_d;
+  }
+  if (mirror) {  // the row sums of the tile (bx, by) below: this tile's column sums
+    csum[ty][tx] = colacc;
+    __syncthreads();
+    if (ty == 0) {
+      double c = 0.0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) c += csum[e][tx];
+      rowpart[(int64_t)by * kp + j0 + tx] = c;
+    }
   }
   if (bad) atomicOr(flag, 1);
 }
