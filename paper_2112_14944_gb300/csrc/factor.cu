@@ -698,7 +698,7 @@ constexpr int NCH = NB / KC;                // chunks per tile
 constexpr int CROW = TM * 4 + 16;           // staged C row stride: 528 B, conflict-free 16-byte accesses
 constexpr int SMEM = NST * CHUNK + TM * CROW + 1024;
 constexpr int THREADS = 256;
-constexpr int SIDE_SMS = 16;                // SMs left to the next pivot's inverse and panel
+constexpr int SIDE_SMS = 8;                 // SMs left to the next pivot's inverse and panel
 }  // namespace tcp
 
 namespace {

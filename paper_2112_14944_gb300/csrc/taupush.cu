@@ -112,12 +112,12 @@ __global__ void k_tp_means(const int64_t *__restrict__ leaf_ptr, const int32_t *
 // Forward start (Algorithm 2, initial residues): r(V_i, v) = d(v) / |F(V_i)|
 // on the leaves of every source V_i; the leaves are marked for the collect pass.
 __global__ void k_tp_fwd_init(int64_t nleaf, const int64_t *__restrict__ leaf_ptr,
-                              const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ psup, int32_t K,
+                              const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ psup, int32_t KR,
                               const double *__restrict__ deg, double *__restrict__ R, uint8_t *__restrict__ dirty) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nleaf) return;
   const int32_t i = psup[p], v = leaf_idx[p];
-  R[(size_t)v * K + i] = deg[v] / (double)(leaf_ptr[i + 1] - leaf_ptr[i]);
+  R[(size_t)v * KR + i] = deg[v] / (double)(leaf_ptr[i + 1] - leaf_ptr[i]);
   dirty[v] = 1;
 }
 
@@ -125,14 +125,14 @@ __global__ void k_tp_fwd_init(int64_t nleaf, const int64_t *__restrict__ leaf_pt
 // the leaves of every refined target V_j (slot[j] >= 0).
 __global__ void k_tp_bwd_init(int64_t nleaf, const int64_t *__restrict__ leaf_ptr,
                               const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ psup,
-                              const int32_t *__restrict__ slot, int32_t K, double *__restrict__ R,
+                              const int32_t *__restrict__ slot, int32_t KR, double *__restrict__ R,
                               uint8_t *__restrict__ dirty) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nleaf) return;
   const int32_t j = psup[p], jb = slot[j];
   if (jb < 0) return;
   const int32_t v = leaf_idx[p];
-  R[(size_t)v * K + jb] = 1.0 / (double)(leaf_ptr[j + 1] - leaf_ptr[j]);
+  R[(size_t)v * KR + jb] = 1.0 / (double)(leaf_ptr[j + 1] - leaf_ptr[j]);
   dirty[v] = 1;
 }
 
@@ -142,18 +142,19 @@ __global__ void k_tp_bwd_init(int64_t nleaf, const int64_t *__restrict__ leaf_pt
 // walk's own self-loop at a node without out-edges was summed when its
 // residue was taken. The add is a reduction (no value read back).
 template <bool BWD>
-__device__ __forceinline__ void push_unit(int64_t q, int32_t v, const TpPair &pr, int32_t K,
+__device__ __forceinline__ void push_unit(int64_t q, int32_t v, const TpPair &pr, int32_t KR,
                                           double *__restrict__ R, const int64_t *__restrict__ rp,
                                           const int32_t *__restrict__ ncol, const float *__restrict__ nw,
                                           const double *__restrict__ invdw, uint8_t *__restrict__ dirty) {
   const int32_t x = ncol[q];
-  double add = pr.share * (nw ? (double)nw[q] : 1.0);
+  double add = pr.share;  // FP64 arithmetic is scarce on this GPU: no multiply by a unit weight
+  if (nw) add *= (double)nw[q];
   if (BWD) {
     if (x == v && rp[v + 1] == rp[v]) return;
     add *= invdw[x];
   }
-  if (!(add > 0.0)) return;
-  atomicAdd(&R[(size_t)x * K + pr.s], add);
+  if (__double_as_longlong(add) <= 0) return;  // add >= 0: skip the zero weights by the bits
+  atomicAdd(&R[(size_t)x * KR + pr.s], add);
   dirty[x] = 1;
 }
 
@@ -181,7 +182,7 @@ constexpr int32_t TP_PIECE = 1024;  // larger work is cut into pieces of at most
 template <bool BWD>
 __global__ void __launch_bounds__(TP_TPB, 4)
     k_tp_push(int64_t round, const TpRec *__restrict__ small, const TpRec *__restrict__ big,
-              const TpPair *__restrict__ pairs, int32_t K, double *__restrict__ R, const int64_t *__restrict__ rp,
+              const TpPair *__restrict__ pairs, int32_t KR, double *__restrict__ R, const int64_t *__restrict__ rp,
               const int32_t *__restrict__ ncol, const float *__restrict__ nw, const double *__restrict__ invdw,
               uint8_t *__restrict__ dirty, int64_t small_cap, int64_t big_cap, const TpCounters *__restrict__ cnt) {
   const int64_t S = min((int64_t)cnt->small[round], small_cap);  // beyond the caps only after an overflow
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(TP_TPB, 4)
           if (j < 32) {
             const int32_t o = (int32_t)(t - (j > 0 ? prev : 0));
             const int32_t ed = o / c;
-            push_unit<BWD>(q0 + ed, v, pairs[pb + (o - ed * c)], K, R, rp, ncol, nw, invdw, dirty);
+            push_unit<BWD>(q0 + ed, v, pairs[pb + (o - ed * c)], KR, R, rp, ncol, nw, invdw, dirty);
           }
         }
       }
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(TP_TPB, 4)
           const int32_t o = o0 + 32 * u + lane;
           if (o < work) {
             const int32_t ed = o / r.c;
-            push_unit<BWD>(r.q0 + ed, r.v, pairs[r.pb + (o - ed * r.c)], K, R, rp, ncol, nw, invdw, dirty);
+            push_unit<BWD>(r.q0 + ed, r.v, pairs[r.pb + (o - ed * r.c)], KR, R, rp, ncol, nw, invdw, dirty);
           }
         }
       }
@@ -249,6 +250,14 @@ __device__ __forceinline__ T warp_incl(T v, int lane) {
   return v;
 }
 
+// r > thr for non-negative doubles (residues and thresholds are >= 0, NaN
+// never occurs, INFINITY orders last) by their bit patterns: the ordering of
+// non-negative IEEE doubles is that of their bits as integers, and the
+// integer compare keeps the comparisons off this GPU's narrow FP64 pipe.
+__device__ __forceinline__ bool above(double r, double thr) {
+  return __double_as_longlong(r) > __double_as_longlong(thr);
+}
+
 // Collect pass (builds round `round`): one thread per node x; a dirty x has
 // its mark cleared and each residue above its threshold (forward
 // d(x) r_max, backward the target's thr_b) taken. Forward (Algorithm 2): the
@@ -262,7 +271,7 @@ __device__ __forceinline__ T warp_incl(T v, int lane) {
 // probability.
 template <bool BWD>
 __global__ void __launch_bounds__(TP_TPB)
-    k_tp_collect_front(int64_t round, int64_t n, int32_t K, double *__restrict__ R, double *__restrict__ Q,
+    k_tp_collect_front(int64_t round, int64_t n, int32_t K, int32_t KR, double *__restrict__ R, double *__restrict__ Q,
                        uint8_t *__restrict__ dirty, const int32_t *__restrict__ pos_of,
                        const int64_t *__restrict__ rp, const int64_t *__restrict__ nrp,
                        const double *__restrict__ deg, const double *__restrict__ invdw, double alpha, double r_max,
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(TP_TPB)
     int64_t q0 = 0;
     bool stays = false;
     double thr = 0.0, dx = 0.0;
-    double *Rx = R + (size_t)x * K;
+    double *Rx = R + (size_t)x * KR;  // KR even: 16-byte aligned pairs
     if (mine) {
       dirty[x] = 0;
       stays = rp[x + 1] == rp[x];
@@ -289,8 +298,12 @@ __global__ void __launch_bounds__(TP_TPB)
       dx = deg[x];
       thr = dx * r_max;
       // how many residues of x are above their thresholds
-#pragma unroll 8
-      for (int32_t sl = 0; sl < K; ++sl) c += Rx[sl] > (BWD ? thr_b[sl] : thr);
+#pragma unroll 4
+      for (int32_t sl = 0; sl < K; sl += 2) {
+        const double2 r2 = *reinterpret_cast<const double2 *>(Rx + sl);
+        c += above(r2.x, BWD ? thr_b[sl] : thr);
+        if (sl + 1 < K) c += above(r2.y, BWD ? thr_b[sl + 1] : thr);
+      }
     }
     const bool listed = ne > 0 && c > 0;
     const int64_t work = (int64_t)ne * c;
@@ -322,11 +335,19 @@ __global__ void __launch_bounds__(TP_TPB)
     const int64_t pb = (int64_t)pb0 + pin - pc, sb = (int64_t)sb0 + sin_ - nsm, bb = (int64_t)bb0 + bin - npc;
     const bool fits = pb + pc <= pair_cap && sb + nsm <= small_cap && bb + npc <= big_cap;
     if (!fits) atomicOr(&cnt->overflow, 1);
+    double rnext = 0.0;
     int32_t k = 0;
     const double inv = invdw[x];
     for (int32_t sl = 0; sl < K; ++sl) {
-      const double r = Rx[sl];
-      if (!(r > (BWD ? thr_b[sl] : thr))) continue;
+      double r;
+      if ((sl & 1) == 0) {
+        const double2 r2 = *reinterpret_cast<const double2 *>(Rx + sl);
+        r = r2.x;
+        rnext = r2.y;
+      } else {
+        r = rnext;
+      }
+      if (!above(r, BWD ? thr_b[sl] : thr)) continue;
       Rx[sl] = 0.0;
       double share;
       if (!BWD) {
@@ -504,11 +525,12 @@ int tp_phase(pprviz_ctx *ctx, const pprviz_graph *g, const TpBufs &B, int32_t K,
   const float *nw = BWD ? pull_w(g) : (g->weighted ? g->w.as<float>() : nullptr);
   const double *deg = g->deg.as<double>();
   const double *invdw = g->invdw_d.as<double>();
+  const int32_t KR = (K + 1) & ~1;  // residue row stride (even)
   const unsigned grid = 152 * 8;
   auto collect = [&](int64_t r) -> int {
     {
       PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH);
-      k_tp_collect_front<BWD><<<grid, TP_TPB, 0, ctx->stream>>>(r, n, K, B.R, B.Q, B.dirty, B.pos_of, rp, nrp, deg,
+      k_tp_collect_front<BWD><<<grid, TP_TPB, 0, ctx->stream>>>(r, n, K, KR, B.R, B.Q, B.dirty, B.pos_of, rp, nrp, deg,
                                                                 invdw, alpha, r_max, thr_b, B.small, B.big, B.pairs,
                                                                 B.small_cap, B.big_cap, B.pair_cap, B.cnt);
     }
@@ -523,7 +545,7 @@ int tp_phase(pprviz_ctx *ctx, const pprviz_graph *g, const TpBufs &B, int32_t K,
     for (int b = 0; b < batch && r < TP_MAX_ROUNDS; ++b, ++r) {
       {
         PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH);
-        k_tp_push<BWD><<<grid, TP_TPB, 0, ctx->stream>>>(r, B.small, B.big, B.pairs, K, B.R, rp, ncol, nw, invdw,
+        k_tp_push<BWD><<<grid, TP_TPB, 0, ctx->stream>>>(r, B.small, B.big, B.pairs, KR, B.R, rp, ncol, nw, invdw,
                                                          B.dirty, B.small_cap, B.big_cap, B.cnt);
       }
       PPRVIZ_LAUNCHED(ctx);
@@ -583,7 +605,8 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
   const int64_t small_cap = n;
   const int64_t big_cap = n + nnz_max / std::max<int64_t>(1, TP_PIECE / K) + 1;
   const int64_t pair_cap = n * K;
-  PPRVIZ_TRY(ws_ensure(ctx, WS_TPR, sizeof(double) * (size_t)(n * K)));
+  const int64_t KR = (K + 1) & ~(int64_t)1;  // residue row stride: even, so that rows are 16-byte aligned
+  PPRVIZ_TRY(ws_ensure(ctx, WS_TPR, sizeof(double) * (size_t)(n * KR)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPQ, sizeof(double) * (size_t)(nleaf * K)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPFA, sizeof(TpRec) * (size_t)(small_cap + big_cap)));
   PPRVIZ_TRY(ws_ensure(ctx, WS_TPFB, sizeof(TpPair) * (size_t)pair_cap));
@@ -647,12 +670,12 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
   inf.backward_targets = Kb;
 
   // forward phase (GFP from every child)
-  PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.R, 0, sizeof(double) * (size_t)(n * K), ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.R, 0, sizeof(double) * (size_t)(n * KR), ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.Q, 0, sizeof(double) * (size_t)(nleaf * K), ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(TpCounters), ctx->stream));
   PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.dirty, 0, (size_t)n, ctx->stream));
   if (std::isfinite(r_max)) {
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_fwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, (int32_t)K, deg, B.R, B.dirty); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_fwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, (int32_t)KR, deg, B.R, B.dirty); }
     PPRVIZ_LAUNCHED(ctx);
     int64_t rounds = 0, pushes = 0, edges = 0;
     const int st = tp_phase<false>(ctx, g, B, (int32_t)K, alpha, r_max, nullptr, &rounds, &pushes, &edges);
@@ -679,11 +702,11 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
                                      ctx->stream));
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(tsel, tsel_h.data(), sizeof(int32_t) * (size_t)Kb, cudaMemcpyHostToDevice,
                                      ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.R, 0, sizeof(double) * (size_t)(n * Kb), ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.R, 0, sizeof(double) * (size_t)(n * ((Kb + 1) & ~1)), ctx->stream));
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.Q, 0, sizeof(double) * (size_t)(nleaf * Kb), ctx->stream));
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(TpCounters), ctx->stream));
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(B.dirty, 0, (size_t)n, ctx->stream));
-    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_bwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, slot, Kb, B.R, B.dirty); }
+    { PPRVIZ_PROF(ctx, PPRVIZ_K_PUSH); k_tp_bwd_init<<<blocks_for(nleaf, TP_TPB), TP_TPB, 0, ctx->stream>>>(nleaf, leaf_ptr_d, leaf_idx_d, B.psup, slot, (Kb + 1) & ~1, B.R, B.dirty); }
     PPRVIZ_LAUNCHED(ctx);
     int64_t rounds = 0, pushes = 0, edges = 0;
     const int st = tp_phase<true>(ctx, g, B, Kb, alpha, 0.0, thr_b, &rounds, &pushes, &edges);
