@@ -698,32 +698,65 @@ __global__ void k_init_defl_batch(int64_t nrows, int64_t ld, int64_t row0, int32
 // out[(g0 + q) * k + r] = d(view[g0+q]) * dw(view[r]) * (y_hi + y_lo)[view[r]][q]
 // for q < gvalid, r < k: DPPR rows of the group, transposed through shared
 // memory so that both the state reads and the output writes are coalesced.
+// FP32 state: the products in float-float arithmetic (TwoProd by FMA) with dw
+// as its float pair, ~2^-46 relative: GB300's FP64 rate is too low to spend a
+// division per entry. FP64 state: FP64 arithmetic.
 template <typename T, typename TO>
 __global__ void k_extract(int32_t k, int32_t g0, int32_t gvalid, int64_t ld,
                           const int32_t *__restrict__ view, const double *__restrict__ deg,
-                          const double *__restrict__ invdw, const T *__restrict__ yhi,
-                          const float *__restrict__ ylo, TO *__restrict__ out) {
-  __shared__ double tile[32][33];
+                          const double *__restrict__ invdw, const float2 *__restrict__ dwff,
+                          const T *__restrict__ yhi, const float *__restrict__ ylo, TO *__restrict__ out) {
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int rr = ty; rr < 32; rr += 8) {
-    const int r = r0 + rr, q = q0 + tx;
-    double v = 0.0;
-    if (r < k && q < gvalid) {
-      const int32_t t = view[r];
-      const int64_t p = (int64_t)t * ld + q;
-      double y = (double)yhi[p];
-      if (ylo) y += (double)ylo[p];
-      v = y / invdw[t];
+  if constexpr (std::is_same<T, float>::value) {
+    __shared__ float2 tile[32][33];
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int r = r0 + rr, q = q0 + tx;
+      float2 v = make_float2(0.0f, 0.0f);
+      if (r < k && q < gvalid) {
+        const int32_t t = view[r];
+        const int64_t p = (int64_t)t * ld + q;
+        const float yh = yhi[p], yl = ylo ? ylo[p] : 0.0f;
+        const float2 dw = dwff[t];
+        const float ph = yh * dw.x;
+        v = make_float2(ph, fmaf(yh, dw.x, -ph) + fmaf(yh, dw.y, yl * dw.x));
+      }
+      tile[rr][tx] = v;
     }
-    tile[rr][tx] = v;
-  }
-  __syncthreads();
-  for (int qq = ty; qq < 32; qq += 8) {
-    const int q = q0 + qq, r = r0 + tx;
-    if (q < gvalid && r < k) {
-      const double ds = deg[view[g0 + q]];
-      out[(int64_t)(g0 + q) * k + r] = (TO)(ds * tile[tx][qq]);
+    __syncthreads();
+    for (int qq = ty; qq < 32; qq += 8) {
+      const int q = q0 + qq, r = r0 + tx;
+      if (q < gvalid && r < k) {
+        const double ds = deg[view[g0 + q]];
+        const float sh = (float)ds, sl = (float)(ds - (double)sh);
+        const float2 v = tile[tx][qq];
+        const float oh = sh * v.x;
+        const float ol = fmaf(sh, v.x, -oh) + fmaf(sh, v.y, sl * v.x);
+        if constexpr (std::is_same<TO, float>::value) out[(int64_t)(g0 + q) * k + r] = oh + ol;
+        else out[(int64_t)(g0 + q) * k + r] = (double)oh + (double)ol;
+      }
+    }
+  } else {
+    __shared__ double tile[32][33];
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int r = r0 + rr, q = q0 + tx;
+      double v = 0.0;
+      if (r < k && q < gvalid) {
+        const int32_t t = view[r];
+        const int64_t p = (int64_t)t * ld + q;
+        double y = (double)yhi[p];
+        if (ylo) y += (double)ylo[p];
+        v = y / invdw[t];
+      }
+      tile[rr][tx] = v;
+    }
+    __syncthreads();
+    for (int qq = ty; qq < 32; qq += 8) {
+      const int q = q0 + qq, r = r0 + tx;
+      if (q < gvalid && r < k) {
+        const double ds = deg[view[g0 + q]];
+        out[(int64_t)(g0 + q) * k + r] = (TO)(ds * tile[tx][qq]);
+      }
     }
   }
 }
@@ -1378,17 +1411,17 @@ int dppr_solve(pprviz_ctx *ctx, const pprviz_graph *g, const int32_t *view_d,
       if (fp64) {
         if (out64)
           { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<double, double><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
-              g->invdw_d.as<double>(), (const double *)yhi, nullptr, (double *)dppr_d); }
+              g->invdw_d.as<double>(), g->dwff.as<float2>(), (const double *)yhi, nullptr, (double *)dppr_d); }
         else
           { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<double, float><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
-              g->invdw_d.as<double>(), (const double *)yhi, nullptr, (float *)dppr_d); }
+              g->invdw_d.as<double>(), g->dwff.as<float2>(), (const double *)yhi, nullptr, (float *)dppr_d); }
       } else {
         if (out64)
           { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<float, double><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
-              g->invdw_d.as<double>(), (const float *)yhi, ylo, (double *)dppr_d); }
+              g->invdw_d.as<double>(), g->dwff.as<float2>(), (const float *)yhi, ylo, (double *)dppr_d); }
         else
           { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<float, float><<<grid, block, 0, ctx->stream>>>(k, g0, gvalid, ld, view_d, g->deg.as<double>(),
-              g->invdw_d.as<double>(), (const float *)yhi, ylo, (float *)dppr_d); }
+              g->invdw_d.as<double>(), g->dwff.as<float2>(), (const float *)yhi, ylo, (float *)dppr_d); }
       }
       PPRVIZ_LAUNCHED(ctx);
     }
@@ -2119,7 +2152,8 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
         dim3 block(32, 8);
         { PPRVIZ_PROF(ctx, PPRVIZ_K_EXTRACT); k_extract<float, float><<<grid, block, 0, ctx->stream>>>(
             (int32_t)g->n, (int32_t)g0, (int32_t)gv, ld, iota_d, U.deg.as<double>() + uoff[v],
-            U.invdw_d.as<double>() + uoff[v], hi + rs * ld, lo ? lo + rs * ld : nullptr, dppr_w + doff[w]); }
+            U.invdw_d.as<double>() + uoff[v], U.dwff.as<float2>() + uoff[v], hi + rs * ld,
+            lo ? lo + rs * ld : nullptr, dppr_w + doff[w]); }
         PPRVIZ_LAUNCHED(ctx);
       }
     }
