@@ -1221,6 +1221,9 @@ def run_ours(args, rank, world, local_rank):
                    "sweeps_per_step": sweeps / args.steps, "final_stress": stress,
                    "wall_s_timed_region": wall},
         "roofline": roof, "roofline_kernels": kernels, "kernel_share": share,
+        "kernel_share_note": "per class and step: the mean CUDA-event duration of the class's timed launches "
+                             "times all its launches; classes overlap (the inverse's lookahead stream, "
+                             "programmatic dependent launches of the row reduces), so the sum exceeds the step",
         "gpu_launches": int(launches), "errors": errors, "vs_fp64_gpu": fp64,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": sampler.summary(),
     }
