@@ -968,7 +968,7 @@ cudaError_t launch_dependent(pprviz_ctx *ctx, void (*kernel)(P...), unsigned gri
 // L2 bytes of each pass matrix kept resident across updates (evict_last):
 // the two matrices together stay well inside the 126 MB L2 next to the
 // partial sums and coordinates; the rest of each matrix streams from HBM
-constexpr double kPinBytes = 40.0 * 1024 * 1024;
+constexpr double kPinBytes = 32.0 * 1024 * 1024;
 
 int pass_pair(pprviz_ctx *ctx, unsigned grid, const PassTables &pt, const CUtensorMap *maps, const BatchView *views_d,
               float2 *X, float2 *Bv, float2 *Part, float2 *RunPart, int *perr) {
