@@ -411,7 +411,7 @@ __device__ __forceinline__ void load4(const double *hi, const float *lo, double 
 // (Sec. 3.2, Eq. (2)): b_jq = alpha d(j) / |F(V_q)| for the leaves j of V_q,
 // given per node by src[j] = its supernode (-1 for none) and bscale[j] =
 // d(j) / |F(V_src[j])| in FP64, so the residual is exact for that b.
-template <typename T, bool WEIGHTED, bool EXACT, bool BATCH, bool LEVEL>
+template <typename T, bool WEIGHTED, bool EXACT, bool BATCH, bool LEVEL, bool LO = true>
 __global__ void __launch_bounds__(kWarps * 32)
 k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
            const float *__restrict__ w, const double *__restrict__ invdw, const float2 *__restrict__ dwff,
@@ -489,7 +489,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
             if (t0 + q < cnt) {
               const int64_t p = ((int64_t)i - rb) * ld + off;
               Vec<float>::load(reinterpret_cast<const float *>(yhi) + p, h[q]);
-              if (ylo) Vec<float>::load(ylo + p, l[q]);
+              if (LO && ylo) Vec<float>::load(ylo + p, l[q]);
             }
           }
 #pragma unroll
@@ -507,7 +507,7 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
               const float bb = s - shi[u];
               sc[u] += ((shi[u] - (s - bb)) + (a - bb)) + pe;
               shi[u] = s;
-              if (ylo) slo[u] = fmaf(wi, l[q][u], slo[u]);
+              if (LO && ylo) slo[u] = fmaf(wi, l[q][u], slo[u]);
             }
           }
         }
@@ -525,10 +525,10 @@ k_residual(int64_t n, int64_t ld, const int64_t *__restrict__ rp, const int32_t 
       const float dwh = dwp.x, dwl = dwp.y;
       float hrow[VEC], lrow[VEC];
       Vec<float>::load(reinterpret_cast<const float *>(yhi) + rowoff, hrow);
-      if (ylo) Vec<float>::load(ylo + rowoff, lrow);
+      if (LO && ylo) Vec<float>::load(ylo + rowoff, lrow);
 #pragma unroll
       for (int u = 0; u < VEC; ++u) {
-        if (!ylo) lrow[u] = 0.0f;
+        if (!(LO && ylo)) lrow[u] = 0.0f;
         // S = shi + ah + al + slo (the neighbour sum), as float-float
         float Sh = shi[u] + ah[u];
         const float bb = Sh - shi[u];
@@ -979,15 +979,17 @@ int launch_residual(pprviz_ctx *ctx, const pprviz_graph *g, int64_t ld, const in
   const int64_t row0 = wv ? wv->row0 : 0;
   const int32_t g0 = wv ? wv->g0 : level_g0;
   if (wv) src = wv->lidx;
-#define PPRVIZ_RES(W, B, L)                                                                                  \
-  k_residual<T, W, EXACT, B, L><<<grid, kWarps * 32, 0, ctx->stream>>>(                                        \
+#define PPRVIZ_RES(W, B, L, LOW)                                                                             \
+  k_residual<T, W, EXACT, B, L, LOW><<<grid, kWarps * 32, 0, ctx->stream>>>(                                   \
       n, ld, pull_rp(g), pull_col(g), w, g->invdw_d.as<double>(), g->dwff.as<float2>(), src,                   \
       yhi, ylo, rhs_out, part, alpha, 1.0 - alpha, brows, row0, g0, bscale)
   {
     PPRVIZ_PROF(ctx, PPRVIZ_K_RESIDUAL);
-    if (wv) { if (pull_weighted(g)) PPRVIZ_RES(true, true, false); else PPRVIZ_RES(false, true, false); }
-    else if (bscale) { if (pull_weighted(g)) PPRVIZ_RES(true, false, true); else PPRVIZ_RES(false, false, true); }
-    else { if (pull_weighted(g)) PPRVIZ_RES(true, false, false); else PPRVIZ_RES(false, false, false); }
+    if (wv) { if (pull_weighted(g)) PPRVIZ_RES(true, true, false, true); else PPRVIZ_RES(false, true, false, true); }
+    else if (bscale) { if (pull_weighted(g)) PPRVIZ_RES(true, false, true, true); else PPRVIZ_RES(false, false, true, true); }
+    else if (pull_weighted(g)) PPRVIZ_RES(true, false, false, true);
+    else if (ylo) PPRVIZ_RES(false, false, false, true);
+    else PPRVIZ_RES(false, false, false, false);  // no low parts: a lighter instance (fewer registers)
   }
 #undef PPRVIZ_RES
   PPRVIZ_LAUNCHED(ctx);
