@@ -117,7 +117,7 @@ def parse():
                     help="one untimed pass of the hot path (for profiler command lines)")
     ap.add_argument("--dense-precision", default="bf16", choices=["bf16", "tf32x3"],
                     help="tensor-core sweep operands of --workload dense (the other mode is timed beside it)")
-    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small", "taupush"],
+    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small", "taupush", "level", "directed", "metrics"],
                     help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000); "
                          "views: the 256 batched SBM views; taupush: Tau-Push queries on the 2M-node graph")
     return ap.parse_args()
@@ -808,6 +808,233 @@ def run_taupush(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- level-l DPPR, directed, metrics
+LEVEL_WORKLOAD = "chung_lu_n2000000_deg10_level1_k25x25"
+DIRECTED_WORKLOAD = "directed_chung_lu_n10000_deg20"
+METRICS_WORKLOAD = "layout_n10000_nd_ulcv"
+
+
+def _timed_steps(args, stream, flush, step):
+    """Warm-up, then args.steps steps between CUDA events on `stream` with the
+    L2 flushed before each and the clocks sampled; returns (ms per step list,
+    last step's result, clock summary)."""
+    import torch
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier_if_group()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms, out = [], None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    sampler.stop()
+    return ms, out, sampler.summary()
+
+
+def run_level(args, rank, world, local_rank):
+    """Exact level-l DPPR (Sec. 3.2, Definition 2, Eq. (2)) for the Tau-Push
+    queries of `--workload taupush`: the 2M-node Chung-Lu graph, 8 level-1
+    supernodes of 25 children x 25 leaves (seeds 1000..1007); one certified
+    FP32 propagation per child from its group start, eps = 1e-6; one step =
+    the 8 queries."""
+    import torch
+
+    import oracle as O
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = synth.chung_lu(2_000_000, 10, 2.5, seed=0)
+    k = 25
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    G = ctx.upload_graph(g)
+    qs = [synth.random_leaf_sets(g.n, [25] * k, seed=1000 + q) for q in range(TP_QUERIES)]
+    sets = [[b[a[i]:a[i + 1]] for i in range(k)] for a, b in qs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    state = {}
+
+    def step():
+        outs, launches, sweeps, bsweep, cmax = [], 0, 0, 0.0, 0.0
+        for ls in sets:
+            D, _, cert, st = ctx.level_dppr(G, ls, ALPHA, EPS, out64=True)
+            assert st == 0 and cert.max() <= EPS
+            s = ctx.stats()
+            launches += s["kernel_launches"]
+            sweeps += s["sweeps_main"] + s["sweeps_refine"]
+            cmax = max(cmax, float(cert.max()))
+            outs.append(D)
+        # 12 B per (node, source) and sweep: y_k and y_k-1 read, y_k+1 written
+        state.update(launches=launches, sweeps=sweeps, bytes_per_sweep=12.0 * g.n * s["source_group"], cmax=cmax)
+        return outs
+
+    ctx.profile(PROF_EVERY)
+    ms, outs, clocks = _timed_steps(args, stream, flush, step)
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    total = max_over_ranks(sum(ms), dev)
+    if rank != 0:
+        return
+    hbm, _, peak_kind = peaks()
+    sw_ms, sw_all, sw_n = ktimes["sweep"]
+    per = state["bytes_per_sweep"]
+    ach = per / (sw_ms / max(1, sw_n) / 1e3) / 1e9 if sw_n else None
+    roof = {"kernel": "propagation sweep (k_sweep_sp): the [2M][128] state streams from HBM", "bound": "hbm",
+            "alg_bytes_per_launch": per,
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+            "avg_launch_us": 1e3 * sw_ms / max(1, sw_n), "traffic": None,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
+    # query 0, row 0 against the oracle's group-start power iteration
+    Pm = O.transition_matrix(g.n, g.row_ptr, g.col)
+    d = O.degrees(g.n, g.row_ptr, g.col)
+    exact = O.level_dppr_rows_power(Pm, d, [x.astype(np.int64) for x in sets[0]], [0], ALPHA, tol=1e-12)[0]
+    err = float(np.abs(outs[0][0] - exact).max())
+    line = {
+        "metric": "exact level-l DPPR queries/s (25 children x 25 leaves, eps 1e-6), 2M-node power-law graph",
+        "value": whole_job_rate(float(TP_QUERIES), args.steps, world, total), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "ms_per_query": total / args.steps / TP_QUERIES, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": LEVEL_WORKLOAD, "graph": "chung-lu", "n": g.n, "mean_degree": 10, "exponent": 2.5,
+                   "seed": 0, "queries_per_step": TP_QUERIES, "query": "the taupush workload's queries",
+                   "alpha": ALPHA, "eps": EPS, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "sweeps_per_step": state["sweeps"] / 1.0, "max_cert": state["cmax"],
+        "errors": {"query0_row0_max_abs_vs_oracle": err, "oracle_tol": 1e-12},
+        "roofline": roof, "kernel_share": class_share(ktimes, args.steps + args.warmup),
+        "gpu_launches": int(state["launches"] * args.steps), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_directed(args, rank, world, local_rank):
+    """Directed input (Sec. 2.1): the n = 10k Chung-Lu graph (mean degree 20,
+    seed 0) made directed (each edge kept both ways with probability 0.3,
+    otherwise one random way; 2 % of the nodes dangling; seed 0); all-pairs
+    FP32 DPPR + PDist with the FP64 certificate (power sweeps: the walk is not
+    reversible), eps = 1e-6."""
+    import torch
+
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = synth.directed_from(synth.chung_lu(10000, 20, 2.5, seed=0), p_both=0.3, dangling=0.02, seed=0)
+    n = g.n
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    G = ctx.upload_graph(g)
+    view = torch.arange(n, dtype=torch.int32, device=dev)
+    D = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Dl = torch.empty_like(D)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    state = {}
+
+    def step():
+        _, _, cert, st = ctx.dppr(G, view, ALPHA, EPS, P.FP32, dppr_out=D, pdist_out=Dl, cert=True)
+        s = ctx.stats()
+        state.update(st=st, cert=cert, launches=s["kernel_launches"], sweeps=s["sweeps_main"] + s["sweeps_refine"],
+                     bsweep=s["bytes_sweep"])
+        return st
+
+    ctx.profile(PROF_EVERY)
+    ms, _, clocks = _timed_steps(args, stream, flush, step)
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    assert state["st"] == 0 and float(state["cert"].max()) <= EPS
+    total = max_over_ranks(sum(ms), dev)
+    errors = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        src = synth.sample_view(n, 16, seed=1)
+        errors = oracle_errors(g, src, D[torch.from_numpy(src).to(dev).long()].cpu().numpy(),
+                               Dl[torch.from_numpy(src).to(dev).long()].cpu().numpy(), state["cert"])
+    if rank != 0:
+        return
+    hbm, _, peak_kind = peaks()
+    sw_ms, sw_all, sw_n = ktimes["sweep"]
+    per = state["bsweep"] / max(1, sw_all / (args.steps + args.warmup))
+    ach = per / (sw_ms / max(1, sw_n) / 1e3) / 1e9 if sw_n else None
+    roof = {"kernel": "propagation sweep (k_sweep_sp, power sweeps over the pull CSR)", "bound": "hbm",
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+            "avg_launch_us": 1e3 * sw_ms / max(1, sw_n), "traffic": None,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
+    line = {
+        "metric": "DPPR entries/s, directed Chung-Lu n=10k, err<=1e-6 vs FP64 (DPPR + PDist)",
+        "value": whole_job_rate(float(n) * n, args.steps, world, total), "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": DIRECTED_WORKLOAD, "graph": "directed chung-lu", "n": n, "nnz": int(g.nnz),
+                   "p_both": 0.3, "dangling": 0.02, "seed": 0, "alpha": ALPHA, "eps": EPS,
+                   "view": "all nodes (k = n)", "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "sweeps_per_step": state["sweeps"], "max_cert": float(state["cert"].max()), "errors": errors,
+        "roofline": roof, "kernel_share": class_share(ktimes, args.steps + args.warmup),
+        "gpu_launches": int(state["launches"] * args.steps), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_metrics(args, rank, world, local_rank):
+    """ND and ULCV (Sec. 2) of a 10,000-node layout: U[-1,1]^2 coordinates
+    (seed 0) of the n = 10k Chung-Lu graph (mean degree 20, seed 0); ND over
+    the 5.0e7 pairs, ULCV over the 99,665 edges, FP64 arithmetic; one step =
+    one pprviz_layout_metrics call on device buffers."""
+    import torch
+
+    import oracle as O
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = synth.chung_lu(10000, 20, 2.5, seed=0)
+    n = g.n
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    G = ctx.upload_graph(g)
+    xh = synth.uniform_x0(n, seed=0)
+    x = torch.from_numpy(xh).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ms, res, clocks = _timed_steps(args, stream, flush, lambda: ctx.layout_metrics(x, G))
+    launches = ctx.stats()["kernel_launches"]
+    total = max_over_ranks(sum(ms), dev)
+    if rank != 0:
+        return
+    nd, ul = res
+    iu = np.triu_indices(n, 1)
+    e = np.stack([np.repeat(np.arange(n), np.diff(g.row_ptr)), g.col], 1)
+    e = e[e[:, 0] < e[:, 1]]
+    nd_ref = O.node_distribution(xh.astype(np.float64))
+    ul_ref = O.ulcv(xh.astype(np.float64), e)
+    pairs = n * (n - 1) / 2
+    fp64 = 1250.0  # GB300 nominal FP64 (vector) TFLOP/s x 1000 = GFLOP/s
+    ach = 7.0 * pairs / (total / args.steps / 1e3) / 1e9
+    line = {
+        "metric": "layout metrics (ND over all pairs + ULCV over the edges) of a 10,000-node layout, ms per call",
+        "value": total / args.steps, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": METRICS_WORKLOAD, "graph": "chung-lu", "n": n, "pairs": int(pairs), "edges": int(len(e)),
+                   "coordinates": "U[-1,1]^2 (seed 0)", "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "errors": {"nd_rel": abs(nd - nd_ref) / abs(nd_ref), "ulcv_rel": abs(ul - ul_ref) / abs(ul_ref)},
+        "roofline": {"kernel": "k_nd (FP64 per pair: 2 sub, 2 mul, add, divide, accumulate)", "bound": "alu",
+                     "achieved": ach, "peak": fp64, "unit": "GFLOP/s (FP64, 7 per pair)", "frac": ach / fp64,
+                     "peak_kind": "nominal FP64 rate of the part (1.25 TFLOP/s), not measured", "traffic": None},
+        "gpu_launches": int(launches * args.steps), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- view of a 2M-node graph
 VIEW2M_WORKLOAD = "chung_lu_n2000000_deg10_view8192"
 
@@ -1252,6 +1479,12 @@ def main():
         run_views(args, rank, world, local_rank)
     elif args.workload == "taupush":
         run_taupush(args, rank, world, local_rank)
+    elif args.workload == "level":
+        run_level(args, rank, world, local_rank)
+    elif args.workload == "directed":
+        run_directed(args, rank, world, local_rank)
+    elif args.workload == "metrics":
+        run_metrics(args, rank, world, local_rank)
     elif args.workload == "view2m":
         run_view2m(args, rank, world, local_rank)
     elif args.workload == "small":
