@@ -6,3 +6,7 @@ Python binding) never imports, links or executes anything here.
 """
 from .pprviz_oracle import *  # noqa: F401,F403
 from .pprviz_oracle import __all__  # noqa: F401
+from .hierarchy import *  # noqa: F401,F403,E402
+from .hierarchy import __all__ as _hier_all  # noqa: E402
+
+__all__ = list(__all__) + list(_hier_all)

@@ -575,3 +575,97 @@ def test_level_dppr_rows_power_matches_the_definition():
         P, d, exact = _tp_exact(n, rp, col, w, leaf_sets, ALPHA)
         rows = O.level_dppr_rows_power(P, d, leaf_sets, [0, 2, 3], ALPHA)
         assert np.abs(rows - exact[[0, 2, 3]]).max() < 1e-13, name
+
+
+# --------------------------------------------------------------------------
+# Louvain+ hierarchy (Sec. 5 preprocessing; Appendix A merge rules)
+# --------------------------------------------------------------------------
+def test_louvain_gain_is_the_change_of_newman_modularity():
+    """Q^(S, T) summed from the appendix's q(V_i, T) must equal the change of
+    the partition's modularity (Newman's definition, brute force over the
+    leaf edges) when S is merged into T, for level nodes that are groups of
+    leaves and for S and T that are groups of level nodes."""
+    rng = np.random.default_rng(3)
+    for trial in range(12):
+        n = int(rng.integers(8, 30))
+        edges = {(int(a), int(b)) for a, b in rng.integers(0, n, size=(3 * n, 2)) if a != b}
+        row_ptr, col = _csr_from_edges(n, edges, undirected=True)
+        if row_ptr[-1] == 0:
+            continue
+        # level nodes: random groups of leaves; supernodes S, T: random sets of level nodes
+        nl = int(rng.integers(3, min(n, 10) + 1))
+        level_of_leaf = [int(x) for x in rng.permutation(np.arange(n) % nl)]
+        leaves_of = {A: [u for u in range(n) if level_of_leaf[u] == A] for A in range(nl)}
+        nodes = [int(x) for x in rng.permutation(nl)]
+        cut = int(rng.integers(1, nl))
+        S = set(nodes[:cut])
+        T = set(nodes[cut:cut + int(rng.integers(1, nl - cut + 1))])
+        # partition of the leaves before (each level node alone, T as one community) and after
+        def part_of(merge):
+            part = []
+            for u in range(n):
+                A = level_of_leaf[u]
+                if A in T or (merge and A in S):
+                    part.append(-1)
+                elif A in S:
+                    part.append(-2)  # S as one community before the merge
+                else:
+                    part.append(A)
+            return part
+        before = O.modularity(row_ptr, col, part_of(False))
+        after = O.modularity(row_ptr, col, part_of(True))
+        gain = O.louvain_gain(S, T, leaves_of, row_ptr, col, level_of_leaf)
+        assert gain == after - before, trial
+
+
+def test_louvain_plus_splits_two_cliques_at_the_bridge():
+    """Two 4-cliques joined by one edge: modularity's textbook optimum puts
+    each clique in its own community (k = 4 forbids nothing else)."""
+    edges = [(a, b) for a in range(4) for b in range(a + 1, 4)]
+    edges += [(a + 4, b + 4) for a, b in edges] + [(3, 4)]
+    row_ptr, col = _csr_from_edges(8, edges, undirected=True)
+    levels = O.louvain_plus(8, row_ptr, col, 4)
+    assert len(levels) == 1
+    assert levels[0].tolist() == [0, 0, 0, 0, 1, 1, 1, 1]
+    assert O.louvain_plus(8, row_ptr, col, 8) == []  # n <= k: the leaves fit one view
+
+
+def test_louvain_plus_rule_i_on_a_star_and_a_path():
+    """Rule (i) by hand. Star of 6 leaves, k = 4: every leaf's only neighbour
+    is the hub, which takes leaves 1-3 (cap 4); leaves 4-6 stay alone.
+    Path 0-..-5, k = 2: the ends join their neighbours by rule (i), the
+    middle pair by rule (ii) (gain 2m - 2*2*2 > 0); at level 2 the first
+    pair takes the middle pair (rule (i)), the last pair is left by the cap."""
+    row_ptr, col = _csr_from_edges(7, [(0, i) for i in range(1, 7)], undirected=True)
+    levels = O.louvain_plus(7, row_ptr, col, 4)
+    assert [p.tolist() for p in levels] == [[0, 0, 0, 0, 1, 2, 3]]
+    row_ptr, col = _csr_from_edges(6, [(i, i + 1) for i in range(5)], undirected=True)
+    levels = O.louvain_plus(6, row_ptr, col, 2)
+    assert [p.tolist() for p in levels] == [[0, 0, 1, 1, 2, 2], [0, 0, 1]]
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_louvain_plus_hierarchy_invariants(k):
+    """On a connected power-law graph: every supernode has at most k
+    children, every level is onto 0..n_l-1 and numbered by smallest child,
+    every level is smaller than the one below, and the top has at most k
+    supernodes."""
+    g = synth.chung_lu(160, 5, 2.5, seed=2)
+    # keep the largest connected component's guarantee simple: join the graph by a path
+    edges = {(u, int(v)) for u in range(g.n) for v in g.col[g.row_ptr[u]:g.row_ptr[u + 1]] if u < v}
+    edges |= {(i, i + 1) for i in range(g.n - 1)}
+    row_ptr, col = _csr_from_edges(g.n, edges, undirected=True)
+    levels = O.louvain_plus(g.n, row_ptr, col, k)
+    assert levels
+    n_prev = g.n
+    for p in levels:
+        assert len(p) == n_prev
+        n_l = int(p.max()) + 1
+        assert n_l < n_prev
+        counts = np.bincount(p, minlength=n_l)
+        assert counts.min() >= 1 and counts.max() <= k
+        first = [int(p[np.flatnonzero(p == s)[0]]) for s in range(n_l)]
+        firsts = [int(np.flatnonzero(p == s)[0]) for s in range(n_l)]
+        assert first == list(range(n_l)) and firsts == sorted(firsts)
+        n_prev = n_l
+    assert n_prev <= k
