@@ -24,7 +24,9 @@ PDist among the view, then the stress energy and its backward through the
 autograd function). `--workload small`: the n = 1,000 FP64 plain-method
 workload (DPPR + PDist + 300 FP64 layout updates). `--workload taupush`: Tau-Push
 queries (Sec. 4) on the 2M-node Chung-Lu graph, 8 level-1 supernodes of 25
-children x 25 leaves per step. None of these is the default line.
+children x 25 leaves per step. `--workload hierarchy`: the Louvain+ hierarchy
+(Sec. 5, Appendix A) of the same graph with k = 25. None of these is the
+default line.
 
 `--workload dense` measures the dense-view propagation instead (not the
 default line): a dense clustered weighted view, n = 20,000, 20 blocks, 15 %
@@ -117,7 +119,7 @@ def parse():
                     help="one untimed pass of the hot path (for profiler command lines)")
     ap.add_argument("--dense-precision", default="bf16", choices=["bf16", "tf32x3"],
                     help="tensor-core sweep operands of --workload dense (the other mode is timed beside it)")
-    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small", "taupush", "level", "directed", "metrics"],
+    ap.add_argument("--workload", default="chung_lu", choices=["chung_lu", "dense", "views", "view2m", "small", "taupush", "level", "directed", "metrics", "hierarchy"],
                     help="dense: the dense weighted view on the tensor-core sweeps (--n defaults to 20000); "
                          "views: the 256 batched SBM views; taupush: Tau-Push queries on the 2M-node graph")
     return ap.parse_args()
@@ -1035,6 +1037,108 @@ def run_metrics(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- Louvain+ hierarchy
+HIER_WORKLOAD = "chung_lu_n2000000_deg10_louvain_plus_k25"
+
+
+def run_hierarchy(args, rank, world, local_rank):
+    """The Louvain+ supergraph hierarchy (Sec. 5 preprocessing; Appendix A)
+    of the 2M-node Chung-Lu graph of the Tau-Push workload (mean degree 10,
+    exponent 2.5, seed 0), k = 25; one step = one pprviz_louvain_plus call on
+    the resident graph, its parent arrays read back to the host (part of the
+    call). value = leaf nodes per second."""
+    import torch
+
+    import oracle as O
+    import paper_2112_14944_gb300 as P
+    import synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = synth.chung_lu(2_000_000, 10, 2.5, seed=0)
+    k = 25
+    ctx = P.Context(local_rank, torch_stream=True)
+    stream = ctx._stream
+    G = ctx.upload_graph(g)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ms, res, clocks = _timed_steps(args, stream, flush, lambda: ctx.louvain_plus(G, k, with_info=True))
+    launches = ctx.stats()["kernel_launches"]
+    levels, info = res
+    total = max_over_ranks(sum(ms), dev)
+    ctx.profile(1)
+    ctx.louvain_plus(G, k)
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    # end to end through the public API from host buffers: the CSR uploaded
+    # (and validated) in every step, the parent arrays returned to the host
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Gh = ctx.upload_graph(g)
+        ctx.louvain_plus(Gh, k)
+        Gh.free()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    if rank != 0:
+        return
+    hbm, _, peak_kind = peaks()
+    per = total / args.steps
+    sizes = [g.n] + [int(p.max()) + 1 for p in levels]
+    deg = np.diff(g.row_ptr)
+    part = O.louvain_leaf_groups(g.n, levels)[0]
+    src = np.repeat(np.arange(g.n), deg)
+    same = part[src] == part[g.col]
+    inside = np.bincount(part[src][same], minlength=sizes[1])
+    dsum = np.bincount(part, weights=deg, minlength=sizes[1])
+    Q1 = float(np.sum(inside / g.nnz - (dsum / g.nnz) ** 2))
+    h_ms, h_n, _ = ktimes["hier"]
+    # algorithmic bytes of the merge rounds and lifts: the level's share of
+    # the pair table cleared and scanned twice (3 x 12 B per slot visit); per
+    # pair summed into the table its 12 B record, its two group ids (8 B) and
+    # one key and count (12 B); per level node and round ~16 words of node
+    # state (64 B)
+    alg = 36.0 * info["slot_visits"] + 32.0 * info["pair_visits"] + 64.0 * info["node_visits"]
+    ach = alg / (h_ms / 1e3) / 1e9 if h_ms else None
+    roof = {"kernel": "Louvain+ merge rounds (k_lp_*): pair-table atomics, table scans, node passes",
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
+            "launches": h_n, "alg_bytes_per_step": alg,
+            "alg_bytes_note": "36 B per table slot visit + 32 B per pair visit + 64 B per node visit",
+            "device_ms_per_step": h_ms, "traffic": None,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
+    cpu = None
+    errors = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample: a 1,000-node graph of the same kind,
+        # k = 25; the GPU's hierarchy of the same sample must be identical
+        gs = synth.chung_lu(1000, 10, 2.5, seed=0)
+        t0 = time.perf_counter()
+        ref = O.louvain_plus(gs.n, gs.row_ptr, gs.col, k)
+        dt = time.perf_counter() - t0
+        got = ctx.louvain_plus(ctx.upload_graph(gs), k)
+        errors = {"sample_hierarchy_identical": len(got) == len(ref) and all(
+            np.array_equal(np.asarray(a, np.int64), np.asarray(b, np.int64)) for a, b in zip(got, ref)),
+                  "sample_levels": [int(p.max()) + 1 for p in ref]}
+        cpu = {"value": gs.n / dt, "unit": "leaf nodes/s", "cores": 1, "kind": "oracle",
+               "sample": "the oracle's Louvain+ hierarchy (exact rational gains, plain Python) of a 1,000-node "
+                         "Chung-Lu graph of the same kind, k = 25"}
+    line = {
+        "metric": "Louvain+ hierarchy of a 2M-node power-law graph (k = 25), leaf nodes per second",
+        "value": g.n / (per / 1e3), "unit": "leaf nodes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": HIER_WORKLOAD, "graph": "chung-lu", "n": g.n, "nnz": int(g.nnz), "mean_degree": 10,
+                   "exponent": 2.5, "seed": 0, "k": k, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "levels": sizes, "rounds": info["rounds"], "level1_modularity": Q1,
+        "isolated_leaves": int((deg == 0).sum()),
+        "errors": errors, "roofline": roof,
+        "e2e": {"value": g.n / (float(np.median(e2e_ms)) / 1e3), "unit": "leaf nodes/s",
+                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes),
+                "d2h_bytes_per_step": int(4 * sum(sizes[:-1])), "ms_per_step": float(np.median(e2e_ms))},
+        "cpu_baseline": cpu, "gpu_launches": int(launches * args.steps), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- view of a 2M-node graph
 VIEW2M_WORKLOAD = "chung_lu_n2000000_deg10_view8192"
 
@@ -1485,6 +1589,8 @@ def main():
         run_directed(args, rank, world, local_rank)
     elif args.workload == "metrics":
         run_metrics(args, rank, world, local_rank)
+    elif args.workload == "hierarchy":
+        run_hierarchy(args, rank, world, local_rank)
     elif args.workload == "view2m":
         run_view2m(args, rank, world, local_rank)
     elif args.workload == "small":

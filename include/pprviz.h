@@ -121,7 +121,8 @@ typedef struct pprviz_stats {
 #define PPRVIZ_K_ENERGY 8        /* energy / gradient passes and reductions */
 #define PPRVIZ_K_OTHER 9         /* initialisation, casts, small helpers */
 #define PPRVIZ_K_PUSH 10         /* Tau-Push rounds and the DPR power iterations */
-#define PPRVIZ_NKCLASS 11
+#define PPRVIZ_K_HIER 11         /* Louvain+ merge rounds and level lifts */
+#define PPRVIZ_NKCLASS 12
 
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
  * to run on (borrowed, not destroyed), or NULL for a stream the context owns.
@@ -338,6 +339,52 @@ typedef struct pprviz_tau_info {
 int pprviz_tau_push(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
                     const int32_t *leaf_idx, const double *dpr, double alpha, double eps, double delta, double tau,
                     void *ldppr_out, void *pdist_out, int64_t n_clamp, pprviz_tau_info *info, uint32_t mem_flags);
+
+/* What one pprviz_louvain_plus call did (host struct). */
+typedef struct pprviz_louvain_info {
+    int32_t levels;           /* L: levels above the leaves */
+    int32_t rounds;           /* merge rounds, all levels */
+    int64_t parent_need;      /* sum_{l < L} level_n[l]: the parent entries needed */
+    int64_t slot_visits;      /* pair-table slots cleared and scanned, all rounds and lifts */
+    int64_t pair_visits;      /* level-graph pairs summed into the table, all rounds and lifts */
+    int64_t node_visits;      /* level nodes processed, all rounds */
+} pprviz_louvain_info;
+
+/* Louvain+ supergraph hierarchy (Sec. 5, the preprocessing step; Appendix A,
+ * "Louvain+"): level l+1 groups the supernodes of level l (level 0: the
+ * leaves) so that no supernode has more than k children, and levels are added
+ * until one has at most k supernodes. A supernode S is merged into a
+ * neighbouring T by rule (i), T being S's only neighbour, or rule (ii), the T
+ * of the largest modularity gain Q^(S, T) = sum_{V_i in S} q(V_i, T), with
+ * w(.) and w_cr counted as ordered leaf pairs (the count under which q is the
+ * change of modularity). Decisions use exact integer gains. Schedule (the
+ * appendix fixes the rules, not their order): synchronous rounds; every
+ * supernode proposes its target from the round's starting state (rule (ii)
+ * only on a positive gain until a round of the level merges nothing, then on
+ * any gain; ties to the smaller id); S moves when its target does not; a
+ * target takes its movers in increasing id order while it keeps at most k
+ * children. A level ends with a round that merges nothing; the hierarchy ends
+ * when a level has at most k supernodes or merged nothing (so a graph of more
+ * than k connected components keeps more than k supernodes at the top).
+ * g:          an undirected graph; weights are ignored (edges are counted);
+ *             fewer than 2^31 stored edges.
+ * k:          children per supernode and supernodes at the top, at most; >= 2.
+ * level_n:    host, level_cap + 1 int64: level_n[0] = n, level_n[l] = the
+ *             number of level-l supernodes, l = 1..L.
+ * parent:     host, parent_cap int32: for l = 1..L in turn, the level-l
+ *             supernode of every level-(l-1) node (level_n[l - 1] entries),
+ *             supernodes numbered from 0 in the order of their smallest child.
+ * info:       host, required: what the call did (pprviz_louvain_info); its
+ *             levels and parent_need are written also when parent_cap or
+ *             level_cap is too small (E_INVALID_ARG, level_n and parent
+ *             untouched).
+ * Scratch (kept by the context): about 80 B per node, 24 B per stored edge
+ * and a pair table of 12 B x the power of two >= 2 x the stored edges (each
+ * level clears and scans only the power of two its own pairs need).
+ * Errors: E_INVALID_ARG (NULL, k < 2, a directed graph, short outputs),
+ * E_NOT_CONVERGED (100,000 rounds or 64 levels), E_OOM, E_CUDA. */
+int pprviz_louvain_plus(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int64_t *level_n, int32_t level_cap,
+                        int32_t *parent, int64_t parent_cap, pprviz_louvain_info *info);
 
 /* P3 alone - PDist from a k*k DPPR matrix (Sec. 3.1, Eq. (1)):
  * Delta[i][j] = min(max(1 - ln(D[i][j] + D[j][i]), 2), 2 ln n_clamp), zero

@@ -189,6 +189,28 @@ class Context:
         self._leave(dev, out)
         return out, cert
 
+    def louvain_plus(self, graph: Graph, k, with_info=False):
+        """Louvain+ supergraph hierarchy (Sec. 5; Appendix A): a list of
+        parent arrays, levels 1..L, where entry A of level l is the level-l
+        supernode of level-(l-1) node A (level 0 = the leaves). With
+        with_info, also the call's counters (levels, rounds, visits)."""
+        n = graph.n
+        level_n = np.zeros(65, dtype=np.int64)
+        cap = 2 * n + 64
+        while True:
+            parent = np.empty(cap, dtype=np.int32)
+            ok, info = B.pprviz_louvain_plus(self.h, graph.h, k, level_n, 64, parent, cap)
+            if ok:
+                break
+            if info["parent_need"] <= cap:
+                raise RuntimeError("pprviz_louvain_plus: more than 64 levels")
+            cap = info["parent_need"]  # a deep hierarchy: once more with room for it
+        levels, off = [], 0
+        for l in range(1, info["levels"] + 1):
+            levels.append(parent[off:off + level_n[l - 1]].copy())
+            off += level_n[l - 1]
+        return (levels, info) if with_info else levels
+
     @staticmethod
     def leaf_csr(leaf_sets):
         """(leaf_ptr int64, leaf_idx int32) of a list of leaf-id arrays."""

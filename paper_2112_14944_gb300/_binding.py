@@ -33,7 +33,7 @@ PPRVIZ_FP32_CSR = 2
 PPRVIZ_FP32_TC = 3
 PPRVIZ_FP32_BF16TC = 4
 KERNEL_CLASSES = ["graph", "sweep", "residual", "extract", "pdist", "factor", "ly", "apply", "energy", "other",
-                  "push"]
+                  "push", "hier"]
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID_ARG", 2: "E_BAD_GRAPH", 3: "E_OOM", 4: "E_CUDA",
                 5: "E_NOT_CONVERGED", 6: "E_TIMEOUT"}
@@ -68,6 +68,7 @@ _SIGS = {
     "pprviz_energy_noalloc": (C.c_int, [_VP, C.c_int32, _VP, C.c_double, _VP, _VP, _VP, _VP]),
     "pprviz_layout_metrics": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, _VP, _VP, C.c_uint32]),
     "pprviz_dpr": (C.c_int, [_VP, _VP, C.c_double, C.c_double, _VP, _VP, C.c_uint32]),
+    "pprviz_louvain_plus": (C.c_int, [_VP, _VP, C.c_int32, _VP, C.c_int32, _VP, C.c_int64, _VP]),
     "pprviz_tau_push": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_double,
                                   _VP, _VP, C.c_int64, _VP, C.c_uint32]),
 }
@@ -242,6 +243,25 @@ def pprviz_dpr(ctx, g, alpha, eps, dpr_out, mem_flags):
     cert = C.c_double()
     _check(ctx, load().pprviz_dpr(ctx, g, float(alpha), float(eps), _ptr(dpr_out)[0], C.byref(cert), mem_flags))
     return cert.value
+
+
+class pprviz_louvain_info(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("rounds", C.c_int32), ("parent_need", C.c_int64),
+                ("slot_visits", C.c_int64), ("pair_visits", C.c_int64), ("node_visits", C.c_int64)]
+
+
+def pprviz_louvain_plus(ctx, g, k, level_n, level_cap, parent, parent_cap):
+    """level_n / parent: host numpy int64 / int32 arrays. Returns (ok, info
+    dict); ok is False (and info holds levels and parent_need) when the
+    outputs were too short, any other failure raises."""
+    info = pprviz_louvain_info()
+    st = load().pprviz_louvain_plus(ctx, g, int(k), _ptr(level_n)[0], int(level_cap), _ptr(parent)[0],
+                                    int(parent_cap), C.byref(info))
+    out = {name: getattr(info, name) for name, _ in info._fields_}
+    if st == PPRVIZ_E_INVALID_ARG and info.parent_need > 0:  # written only once the hierarchy is built
+        return False, out
+    _check(ctx, st)
+    return True, out
 
 
 def pprviz_tau_push(ctx, g, nsup, leaf_ptr, leaf_idx, dpr, alpha, eps, delta, tau, ldppr_out, pdist_out, n_clamp,

@@ -544,6 +544,27 @@ int pprviz_dpr(pprviz_ctx *ctx, const pprviz_graph *g, double alpha, double eps,
   return finish(ctx, PPRVIZ_OK);
 }
 
+int pprviz_louvain_plus(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int64_t *level_n, int32_t level_cap,
+                        int32_t *parent, int64_t parent_cap, pprviz_louvain_info *info) {
+  if (!ctx) return PPRVIZ_E_INVALID_ARG;
+  PPRVIZ_TRY(begin(ctx));
+  if (info) memset(info, 0, sizeof(*info));
+  if (!g || !level_n || !parent || !info) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "graph or an output is NULL");
+  if (k < 2) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "Louvain+ needs k >= 2");
+  if (level_cap < 0 || parent_cap < 0) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "negative capacity");
+  if (g->directed)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "Louvain+ takes an undirected graph (symmetrise a directed one first)");
+  if (g->nnz >= ((int64_t)1 << 31)) return set_err(ctx, PPRVIZ_E_INVALID_ARG, "Louvain+ takes graphs below 2^31 stored edges");
+  std::vector<int32_t> par;
+  std::vector<int64_t> ln;
+  PPRVIZ_TRY(louvain_plus_solve(ctx, g, k, par, ln, info));
+  if (info->levels > level_cap || info->parent_need > parent_cap)
+    return set_err(ctx, PPRVIZ_E_INVALID_ARG, "Louvain+: level_n or parent too short for the hierarchy (see info)");
+  memcpy(level_n, ln.data(), sizeof(int64_t) * ln.size());
+  if (!par.empty()) memcpy(parent, par.data(), sizeof(int32_t) * par.size());
+  return finish(ctx, PPRVIZ_OK);
+}
+
 int pprviz_tau_push(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const int64_t *leaf_ptr,
                     const int32_t *leaf_idx, const double *dpr, double alpha, double eps, double delta, double tau,
                     void *ldppr_out, void *pdist_out, int64_t n_clamp, pprviz_tau_info *info, uint32_t mem_flags) {

@@ -57,6 +57,8 @@ enum Slot {
   // Tau-Push: residues, reserves, push records, (slot, share) pairs, dirty
   // marks, per-round counters, leaf maps and small per-supernode tables
   WS_TPR, WS_TPQ, WS_TPFA, WS_TPFB, WS_TPVAL, WS_TPCNT, WS_TPMAP, WS_TPTAB,
+  // Louvain+: per-node round state, scan scratch, the level pair lists, the pair table
+  WS_LPNODE, WS_LPSCAN, WS_LPEDGE, WS_LPHASH,
   WS_COUNT
 };
 
@@ -219,6 +221,13 @@ int tau_push_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t nsup, const i
                    const int32_t *leaf_idx_d, const std::vector<int64_t> &leaf_ptr_h, const double *dpr_d,
                    double alpha, double eps, double delta, double tau, void *out_d, bool out64,
                    pprviz_tau_info *info);
+
+// ---- Louvain+ hierarchy (louvain.cu) ----------------------------------------
+// The hierarchy of an undirected graph with at most k children per supernode:
+// parents = the parent arrays of levels 1..L concatenated, level_n = n and the
+// sizes of levels 1..L (host); info: filled (levels, parent_need, counters).
+int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::vector<int32_t> &parents,
+                       std::vector<int64_t> &level_n, pprviz_louvain_info *info);
 
 // ---- graph analysis for the deflated sweeps (spectral.cu) ------------------
 // Fills g->comp / h_comp / h_mc / spec_b / spec_deflate once per graph.
