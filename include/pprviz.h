@@ -194,6 +194,7 @@ int pprviz_kernel_times(pprviz_ctx *ctx, double *ms_out, int64_t *launches_out, 
 int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr,
                         const int32_t *col_idx, const float *weights, uint32_t flags,
                         uint32_t mem_flags, pprviz_graph **out);
+/* Frees a graph's device memory; valid before or after its context is destroyed. */
 void pprviz_graph_free(pprviz_graph *g);
 /* Copy the n degrees d(v) (double) computed on the device into deg_out (host
  * or device per mem_flags) and report n, nnz and m = sum_v d(v). */

@@ -12,6 +12,8 @@ memory and streams.
 """
 from __future__ import annotations
 
+import weakref
+
 import numpy as np
 
 from . import _binding as B
@@ -75,6 +77,7 @@ class Context:
             self._stream = torch.cuda.Stream(device=device)
             handle = self._stream.cuda_stream
         self.device = device
+        self._graphs = weakref.WeakSet()  # live graphs, freed by close()
         self.h = B.pprviz_create(device, handle)
 
     # -- stream ordering for device (torch) buffers --
@@ -93,6 +96,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for g in list(self._graphs):
+                g.free()
             B.pprviz_destroy(self.h)
             self.h = 0
 
@@ -131,7 +136,9 @@ class Context:
         self._enter(dev)
         h = B.pprviz_graph_upload(self.h, n, row_ptr, col, weights, flags)
         self._leave(dev)
-        return Graph(self, h, int(n))
+        gr = Graph(self, h, int(n))
+        self._graphs.add(gr)
+        return gr
 
     def upload_graph(self, g, validate=True) -> Graph:
         """Upload a synth.Graph-like object (n, row_ptr, col, weight[, directed])."""

@@ -269,6 +269,7 @@ int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr, cons
   pprviz_graph *g = new (std::nothrow) pprviz_graph();
   if (!g) return set_err(ctx, PPRVIZ_E_OOM, "host allocation failed");
   g->ctx = ctx;
+  g->device = ctx->device;
   g->n = n;
   g->nnz = nnz;
   g->weighted = weights != nullptr;
@@ -315,7 +316,7 @@ int pprviz_graph_upload(pprviz_ctx *ctx, int64_t n, const int64_t *row_ptr, cons
 
 void pprviz_graph_free(pprviz_graph *g) {
   if (!g) return;
-  if (g->ctx) cudaSetDevice(g->ctx->device);
+  cudaSetDevice(g->device);  // the context may already be destroyed
   g->rp.release();
   g->col.release();
   g->w.release();

@@ -92,7 +92,8 @@ struct pprviz_ctx {
 };
 
 struct pprviz_graph {
-  pprviz_ctx *ctx = nullptr;
+  pprviz_ctx *ctx = nullptr;  // the uploading context; not used by pprviz_graph_free
+  int device = 0;             // its device, for freeing after the context is gone
   int64_t n = 0, nnz = 0;
   bool weighted = false;
   uint32_t flags = 0;

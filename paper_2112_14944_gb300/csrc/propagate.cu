@@ -1872,6 +1872,7 @@ int dppr_views_solve(pprviz_ctx *ctx, int32_t nviews, const pprviz_graph *const 
   PPRVIZ_LAUNCHED(ctx);
   pprviz_graph U;
   U.ctx = ctx;
+  U.device = ctx->device;
   U.n = N;
   U.nnz = NNZ;
   U.weighted = weighted;
