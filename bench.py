@@ -1091,17 +1091,19 @@ def run_hierarchy(args, rank, world, local_rank):
     dsum = np.bincount(part, weights=deg, minlength=sizes[1])
     Q1 = float(np.sum(inside / g.nnz - (dsum / g.nnz) ** 2))
     h_ms, h_n, _ = ktimes["hier"]
-    # algorithmic bytes of the merge rounds and lifts: the level's share of
-    # the pair table cleared and scanned twice (3 x 12 B per slot visit); per
-    # pair summed into the table its 12 B record, its two group ids (8 B) and
-    # one key and count (12 B); per level node and round ~16 words of node
-    # state (64 B)
-    alg = 36.0 * info["slot_visits"] + 32.0 * info["pair_visits"] + 64.0 * info["node_visits"]
+    # algorithmic bytes of the merge rounds: per pair scanned for the gains,
+    # twice (largest gain, then its smallest arg), the 12 B record and the
+    # size and degree sum of both groups (24 B); per pair contracted its 12 B
+    # record, its two mapped ids (8 B) and one key and count (12 B); per
+    # table slot its clear and the compaction scan (2 x 12 B); per level node
+    # and round ~16 words of node state (64 B)
+    alg = (72.0 * info["list_visits"] + 32.0 * info["pair_visits"] + 24.0 * info["slot_visits"]
+           + 64.0 * info["node_visits"])
     ach = alg / (h_ms / 1e3) / 1e9 if h_ms else None
     roof = {"kernel": "Louvain+ merge rounds (k_lp_*): pair-table atomics, table scans, node passes",
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
             "launches": h_n, "alg_bytes_per_step": alg,
-            "alg_bytes_note": "36 B per table slot visit + 32 B per pair visit + 64 B per node visit",
+            "alg_bytes_note": "72 B per pair scanned for the gains + 32 B per pair contracted + 24 B per table slot + 64 B per node visit",
             "device_ms_per_step": h_ms, "traffic": None,
             "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
     cpu = None

@@ -346,8 +346,9 @@ typedef struct pprviz_louvain_info {
     int32_t levels;           /* L: levels above the leaves */
     int32_t rounds;           /* merge rounds, all levels */
     int64_t parent_need;      /* sum_{l < L} level_n[l]: the parent entries needed */
-    int64_t slot_visits;      /* pair-table slots cleared and scanned, all rounds and lifts */
-    int64_t pair_visits;      /* level-graph pairs summed into the table, all rounds and lifts */
+    int64_t slot_visits;      /* pair-table slots cleared and scanned, all contractions */
+    int64_t pair_visits;      /* pairs summed into the table, all contractions */
+    int64_t list_visits;      /* pairs scanned for the gains, all rounds */
     int64_t node_visits;      /* level nodes processed, all rounds */
 } pprviz_louvain_info;
 
@@ -381,7 +382,8 @@ typedef struct pprviz_louvain_info {
  *             untouched).
  * Scratch (kept by the context): about 80 B per node, 24 B per stored edge
  * and a pair table of 12 B x the power of two >= 2 x the stored edges (each
- * level clears and scans only the power of two its own pairs need).
+ * contraction of the pair list clears and scans only the power of two it
+ * needs).
  * Errors: E_INVALID_ARG (NULL, k < 2, a directed graph, short outputs),
  * E_NOT_CONVERGED (100,000 rounds or 64 levels), E_OOM, E_CUDA. */
 int pprviz_louvain_plus(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, int64_t *level_n, int32_t level_cap,

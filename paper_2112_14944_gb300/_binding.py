@@ -247,7 +247,8 @@ def pprviz_dpr(ctx, g, alpha, eps, dpr_out, mem_flags):
 
 class pprviz_louvain_info(C.Structure):
     _fields_ = [("levels", C.c_int32), ("rounds", C.c_int32), ("parent_need", C.c_int64),
-                ("slot_visits", C.c_int64), ("pair_visits", C.c_int64), ("node_visits", C.c_int64)]
+                ("slot_visits", C.c_int64), ("pair_visits", C.c_int64), ("list_visits", C.c_int64),
+                ("node_visits", C.c_int64)]
 
 
 def pprviz_louvain_plus(ctx, g, k, level_n, level_cap, parent, parent_cap):

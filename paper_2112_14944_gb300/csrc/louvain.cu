@@ -23,14 +23,15 @@
 // numbered by their smallest member. The hierarchy ends when a level has at
 // most k nodes or merged nothing.
 //
-// Data per level: the level graph as a list of ordered pairs (A, B, count)
-// with A != B (level 0: the CSR entries), the degree sum of every node, and
-// the group of every node (a representative: the id of a member; targets
-// never move in their round, so one relabelling step applies a round). The
-// pair counts of a round, c(S, T) for the current groups, are summed into an
-// open-addressing table keyed by (S, T) with integer atomics; the round's
-// per-group maxima and minima are integer atomics too, so the result does
-// not depend on the order of any atomic.
+// Data per level: the degree sum of every node, the group of every node (a
+// representative: the id of a member; targets never move in their round, so
+// one relabelling step applies a round), and the list of the current groups'
+// pairs (S, T, c(S, T)), S != T, each once. After every round that merged,
+// the list is mapped through the merges and summed per distinct pair in an
+// open-addressing table keyed by (S, T) (integer atomics), so it shrinks as
+// the groups grow; at the end of a level its representatives are relabelled
+// to the next level's ids. The round's per-group maxima and minima are
+// integer atomics too: the result does not depend on the order of any atomic.
 #include <cstdio>
 #include <cstring>
 
@@ -132,32 +133,44 @@ __device__ __forceinline__ long long lp_gain(long long m2, int32_t c, long long 
   return m2 * (long long)c - wS * wT;
 }
 
-// per group: distinct neighbours, and the largest gain among the neighbours it fits with
-__global__ void k_lp_best(unsigned long long H, const unsigned long long *__restrict__ keys,
-                          const int32_t *__restrict__ vals, const int32_t *__restrict__ gsize,
+// per group: distinct neighbours, and the largest gain among the neighbours
+// it fits with (the pair list holds each (S, T) of the current groups once)
+__global__ void k_lp_best(int64_t E, const int32_t *__restrict__ eA, const int32_t *__restrict__ eB,
+                          const int32_t *__restrict__ ew, const int32_t *__restrict__ gsize,
                           const long long *__restrict__ gwin, int32_t k, long long m2, int32_t *__restrict__ nbr,
                           long long *__restrict__ bgain) {
-  for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h < H;
-       h += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long key = keys[h];
-    if (key == kLpEmpty) continue;
-    const int32_t S = (int32_t)(key >> 32), T = (int32_t)(key & 0xffffffffu);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t S = eA[e], T = eB[e];
     atomicAdd(&nbr[S], 1);
-    if (gsize[S] + gsize[T] <= k) atomicMax(&bgain[S], lp_gain(m2, vals[h], gwin[S], gwin[T]));
+    if (gsize[S] + gsize[T] <= k) atomicMax(&bgain[S], lp_gain(m2, ew[e], gwin[S], gwin[T]));
   }
 }
 
 // per group: the smallest neighbour id that reaches the largest gain
-__global__ void k_lp_argbest(unsigned long long H, const unsigned long long *__restrict__ keys,
-                             const int32_t *__restrict__ vals, const int32_t *__restrict__ gsize,
+__global__ void k_lp_argbest(int64_t E, const int32_t *__restrict__ eA, const int32_t *__restrict__ eB,
+                             const int32_t *__restrict__ ew, const int32_t *__restrict__ gsize,
                              const long long *__restrict__ gwin, int32_t k, long long m2,
                              const long long *__restrict__ bgain, int32_t *__restrict__ bt) {
-  for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h < H;
-       h += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long key = keys[h];
-    if (key == kLpEmpty) continue;
-    const int32_t S = (int32_t)(key >> 32), T = (int32_t)(key & 0xffffffffu);
-    if (gsize[S] + gsize[T] <= k && lp_gain(m2, vals[h], gwin[S], gwin[T]) == bgain[S]) atomicMin(&bt[S], T);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t S = eA[e], T = eB[e];
+    if (gsize[S] + gsize[T] <= k && lp_gain(m2, ew[e], gwin[S], gwin[T]) == bgain[S]) atomicMin(&bt[S], T);
+  }
+}
+
+// the group of every current group after the round: its target if it moved
+__global__ void k_lp_gmap(int32_t nl, const int32_t *__restrict__ acc, const int32_t *__restrict__ prop,
+                          int32_t *__restrict__ gmap) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nl; a += (int64_t)gridDim.x * blockDim.x)
+    gmap[a] = acc[a] ? prop[a] : (int32_t)a;
+}
+
+// the level's final pair list relabelled to the next level's ids (distinct
+// groups have distinct parents, so no two pairs merge)
+__global__ void k_lp_relabel(int64_t E, int32_t *__restrict__ eA, int32_t *__restrict__ eB,
+                             const int32_t *__restrict__ parent) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    eA[e] = parent[eA[e]];
+    eB[e] = parent[eB[e]];
   }
 }
 
@@ -396,15 +409,15 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
   const int64_t n = g->n, E0 = g->nnz;
   if (n <= k || E0 == 0) return PPRVIZ_OK;
   const long long m2 = (long long)E0;
-  // pair table: a power of two of at least twice the level-0 pairs (each
-  // level uses the leading power of two it needs)
+  // pair table: a power of two of at least twice the level-0 pairs (every
+  // contraction uses the leading power of two its own pairs need)
   unsigned long long H = 1024;
   while (H < 2ull * (unsigned long long)E0) H <<= 1;
   const size_t ni = (size_t)n;
   // node arrays (sized for level 0; later levels are smaller), each starting
   // on a 16-byte boundary
   const size_t a32 = (sizeof(int32_t) * ni + 15) & ~(size_t)15, a64 = (sizeof(long long) * ni + 15) & ~(size_t)15;
-  PPRVIZ_TRY(ws_ensure(ctx, WS_LPNODE, 12 * a32 + 4 * a64));
+  PPRVIZ_TRY(ws_ensure(ctx, WS_LPNODE, 13 * a32 + 4 * a64));
   char *base = ctx->ws[WS_LPNODE].as<char>();
   auto take = [&](size_t bytes) {
     char *p = base;
@@ -423,6 +436,7 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
   int32_t *acc = (int32_t *)take(sizeof(int32_t) * ni);
   int32_t *minm = (int32_t *)take(sizeof(int32_t) * ni);
   int32_t *parent = (int32_t *)take(sizeof(int32_t) * ni);
+  int32_t *gmap = (int32_t *)take(sizeof(int32_t) * ni);
   long long *gwin = (long long *)take(sizeof(long long) * ni);
   long long *bgain = (long long *)take(sizeof(long long) * ni);
   long long *win = (long long *)take(sizeof(long long) * ni);
@@ -432,7 +446,8 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
   int64_t *moff = ctx->ws[WS_LPSCAN].as<int64_t>();
   int64_t *bsum = moff + ni + 1;
   int64_t *misc = bsum + (ni + kScanB) / kScanB + 1;  // [0] scan total, [1] pair count, [2] accepted + error
-  // pair lists (two, ping-pong between levels) and the table
+  int *flags = reinterpret_cast<int *>(misc + 2);      // [0] accepted in the round, [1] table error
+  // pair lists (two, ping-pong) and the table
   const size_t eb = (sizeof(int32_t) * 3) * (size_t)E0;
   PPRVIZ_TRY(ws_ensure(ctx, WS_LPEDGE, 2 * eb + 64));
   int32_t *eA = ctx->ws[WS_LPEDGE].as<int32_t>();
@@ -441,23 +456,50 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
   PPRVIZ_TRY(ws_ensure(ctx, WS_LPHASH, (sizeof(unsigned long long) + sizeof(int32_t)) * (size_t)H));
   unsigned long long *keys = ctx->ws[WS_LPHASH].as<unsigned long long>();
   int32_t *vals = reinterpret_cast<int32_t *>(keys + H);
-  int *flags = reinterpret_cast<int *>(misc + 2);  // [0] accepted in the round, [1] table error
+  int64_t E = E0;
 
+  // the pair list mapped through `map` and summed per distinct (S, T), S != T
+  auto contract = [&](const int32_t *map) -> int {
+    unsigned long long Hl = 1024;
+    while (Hl < 2ull * (unsigned long long)E) Hl <<= 1;
+    info->slot_visits += (int64_t)Hl;
+    info->pair_visits += E;
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * Hl, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(vals, 0, sizeof(int32_t) * Hl, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemsetAsync(misc + 1, 0, 2 * sizeof(int64_t), ctx->stream));
+    k_lp_pairs<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, ew, map, keys, vals, Hl - 1, flags + 1);
+    PPRVIZ_LAUNCHED(ctx);
+    k_lp_compact<<<grid_for((int64_t)Hl), kLpTpb, 0, ctx->stream>>>(
+        Hl, keys, vals, fA, fB, fw, reinterpret_cast<unsigned long long *>(misc + 1));
+    PPRVIZ_LAUNCHED(ctx);
+    int64_t count = 0;
+    int full = 0;
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&count, misc + 1, sizeof(count), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&full, flags + 1, sizeof(full), cudaMemcpyDeviceToHost, ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (full) return set_err(ctx, PPRVIZ_E_CUDA, "Louvain+: pair table full (internal error)");
+    std::swap(eA, fA);
+    std::swap(eB, fB);
+    std::swap(ew, fw);
+    E = count;
+    return PPRVIZ_OK;
+  };
+
+  int32_t nl = (int32_t)n;
   k_lp_edges0<<<grid_for(n), kLpTpb, 0, ctx->stream>>>(n, pull_rp(g), pull_col(g), eA, eB, ew, (int64_t *)win);
   PPRVIZ_LAUNCHED(ctx);
-  int64_t E = E0;
-  int32_t nl = (int32_t)n;
+  {
+    // level-0 pairs: each (u, v), u != v, once with its multiplicity
+    PPRVIZ_PROF(ctx, PPRVIZ_K_HIER);
+    k_lp_iota<<<grid_for(nl), kLpTpb, 0, ctx->stream>>>(nl, gmap);
+    PPRVIZ_LAUNCHED(ctx);
+    PPRVIZ_TRY(contract(gmap));
+  }
   int rounds = 0;
-  bool done = false;  // a level merged nothing or reached at most k nodes
+  bool done = false;  // a level reached at most k nodes
   for (int level = 0; !done; ++level) {
     if (level == kLpMaxLevels) return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "Louvain+: level cap reached");
     const unsigned gn = grid_for(nl);
-    // this level's share of the table: a power of two of at least twice its
-    // pairs (the lifted pairs of the next level are no more)
-    unsigned long long Hl = 1024;
-    while (Hl < 2ull * (unsigned long long)E) Hl <<= 1;
-    const unsigned long long maskl = Hl - 1;
-    const unsigned gh = grid_for((int64_t)Hl);
     k_lp_iota<<<gn, kLpTpb, 0, ctx->stream>>>(nl, grp);
     PPRVIZ_LAUNCHED(ctx);
     bool relaxed = false;
@@ -465,22 +507,17 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
     for (;;) {
       if (++rounds > kLpMaxRounds)
         return set_err(ctx, PPRVIZ_E_NOT_CONVERGED, "Louvain+: round cap reached");
-      info->pair_visits += E;
+      info->list_visits += E;
       info->node_visits += nl;
-      info->slot_visits += (int64_t)Hl;
       PPRVIZ_PROF(ctx, PPRVIZ_K_HIER);
       k_lp_round_init<<<gn, kLpTpb, 0, ctx->stream>>>(nl, gsize, gwin, nbr, bgain, bt, prop, mcnt, mcur, acc);
       PPRVIZ_LAUNCHED(ctx);
-      PPRVIZ_CUDA(ctx, cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * Hl, ctx->stream));
-      PPRVIZ_CUDA(ctx, cudaMemsetAsync(vals, 0, sizeof(int32_t) * Hl, ctx->stream));
       PPRVIZ_CUDA(ctx, cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx->stream));
       k_lp_gstats<<<gn, kLpTpb, 0, ctx->stream>>>(nl, grp, win, gsize, gwin);
       PPRVIZ_LAUNCHED(ctx);
-      k_lp_pairs<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, ew, grp, keys, vals, maskl, flags + 1);
+      k_lp_best<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, ew, gsize, gwin, k, m2, nbr, bgain);
       PPRVIZ_LAUNCHED(ctx);
-      k_lp_best<<<gh, kLpTpb, 0, ctx->stream>>>(Hl, keys, vals, gsize, gwin, k, m2, nbr, bgain);
-      PPRVIZ_LAUNCHED(ctx);
-      k_lp_argbest<<<gh, kLpTpb, 0, ctx->stream>>>(Hl, keys, vals, gsize, gwin, k, m2, bgain, bt);
+      k_lp_argbest<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, ew, gsize, gwin, k, m2, bgain, bt);
       PPRVIZ_LAUNCHED(ctx);
       k_lp_propose<<<gn, kLpTpb, 0, ctx->stream>>>(nl, gsize, nbr, bgain, bt, relaxed ? 1 : 0, prop);
       PPRVIZ_LAUNCHED(ctx);
@@ -493,21 +530,23 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
       PPRVIZ_LAUNCHED(ctx);
       k_lp_apply<<<gn, kLpTpb, 0, ctx->stream>>>(nl, grp, acc, prop);
       PPRVIZ_LAUNCHED(ctx);
-      int hf[2];
-      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, ctx->stream));
+      int accepted = 0;
+      PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&accepted, flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      if (hf[1]) return set_err(ctx, PPRVIZ_E_CUDA, "Louvain+: pair table full (internal error)");
-      if (hf[0] == 0) {
+      if (accepted == 0) {
         if (relaxed) break;
         relaxed = true;
         continue;
       }
-      merges += hf[0];
+      merges += accepted;
+      // the pair list of the merged groups
+      k_lp_gmap<<<gn, kLpTpb, 0, ctx->stream>>>(nl, acc, prop, gmap);
+      PPRVIZ_LAUNCHED(ctx);
+      PPRVIZ_TRY(contract(gmap));
     }
     if (merges == 0) break;  // nothing merged: the hierarchy ends below this level
     // number the groups by smallest member
     PPRVIZ_PROF(ctx, PPRVIZ_K_HIER);
-    info->pair_visits += E;
     k_lp_fill<<<gn, kLpTpb, 0, ctx->stream>>>(nl, minm, INT32_MAX);
     PPRVIZ_LAUNCHED(ctx);
     k_lp_minmember<<<gn, kLpTpb, 0, ctx->stream>>>(nl, grp, minm);
@@ -517,7 +556,6 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
     PPRVIZ_TRY(lp_scan(ctx, nl, mcnt, moff, bsum, misc));
     k_lp_parent<<<gn, kLpTpb, 0, ctx->stream>>>(nl, grp, minm, moff, parent);
     PPRVIZ_LAUNCHED(ctx);
-    // the next level: degree sums and pairs lifted through parent
     int64_t nl2h = 0;
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&nl2h, misc, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -526,37 +564,22 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
     parents.resize(off + (size_t)nl);
     PPRVIZ_CUDA(ctx, cudaMemcpyAsync(parents.data() + off, parent, sizeof(int32_t) * (size_t)nl, cudaMemcpyDeviceToHost,
                                      ctx->stream));
+    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     level_n.push_back(nl2);
     if (nl2 <= k) {
-      PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
       done = true;
       break;
     }
+    // the next level: degree sums lifted, the pair list (already one entry
+    // per pair of final groups, keyed by their representatives, whose parent
+    // is the group's new id) relabelled
     k_lp_zero64<<<grid_for(nl2), kLpTpb, 0, ctx->stream>>>(nl2, win2);
     PPRVIZ_LAUNCHED(ctx);
     k_lp_lift_win<<<gn, kLpTpb, 0, ctx->stream>>>(nl, parent, win, win2);
     PPRVIZ_LAUNCHED(ctx);
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * Hl, ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(vals, 0, sizeof(int32_t) * Hl, ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(misc + 1, 0, sizeof(int64_t), ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx->stream));
-    info->slot_visits += (int64_t)Hl;
-    k_lp_pairs<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, ew, parent, keys, vals, maskl, flags + 1);
+    k_lp_relabel<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, parent);
     PPRVIZ_LAUNCHED(ctx);
-    k_lp_compact<<<gh, kLpTpb, 0, ctx->stream>>>(Hl, keys, vals, fA, fB, fw,
-                                                 reinterpret_cast<unsigned long long *>(misc + 1));
-    PPRVIZ_LAUNCHED(ctx);
-    int64_t E2 = 0;
-    int terr = 0;
-    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&E2, misc + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaMemcpyAsync(&terr, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (terr) return set_err(ctx, PPRVIZ_E_CUDA, "Louvain+: pair table full (internal error)");
-    std::swap(eA, fA);
-    std::swap(eB, fB);
-    std::swap(ew, fw);
     std::swap(win, win2);
-    E = E2;
     nl = nl2;
   }
   info->levels = (int32_t)level_n.size() - 1;
