@@ -292,18 +292,27 @@ __global__ void k_lp_zero64(int64_t n, long long *__restrict__ x) {
     x[a] = 0;
 }
 
-// the table's pairs as the next level's pair list (any order)
+// the table's pairs as a pair list (any order); one counter atomic per warp
+// (H is a power of two >= 1,024 and the grid a multiple of 32 threads, so
+// every lane of a warp is in range together)
 __global__ void k_lp_compact(unsigned long long H, const unsigned long long *__restrict__ keys,
                              const int32_t *__restrict__ vals, int32_t *__restrict__ eA, int32_t *__restrict__ eB,
                              int32_t *__restrict__ ew, unsigned long long *__restrict__ count) {
-  for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h < H;
-       h += (unsigned long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h < H; h += stride) {
     const unsigned long long key = keys[h];
-    if (key == kLpEmpty) continue;
-    const unsigned long long i = atomicAdd(count, 1ull);
-    eA[i] = (int32_t)(key >> 32);
-    eB[i] = (int32_t)(key & 0xffffffffu);
-    ew[i] = vals[h];
+    const bool has = key != kLpEmpty;
+    const unsigned mask = __ballot_sync(0xffffffffu, has);
+    unsigned long long first = 0;
+    if (lane == 0 && mask) first = atomicAdd(count, (unsigned long long)__popc(mask));
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (has) {
+      const unsigned long long i = first + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
+      eA[i] = (int32_t)(key >> 32);
+      eB[i] = (int32_t)(key & 0xffffffffu);
+      ew[i] = vals[h];
+    }
   }
 }
 
