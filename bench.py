@@ -1095,15 +1095,15 @@ def run_hierarchy(args, rank, world, local_rank):
     # twice (largest gain, then its smallest arg), the 12 B record and the
     # size and degree sum of both groups (24 B); per pair contracted its 12 B
     # record, its two mapped ids (8 B) and one key and count (12 B); per
-    # table slot its clear and the compaction scan (2 x 12 B); per level node
-    # and round ~16 words of node state (64 B)
-    alg = (72.0 * info["list_visits"] + 32.0 * info["pair_visits"] + 24.0 * info["slot_visits"]
+    # table slot the compaction scan (12 B; it also clears what it emits);
+    # per level node and round ~16 words of node state (64 B)
+    alg = (72.0 * info["list_visits"] + 32.0 * info["pair_visits"] + 12.0 * info["slot_visits"]
            + 64.0 * info["node_visits"])
     ach = alg / (h_ms / 1e3) / 1e9 if h_ms else None
     roof = {"kernel": "Louvain+ merge rounds (k_lp_*): pair-table atomics, table scans, node passes",
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm if ach else None,
             "launches": h_n, "alg_bytes_per_step": alg,
-            "alg_bytes_note": "72 B per pair scanned for the gains + 32 B per pair contracted + 24 B per table slot + 64 B per node visit",
+            "alg_bytes_note": "72 B per pair scanned for the gains + 32 B per pair contracted + 12 B per table slot + 64 B per node visit",
             "device_ms_per_step": h_ms, "traffic": None,
             "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth), frac of {peak_kind}"}
     cpu = None

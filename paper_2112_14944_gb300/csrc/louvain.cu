@@ -292,11 +292,12 @@ __global__ void k_lp_zero64(int64_t n, long long *__restrict__ x) {
     x[a] = 0;
 }
 
-// the table's pairs as a pair list (any order); one counter atomic per warp
-// (H is a power of two >= 1,024 and the grid a multiple of 32 threads, so
-// every lane of a warp is in range together)
-__global__ void k_lp_compact(unsigned long long H, const unsigned long long *__restrict__ keys,
-                             const int32_t *__restrict__ vals, int32_t *__restrict__ eA, int32_t *__restrict__ eB,
+// the table's pairs as a pair list (any order), each emitted slot cleared
+// so that the table is empty again for the next contraction; one counter
+// atomic per warp (H is a power of two >= 1,024 and the grid a multiple of
+// 32 threads, so every lane of a warp is in range together)
+__global__ void k_lp_compact(unsigned long long H, unsigned long long *__restrict__ keys,
+                             int32_t *__restrict__ vals, int32_t *__restrict__ eA, int32_t *__restrict__ eB,
                              int32_t *__restrict__ ew, unsigned long long *__restrict__ count) {
   const int lane = threadIdx.x & 31;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -312,6 +313,8 @@ __global__ void k_lp_compact(unsigned long long H, const unsigned long long *__r
       eA[i] = (int32_t)(key >> 32);
       eB[i] = (int32_t)(key & 0xffffffffu);
       ew[i] = vals[h];
+      keys[h] = kLpEmpty;
+      vals[h] = 0;
     }
   }
 }
@@ -473,8 +476,7 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
     while (Hl < 2ull * (unsigned long long)E) Hl <<= 1;
     info->slot_visits += (int64_t)Hl;
     info->pair_visits += E;
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * Hl, ctx->stream));
-    PPRVIZ_CUDA(ctx, cudaMemsetAsync(vals, 0, sizeof(int32_t) * Hl, ctx->stream));
+    // the table is empty here: cleared once below, then by every compaction
     PPRVIZ_CUDA(ctx, cudaMemsetAsync(misc + 1, 0, 2 * sizeof(int64_t), ctx->stream));
     k_lp_pairs<<<grid_for(E), kLpTpb, 0, ctx->stream>>>(E, eA, eB, ew, map, keys, vals, Hl - 1, flags + 1);
     PPRVIZ_LAUNCHED(ctx);
@@ -494,6 +496,8 @@ int louvain_plus_solve(pprviz_ctx *ctx, const pprviz_graph *g, int32_t k, std::v
     return PPRVIZ_OK;
   };
 
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * H, ctx->stream));
+  PPRVIZ_CUDA(ctx, cudaMemsetAsync(vals, 0, sizeof(int32_t) * H, ctx->stream));
   int32_t nl = (int32_t)n;
   k_lp_edges0<<<grid_for(n), kLpTpb, 0, ctx->stream>>>(n, pull_rp(g), pull_col(g), eA, eB, ew, (int64_t *)win);
   PPRVIZ_LAUNCHED(ctx);
