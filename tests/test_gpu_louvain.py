@@ -131,3 +131,26 @@ def test_two_million_node_graph_invariants(ctx):
     two_m = float(g.nnz)
     Q = float(np.sum(inside / two_m - (dsum / two_m) ** 2))
     assert Q > 0.15, Q
+
+
+def test_short_outputs_report_the_size_needed(ctx):
+    """The C call with too small outputs: E_INVALID_ARG with the needed
+    parent entries and the level count filled, outputs untouched; with room
+    it returns the same hierarchy as the Python method."""
+    from paper_2112_14944_gb300 import _binding as B
+    g = synth.chung_lu(300, 6, 2.5, seed=1)
+    G = ctx.upload_graph(g)
+    ref = ctx.louvain_plus(G, 10)
+    need = sum(len(p) for p in ref)
+    level_n = np.zeros(65, dtype=np.int64)
+    small = np.full(need - 1, -7, dtype=np.int32)
+    ok, info = B.pprviz_louvain_plus(ctx.h, G.h, 10, level_n, 64, small, need - 1)
+    assert not ok and info["parent_need"] == need and info["levels"] == len(ref)
+    assert np.all(small == -7) and np.all(level_n == 0)
+    ok, info = B.pprviz_louvain_plus(ctx.h, G.h, 10, level_n, len(ref) - 1, np.empty(need, np.int32), need)
+    assert not ok and info["levels"] == len(ref)
+    parent = np.empty(need, dtype=np.int32)
+    ok, info = B.pprviz_louvain_plus(ctx.h, G.h, 10, level_n, len(ref), parent, need)
+    assert ok and info["levels"] == len(ref) and info["rounds"] > 0
+    assert level_n[0] == g.n and list(level_n[1:len(ref) + 1]) == [int(p.max()) + 1 for p in ref]
+    _same(np.split(parent, np.cumsum([len(p) for p in ref])[:-1]), ref)
