@@ -37,6 +37,13 @@ def _same(gpu, ref):
         assert np.array_equal(np.asarray(a, dtype=np.int64), np.asarray(b, dtype=np.int64)), lvl
 
 
+def _ring_of_cliques(c, q):
+    e = []
+    for b in range(q):
+        e += [(b * c + i, b * c + j) for i in range(c) for j in range(i + 1, c)] + [(b * c + c - 1, ((b + 1) % q) * c)]
+    return _csr(c * q, e)
+
+
 def _cliques_bridge():
     e = [(a, b) for a in range(4) for b in range(a + 1, 4)]
     return _csr(8, e + [(a + 4, b + 4) for a, b in e] + [(3, 4)])
@@ -50,6 +57,7 @@ def _cliques_bridge():
     ("chung-lu 300", lambda: synth.chung_lu(300, 6, 2.5, seed=1), 10),
     ("chung-lu 600", lambda: synth.chung_lu(600, 8, 2.5, seed=3), 12),
     ("sbm 8x40", lambda: synth.sbm([40] * 8, 0.25, 0.01, seed=1), 48),
+    ("ring of cliques", lambda: _ring_of_cliques(5, 6), 5),
 ])
 def test_louvain_plus_matches_the_oracle(ctx, name, make, k):
     g = make()

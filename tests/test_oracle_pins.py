@@ -630,6 +630,30 @@ def test_louvain_plus_splits_two_cliques_at_the_bridge():
     assert O.louvain_plus(8, row_ptr, col, 8) == []  # n <= k: the leaves fit one view
 
 
+def _ring_of_cliques(c, q):
+    edges = []
+    for b in range(q):
+        base = b * c
+        edges += [(base + i, base + j) for i in range(c) for j in range(i + 1, c)]
+        edges.append((base + c - 1, ((b + 1) % q) * c))
+    return _csr_from_edges(c * q, edges, undirected=True)
+
+
+def test_louvain_plus_finds_the_cliques_of_a_ring():
+    """A ring of six 5-cliques, each joined to the next by one edge: the
+    partition into the cliques is modularity's optimum (Q = 0.742 here;
+    the ring is far below the resolution limit), and it is level 1 for k = 5
+    and k = 7 (for k = 7 also the top: 6 <= k)."""
+    row_ptr, col = _ring_of_cliques(5, 6)
+    cliques = np.repeat(np.arange(6), 5)
+    for k in (5, 7):
+        levels = O.louvain_plus(30, row_ptr, col, k)
+        assert levels[0].tolist() == cliques.tolist()
+    assert len(O.louvain_plus(30, row_ptr, col, 7)) == 1
+    q = O.modularity(row_ptr, col, cliques)
+    assert abs(float(q) - (60 / 66 - 6 * (22 / 132) ** 2)) < 1e-15
+
+
 def test_louvain_plus_rule_i_on_a_star_and_a_path():
     """Rule (i) by hand. Star of 6 leaves, k = 4: every leaf's only neighbour
     is the hub, which takes leaves 1-3 (cap 4); leaves 4-6 stay alone.
