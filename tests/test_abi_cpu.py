@@ -109,3 +109,43 @@ def test_noalloc_binding_rejects_bad_buffers_before_the_call():
         B._check_noalloc_buffers(k, np.zeros(k * k, np.float32), ok_x, None, None)
     with pytest.raises(ValueError, match="needs pdist and x"):
         B._check_noalloc_buffers(k, None, ok_x, None, None)
+
+
+def test_louvain_plus_null_context_and_host_marshalling(lib, monkeypatch):
+    """pprviz_louvain_plus rejects a NULL context without touching a device;
+    the Python method splits the concatenated parent arrays per level and,
+    when the first buffer is short, calls again with the size the library
+    reported (the library call is replaced by a fake here: no GPU)."""
+    import paper_2112_14944_gb300 as P
+    from paper_2112_14944_gb300 import _binding as B
+    ln = np.zeros(65, np.int64)
+    par = np.zeros(4, np.int32)
+    info = B.pprviz_louvain_info()
+    assert lib.pprviz_louvain_plus(None, None, 5, ln.ctypes.data, 64, par.ctypes.data, 4, ctypes.byref(info)) == \
+        B.PPRVIZ_E_INVALID_ARG
+    # a three-level hierarchy of 5000 leaves: 5000 -> 3000 -> 40 -> 2
+    levels = [np.arange(5000) % 3000, np.arange(3000) % 40, np.arange(40) % 2]
+    need = sum(len(p) for p in levels)
+    calls = []
+
+    def fake(ctx, g, k, level_n, level_cap, parent, parent_cap):
+        calls.append(parent_cap)
+        out = {"levels": 3, "rounds": 9, "parent_need": need, "slot_visits": 0, "pair_visits": 0,
+               "list_visits": 0, "node_visits": 0}
+        if parent_cap < need:
+            return False, out
+        level_n[:4] = [5000, 3000, 40, 2]
+        parent[:need] = np.concatenate(levels)
+        return True, out
+
+    monkeypatch.setattr(B, "pprviz_louvain_plus", fake)
+
+    class FakeGraph:
+        n, h = 1000, 1  # the graph's n sets the first guess (2 n + 64 entries), below `need`
+
+    ctx = P.Context.__new__(P.Context)
+    ctx.h = 1
+    got, info = ctx.louvain_plus(FakeGraph(), 25, with_info=True)
+    ctx.h = 0
+    assert calls == [2 * 1000 + 64, need] and info["levels"] == 3
+    assert len(got) == 3 and all(np.array_equal(a, b) for a, b in zip(got, levels))
